@@ -1,0 +1,224 @@
+"""Pins of the oracle's time stepper against closed forms and invariants:
+viscosity (shear-wave decay), the wall-bounded body-force channel,
+the unsteady Stokeslet in Fourier space (Eq. oseen), conservation,
+force multipoles, the a_L sum of Appendix A, the Faxen update of Sec. IV
+and a long-double self-check."""
+import numpy as np
+import pytest
+
+import oracle
+
+
+def _shear_wave_rate_error(L, tau, U=1e-4):
+    lb = oracle.OracleLB((1, 1, L), tau, tau)
+    c, w = oracle.lattice()
+    z = np.arange(L)
+    k = 2 * np.pi / L
+    ux = U * np.sin(k * z)
+    for i in range(19):
+        cu = c[i, 0] * ux
+        lb.df[i, :, 0, 0] = w[i] * (3 * cu + 4.5 * cu * cu - 1.5 * ux * ux)
+    nu = tau / 3
+    T = int(0.5 / (nu * k * k))
+    lb.step(10)
+    a0 = lb.observe()["u"][0, :, 0, 0]
+    lb.step(T)
+    a1 = lb.observe()["u"][0, :, 0, 0]
+    amp0 = 2 * np.mean(a0 * np.sin(k * z))
+    amp1 = 2 * np.mean(a1 * np.sin(k * z))
+    return np.log(amp0 / amp1) / T / (nu * k * k) - 1
+
+
+@pytest.mark.parametrize("tau", [0.5, 0.8])
+def test_shear_wave_viscosity(tau):
+    # Sec. II: shear modes decay at eta k^2 with eta = rho cs^2 tau
+    # (the reading tau -> eta used throughout); the lattice error falls at
+    # least as L^-2.
+    e16, e32, e64 = (_shear_wave_rate_error(L, tau) for L in (16, 32, 64))
+    assert abs(e32) < 2e-3
+    assert abs(e64) < 5e-4
+    assert abs(e32) / abs(e64) > 3.5  # second (or better) order
+
+
+def _startup_series(z, t, g, nu, H, M=4001):
+    zeta = z - 0.5
+    u = g / (2 * nu) * zeta * (H - zeta)
+    for m in range(1, M, 2):
+        u = u - 4 * g * H * H / (nu * np.pi ** 3 * m ** 3) * np.sin(m * np.pi * zeta / H) \
+            * np.exp(-m * m * np.pi ** 2 * nu * t / (H * H))
+    return u
+
+
+def test_poiseuille_steady_curvature_and_slip():
+    # Body-force channel between halfway bounce-back walls: at steady state
+    # the second difference of u in the bulk is exactly -g/nu, and the
+    # deviation from the parabola (wall slip) falls as H^-2.
+    errs = []
+    for L in (18, 34):
+        g, tau = 1e-6, 0.5
+        nu = tau / 3
+        H = L - 2
+        lb = oracle.OracleLB((1, 1, L), tau, tau, g=(g, 0, 0), walls=(0, L - 1), counter=False)
+        lb.step(int(5 * H * H / nu))
+        u = lb.observe()["u"][0, :, 0, 0]
+        d2 = u[3:L - 1] - 2 * u[2:L - 2] + u[1:L - 3]
+        assert np.allclose(d2, -g / nu, rtol=1e-9, atol=0)
+        zeta = np.arange(L) - 0.5
+        ex = g / (2 * nu) * zeta * (H - zeta)
+        errs.append(np.abs(u[1:-1] - ex[1:-1]).max() / ex.max())
+        assert u[0] == 0 and u[-1] == 0
+    assert errs[0] < 2e-3
+    assert 3.5 < errs[0] / errs[1] < 4.5
+
+
+def test_poiseuille_startup_256():
+    # The wall-bounded channel workload (256 nodes across, g = 1e-6, 2000
+    # steps) against the start-up series of the unsteady Stokes equation.
+    L, g, tau, T = 256, 1e-6, 0.5, 2000
+    nu, H = tau / 3, L - 2
+    lb = oracle.OracleLB((1, 1, L), tau, tau, g=(g, 0, 0), walls=(0, L - 1), counter=False)
+    lb.step(T)
+    u = lb.observe()["u"][0, :, 0, 0]
+    ex = _startup_series(np.arange(L), T, g, nu, H)
+    assert np.abs(u[1:-1] - ex[1:-1]).max() / np.abs(ex).max() < 1e-3
+
+
+def test_stokeslet_fourier_modes_c1():
+    # Eq. (oseen): solenoidal Fourier modes of the velocity of an
+    # impulsively started regularised Stokeslet, 32^3, eta = 1/6, 1000
+    # steps, F(k) the exact lattice transform of the spread force.  Low
+    # modes agree to < 1 %, the departure grows with k (Fig. oseen).
+    L, tau, T = 32, 0.5, 1000
+    eta = tau / 3
+    R = np.array([16.3, 15.7, 16.45])
+    F0 = np.array([0, 0, 1e-5])
+    lb = oracle.OracleLB((L, L, L), tau, tau)
+    lb.add_points(oracle.STOKESLET, R, F0)
+    lb.step(T)
+    u = lb.observe()["u"]
+    uk = np.fft.fftn(u, axes=(1, 2, 3))
+    Fk = np.fft.fftn(oracle.force_field((L, L, L), R, F0), axes=(1, 2, 3))
+    scale = None
+    for n, tol in [((1, 0, 0), 0.01), ((0, 1, 0), 0.01), ((1, 1, 0), 0.01), ((1, 0, 1), 0.01),
+                   ((2, 0, 0), 0.01), ((2, 1, 1), 0.01), ((4, 0, 0), 0.01), ((8, 0, 0), 0.05),
+                   ((0, 0, 1), None), ((0, 0, 3), None)]:
+        kv = 2 * np.pi * np.array(n) / L
+        k2 = kv @ kv
+        P = np.eye(3) - np.outer(kv, kv) / k2
+        idx = (slice(None), n[2] % L, n[1] % L, n[0] % L)
+        th = (1 - np.exp(-eta * k2 * T)) / (eta * k2) * (P @ Fk[idx])
+        sim = P @ uk[idx]
+        if scale is None:
+            scale = np.abs(th).max()
+        if tol is None:  # purely longitudinal force mode: no solenoidal response
+            assert np.abs(sim).max() < 1e-9 * scale
+        else:
+            assert np.abs(sim - th).max() < tol * np.abs(th).max()
+
+
+def test_conservation_mass_momentum():
+    # Eq. (conservation): total mass is constant; the momentum of the
+    # physical distribution grows by the net force each step,
+    # P(n) = (n + 1/2) sum F (rho v = j + F/2), and stays zero when the
+    # counter-force balances it or the force is a stresslet/rotlet.
+    n = (10, 9, 8)
+    F0 = np.array([1e-5, -2e-6, 3e-6])
+    lb = oracle.OracleLB(n, 0.6, 0.9, counter=False)
+    lb.add_points(oracle.STOKESLET, [3.3, 4.1, 5.9], F0)
+    for steps in (1, 7, 20):
+        lb.step(steps if steps == 1 else steps - prev)
+        prev = steps
+        tot = lb.observe(fields=False)["totals"]
+        assert abs(tot[0] - np.prod(n)) < 1e-12
+        assert np.allclose(tot[1:], (steps + 0.5) * F0, rtol=1e-12, atol=1e-20)
+    for kind, param in ((oracle.STOKESLET, None), (oracle.STRESSLET, [2.0]), (oracle.ROTLET, [2.0])):
+        lb = oracle.OracleLB(n, 0.6, 0.9, counter=(kind == oracle.STOKESLET))
+        lb.add_points(kind, [4.2, 3.3, 2.8], [1e-4, 2e-5, -3e-5], param)
+        lb.step(25)
+        tot = lb.observe(fields=False)["totals"]
+        assert abs(tot[0] - np.prod(n)) < 1e-12
+        assert np.abs(tot[1:]).max() < 1e-17
+
+
+def test_force_multipole_fields_have_zero_net_force():
+    n = (16, 16, 16)
+    for kind in (oracle.STRESSLET, oracle.ROTLET):
+        P, f, _, _ = oracle.expand_points(kind, [8.1, 7.7, 8.4], [0, 0, 1e-4], [2.0])
+        F = oracle.force_field(n, P, f)
+        assert np.abs(F.sum(axis=(1, 2, 3))).max() < 1e-19
+    # rotlet: net torque of the grid force equals the point torque
+    R = np.array([8.1, 7.7, 8.4])
+    P, f, _, _ = oracle.expand_points(oracle.ROTLET, R, [0, 0, 1e-4], [2.0])
+    F = oracle.force_field(n, P, f)
+    z, y, x = np.meshgrid(np.arange(16), np.arange(16), np.arange(16), indexing="ij")
+    r = np.stack([x - R[0], y - R[1], z - R[2]])
+    tq = np.cross(r.reshape(3, -1).T, F.reshape(3, -1).T).sum(0)
+    assert np.allclose(tq, [0, 0, 1e-4], rtol=1e-12, atol=1e-18)
+
+
+@pytest.mark.parametrize("L,R", [(12, [8.0, 8.0, 8.0]), (16, [8.3, 7.6, 8.45]), (16, [8.5, 8.5, 8.5])])
+def test_aL_ksum_matches_steady_lattice_response(L, R):
+    # Appendix A: F/(6 pi eta a_L) is the velocity a regularised Stokeslet
+    # induces at its own position (periodic box, k = 0 removed).  Hold a
+    # point force fixed, run the lattice to steady state and interpolate:
+    # the k-sum (continuum k^2) and the lattice agree to a few percent
+    # (measured 1.3-1.6 %, the lattice's high-k dispersion), for any L
+    # and offset.  A missing 1/V or a wrong projector is off by far more.
+    tau = 0.5
+    eta = tau / 3
+    F0 = np.array([0, 0, 1e-6])
+    lb = oracle.OracleLB((L, L, L), tau, tau)
+    lb.add_points(oracle.STOKESLET, R, F0)
+    lb.step(int(12 / (eta * (2 * np.pi / L) ** 2)))
+    vz = lb.observe(qpos=np.array([R]), fields=False)["qv"][0, 2]
+    inv_meas = vz / F0[2] * 6 * np.pi * eta
+    T = oracle.inv_aL_tensor((L, L, L), R)
+    assert abs(inv_meas / T[2, 2] - 1) < 0.03
+    # isotropy of the k-sum at a lattice-symmetric point
+    if R[0] == R[1] == R[2]:
+        assert np.allclose(np.diag(T), T[0, 0], rtol=1e-12)
+        assert np.abs(T - np.diag(np.diag(T))).max() < 1e-12 * T[0, 0]
+
+
+def test_colloid_sediments_at_stokes_speed():
+    # Sec. IV: with a_L from Appendix A the interpolated self-flow is
+    # subtracted and an isolated point colloid moves at F / (6 pi eta a).
+    L, tau, a = 16, 0.5, 0.117
+    eta = tau / 3
+    R0 = np.array([8.3, 7.6, 8.45])
+    F0 = np.array([0, 0, -1e-6])
+    lb = oracle.OracleLB((L, L, L), tau, tau, a_L=oracle.aL_along((L, L, L), R0, [0, 0, 1]))
+    lb.add_points(oracle.COLLOID, R0, F0, [a])
+    lb.step(int(12 / (eta * (2 * np.pi / L) ** 2)))
+    p1 = lb.pos.copy()
+    lb.step(100)
+    v = ((lb.pos - p1) / 100)[0]
+    v0 = F0[2] / (6 * np.pi * eta * a)
+    assert abs(v[2] / v0 - 1) < 3e-3
+    assert abs(v[0]) < 1e-12 and abs(v[1]) < 1e-12
+    # without the subtraction the colloid moves too fast by F/(6 pi eta a_L)
+    lb2 = oracle.OracleLB((L, L, L), tau, tau, a_L=np.inf)
+    lb2.add_points(oracle.COLLOID, R0, F0, [a])
+    lb2.step(int(12 / (eta * (2 * np.pi / L) ** 2)))
+    q1 = lb2.pos.copy()
+    lb2.step(100)
+    v2 = ((lb2.pos - q1) / 100)[0]
+    assert v2[2] / v0 - 1 > 0.05
+
+
+def test_long_double_selfcheck():
+    # The FP64 oracle against its long-double build: the rounding of the
+    # FP64 oracle is far below the 1e-12 parity bar.
+    n = (8, 8, 8)
+    runs = []
+    for prec in ("double", "longdouble"):
+        lb = oracle.OracleLB(n, 0.6, 0.8, a_L=1.7, precision=prec)
+        lb.add_points(oracle.STOKESLET, [3.3, 4.6, 2.2], [0, 0, 1e-5])
+        lb.add_points(oracle.STRESSLET, [5.1, 2.7, 6.3], [1e-5, 0, 5e-5], [2.0])
+        lb.add_points(oracle.COLLOID, [1.2, 6.6, 4.4], [0, 0, -1e-5], [0.117])
+        lb.step(100)
+        o = lb.observe()
+        runs.append((o["u"].astype(np.float64), lb.pos.astype(np.float64)))
+    (u64, p64), (uld, pld) = runs
+    assert np.abs(u64 - uld).max() < 1e-13 * np.abs(uld).max()
+    assert np.abs(p64 - pld).max() < 1e-13
