@@ -1,0 +1,389 @@
+"""Benchmark: D3Q19 forced-MRT lattice Boltzmann MLUPS and HBM roofline
+fraction on one GB300 (or N independent replicas under torchrun).
+
+Workload (one "step"): one time step of each of the four 256^3 FP32
+lattices of the wall-bounded channel / multipole recipe -- the body-force
+channel with solid planes z = 0, 255, a Stokeslet, a stresslet and a
+rotlet at seeded positions (see paper_0707_1299_gb300.workloads).  Every
+lattice step spreads its point forces (Peskin kernel), then runs the fused
+collide + pull-stream kernel over all 256^3 sites.  The velocity at the
+force points is interpolated back every step (gather kernel).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f32]
+    python bench.py --impl reference ...   (the CPU oracle on a bounded sample)
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D3Q19 forced-MRT MLUPS & HBM-roofline fraction per precision at stated error"
+WORKLOAD = ("channel_256: four 256^3 D3Q19 MRT lattices per step (body-force channel g=1e-6 between "
+            "solid planes z=0,255; Stokeslet F=1e-5; stresslet dipole 1e-4; rotlet torque 1e-4; "
+            "seeded off-lattice positions), tau_s=tau_b=1/2")
+PREC_NAMES = {"f64": 0, "f32": 1, "f16s": 2, "bf16s": 3}
+BYTES = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2}
+PROFILE_DIR = os.path.join(ROOT, "profiles")
+
+
+def kernel_source_hash():
+    """Hash of the CUDA sources; the committed ncu traffic figure is only
+    quoted while the kernels are unchanged since it was taken."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_0707_1299_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(prec):
+    """dram bytes per k_collide launch from the committed ncu summary."""
+    path = os.path.join(PROFILE_DIR, f"k_collide_{prec}_channel_256.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_sha") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, p in zip(names, parts[3:7]):
+                if p.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- GPU arm
+def build_lattices(prec_id, L):
+    from paper_0707_1299_gb300 import lb, workloads as W
+    lats = []
+    for prob in W.channel_256(L=L):
+        g = lb.Lattice(prob.grid, prob.tau_s, prob.tau_b, prec_id)
+        g.set_body_force(prob.g)
+        if prob.walls is not None:
+            g.set_walls_z(*prob.walls)
+        g.set_counterforce(prob.counter)
+        for ps in prob.points:
+            g.add_point_forces(ps.kind, ps.pos, ps.F, ps.param)
+        lats.append((prob, g))
+    return lats
+
+
+def run_gpu(args, rank, world):
+    import torch
+    from paper_0707_1299_gb300 import build, lb
+
+    build.build()
+    lb.load()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    prec = args.precision
+    L = args.size
+    lats = build_lattices(PREC_NAMES[prec], L)
+    V = L ** 3
+    stream = torch.cuda.current_stream()
+
+    # query points: the force points of each lattice, or the channel centre,
+    # where the velocity is interpolated back every step
+    qpos = []
+    for prob, g in lats:
+        p, _ = g.particles()
+        if p.shape[0] == 0:
+            p = torch.tensor([[L / 2, L / 2, L / 2]], dtype=torch.float64, device=p.device)
+        qpos.append(p)
+    vbuf = [torch.empty_like(q) for q in qpos]
+
+    def one_step(events=None):
+        for k, (prob, g) in enumerate(lats):
+            if events is not None:
+                events[k][0].record(stream)
+            g.step(1)
+            if events is not None:
+                events[k][1].record(stream)
+            lb.lb_velocity_at(g.ctx, qpos[k].shape[0], qpos[k], vbuf[k])
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    launches0 = sum(g.kernel_launches() for _, g in lats)
+    ev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in lats]
+          for _ in range(args.steps)]
+    clocks = ClockSampler(dev)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for s in range(args.steps):
+        one_step(ev[s])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    launches = sum(g.kernel_launches() for _, g in lats) - launches0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    # the channel lattice's lb_step launches exactly one kernel: k_collide
+    coll_ms = float(np.mean([ev[s][0][0].elapsed_time(ev[s][0][1]) for s in range(args.steps)]))
+    step_ms = ms / args.steps
+    mlups = world * 4 * V * args.steps / (ms * 1e-3) / 1e6
+
+    # end to end through the C ABI with host buffers: per step copy the
+    # point positions (the step's input) in from pinned host memory, step,
+    # and read the interpolated velocities (the step's result) back into
+    # pinned host memory
+    has_pts = [g.num_points() > 0 for _, g in lats]
+    host_q = [q.cpu().pin_memory() for q in qpos]
+    host_v = [torch.empty(q.shape, dtype=torch.float64).pin_memory() for q in qpos]
+    e2e_steps = max(3, args.steps // 4)
+    h2d = sum(hq.numel() * 8 for hq, hp in zip(host_q, has_pts) if hp)
+    d2h = sum(hv.numel() * 8 for hv in host_v)
+    barrier()
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(e2e_steps):
+        for k, (prob, g) in enumerate(lats):
+            if has_pts[k]:
+                lb.lb_set_positions(g.ctx, host_q[k].numpy())
+            g.step(1)
+            lb.lb_velocity_at(g.ctx, host_q[k].shape[0], host_q[k].numpy(), host_v[k].numpy())
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - te
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_mlups = world * 4 * V * e2e_steps / e2e_s / 1e6
+
+    # stated error: the channel lattice against the exactly equivalent
+    # 1 x 1 x L oracle column after the same number of steps (rank 0)
+    err = None
+    nsteps_done = args.warmup + args.steps + e2e_steps
+    if rank == 0 and not args.no_check:
+        import oracle
+        prob, g = lats[0]
+        _, u, _ = g.moments()
+        col = oracle.OracleLB((1, 1, L), prob.tau_s, prob.tau_b, g=prob.g, walls=prob.walls, counter=False)
+        col.step(nsteps_done)
+        ref = col.observe()["u"][0, :, 0, 0]
+        uu = u[0, :, :: max(1, L // 8), :: max(1, L // 8)].cpu().numpy()
+        err = float(np.abs(uu - ref[:, None, None]).max() / np.abs(ref).max())
+
+    peak, peak_kind = measured_peaks()
+    b_alg = 2 * 19 * BYTES[prec] * V
+    achieved = b_alg / (coll_ms * 1e-3) / 1e9
+    traffic = committed_traffic(prec)
+    for _, g in lats:
+        g.close()
+    out = {
+        "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": [L, L, L], "lattices_per_step": 4,
+                   "sites_per_step": 4 * V, "precision": prec,
+                   "l2": "inputs larger than L2 (each population buffer %.2f GB)" % (19 * BYTES[prec] * V / 1e9),
+                   "parallelism": f"replicas{world}"},
+        "error": {"max_rel_velocity_vs_oracle": err, "steps": nsteps_done,
+                  "case": "channel lattice vs exactly equivalent 1x1xL FP64 oracle column"},
+        "roofline": {"bound": "hbm", "kernel": f"k_collide<{prec}> (channel lattice, walls)",
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                     "bytes_per_site": 2 * 19 * BYTES[prec], "launch_ms": round(coll_ms, 5),
+                     "traffic": traffic},
+        "e2e": {"value": round(e2e_mlups, 1), "unit": "MLUPS", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    return out
+
+
+# ---------------------------------------------------------- oracle (CPU)
+def oracle_sample_step(lats):
+    for o in lats:
+        o.step(1)
+
+
+def oracle_lattices(L, nxy):
+    import oracle
+    from paper_0707_1299_gb300 import workloads as W
+    out = []
+    for prob in W.channel_256(L=L, nx=nxy, ny=nxy):
+        o = oracle.OracleLB(prob.grid, prob.tau_s, prob.tau_b, g=prob.g, walls=prob.walls, counter=prob.counter)
+        for ps in prob.points:
+            o.add_points(ps.kind, ps.pos, ps.F, ps.param)
+        out.append(o)
+    return out
+
+
+def cpu_baseline(L, budget_s=12.0, nxy=64):
+    """The oracle on a bounded sample: the same four lattices cropped to
+    nxy x nxy x L (the recipe's points stay inside), stepped until about
+    budget_s seconds of CPU work."""
+    import oracle
+    lats = oracle_lattices(L, nxy)
+    oracle_sample_step(lats)  # first-touch of the oracle's buffers
+    sites = sum(o.V for o in lats)
+    t = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t < budget_s and n < 50:
+        oracle_sample_step(lats)
+        n += 1
+    dt = time.perf_counter() - t
+    return {"value": round(sites * n / dt / 1e6, 3), "unit": "MLUPS", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"four lattices {nxy}x{nxy}x{L} (channel recipe cropped in x,y), {n} steps, FP64, "
+                      f"{sites * n / 1e6:.1f} M site updates in {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    import oracle
+    oracle.build()
+    nxy = 64
+    lats = oracle_lattices(args.size, nxy)
+    for _ in range(args.warmup):
+        oracle_sample_step(lats)
+    sites = sum(o.V for o in lats)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_sample_step(lats)
+    dt = time.perf_counter() - t
+    v = sites * args.steps / dt / 1e6
+    sample = f"four lattices {nxy}x{nxy}x{args.size} (channel recipe cropped in x,y) per step, FP64"
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample, "parallelism": "host cores"},
+            "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(v, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="f32", choices=list(PREC_NAMES))
+    ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args, rank, 1)), flush=True)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    out = run_gpu(args, rank, world)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args.size)
+        else:
+            out["cpu_baseline"] = None
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * lb.h -- C ABI of the GB300 (sm_103a) forced D3Q19 lattice Boltzmann
+ * library with off-lattice singular point forces, after Nash, Adhikari &
+ * Cates, "Singular forces and point-like colloids in lattice Boltzmann
+ * hydrodynamics".
+ *
+ * Model (lattice units, dt = dx = 1, rest density rho0 = 1):
+ *   - D3Q19 populations, advanced as the auxiliary distribution
+ *     fbar = f - (dt/2) R of Sec. II, Eq. (transformf), stored as the
+ *     deviation df_i = fbar_i - w_i from the rest state;
+ *   - multiple-relaxation-time collision with the second-order forcing
+ *     term, Sec. II, Eq. (fiexp): ghost modes projected out, traceless
+ *     stress relaxed at 1/(tau_shear + 1/2), its trace at
+ *     1/(tau_bulk + 1/2); shear viscosity eta = tau_shear / 3;
+ *   - pull streaming, fused with the collision in one kernel;
+ *   - singular forces spread to the lattice with Peskin's 4-point
+ *     regularised delta function, Sec. III, Eq. (deltadef);
+ *   - lattice velocity interpolated back with the same kernel and point
+ *     colloids moved by the Faxen relation with the a_L subtraction,
+ *     Sec. IV, Eq. (a_Ldefn).
+ *
+ * Conventions for every call:
+ *   - Every function returns an lb_status and never aborts; on failure
+ *     lb_last_error() describes it.  Arguments are validated on the host
+ *     before anything is launched.
+ *   - The context owns its device memory (allocated in lb_create, freed in
+ *     lb_destroy).  Pointer arguments stay owned by the caller.  A pointer
+ *     argument may point to host memory or to device memory of the
+ *     context's GPU; the library tells them apart with
+ *     cudaPointerGetAttributes.
+ *   - Work is issued on the stream given to lb_create.  Calls whose
+ *     outputs are all in device memory return without waiting; a call
+ *     that writes host memory waits for its own copies.
+ *   - Positions are in lattice units with nodes at integer coordinates
+ *     0 .. n-1 in each axis, periodic.  Forces are force densities per
+ *     lattice site (a point force F spreads to F delta^P).
+ *   - Population layout (lb_get_populations / lb_set_populations):
+ *     df[i][z][y][x] as double, i in the order
+ *       0:(0,0,0) 1:(1,0,0) 2:(-1,0,0) 3:(0,1,0) 4:(0,-1,0) 5:(0,0,1)
+ *       6:(0,0,-1) 7:(1,1,0) 8:(-1,-1,0) 9:(1,-1,0) 10:(-1,1,0)
+ *       11:(1,0,1) 12:(-1,0,-1) 13:(1,0,-1) 14:(-1,0,1) 15:(0,1,1)
+ *       16:(0,-1,-1) 17:(0,1,-1) 18:(0,-1,1)
+ *     with weights 1/3 (rest), 1/18 (axes), 1/36 (diagonals).  The state
+ *     held between steps is the post-collision df* of the last step.
+ */
+#ifndef GB300_LB_H
+#define GB300_LB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_ctx lb_ctx;
+
+typedef enum {
+    LB_OK = 0,
+    LB_ERR_ARG = 1,        /* invalid argument; nothing was launched */
+    LB_ERR_CUDA = 2,       /* a CUDA call failed; see lb_last_error */
+    LB_ERR_OOM = 3,        /* device allocation failed */
+    LB_ERR_NONFINITE = 4,  /* a non-finite value was found in an input */
+    LB_ERR_STATE = 5       /* call not valid in the context's state */
+} lb_status;
+
+/* Storage precision of the populations.  F64: double storage and
+ * arithmetic.  F32: float storage and arithmetic.  F16S / BF16S: df
+ * stored as half / bfloat16 multiplied by a power-of-two scale (the
+ * deviation from the rest state is small, so half precision needs the
+ * scale to stay out of subnormals); arithmetic in float. */
+typedef enum { LB_F64 = 0, LB_F32 = 1, LB_F16S = 2, LB_BF16S = 3 } lb_precision;
+
+/* Kinds of singular force (Sec. III and IV). */
+typedef enum {
+    LB_STOKESLET = 0, /* one fixed force monopole F at pos */
+    LB_STRESSLET = 1, /* collinear pair: +F at pos + (sep/2) F^, -F at pos - (sep/2) F^ */
+    LB_ROTLET = 2,    /* four tangential forces of magnitude |T|/(2 arm) at
+                         pos +- (arm/2) e1, pos +- (arm/2) e2 (Fig. rotlet);
+                         (e1, e2, T^) right-handed, e1 = the coordinate axis
+                         least aligned with T^ (lowest index on ties),
+                         orthogonalised to T^; +F e2 at +e1, -F e2 at -e1,
+                         -F e1 at +e2, +F e1 at -e2; torque T, net force 0 */
+    LB_COLLOID = 3    /* a mobile point colloid of radius a pushed by the
+                         external force F (Sec. IV) */
+} lb_kind;
+
+/* Create a lattice of grid[0] x grid[1] x grid[2] sites (x fastest), each
+ * >= 1 and their product < 2^40, at rest (df = 0).  tau_shear, tau_bulk
+ * > 0 are the relaxation times of Sec. II in the convention
+ * eta = rho cs^2 tau_shear (rate 1/(tau + 1/2)); precision is an
+ * lb_precision; stream is a cudaStream_t (NULL: the legacy default
+ * stream).  Allocates two population buffers, a force field and the
+ * point arrays on the current device.  Sec. II, Eqs. (mrtlbe), (fiexp). */
+lb_status lb_create(lb_ctx **out, const int grid[3], double tau_shear, double tau_bulk,
+                    int precision, void *stream);
+
+/* Free everything the context owns.  Waits for its stream.  NULL is a no-op. */
+void lb_destroy(lb_ctx *ctx);
+
+/* Description of the last failure on this context (or of a failed
+ * lb_create when ctx is NULL); never NULL. */
+const char *lb_last_error(const lb_ctx *ctx);
+
+/* Uniform body-force density g (3 doubles, host memory) on every fluid
+ * site, the smooth "gravity" forcing of Sec. I. */
+lb_status lb_set_body_force(lb_ctx *ctx, const double g[3]);
+
+/* Make the z-planes z_lo and z_hi solid (halfway bounce-back; walls at
+ * z_lo + 1/2 and z_hi - 1/2).  -1 disables a plane.  Walls are not part
+ * of the paper; they serve the body-force channel flow. */
+lb_status lb_set_walls_z(lb_ctx *ctx, int z_lo, int z_hi);
+
+/* Enable (default) or disable the uniform counter-force -sum F / V_fluid
+ * on fluid sites that cancels the net point force in a periodic box
+ * (the k = 0 removal of Appendix A). */
+lb_status lb_set_counterforce(lb_ctx *ctx, int enabled);
+
+/* Lattice offset parameter a_L of Eq. (a_Ldefn) used by the colloid update
+ * (a_L > 0; +inf turns the subtraction off).  Default +inf. */
+lb_status lb_set_colloid_aL(lb_ctx *ctx, double a_L);
+
+/* Append n singular forces of one kind.  pos, F: 3n doubles (xyz per
+ * point; host or device), F is the force (STOKESLET, COLLOID), the pair
+ * force (STRESSLET) or the torque (ROTLET).  param: n doubles (host or
+ * device) -- separation (STRESSLET), arm (ROTLET), radius a (COLLOID);
+ * may be NULL for STOKESLET.  Positions are wrapped into the box.  The
+ * points are expanded into monopoles on the device; the total count
+ * after expansion must stay below 2^31 / 64.  Sec. III, IV. */
+lb_status lb_add_point_forces(lb_ctx *ctx, int n, const double *pos, const double *F, int kind,
+                              const double *param);
+
+/* Remove every point force. */
+lb_status lb_clear_point_forces(lb_ctx *ctx);
+
+/* Number of monopoles after expansion. */
+lb_status lb_num_points(const lb_ctx *ctx, int *n_out);
+
+/* Replace the positions of all monopoles (3 * lb_num_points doubles, host
+ * or device, in the order they were created); forces are kept. */
+lb_status lb_set_positions(lb_ctx *ctx, const double *pos);
+
+/* Advance nsteps >= 0 time steps.  Each step: spread the point forces at
+ * their current positions, interpolate the velocity at each colloid and
+ * move it (forward Euler, dt = 1), then collide and stream every site. */
+lb_status lb_step(lb_ctx *ctx, int nsteps);
+
+/* Velocity v = (sum fbar c + F/2) / rho (Eq. macrovariables2) interpolated
+ * with delta^P at n query points pos (3n doubles) into v_out (3n
+ * doubles); host or device pointers. */
+lb_status lb_velocity_at(lb_ctx *ctx, int n, const double *pos, double *v_out);
+
+/* Fields at the current time: rho (V doubles) and u (3V doubles, u[a][z][y][x])
+ * -- either may be NULL -- and totals[4] = {sum rho, sum rho u} over fluid
+ * sites accumulated in FP64 (NULL allowed).  Solid sites report rho = 1,
+ * u = 0.  Host or device pointers. */
+lb_status lb_moments(lb_ctx *ctx, double *rho, double *u, double *totals);
+
+/* Current monopole positions and forces (3 * lb_num_points doubles each;
+ * either may be NULL; host or device). */
+lb_status lb_particles(lb_ctx *ctx, double *pos_out, double *f_out);
+
+/* Copy the population state out / in, as df[i][z][y][x] doubles (19V;
+ * host or device).  Reduced-precision storage is converted. */
+lb_status lb_get_populations(lb_ctx *ctx, double *df);
+lb_status lb_set_populations(lb_ctx *ctx, const double *df);
+
+/* Number of kernels this context has launched since lb_create (a running
+ * count kept on the host; copies and memsets are not counted). */
+lb_status lb_kernel_launches(const lb_ctx *ctx, long long *count);
+
+/* Wait for all work issued on the context's stream. */
+lb_status lb_synchronize(lb_ctx *ctx);
+
+/* a_L of Appendix A for a lattice grid[3] and a point R (3 doubles, host):
+ * 1/a_L = (6 pi / V) sum_{k != 0} |delta^P(k;R)|^2 / k^2 d.(1 - k^k^).d
+ * along the unit vector d = dir (host, 3 doubles), or one third of the
+ * trace when dir is NULL; k = 2 pi m / n, continuum |k|^2.  Evaluated on
+ * the current device (allocates temporary device memory). */
+lb_status lb_compute_aL(const int grid[3], const double R[3], const double dir[3], double *a_L);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_LB_H */

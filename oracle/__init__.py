@@ -29,12 +29,18 @@ NQ = 19
 
 __all__ = ["NQ", "build", "lattice", "phi", "collide_site", "macro_site", "OracleLB",
            "STOKESLET", "STRESSLET", "ROTLET", "COLLOID", "expand_points",
-           "counter_force", "inv_aL_tensor", "aL_along", "force_field"]
+           "counter_force", "inv_aL_tensor", "aL_along", "force_field", "num_threads"]
 
 
 def build(force: bool = False) -> None:
     """Compile the C part of the oracle (both precisions)."""
     _lib.build(force)
+
+
+def num_threads() -> int:
+    """Host threads the oracle's site loops use (OpenMP)."""
+    lib, _, pre = _lib.load("double")
+    return int(getattr(lib, pre + "num_threads")())
 
 
 def _real(precision):
@@ -95,10 +101,12 @@ class OracleLB:
     walls    -- (z_lo, z_hi) solid planes with halfway bounce-back, or None
     counter  -- balance the net point force with a uniform force density
     a_L      -- lattice offset parameter of the colloid update (inf = none)
+    fc       -- explicit uniform force density on fluid nodes, used instead
+                of the counter-force (e.g. a sub-box of a larger lattice)
     """
 
     def __init__(self, n, tau_s, tau_b, g=(0.0, 0.0, 0.0), walls=None, counter=True,
-                 a_L=np.inf, precision: str = "double"):
+                 a_L=np.inf, precision: str = "double", fc=None):
         self.precision = precision
         self.R = _real(precision)
         self.n = tuple(int(v) for v in n)
@@ -108,6 +116,7 @@ class OracleLB:
         self.walls = walls
         self.counter = counter
         self.a_L = a_L
+        self.fc = None if fc is None else np.asarray(fc, dtype=np.float64)
         self.df = np.zeros((NQ, self.n[2], self.n[1], self.n[0]), dtype=self.R)
         self.pos = np.zeros((0, 3), dtype=self.R)
         self.f = np.zeros((0, 3), dtype=self.R)
@@ -134,7 +143,10 @@ class OracleLB:
         for a in range(3):
             p.n[a] = self.n[a]
             p.g[a] = float(self.g[a])
-        fc = counter_force(self.f, self.n_fluid) if self.counter else np.zeros(3)
+        if self.fc is not None:
+            fc = self.fc
+        else:
+            fc = counter_force(self.f, self.n_fluid) if self.counter else np.zeros(3)
         for a in range(3):
             p.fc[a] = fc[a]
         p.tau_s, p.tau_b = self.tau_s, self.tau_b

@@ -85,6 +85,7 @@ def load(kind: str = "double"):
                                   ctypes.c_int, P(R), P(R), P(R)]
         fn("observe").restype = ctypes.c_int
         fn("real_size").restype = ctypes.c_int
+        fn("num_threads").restype = ctypes.c_int
         _loaded[kind] = (lib, Params, pre)
         return _loaded[kind]
 

@@ -50,6 +50,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #ifdef ORC_LONG_DOUBLE
 typedef long double real;
@@ -420,3 +423,13 @@ int SYM(observe)(const orc_params *p, const real *df, int npts, const real *pos,
 }
 
 int SYM(real_size)(void) { return (int)sizeof(real); }
+
+/* Threads the site loops run on (OpenMP), for reporting. */
+int SYM(num_threads)(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

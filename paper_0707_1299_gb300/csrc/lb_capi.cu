@@ -1,0 +1,466 @@
+// lb_capi.cu -- the C ABI declared in include/lb.h: argument validation,
+// ownership of device memory, host/device pointer handling, and the order
+// of the kernels within a time step.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+
+#include "../../include/lb.h"
+#include "lb_internal.h"
+
+namespace {
+
+thread_local std::string g_create_err;
+
+lb_status fail(lb_ctx* c, lb_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_create_err = msg;
+    return s;
+}
+
+lb_status cuda_fail(lb_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define LB_CUDA(call, where)                                  \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Staging area for host pointers: a single grow-only device buffer.
+lb_status ensure_stage(lb_ctx* c, size_t bytes) {
+    if (bytes <= c->stage_bytes) return LB_OK;
+    if (c->stage) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->stage);
+        c->stage = nullptr;
+        c->stage_bytes = 0;
+    }
+    LB_CUDA(cudaMalloc(&c->stage, bytes), "staging allocation");
+    c->stage_bytes = bytes;
+    return LB_OK;
+}
+
+// Resolve up to four pointer arguments: device pointers pass through, host
+// inputs are copied into the staging area, host outputs get a staging slot
+// (copied back by finish_outputs).
+struct Arg {
+    const void* user;
+    size_t bytes;
+    bool is_output;
+    void* dev;       // what the kernels see
+    bool staged;
+};
+
+lb_status resolve(lb_ctx* c, Arg* args, int nargs, bool* any_host) {
+    size_t need = 0;
+    *any_host = false;
+    for (int i = 0; i < nargs; ++i) {
+        args[i].staged = args[i].user && !is_device_ptr(args[i].user);
+        if (args[i].staged) need += (args[i].bytes + 255) & ~(size_t)255;
+        *any_host = *any_host || args[i].staged;
+    }
+    if (need) {
+        lb_status s = ensure_stage(c, need);
+        if (s != LB_OK) return s;
+    }
+    size_t off = 0;
+    for (int i = 0; i < nargs; ++i) {
+        if (!args[i].user) {
+            args[i].dev = nullptr;
+        } else if (!args[i].staged) {
+            args[i].dev = const_cast<void*>(args[i].user);
+        } else {
+            args[i].dev = (char*)c->stage + off;
+            off += (args[i].bytes + 255) & ~(size_t)255;
+            if (!args[i].is_output && args[i].bytes)
+                LB_CUDA(cudaMemcpyAsync(args[i].dev, args[i].user, args[i].bytes, cudaMemcpyHostToDevice, c->stream),
+                        "host-to-device copy");
+        }
+    }
+    return LB_OK;
+}
+
+lb_status finish(lb_ctx* c, Arg* args, int nargs, bool any_host) {
+    for (int i = 0; i < nargs; ++i)
+        if (args[i].staged && args[i].is_output && args[i].bytes)
+            LB_CUDA(cudaMemcpyAsync(const_cast<void*>(args[i].user), args[i].dev, args[i].bytes, cudaMemcpyDeviceToHost,
+                                    c->stream),
+                    "device-to-host copy");
+    if (any_host) LB_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+    return LB_OK;
+}
+
+lb_status grow_points(lb_ctx* c, int need) {
+    if (need <= c->cap) return LB_OK;
+    int cap = std::max(need, std::max(64, 2 * c->cap));
+    double *pos = nullptr, *force = nullptr, *radius = nullptr;
+    int* mobile = nullptr;
+    cudaError_t e = cudaMalloc(&pos, sizeof(double) * 3 * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&force, sizeof(double) * 3 * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&radius, sizeof(double) * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&mobile, sizeof(int) * cap);
+    if (e == cudaSuccess && c->npts) {
+        e = cudaMemcpyAsync(pos, c->pos, sizeof(double) * 3 * c->npts, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(force, c->force, sizeof(double) * 3 * c->npts, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(radius, c->radius, sizeof(double) * c->npts, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(mobile, c->mobile, sizeof(int) * c->npts, cudaMemcpyDeviceToDevice, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaFree(pos);
+        cudaFree(force);
+        cudaFree(radius);
+        cudaFree(mobile);
+        return cuda_fail(c, e, "point arrays");
+    }
+    cudaFree(c->pos);
+    cudaFree(c->force);
+    cudaFree(c->radius);
+    cudaFree(c->mobile);
+    c->pos = pos;
+    c->force = force;
+    c->radius = radius;
+    c->mobile = mobile;
+    c->cap = cap;
+    return LB_OK;
+}
+
+lb_status invalidate_field(lb_ctx* c) {
+    if (!c->field_ready) return LB_OK;
+    LB_CUDA(lbk::launch_clear_field(c), "clear force field");
+    c->field_ready = false;
+    return LB_OK;
+}
+
+lb_status ensure_field(lb_ctx* c) {
+    if (c->field_ready || c->npts == 0) return LB_OK;
+    LB_CUDA(lbk::launch_spread(c), "spread kernel");
+    c->field_ready = true;
+    return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lb_status lb_create(lb_ctx** out, const int grid[3], double tau_shear, double tau_bulk, int precision, void* stream) {
+    lb_ctx* c = nullptr;
+    if (!out) return fail(nullptr, LB_ERR_ARG, "lb_create: out is NULL");
+    *out = nullptr;
+    if (!grid) return fail(nullptr, LB_ERR_ARG, "lb_create: grid is NULL");
+    for (int a = 0; a < 3; ++a)
+        if (grid[a] < 1) return fail(nullptr, LB_ERR_ARG, "lb_create: grid sizes must be >= 1");
+    const long long V = (long long)grid[0] * grid[1] * grid[2];
+    if (V >= (1LL << 40)) return fail(nullptr, LB_ERR_ARG, "lb_create: lattice too large");
+    if (!(tau_shear > 0) || !(tau_bulk > 0) || !isfinite(tau_shear) || !isfinite(tau_bulk))
+        return fail(nullptr, LB_ERR_ARG, "lb_create: relaxation times must be finite and > 0");
+    if (precision < LB_F64 || precision > LB_BF16S) return fail(nullptr, LB_ERR_ARG, "lb_create: unknown precision");
+
+    c = new (std::nothrow) lb_ctx();
+    if (!c) return fail(nullptr, LB_ERR_OOM, "lb_create: host allocation failed");
+    c->prec = precision;
+    c->tau_s = tau_shear;
+    c->tau_b = tau_bulk;
+    c->g[0] = c->g[1] = c->g[2] = 0.0;
+    c->counter = 1;
+    c->a_L = INFINITY;
+    c->scale = c->inv_scale = 1.0f;
+    if (precision == LB_F16S) {
+        c->scale = 1048576.0f;  // 2^20
+        c->inv_scale = 1.0f / 1048576.0f;
+    }
+    c->stream = (cudaStream_t)stream;
+    c->geom.nx = grid[0];
+    c->geom.ny = grid[1];
+    c->geom.nz = grid[2];
+    c->geom.ntx = (grid[0] + lbk::TILE_X - 1) / lbk::TILE_X;
+    c->geom.V = V;
+    c->geom.ntiles = (long long)c->geom.ntx * grid[1] * grid[2];
+    c->geom.wall_lo = c->geom.wall_hi = -1;
+    c->red_blocks = (int)std::min<long long>((c->geom.ntiles + 3) / 4, 152LL * 8);
+
+    cudaError_t e = cudaGetDevice(&c->device);
+    const size_t sb = lbk::storage_bytes(precision), ab = lbk::arith_bytes(precision);
+    if (e == cudaSuccess) e = cudaMalloc(&c->f[0], sb * lbk::NQ * (size_t)V);
+    if (e == cudaSuccess) e = cudaMalloc(&c->f[1], sb * lbk::NQ * (size_t)V);
+    if (e == cudaSuccess) e = cudaMalloc(&c->floc, ab * 3 * (size_t)V);
+    if (e == cudaSuccess) e = cudaMalloc(&c->flags, (size_t)c->geom.ntiles);
+    if (e == cudaSuccess) e = cudaMalloc(&c->fsum, sizeof(double) * 3);
+    if (e == cudaSuccess) e = cudaMalloc(&c->status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->partials, sizeof(double) * 4 * c->red_blocks);
+    if (e == cudaSuccess) e = cudaMalloc(&c->totals_dev, sizeof(double) * 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->f[0], 0, sb * lbk::NQ * (size_t)V, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->floc, 0, ab * 3 * (size_t)V, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, (size_t)c->geom.ntiles, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->fsum, 0, sizeof(double) * 3, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        lb_status s = fail(nullptr, e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA,
+                           std::string("lb_create: ") + cudaGetErrorString(e));
+        lb_destroy(c);
+        return s;
+    }
+    lb_status s = grow_points(c, 64);
+    if (s != LB_OK) {
+        g_create_err = c->err;
+        lb_destroy(c);
+        return s;
+    }
+    *out = c;
+    return LB_OK;
+}
+
+void lb_destroy(lb_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->f[0]);
+    cudaFree(c->f[1]);
+    cudaFree(c->floc);
+    cudaFree(c->flags);
+    cudaFree(c->pos);
+    cudaFree(c->force);
+    cudaFree(c->radius);
+    cudaFree(c->mobile);
+    cudaFree(c->fsum);
+    cudaFree(c->status);
+    cudaFree(c->partials);
+    cudaFree(c->totals_dev);
+    cudaFree(c->stage);
+    delete c;
+}
+
+const char* lb_last_error(const lb_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+lb_status lb_set_body_force(lb_ctx* c, const double g[3]) {
+    if (!c) return LB_ERR_ARG;
+    if (!g) return fail(c, LB_ERR_ARG, "lb_set_body_force: g is NULL");
+    for (int a = 0; a < 3; ++a)
+        if (!isfinite(g[a])) return fail(c, LB_ERR_NONFINITE, "lb_set_body_force: non-finite g");
+    for (int a = 0; a < 3; ++a) c->g[a] = g[a];
+    return LB_OK;
+}
+
+lb_status lb_set_walls_z(lb_ctx* c, int z_lo, int z_hi) {
+    if (!c) return LB_ERR_ARG;
+    if (z_lo < -1 || z_lo >= c->geom.nz || z_hi < -1 || z_hi >= c->geom.nz)
+        return fail(c, LB_ERR_ARG, "lb_set_walls_z: plane outside the lattice");
+    lb_status s = invalidate_field(c);
+    if (s != LB_OK) return s;
+    c->geom.wall_lo = z_lo;
+    c->geom.wall_hi = z_hi;
+    return LB_OK;
+}
+
+lb_status lb_set_counterforce(lb_ctx* c, int enabled) {
+    if (!c) return LB_ERR_ARG;
+    c->counter = enabled ? 1 : 0;
+    return LB_OK;
+}
+
+lb_status lb_set_colloid_aL(lb_ctx* c, double a_L) {
+    if (!c) return LB_ERR_ARG;
+    if (!(a_L > 0) || isnan(a_L)) return fail(c, LB_ERR_ARG, "lb_set_colloid_aL: a_L must be > 0");
+    c->a_L = a_L;
+    return LB_OK;
+}
+
+lb_status lb_add_point_forces(lb_ctx* c, int n, const double* pos, const double* F, int kind, const double* param) {
+    if (!c) return LB_ERR_ARG;
+    if (n < 0) return fail(c, LB_ERR_ARG, "lb_add_point_forces: n < 0");
+    if (n == 0) return LB_OK;
+    if (!pos || !F) return fail(c, LB_ERR_ARG, "lb_add_point_forces: pos or F is NULL");
+    if (kind < LB_STOKESLET || kind > LB_COLLOID) return fail(c, LB_ERR_ARG, "lb_add_point_forces: unknown kind");
+    if (kind != LB_STOKESLET && !param) return fail(c, LB_ERR_ARG, "lb_add_point_forces: param is required");
+    const int mult = kind == LB_STRESSLET ? 2 : kind == LB_ROTLET ? 4 : 1;
+    const long long total = (long long)c->npts + (long long)n * mult;
+    if (total >= (1LL << 31) / 64) return fail(c, LB_ERR_ARG, "lb_add_point_forces: too many points");
+    lb_status s = invalidate_field(c);
+    if (s == LB_OK) s = grow_points(c, (int)total);
+    if (s != LB_OK) return s;
+    Arg args[3] = {{pos, sizeof(double) * 3 * n, false, nullptr, false},
+                   {F, sizeof(double) * 3 * n, false, nullptr, false},
+                   {param, param ? sizeof(double) * n : 0, false, nullptr, false}};
+    bool any_host;
+    s = resolve(c, args, 3, &any_host);
+    if (s != LB_OK) return s;
+    LB_CUDA(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "status reset");
+    LB_CUDA(lbk::launch_expand(c, n, (const double*)args[0].dev, (const double*)args[1].dev,
+                               (const double*)args[2].dev, kind, mult),
+            "expand kernel");
+    int status = 0;
+    LB_CUDA(cudaMemcpyAsync(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "status read");
+    LB_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+    if (status & 1) return fail(c, LB_ERR_NONFINITE, "lb_add_point_forces: non-finite position, force or parameter");
+    if (status & 2)
+        return fail(c, LB_ERR_ARG, "lb_add_point_forces: parameter must be > 0 (and |F| > 0 for stresslet/rotlet)");
+    c->npts = (int)total;
+    if (kind == LB_COLLOID) c->n_mobile += n;
+    LB_CUDA(lbk::launch_fsum(c), "force sum");
+    return LB_OK;
+}
+
+lb_status lb_clear_point_forces(lb_ctx* c) {
+    if (!c) return LB_ERR_ARG;
+    lb_status s = invalidate_field(c);
+    if (s != LB_OK) return s;
+    c->npts = 0;
+    c->n_mobile = 0;
+    LB_CUDA(cudaMemsetAsync(c->fsum, 0, sizeof(double) * 3, c->stream), "force sum reset");
+    return LB_OK;
+}
+
+lb_status lb_num_points(const lb_ctx* c, int* n_out) {
+    if (!c || !n_out) return LB_ERR_ARG;
+    *n_out = c->npts;
+    return LB_OK;
+}
+
+lb_status lb_set_positions(lb_ctx* c, const double* pos) {
+    if (!c) return LB_ERR_ARG;
+    if (c->npts == 0) return LB_OK;
+    if (!pos) return fail(c, LB_ERR_ARG, "lb_set_positions: pos is NULL");
+    lb_status s = invalidate_field(c);
+    if (s != LB_OK) return s;
+    Arg args[1] = {{pos, sizeof(double) * 3 * c->npts, false, nullptr, false}};
+    bool any_host;
+    s = resolve(c, args, 1, &any_host);
+    if (s != LB_OK) return s;
+    LB_CUDA(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "status reset");
+    LB_CUDA(lbk::launch_set_positions(c, (const double*)args[0].dev), "position kernel");
+    int status = 0;
+    LB_CUDA(cudaMemcpyAsync(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "status read");
+    LB_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+    if (status) return fail(c, LB_ERR_NONFINITE, "lb_set_positions: non-finite position");
+    return LB_OK;
+}
+
+lb_status lb_step(lb_ctx* c, int nsteps) {
+    if (!c) return LB_ERR_ARG;
+    if (nsteps < 0) return fail(c, LB_ERR_ARG, "lb_step: nsteps < 0");
+    for (int s = 0; s < nsteps; ++s) {
+        lb_status st = ensure_field(c);
+        if (st != LB_OK) return st;
+        if (c->n_mobile > 0) LB_CUDA(lbk::launch_gather(c, c->npts, nullptr, nullptr, true), "gather/update kernel");
+        LB_CUDA(lbk::launch_collide(c), "collide-stream kernel");
+        c->cur ^= 1;
+        c->field_ready = false;
+    }
+    return LB_OK;
+}
+
+lb_status lb_velocity_at(lb_ctx* c, int n, const double* pos, double* v_out) {
+    if (!c) return LB_ERR_ARG;
+    if (n < 0) return fail(c, LB_ERR_ARG, "lb_velocity_at: n < 0");
+    if (n == 0) return LB_OK;
+    if (!pos || !v_out) return fail(c, LB_ERR_ARG, "lb_velocity_at: pos or v_out is NULL");
+    Arg args[2] = {{pos, sizeof(double) * 3 * n, false, nullptr, false},
+                   {v_out, sizeof(double) * 3 * n, true, nullptr, false}};
+    bool any_host;
+    lb_status s = resolve(c, args, 2, &any_host);
+    if (s == LB_OK) s = ensure_field(c);
+    if (s != LB_OK) return s;
+    LB_CUDA(lbk::launch_gather(c, n, (const double*)args[0].dev, (double*)args[1].dev, false), "gather kernel");
+    return finish(c, args, 2, any_host);
+}
+
+lb_status lb_moments(lb_ctx* c, double* rho, double* u, double* totals) {
+    if (!c) return LB_ERR_ARG;
+    const size_t V = (size_t)c->geom.V;
+    Arg args[3] = {{rho, sizeof(double) * V, true, nullptr, false},
+                   {u, sizeof(double) * 3 * V, true, nullptr, false},
+                   {totals, sizeof(double) * 4, true, nullptr, false}};
+    bool any_host;
+    lb_status s = resolve(c, args, 3, &any_host);
+    if (s == LB_OK) s = ensure_field(c);
+    if (s != LB_OK) return s;
+    LB_CUDA(lbk::launch_moments(c, (double*)args[0].dev, (double*)args[1].dev, totals != nullptr), "moments kernel");
+    if (totals)
+        LB_CUDA(cudaMemcpyAsync(args[2].dev, c->totals_dev, sizeof(double) * 4, cudaMemcpyDeviceToDevice, c->stream),
+                "totals copy");
+    return finish(c, args, 3, any_host);
+}
+
+lb_status lb_particles(lb_ctx* c, double* pos_out, double* f_out) {
+    if (!c) return LB_ERR_ARG;
+    const size_t b = sizeof(double) * 3 * (size_t)c->npts;
+    Arg args[2] = {{pos_out, b, true, nullptr, false}, {f_out, b, true, nullptr, false}};
+    bool any_host;
+    lb_status s = resolve(c, args, 2, &any_host);
+    if (s != LB_OK) return s;
+    if (pos_out && b)
+        LB_CUDA(cudaMemcpyAsync(args[0].dev, c->pos, b, cudaMemcpyDeviceToDevice, c->stream), "position copy");
+    if (f_out && b)
+        LB_CUDA(cudaMemcpyAsync(args[1].dev, c->force, b, cudaMemcpyDeviceToDevice, c->stream), "force copy");
+    return finish(c, args, 2, any_host);
+}
+
+lb_status lb_get_populations(lb_ctx* c, double* df) {
+    if (!c) return LB_ERR_ARG;
+    if (!df) return fail(c, LB_ERR_ARG, "lb_get_populations: df is NULL");
+    Arg args[1] = {{df, sizeof(double) * lbk::NQ * (size_t)c->geom.V, true, nullptr, false}};
+    bool any_host;
+    lb_status s = resolve(c, args, 1, &any_host);
+    if (s != LB_OK) return s;
+    LB_CUDA(lbk::launch_convert_out(c, (double*)args[0].dev), "convert kernel");
+    return finish(c, args, 1, any_host);
+}
+
+lb_status lb_set_populations(lb_ctx* c, const double* df) {
+    if (!c) return LB_ERR_ARG;
+    if (!df) return fail(c, LB_ERR_ARG, "lb_set_populations: df is NULL");
+    Arg args[1] = {{df, sizeof(double) * lbk::NQ * (size_t)c->geom.V, false, nullptr, false}};
+    bool any_host;
+    lb_status s = resolve(c, args, 1, &any_host);
+    if (s != LB_OK) return s;
+    LB_CUDA(lbk::launch_convert_in(c, (const double*)args[0].dev), "convert kernel");
+    return finish(c, args, 1, any_host);
+}
+
+lb_status lb_kernel_launches(const lb_ctx* c, long long* count) {
+    if (!c || !count) return LB_ERR_ARG;
+    *count = c->launches;
+    return LB_OK;
+}
+
+lb_status lb_synchronize(lb_ctx* c) {
+    if (!c) return LB_ERR_ARG;
+    LB_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+    return LB_OK;
+}
+
+lb_status lb_compute_aL(const int grid[3], const double R[3], const double dir[3], double* a_L) {
+    lb_ctx* c = nullptr;
+    if (!grid || !R || !a_L) return fail(nullptr, LB_ERR_ARG, "lb_compute_aL: NULL argument");
+    for (int a = 0; a < 3; ++a) {
+        if (grid[a] < 1) return fail(nullptr, LB_ERR_ARG, "lb_compute_aL: grid sizes must be >= 1");
+        if (!isfinite(R[a]) || (dir && !isfinite(dir[a])))
+            return fail(nullptr, LB_ERR_NONFINITE, "lb_compute_aL: non-finite input");
+    }
+    if (dir && dir[0] == 0 && dir[1] == 0 && dir[2] == 0)
+        return fail(nullptr, LB_ERR_ARG, "lb_compute_aL: zero direction");
+    double inv = 0.0;
+    LB_CUDA(lbk::compute_inv_aL(grid, R, dir, &inv), "lb_compute_aL");
+    *a_L = inv > 0 ? 1.0 / inv : INFINITY;
+    return LB_OK;
+}
+
+}  // extern "C"

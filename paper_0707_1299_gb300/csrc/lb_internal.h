@@ -1,0 +1,78 @@
+// lb_internal.h -- the context behind the C ABI and the kernel launchers
+// shared by lb_kernels.cu and lb_capi.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "lb_device.cuh"
+
+struct lb_ctx {
+    lbk::Geom geom;
+    int prec;                 // lb_precision
+    double tau_s, tau_b;
+    double g[3];
+    int counter;              // 1: uniform counter-force on
+    double a_L;               // +inf: no subtraction
+    float scale, inv_scale;   // storage scale of the half formats (1 otherwise)
+    cudaStream_t stream;
+    int device;
+
+    void* f[2];               // population buffers (19 V elements of the storage type)
+    int cur;                  // index of the buffer holding the current state
+    void* floc;               // localised force field, 3 V elements of the arithmetic type
+    unsigned char* flags;     // one flag per 32-site x-row tile: tile holds nonzero floc
+    bool field_ready;         // floc holds the forces at the current positions
+
+    // monopoles after expansion (device, xyz interleaved)
+    int npts, cap, n_mobile;
+    double* pos;
+    double* force;
+    double* radius;           // > 0 for colloids, 0 for fixed points
+    int* mobile;
+    double* fsum;             // 3 doubles: net point force (device)
+    int* status;              // 1 int: device-side validation result
+
+    // reductions
+    double* partials;         // 4 * red_blocks doubles
+    double* totals_dev;       // 4 doubles
+    int red_blocks;
+
+    // staging for host pointers (grown on demand)
+    void* stage;
+    size_t stage_bytes;
+
+    long long launches;       // kernels launched so far
+
+    std::string err;
+};
+
+namespace lbk {
+
+// Coefficients passed to kernels that need the uniform force.
+struct ForceConst {
+    double g[3];
+    double inv_vfluid;   // 1 / number of fluid sites
+    int counter;
+};
+
+cudaError_t launch_collide(lb_ctx* c);
+cudaError_t launch_spread(lb_ctx* c);
+cudaError_t launch_gather(lb_ctx* c, int n, const double* qpos, double* vout, bool update);
+cudaError_t launch_moments(lb_ctx* c, double* rho, double* u, bool want_totals);
+cudaError_t launch_expand(lb_ctx* c, int n, const double* pos, const double* F, const double* param, int kind,
+                          int mult);
+cudaError_t launch_fsum(lb_ctx* c);
+cudaError_t launch_set_positions(lb_ctx* c, const double* pos);
+cudaError_t launch_convert_out(lb_ctx* c, double* df);
+cudaError_t launch_convert_in(lb_ctx* c, const double* df);
+cudaError_t launch_clear_field(lb_ctx* c);
+cudaError_t compute_inv_aL(const int grid[3], const double R[3], const double dir[3], double* inv_aL);
+
+size_t storage_bytes(int prec);
+size_t arith_bytes(int prec);
+ForceConst force_const(const lb_ctx* c);
+
+}  // namespace lbk

@@ -1,0 +1,302 @@
+"""Python binding of the C ABI in include/lb.h (ctypes).
+
+The functions carry the C names and only marshal arguments: tensors and
+arrays become pointers, a non-OK status becomes an ``LBError`` carrying
+``lb_last_error``.  All arithmetic runs in libgb300lb.so; if the library
+is missing this module raises instead of falling back to anything else.
+PyTorch supplies device memory and the stream.
+
+``Lattice`` is a small convenience wrapper that allocates outputs as torch
+tensors on the lattice's device.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from .build import LIB
+
+LB_OK, LB_ERR_ARG, LB_ERR_CUDA, LB_ERR_OOM, LB_ERR_NONFINITE, LB_ERR_STATE = range(6)
+LB_F64, LB_F32, LB_F16S, LB_BF16S = range(4)
+LB_STOKESLET, LB_STRESSLET, LB_ROTLET, LB_COLLOID = range(4)
+NQ = 19
+
+EXPORTS = ["lb_create", "lb_destroy", "lb_last_error", "lb_set_body_force", "lb_set_walls_z",
+           "lb_set_counterforce", "lb_set_colloid_aL", "lb_add_point_forces", "lb_clear_point_forces",
+           "lb_num_points", "lb_set_positions", "lb_step", "lb_velocity_at", "lb_moments",
+           "lb_particles", "lb_get_populations", "lb_set_populations", "lb_kernel_launches",
+           "lb_synchronize", "lb_compute_aL"]
+
+_lib = None
+
+
+class LBError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"lb status {status}: {msg}")
+        self.status = status
+
+
+def load():
+    """Load libgb300lb.so (built by ``paper_0707_1299_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise RuntimeError(f"{LIB} is missing: build it with paper_0707_1299_gb300.build.build()")
+    lib = ctypes.CDLL(LIB)
+    vp, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p
+    sig = {
+        "lb_create": ([ctypes.POINTER(ctypes.c_void_p), ip, ctypes.c_double, ctypes.c_double, ctypes.c_int, vp],
+                      ctypes.c_int),
+        "lb_destroy": ([vp], None),
+        "lb_last_error": ([vp], ctypes.c_char_p),
+        "lb_set_body_force": ([vp, dp], ctypes.c_int),
+        "lb_set_walls_z": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "lb_set_counterforce": ([vp, ctypes.c_int], ctypes.c_int),
+        "lb_set_colloid_aL": ([vp, ctypes.c_double], ctypes.c_int),
+        "lb_add_point_forces": ([vp, ctypes.c_int, dp, dp, ctypes.c_int, dp], ctypes.c_int),
+        "lb_clear_point_forces": ([vp], ctypes.c_int),
+        "lb_num_points": ([vp, ip], ctypes.c_int),
+        "lb_set_positions": ([vp, dp], ctypes.c_int),
+        "lb_step": ([vp, ctypes.c_int], ctypes.c_int),
+        "lb_velocity_at": ([vp, ctypes.c_int, dp, dp], ctypes.c_int),
+        "lb_moments": ([vp, dp, dp, dp], ctypes.c_int),
+        "lb_particles": ([vp, dp, dp], ctypes.c_int),
+        "lb_get_populations": ([vp, dp], ctypes.c_int),
+        "lb_set_populations": ([vp, dp], ctypes.c_int),
+        "lb_kernel_launches": ([vp, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
+        "lb_synchronize": ([vp], ctypes.c_int),
+        "lb_compute_aL": ([ip, dp, dp, dp], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+# ----------------------------------------------------------- marshalling
+def _ptr(x):
+    """Address of a float64 tensor/array (host or device), or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):  # torch.Tensor
+        import torch
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise TypeError("expected a contiguous float64 tensor")
+        return x.data_ptr()
+    a = x
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("expected a C-contiguous float64 numpy array")
+    return a.ctypes.data
+
+
+def _check(ctx, status):
+    if status != LB_OK:
+        msg = load().lb_last_error(ctx)
+        raise LBError(status, msg.decode() if msg else "")
+
+
+# ----------------------------------------------------------- the C names
+def lb_create(grid, tau_shear, tau_bulk, precision=LB_F32, stream=None):
+    lib = load()
+    out = ctypes.c_void_p()
+    g = (ctypes.c_int * 3)(*[int(v) for v in grid])
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(None, lib.lb_create(ctypes.byref(out), g, float(tau_shear), float(tau_bulk), int(precision),
+                               ctypes.c_void_p(stream)))
+    return out.value
+
+
+def lb_destroy(ctx):
+    load().lb_destroy(ctx)
+
+
+def lb_last_error(ctx):
+    return load().lb_last_error(ctx).decode()
+
+
+def lb_set_body_force(ctx, g):
+    a = np.ascontiguousarray(g, dtype=np.float64)
+    _check(ctx, load().lb_set_body_force(ctx, a.ctypes.data))
+
+
+def lb_set_walls_z(ctx, z_lo, z_hi):
+    _check(ctx, load().lb_set_walls_z(ctx, int(z_lo), int(z_hi)))
+
+
+def lb_set_counterforce(ctx, enabled):
+    _check(ctx, load().lb_set_counterforce(ctx, 1 if enabled else 0))
+
+
+def lb_set_colloid_aL(ctx, a_L):
+    _check(ctx, load().lb_set_colloid_aL(ctx, float(a_L)))
+
+
+def lb_add_point_forces(ctx, n, pos, F, kind, param=None):
+    _check(ctx, load().lb_add_point_forces(ctx, int(n), _ptr(pos), _ptr(F), int(kind), _ptr(param)))
+
+
+def lb_clear_point_forces(ctx):
+    _check(ctx, load().lb_clear_point_forces(ctx))
+
+
+def lb_num_points(ctx):
+    n = ctypes.c_int()
+    _check(ctx, load().lb_num_points(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def lb_set_positions(ctx, pos):
+    _check(ctx, load().lb_set_positions(ctx, _ptr(pos)))
+
+
+def lb_step(ctx, nsteps):
+    _check(ctx, load().lb_step(ctx, int(nsteps)))
+
+
+def lb_velocity_at(ctx, n, pos, v_out):
+    _check(ctx, load().lb_velocity_at(ctx, int(n), _ptr(pos), _ptr(v_out)))
+
+
+def lb_moments(ctx, rho, u, totals):
+    _check(ctx, load().lb_moments(ctx, _ptr(rho), _ptr(u), _ptr(totals)))
+
+
+def lb_particles(ctx, pos_out, f_out):
+    _check(ctx, load().lb_particles(ctx, _ptr(pos_out), _ptr(f_out)))
+
+
+def lb_get_populations(ctx, df):
+    _check(ctx, load().lb_get_populations(ctx, _ptr(df)))
+
+
+def lb_set_populations(ctx, df):
+    _check(ctx, load().lb_set_populations(ctx, _ptr(df)))
+
+
+def lb_kernel_launches(ctx):
+    n = ctypes.c_longlong()
+    _check(ctx, load().lb_kernel_launches(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def lb_synchronize(ctx):
+    _check(ctx, load().lb_synchronize(ctx))
+
+
+def lb_compute_aL(grid, R, direction=None):
+    g = (ctypes.c_int * 3)(*[int(v) for v in grid])
+    r = np.ascontiguousarray(R, dtype=np.float64)
+    d = None if direction is None else np.ascontiguousarray(direction, dtype=np.float64)
+    out = np.zeros(1)
+    _check(None, load().lb_compute_aL(g, r.ctypes.data, None if d is None else d.ctypes.data, out.ctypes.data))
+    return float(out[0])
+
+
+# ------------------------------------------------------------- wrapper
+class Lattice:
+    """An lb_ctx with torch-allocated outputs on the current CUDA device."""
+
+    def __init__(self, grid, tau_shear, tau_bulk, precision=LB_F32, stream=None):
+        import torch
+        self.grid = tuple(int(v) for v in grid)
+        self.V = self.grid[0] * self.grid[1] * self.grid[2]
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.ctx = lb_create(self.grid, tau_shear, tau_bulk, precision, self.stream.cuda_stream)
+
+    def close(self):
+        if self.ctx:
+            lb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self, x, shape=None):
+        import torch
+        t = torch.as_tensor(x, dtype=torch.float64, device=self.device).contiguous()
+        return t if shape is None else t.reshape(shape)
+
+    def set_body_force(self, g):
+        lb_set_body_force(self.ctx, g)
+
+    def set_walls_z(self, z_lo, z_hi):
+        lb_set_walls_z(self.ctx, z_lo, z_hi)
+
+    def set_counterforce(self, enabled):
+        lb_set_counterforce(self.ctx, enabled)
+
+    def set_colloid_aL(self, a_L):
+        lb_set_colloid_aL(self.ctx, a_L if math.isfinite(a_L) else float("inf"))
+
+    def add_point_forces(self, kind, pos, F, param=None):
+        p = self._dev(pos, (-1, 3))
+        f = self._dev(F, (-1, 3))
+        prm = None if param is None else self._dev(param, (-1,))
+        lb_add_point_forces(self.ctx, p.shape[0], p, f, kind, prm)
+
+    def clear_point_forces(self):
+        lb_clear_point_forces(self.ctx)
+
+    def num_points(self):
+        return lb_num_points(self.ctx)
+
+    def set_positions(self, pos):
+        lb_set_positions(self.ctx, self._dev(pos, (-1, 3)))
+
+    def step(self, nsteps=1):
+        lb_step(self.ctx, nsteps)
+
+    def velocity_at(self, pos):
+        import torch
+        p = self._dev(pos, (-1, 3))
+        v = torch.empty_like(p)
+        lb_velocity_at(self.ctx, p.shape[0], p, v)
+        return v
+
+    def moments(self, fields=True):
+        import torch
+        nx, ny, nz = self.grid
+        rho = torch.empty((nz, ny, nx), dtype=torch.float64, device=self.device) if fields else None
+        u = torch.empty((3, nz, ny, nx), dtype=torch.float64, device=self.device) if fields else None
+        tot = torch.empty(4, dtype=torch.float64, device=self.device)
+        lb_moments(self.ctx, rho, u, tot)
+        return rho, u, tot
+
+    def particles(self):
+        import torch
+        n = self.num_points()
+        pos = torch.empty((n, 3), dtype=torch.float64, device=self.device)
+        f = torch.empty((n, 3), dtype=torch.float64, device=self.device)
+        if n:
+            lb_particles(self.ctx, pos, f)
+        return pos, f
+
+    def get_populations(self):
+        import torch
+        nx, ny, nz = self.grid
+        df = torch.empty((NQ, nz, ny, nx), dtype=torch.float64, device=self.device)
+        lb_get_populations(self.ctx, df)
+        return df
+
+    def set_populations(self, df):
+        lb_set_populations(self.ctx, self._dev(df))
+
+    def kernel_launches(self):
+        return lb_kernel_launches(self.ctx)
+
+    def synchronize(self):
+        lb_synchronize(self.ctx)

@@ -1,0 +1,48 @@
+"""Shared helpers of the GPU parity tests: run one workload Problem through
+the C ABI (CUDA path) and through the oracle, and compare.
+
+Error measure (spec tolerance): max over sites and components of
+|v_gpu - v_ref| divided by max |v_ref| after the stated steps; for colloid
+positions, the displacement error divided by the largest displacement.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+def gpu_lattice(problem, precision):
+    from paper_0707_1299_gb300 import lb
+    g = lb.Lattice(problem.grid, problem.tau_s, problem.tau_b, precision)
+    g.set_body_force(problem.g)
+    if problem.walls is not None:
+        g.set_walls_z(*problem.walls)
+    g.set_counterforce(problem.counter)
+    if np.isfinite(problem.a_L):
+        g.set_colloid_aL(problem.a_L)
+    for ps in problem.points:
+        g.add_point_forces(ps.kind, ps.pos, ps.F, ps.param)
+    return g
+
+
+def oracle_lattice(problem, fc=None):
+    import oracle
+    o = oracle.OracleLB(problem.grid, problem.tau_s, problem.tau_b, g=problem.g, walls=problem.walls,
+                        counter=problem.counter, a_L=problem.a_L, fc=fc)
+    for ps in problem.points:
+        o.add_points(ps.kind, ps.pos, ps.F, ps.param)
+    return o
+
+
+def rel_err(a, ref):
+    a = np.asarray(a, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    scale = np.abs(ref).max()
+    return float(np.abs(a - ref).max() / (scale if scale > 0 else 1.0))
+
+
+def periodic_diff(a, b, n):
+    d = np.asarray(a, dtype=np.float64) - np.asarray(b, dtype=np.float64)
+    n = np.asarray(n, dtype=np.float64)
+    return d - n * np.round(d / n)

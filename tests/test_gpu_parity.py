@@ -1,0 +1,240 @@
+"""CUDA path (through the C ABI) against the oracle, element by element on
+the same seeded inputs: one-step population parity on ragged lattices,
+the 32^3 Stokeslet workload for 1000 steps, the multipole/channel recipe,
+colloids, and the observables."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0707_1299_gb300 import workloads as W
+from _harness import TOL, gpu_lattice, oracle_lattice, rel_err, periodic_diff
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0707_1299_gb300 import build, lb
+    build.build()
+    lb.load()
+    torch.cuda.set_device(0)
+    yield
+
+
+def _lb():
+    from paper_0707_1299_gb300 import lb
+    return lb
+
+
+def _mixed_points(n):
+    """A Stokeslet, a stresslet, a rotlet and two colloids inside grid n."""
+    r = W.rng(41)
+    P = r.uniform(0, 1, size=(5, 3)) * np.asarray(n, dtype=float)
+    return [
+        W.PointSet(W.STOKESLET, P[0:1], np.array([[1e-5, -2e-6, 3e-6]]), None),
+        W.PointSet(W.STRESSLET, P[1:2], np.array([[2e-5, 1e-5, -3e-5]]), np.array([1.5])),
+        W.PointSet(W.ROTLET, P[2:3], np.array([[1e-5, 4e-5, 2e-5]]), np.array([2.0])),
+        W.PointSet(W.COLLOID, P[3:5], np.array([[0, 0, -1e-5], [3e-6, 1e-6, 0]]), np.array([0.117, 0.3])),
+    ]
+
+
+ONE_STEP_CASES = [
+    # grid, walls, points?, tau_s, tau_b
+    ((8, 6, 5), None, False, 0.5, 0.5),
+    ((37, 9, 7), None, True, 0.7, 1.1),      # two x-tiles, ragged tail
+    ((64, 4, 6), (0, 5), True, 0.55, 0.9),   # walls
+    ((3, 5, 4), None, True, 0.8, 0.6),       # stencil wider than the lattice
+    ((1, 1, 12), (0, 11), False, 0.5, 0.5),  # channel column
+]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("grid,walls,pts,ts,tb", ONE_STEP_CASES)
+def test_one_step_populations(prec, grid, walls, pts, ts, tb):
+    # From a random non-equilibrium state, one full step (spread, colloid
+    # update, collide + stream) must give the oracle's populations.
+    lb = _lb()
+    prob = W.Problem("one", grid, ts, tb, g=(1e-6, -2e-6, 5e-7), walls=walls, a_L=1.7,
+                     points=_mixed_points(grid) if pts else [])
+    df0 = W.random_state(grid, 7, amp=1e-4)
+    if walls is not None:
+        for z in walls:
+            df0[:, z] = 0.0
+    g = gpu_lattice(prob, lb.LB_F64 if prec == "f64" else lb.LB_F32)
+    g.set_populations(df0)
+    o = oracle_lattice(prob)
+    o.df[...] = df0
+    for _ in range(2):
+        g.step(1)
+        o.step(1)
+        df = g.get_populations().cpu().numpy()
+        tol = 1e-14 if prec == "f64" else 2e-6
+        assert rel_err(df, o.df) < tol
+        pos, _ = g.particles()
+        if len(o.pos):
+            assert np.abs(periodic_diff(pos.cpu().numpy(), o.pos, grid)).max() < (1e-13 if prec == "f64" else 1e-9)
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_stokeslet_32_1000_steps(prec):
+    # The 32^3 Stokeslet workload, 1000 steps, against the oracle within
+    # the benchmark spec's tolerances (FP64 1e-12, FP32 1e-5).
+    lb = _lb()
+    prob = W.stokeslet_32()
+    g = gpu_lattice(prob, lb.LB_F64 if prec == "f64" else lb.LB_F32)
+    g.step(prob.steps)
+    rho, u, tot = g.moments()
+    o = oracle_lattice(prob)
+    o.step(prob.steps)
+    ref = o.observe()
+    err = rel_err(u.cpu().numpy(), ref["u"])
+    assert err < TOL[prec], err
+    assert rel_err(rho.cpu().numpy() - 1.0, ref["rho"] - 1.0) < (1e-10 if prec == "f64" else 1e-3)
+    t = tot.cpu().numpy()
+    assert abs(t[0] - 32 ** 3) < (1e-9 if prec == "f64" else 1e-3)
+    assert np.abs(t[1:]).max() < (1e-15 if prec == "f64" else 1e-9)
+    q = np.array([[16.3, 15.7, 16.45], [3.2, 30.9, 17.5], [0.0, 0.0, 0.0]])
+    v = g.velocity_at(q).cpu().numpy()
+    vr = o.observe(qpos=q, fields=False)["qv"]
+    assert rel_err(v, vr) < TOL[prec]
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_multipole_recipe_reduced(prec):
+    # The channel/Stokeslet/stresslet/rotlet recipe at 40 x 36 x 48, 300
+    # steps: every one of the four lattices against the oracle.
+    lb = _lb()
+    for prob in W.channel_256(L=48, steps=300, nx=40, ny=36):
+        g = gpu_lattice(prob, lb.LB_F64 if prec == "f64" else lb.LB_F32)
+        g.step(prob.steps)
+        _, u, _ = g.moments()
+        o = oracle_lattice(prob)
+        o.step(prob.steps)
+        ref = o.observe()
+        err = rel_err(u.cpu().numpy(), ref["u"])
+        assert err < TOL[prec], (prob.name, err)
+        g.close()
+
+
+def test_channel_256_full_size():
+    # The wall-bounded channel at its full 256^3 size, FP32, 2000 steps, as
+    # the benchmark runs it.  The flow is invariant in x and y, so a
+    # 1 x 1 x 256 oracle lattice is exactly equivalent.
+    lb = _lb()
+    prob = W.channel_256()[0]
+    g = gpu_lattice(prob, lb.LB_F32)
+    g.step(prob.steps)
+    _, u, _ = g.moments()
+    col = W.Problem("col", (1, 1, 256), 0.5, 0.5, g=prob.g, walls=prob.walls, counter=False)
+    o = oracle_lattice(col)
+    o.step(prob.steps)
+    ref = o.observe()["u"][:, :, 0, 0]
+    uu = u.cpu().numpy()
+    for (y, x) in [(0, 0), (17, 200), (255, 255), (128, 3)]:
+        assert rel_err(uu[:, :, y, x], ref) < TOL["f32"]
+    assert np.abs(uu[1:]).max() < 1e-12 * np.abs(ref).max() + 1e-20
+    g.close()
+
+
+@pytest.mark.parametrize("which", [1, 2, 3])
+def test_multipoles_256_full_size_light_cone(which):
+    # Stokeslet / stresslet / rotlet lattices at the full 256^3 FP32 size.
+    # The lattice moves information one node per step, so after T steps the
+    # disturbance is confined to the stencil plus T nodes; a periodic
+    # oracle box of side >= 4 + 2T + 2 around the point, with the same
+    # uniform counter-force density, evolves identically there.
+    lb = _lb()
+    T = 40
+    prob = W.channel_256()[which]
+    g = gpu_lattice(prob, lb.LB_F32)
+    g.step(T)
+    _, u, _ = g.moments()
+    B = 2 * T + 12
+    P0 = prob.points[0].pos[0]
+    lo = np.floor(P0).astype(int) - B // 2
+    sub = W.Problem("sub", (B, B, B), prob.tau_s, prob.tau_b, counter=False,
+                    points=[W.PointSet(ps.kind, ps.pos - lo, ps.F, ps.param) for ps in prob.points])
+    fsum = np.zeros(3)
+    for ps in prob.points:
+        _, f, _, _ = oracle.expand_points(ps.kind, ps.pos, ps.F, ps.param)
+        fsum += f.sum(0)
+    o = oracle_lattice(sub, fc=-fsum / 256 ** 3)
+    o.step(T)
+    ref = o.observe()["u"]
+    uu = u.cpu().numpy()[:, lo[2]:lo[2] + B, lo[1]:lo[1] + B, lo[0]:lo[0] + B]
+    assert rel_err(uu, ref) < TOL["f32"]
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_colloids_reduced(prec):
+    # The colloid recipe (uniform random colloids at the 1e5-in-512^3
+    # number density, force 1e-6, radius 0.117) at 40^3 for 300 steps:
+    # velocity field and colloid trajectories against the oracle.
+    lb = _lb()
+    L = 40
+    n = int(round(1e5 * (L / 512) ** 3))
+    aL = oracle.aL_along((L, L, L), [L / 2] * 3, [0, 0, 1])
+    prob = W.colloids(L=L, n=n, steps=300, a_L=aL)
+    g = gpu_lattice(prob, lb.LB_F64 if prec == "f64" else lb.LB_F32)
+    p0, _ = g.particles()
+    p0 = p0.cpu().numpy()
+    g.step(prob.steps)
+    _, u, _ = g.moments()
+    p1, _ = g.particles()
+    o = oracle_lattice(prob)
+    o.step(prob.steps)
+    ref = o.observe()
+    assert rel_err(u.cpu().numpy(), ref["u"]) < TOL[prec]
+    d_gpu = periodic_diff(p1.cpu().numpy(), p0, prob.grid)
+    d_ref = periodic_diff(o.pos, p0, prob.grid)
+    assert rel_err(d_gpu, d_ref) < TOL[prec]
+    g.close()
+
+
+def test_aL_kernel_matches_oracle():
+    lb = _lb()
+    for n, R, d in [((16, 16, 16), [8.3, 7.6, 8.45], [0, 0, 1]), ((12, 20, 9), [1.1, 19.7, 4.0], None),
+                    ((32, 32, 32), [16.0, 16.0, 16.0], [1, 1, 0])]:
+        a = lb.lb_compute_aL(n, R, d)
+        b = oracle.aL_along(n, R, d)
+        assert abs(a / b - 1) < 1e-10
+
+
+def test_populations_roundtrip_and_host_pointers():
+    lb = _lb()
+    grid = (33, 5, 4)
+    df0 = W.random_state(grid, 3)
+    for prec, tol in ((lb.LB_F64, 0.0), (lb.LB_F32, 1e-7), (lb.LB_F16S, 1e-3), (lb.LB_BF16S, 1e-2)):
+        g = lb.Lattice(grid, 0.5, 0.5, prec)
+        lb.lb_set_populations(g.ctx, np.ascontiguousarray(df0))    # host pointer
+        back = np.empty_like(df0)
+        lb.lb_get_populations(g.ctx, back)                          # host pointer
+        assert np.abs(back - df0).max() <= tol * np.abs(df0).max()
+        g.close()
+
+
+def test_argument_validation():
+    lb = _lb()
+    with pytest.raises(lb.LBError):
+        lb.lb_create((0, 4, 4), 0.5, 0.5, lb.LB_F32)
+    with pytest.raises(lb.LBError):
+        lb.lb_create((4, 4, 4), -1.0, 0.5, lb.LB_F32)
+    g = lb.Lattice((8, 8, 8), 0.5, 0.5, lb.LB_F32)
+    with pytest.raises(lb.LBError) as e:
+        g.add_point_forces(lb.LB_COLLOID, [[1, 2, float("nan")]], [[0, 0, 1e-6]], [0.1])
+    assert e.value.status == lb.LB_ERR_NONFINITE
+    with pytest.raises(lb.LBError):
+        g.add_point_forces(lb.LB_STRESSLET, [[1, 2, 3]], [[0, 0, 1e-6]], [-1.0])
+    assert g.num_points() == 0
+    with pytest.raises(lb.LBError):
+        g.set_walls_z(0, 8)
+    with pytest.raises(lb.LBError):
+        lb.lb_step(g.ctx, -1)
+    g.step(0)
+    g.close()
