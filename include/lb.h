@@ -85,7 +85,7 @@ typedef enum {
 } lb_kind;
 
 /* Create a lattice of grid[0] x grid[1] x grid[2] sites (x fastest), each
- * >= 1 and their product < 2^40, at rest (df = 0).  tau_shear, tau_bulk
+ * >= 1 and their product < 2^32, at rest (df = 0).  tau_shear, tau_bulk
  * > 0 are the relaxation times of Sec. II in the convention
  * eta = rho cs^2 tau_shear (rate 1/(tau + 1/2)); precision is an
  * lb_precision; stream is a cudaStream_t (NULL: the legacy default

@@ -170,7 +170,7 @@ lb_status lb_create(lb_ctx** out, const int grid[3], double tau_shear, double ta
     for (int a = 0; a < 3; ++a)
         if (grid[a] < 1) return fail(nullptr, LB_ERR_ARG, "lb_create: grid sizes must be >= 1");
     const long long V = (long long)grid[0] * grid[1] * grid[2];
-    if (V >= (1LL << 40)) return fail(nullptr, LB_ERR_ARG, "lb_create: lattice too large");
+    if (V >= (1LL << 32)) return fail(nullptr, LB_ERR_ARG, "lb_create: lattice too large (nx*ny*nz >= 2^32)");
     if (!(tau_shear > 0) || !(tau_bulk > 0) || !isfinite(tau_shear) || !isfinite(tau_bulk))
         return fail(nullptr, LB_ERR_ARG, "lb_create: relaxation times must be finite and > 0");
     if (precision < LB_F64 || precision > LB_BF16S) return fail(nullptr, LB_ERR_ARG, "lb_create: unknown precision");
@@ -196,7 +196,7 @@ lb_status lb_create(lb_ctx** out, const int grid[3], double tau_shear, double ta
     c->geom.V = V;
     c->geom.ntiles = (long long)c->geom.ntx * grid[1] * grid[2];
     c->geom.wall_lo = c->geom.wall_hi = -1;
-    c->red_blocks = (int)std::min<long long>((c->geom.ntiles + 3) / 4, 152LL * 8);
+    c->geom.plane = (unsigned)grid[0] * (unsigned)grid[1];
 
     cudaError_t e = cudaGetDevice(&c->device);
     const size_t sb = lbk::storage_bytes(precision), ab = lbk::arith_bytes(precision);
@@ -206,7 +206,7 @@ lb_status lb_create(lb_ctx** out, const int grid[3], double tau_shear, double ta
     if (e == cudaSuccess) e = cudaMalloc(&c->flags, (size_t)c->geom.ntiles);
     if (e == cudaSuccess) e = cudaMalloc(&c->fsum, sizeof(double) * 3);
     if (e == cudaSuccess) e = cudaMalloc(&c->status, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&c->partials, sizeof(double) * 4 * c->red_blocks);
+    if (e == cudaSuccess) e = cudaMalloc(&c->partials, sizeof(double) * 4 * (size_t)lbk::moment_blocks(c->geom));
     if (e == cudaSuccess) e = cudaMalloc(&c->totals_dev, sizeof(double) * 4);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->f[0], 0, sb * lbk::NQ * (size_t)V, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->floc, 0, ab * 3 * (size_t)V, c->stream);
@@ -315,6 +315,9 @@ lb_status lb_add_point_forces(lb_ctx* c, int n, const double* pos, const double*
     c->npts = (int)total;
     if (kind == LB_COLLOID) c->n_mobile += n;
     LB_CUDA(lbk::launch_fsum(c), "force sum");
+    LB_CUDA(cudaMemcpyAsync(c->fsum_host, c->fsum, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream),
+            "force sum read");
+    LB_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
     return LB_OK;
 }
 
@@ -324,6 +327,7 @@ lb_status lb_clear_point_forces(lb_ctx* c) {
     if (s != LB_OK) return s;
     c->npts = 0;
     c->n_mobile = 0;
+    for (int a = 0; a < 3; ++a) c->fsum_host[a] = 0.0;
     LB_CUDA(cudaMemsetAsync(c->fsum, 0, sizeof(double) * 3, c->stream), "force sum reset");
     return LB_OK;
 }

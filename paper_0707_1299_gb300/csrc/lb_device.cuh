@@ -21,10 +21,12 @@ namespace lbk {
 constexpr int NQ = 19;
 constexpr int TILE_X = 32;  // one warp of x-consecutive sites = one force tile
 
-// Lattice geometry, passed by value to every kernel.
+// Lattice geometry, passed by value to every kernel.  Site indices are
+// 32-bit: the C ABI keeps nx * ny * nz below 2^32.
 struct Geom {
     int nx, ny, nz;
     int ntx;            // tiles per x-row: ceil(nx / 32)
+    unsigned plane;     // nx * ny
     long long V;        // nx * ny * nz
     long long ntiles;   // ntx * ny * nz
     int wall_lo, wall_hi;  // solid z-planes, -1 = none
@@ -40,112 +42,176 @@ __device__ __forceinline__ bool is_solid(const Geom& g, int z) {
 template <typename S> struct Store;
 template <> struct Store<double> {
     using T = double;
-    static __device__ __forceinline__ double ld(const double* p, long long i, float) { return __ldg(p + i); }
-    static __device__ __forceinline__ void st(double* p, long long i, double v, float) { __stcs(p + i, v); }
+    static __device__ __forceinline__ double ld(const double* p, unsigned i, float) { return __ldg(p + i); }
+    static __device__ __forceinline__ void st(double* p, unsigned i, double v, float) { __stcs(p + i, v); }
 };
 template <> struct Store<float> {
     using T = float;
-    static __device__ __forceinline__ float ld(const float* p, long long i, float) { return __ldg(p + i); }
-    static __device__ __forceinline__ void st(float* p, long long i, float v, float) { __stcs(p + i, v); }
+    static __device__ __forceinline__ float ld(const float* p, unsigned i, float) { return __ldg(p + i); }
+    static __device__ __forceinline__ void st(float* p, unsigned i, float v, float) { __stcs(p + i, v); }
 };
 template <> struct Store<__half> {
     using T = float;
-    static __device__ __forceinline__ float ld(const __half* p, long long i, float inv_scale) {
+    static __device__ __forceinline__ float ld(const __half* p, unsigned i, float inv_scale) {
         return __half2float(__ldg(p + i)) * inv_scale;
     }
-    static __device__ __forceinline__ void st(__half* p, long long i, float v, float scale) {
+    static __device__ __forceinline__ void st(__half* p, unsigned i, float v, float scale) {
         p[i] = __float2half_rn(v * scale);
     }
 };
 template <> struct Store<__nv_bfloat16> {
     using T = float;
-    static __device__ __forceinline__ float ld(const __nv_bfloat16* p, long long i, float inv_scale) {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p, unsigned i, float inv_scale) {
         return __bfloat162float(__ldg(p + i)) * inv_scale;
     }
-    static __device__ __forceinline__ void st(__nv_bfloat16* p, long long i, float v, float scale) {
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, unsigned i, float v, float scale) {
         p[i] = __float2bfloat16_rn(v * scale);
     }
 };
 
 // ------------------------------------------------------------ pull stream
-// Neighbour coordinates of (x, y, z) with periodic wrap.
+// The 19 population arrays, one pointer each (kernel parameter space), so
+// that every load or store needs one 32-bit index and no 64-bit i * V.
+template <typename S>
+struct Pops {
+    S* p[NQ];
+};
+
+// Site offsets of the neighbours of (x, y, z), periodic, in unsigned
+// 32-bit arithmetic (differences wrap modulo 2^32 and add back exactly).
 struct Nbr {
-    long long c, ym, yp, zm, zp, zmym, zmyp, zpym, zpyp;  // row offsets ((z*ny+y)*nx)
-    int x, xm, xp;
+    unsigned c;              // (z * ny + y) * nx: row of the site
+    unsigned dym, dyp;       // row(y -+ 1) - row(y)
+    unsigned dzm, dzp;       // row(z -+ 1) - row(z)
+    unsigned x, xm, xp;
     bool solid_zm, solid_zp;
 };
 
 __device__ __forceinline__ Nbr neighbours(const Geom& g, int x, int y, int z) {
     Nbr n;
-    const int ym = (y == 0) ? g.ny - 1 : y - 1, yp = (y == g.ny - 1) ? 0 : y + 1;
-    const int zm = (z == 0) ? g.nz - 1 : z - 1, zp = (z == g.nz - 1) ? 0 : z + 1;
-    n.x = x;
-    n.xm = (x == 0) ? g.nx - 1 : x - 1;
-    n.xp = (x == g.nx - 1) ? 0 : x + 1;
-    const long long nx = g.nx, ny = g.ny;
-    n.c = ((long long)z * ny + y) * nx;
-    n.ym = ((long long)z * ny + ym) * nx;
-    n.yp = ((long long)z * ny + yp) * nx;
-    n.zm = ((long long)zm * ny + y) * nx;
-    n.zp = ((long long)zp * ny + y) * nx;
-    n.zmym = ((long long)zm * ny + ym) * nx;
-    n.zmyp = ((long long)zm * ny + yp) * nx;
-    n.zpym = ((long long)zp * ny + ym) * nx;
-    n.zpyp = ((long long)zp * ny + yp) * nx;
-    n.solid_zm = is_solid(g, zm);
-    n.solid_zp = is_solid(g, zp);
+    const unsigned nx = (unsigned)g.nx;
+    n.c = (unsigned)z * g.plane + (unsigned)y * nx;
+    n.dym = (y == 0) ? (unsigned)(g.ny - 1) * nx : 0u - nx;
+    n.dyp = (y == g.ny - 1) ? 0u - (unsigned)(g.ny - 1) * nx : nx;
+    n.dzm = (z == 0) ? (unsigned)(g.nz - 1) * g.plane : 0u - g.plane;
+    n.dzp = (z == g.nz - 1) ? 0u - (unsigned)(g.nz - 1) * g.plane : g.plane;
+    n.x = (unsigned)x;
+    n.xm = (x == 0) ? nx - 1 : (unsigned)x - 1;
+    n.xp = (x == g.nx - 1) ? 0u : (unsigned)x + 1;
+    n.solid_zm = is_solid(g, z == 0 ? g.nz - 1 : z - 1);
+    n.solid_zp = is_solid(g, z == g.nz - 1 ? 0 : z + 1);
     return n;
 }
 
 // df_i(x) = df*_i(x - c_i); where x - c_i is a solid node the population
 // bounces back: df_i(x) = df*_ibar(x).
 template <typename S, bool WALLS>
-__device__ __forceinline__ void pull19(const S* __restrict__ src, long long V, const Nbr& n, float inv_scale,
+__device__ __forceinline__ void pull19(const Pops<S>& src, const Nbr& n, float inv_scale,
                                        typename Store<S>::T f[NQ]) {
     using St = Store<S>;
-    const long long own = n.c + n.x;
-    f[0] = St::ld(src, 0 * V + own, inv_scale);
-    f[1] = St::ld(src, 1 * V + n.c + n.xm, inv_scale);
-    f[2] = St::ld(src, 2 * V + n.c + n.xp, inv_scale);
-    f[3] = St::ld(src, 3 * V + n.ym + n.x, inv_scale);
-    f[4] = St::ld(src, 4 * V + n.yp + n.x, inv_scale);
-    f[7] = St::ld(src, 7 * V + n.ym + n.xm, inv_scale);
-    f[8] = St::ld(src, 8 * V + n.yp + n.xp, inv_scale);
-    f[9] = St::ld(src, 9 * V + n.yp + n.xm, inv_scale);
-    f[10] = St::ld(src, 10 * V + n.ym + n.xp, inv_scale);
+    const unsigned own = n.c + n.x;
+    const unsigned ym = n.c + n.dym, yp = n.c + n.dyp, zm = n.c + n.dzm, zp = n.c + n.dzp;
+    f[0] = St::ld(src.p[0], own, inv_scale);
+    f[1] = St::ld(src.p[1], n.c + n.xm, inv_scale);
+    f[2] = St::ld(src.p[2], n.c + n.xp, inv_scale);
+    f[3] = St::ld(src.p[3], ym + n.x, inv_scale);
+    f[4] = St::ld(src.p[4], yp + n.x, inv_scale);
+    f[7] = St::ld(src.p[7], ym + n.xm, inv_scale);
+    f[8] = St::ld(src.p[8], yp + n.xp, inv_scale);
+    f[9] = St::ld(src.p[9], yp + n.xm, inv_scale);
+    f[10] = St::ld(src.p[10], ym + n.xp, inv_scale);
     if (!WALLS || !n.solid_zm) {
-        f[5] = St::ld(src, 5 * V + n.zm + n.x, inv_scale);
-        f[11] = St::ld(src, 11 * V + n.zm + n.xm, inv_scale);
-        f[14] = St::ld(src, 14 * V + n.zm + n.xp, inv_scale);
-        f[15] = St::ld(src, 15 * V + n.zmym + n.x, inv_scale);
-        f[18] = St::ld(src, 18 * V + n.zmyp + n.x, inv_scale);
+        f[5] = St::ld(src.p[5], zm + n.x, inv_scale);
+        f[11] = St::ld(src.p[11], zm + n.xm, inv_scale);
+        f[14] = St::ld(src.p[14], zm + n.xp, inv_scale);
+        f[15] = St::ld(src.p[15], zm + n.dym + n.x, inv_scale);
+        f[18] = St::ld(src.p[18], zm + n.dyp + n.x, inv_scale);
     } else {
-        f[5] = St::ld(src, 6 * V + own, inv_scale);
-        f[11] = St::ld(src, 12 * V + own, inv_scale);
-        f[14] = St::ld(src, 13 * V + own, inv_scale);
-        f[15] = St::ld(src, 16 * V + own, inv_scale);
-        f[18] = St::ld(src, 17 * V + own, inv_scale);
+        f[5] = St::ld(src.p[6], own, inv_scale);
+        f[11] = St::ld(src.p[12], own, inv_scale);
+        f[14] = St::ld(src.p[13], own, inv_scale);
+        f[15] = St::ld(src.p[16], own, inv_scale);
+        f[18] = St::ld(src.p[17], own, inv_scale);
     }
     if (!WALLS || !n.solid_zp) {
-        f[6] = St::ld(src, 6 * V + n.zp + n.x, inv_scale);
-        f[12] = St::ld(src, 12 * V + n.zp + n.xp, inv_scale);
-        f[13] = St::ld(src, 13 * V + n.zp + n.xm, inv_scale);
-        f[16] = St::ld(src, 16 * V + n.zpyp + n.x, inv_scale);
-        f[17] = St::ld(src, 17 * V + n.zpym + n.x, inv_scale);
+        f[6] = St::ld(src.p[6], zp + n.x, inv_scale);
+        f[12] = St::ld(src.p[12], zp + n.xp, inv_scale);
+        f[13] = St::ld(src.p[13], zp + n.xm, inv_scale);
+        f[16] = St::ld(src.p[16], zp + n.dyp + n.x, inv_scale);
+        f[17] = St::ld(src.p[17], zp + n.dym + n.x, inv_scale);
     } else {
-        f[6] = St::ld(src, 5 * V + own, inv_scale);
-        f[12] = St::ld(src, 11 * V + own, inv_scale);
-        f[13] = St::ld(src, 14 * V + own, inv_scale);
-        f[16] = St::ld(src, 15 * V + own, inv_scale);
-        f[17] = St::ld(src, 18 * V + own, inv_scale);
+        f[6] = St::ld(src.p[5], own, inv_scale);
+        f[12] = St::ld(src.p[11], own, inv_scale);
+        f[13] = St::ld(src.p[14], own, inv_scale);
+        f[16] = St::ld(src.p[15], own, inv_scale);
+        f[17] = St::ld(src.p[18], own, inv_scale);
     }
 }
 
 // ------------------------------------------------------------- moments
 template <typename T>
 struct Moments {
-    T drho, jx, jy, jz;        // sum df, sum df c
+    T drho, jx, jy, jz;              // sum df, sum df c
+    T jx_lo, jy_lo, jz_lo;           // rounding error of j (float: compensated sum; double: 0)
     T pxx, pyy, pzz, pxy, pxz, pyz;  // sum df c_a c_b
+};
+
+// s + e == a + b exactly (Knuth's two-sum; explicit round-to-nearest adds
+// so that nothing is reassociated or contracted).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+// Momentum j as an unevaluated sum hi + lo.  In float the rounding of
+// j = sum df c would otherwise feed back into the populations every step:
+// when j changes by a nearly constant increment (a uniform body force) the
+// rounded increment is the same each step and the error grows linearly.
+template <typename T> struct MomentumSum;
+template <> struct MomentumSum<double> {
+    static __device__ __forceinline__ void eval(const double f[NQ], Moments<double>& m) {
+        const double e78 = f[7] - f[8], e910 = f[9] - f[10], e1112 = f[11] - f[12], e1314 = f[13] - f[14];
+        const double e1516 = f[15] - f[16], e1718 = f[17] - f[18];
+        m.jx = (f[1] - f[2]) + e78 + e910 + e1112 + e1314;
+        m.jy = (f[3] - f[4]) + e78 - e910 + e1516 + e1718;
+        m.jz = (f[5] - f[6]) + e1112 - e1314 + e1516 - e1718;
+        m.jx_lo = m.jy_lo = m.jz_lo = 0.0;
+    }
+};
+template <> struct MomentumSum<float> {
+    static __device__ __forceinline__ void eval(const float f[NQ], Moments<float>& m) {
+        float d12, d34, d56, d78, d910, d1112, d1314, d1516, d1718;
+        float r12, r34, r56, r78, r910, r1112, r1314, r1516, r1718;
+        two_sum(f[1], -f[2], d12, r12);
+        two_sum(f[3], -f[4], d34, r34);
+        two_sum(f[5], -f[6], d56, r56);
+        two_sum(f[7], -f[8], d78, r78);
+        two_sum(f[9], -f[10], d910, r910);
+        two_sum(f[11], -f[12], d1112, r1112);
+        two_sum(f[13], -f[14], d1314, r1314);
+        two_sum(f[15], -f[16], d1516, r1516);
+        two_sum(f[17], -f[18], d1718, r1718);
+        float s, t1, t2, t3, t4;
+        // jx = d12 + d78 + d910 + d1112 + d1314
+        two_sum(d12, d78, s, t1);
+        two_sum(s, d910, s, t2);
+        two_sum(s, d1112, s, t3);
+        two_sum(s, d1314, m.jx, t4);
+        m.jx_lo = ((r12 + r78) + (r910 + r1112)) + (r1314 + ((t1 + t2) + (t3 + t4)));
+        // jy = d34 + d78 - d910 + d1516 + d1718
+        two_sum(d34, d78, s, t1);
+        two_sum(s, -d910, s, t2);
+        two_sum(s, d1516, s, t3);
+        two_sum(s, d1718, m.jy, t4);
+        m.jy_lo = ((r34 + r78) + (r1516 - r910)) + (r1718 + ((t1 + t2) + (t3 + t4)));
+        // jz = d56 + d1112 - d1314 + d1516 - d1718
+        two_sum(d56, d1112, s, t1);
+        two_sum(s, -d1314, s, t2);
+        two_sum(s, d1516, s, t3);
+        two_sum(s, -d1718, m.jz, t4);
+        m.jz_lo = ((r56 + r1112) + (r1516 - r1314)) + (((t1 + t2) + (t3 + t4)) - r1718);
+    }
 };
 
 template <typename T>
@@ -155,11 +221,7 @@ __device__ __forceinline__ Moments<T> moments19(const T f[NQ]) {
     const T d78 = f[7] + f[8], d910 = f[9] + f[10], d1112 = f[11] + f[12], d1314 = f[13] + f[14];
     const T d1516 = f[15] + f[16], d1718 = f[17] + f[18];
     m.drho = f[0] + a12 + a34 + a56 + d78 + d910 + d1112 + d1314 + d1516 + d1718;
-    const T e78 = f[7] - f[8], e910 = f[9] - f[10], e1112 = f[11] - f[12], e1314 = f[13] - f[14];
-    const T e1516 = f[15] - f[16], e1718 = f[17] - f[18];
-    m.jx = (f[1] - f[2]) + e78 + e910 + e1112 + e1314;
-    m.jy = (f[3] - f[4]) + e78 - e910 + e1516 + e1718;
-    m.jz = (f[5] - f[6]) + e1112 - e1314 + e1516 - e1718;
+    MomentumSum<T>::eval(f, m);
     m.pxx = a12 + d78 + d910 + d1112 + d1314;
     m.pyy = a34 + d78 + d910 + d1516 + d1718;
     m.pzz = a56 + d1112 + d1314 + d1516 + d1718;
@@ -176,13 +238,40 @@ struct Coef {
     T tau_s, tau_b, om_s, om_b;
 };
 
+// Lattice weights and Hermite coefficients rounded so that the discrete
+// moment identities hold exactly for the rounded values:
+//   w0 + 6 w1 + 12 w2 == 1          (mass of the reconstruction)
+//   2 a1 + 8 b1 == 1                (momentum: a1 ~ 3 w1 = 1/6, b1 ~ 3 w2 = 1/12)
+// Plain round-to-nearest of 1/6 gives 6 fl(1/6) = 1 + 3e-8 in float, a
+// momentum gain every step that accumulates in slowly varying flows.
+template <typename T> struct Wts;
+template <> struct Wts<float> {
+    static constexpr float w0 = 11184812.0f * 0x1p-25f;   // ~ 1/3
+    static constexpr float w2 = 14913080.0f * 0x1p-29f;   // ~ 1/36
+    static constexpr float w1 = 2.0f * w2;                // ~ 1/18
+    static constexpr float a1 = 11184810.0f * 0x1p-26f;   // ~ 1/6
+    static constexpr float b1 = 11184811.0f * 0x1p-27f;   // ~ 1/12
+};
+template <> struct Wts<double> {
+    static constexpr double w0 = 6004799503160662.0 * 0x1p-54;
+    static constexpr double w2 = 8006399337547548.0 * 0x1p-58;
+    static constexpr double w1 = 2.0 * w2;
+    static constexpr double a1 = 6004799503160660.0 * 0x1p-55;
+    static constexpr double b1 = 6004799503160662.0 * 0x1p-56;
+};
+
 // Post-collision df* from the pulled df and the local force density F:
 //   A = j + F,  v = (j + F/2) / rho,  S = sum df Q,
 //   X = S - rho vv,  Y = vF + Fv,
 //   B = S - om_s dev(X - tau_s Y) - (om_b / 3) tr(X - tau_b Y) 1,
 //   df*_i = w_i [drho + 3 A.c_i + 4.5 c_i.B.c_i - 1.5 tr B].
+// Evaluation order: the momentum term 3 w_i j.c_i, the largest, enters
+// last through fused multiply-adds, so it is rounded once; the force term
+// 3 w_i F.c_i is added to the small terms first, so a force much smaller
+// than j is not lost to the rounding of j + F.
 template <typename T>
 __device__ __forceinline__ void collide19(const T f[NQ], T Fx, T Fy, T Fz, const Coef<T>& k, T out[NQ]) {
+    using W = Wts<T>;
     const Moments<T> m = moments19(f);
     const T third = T(1) / T(3);
     const T rho = T(1) + m.drho;
@@ -205,34 +294,44 @@ __device__ __forceinline__ void collide19(const T f[NQ], T Fx, T Fy, T Fz, const
     const T bxy = m.pxy - k.om_s * (xxy - k.tau_s * yxy);
     const T bxz = m.pxz - k.om_s * (xxz - k.tau_s * yxz);
     const T byz = m.pyz - k.om_s * (xyz - k.tau_s * yyz);
-    const T ax = m.jx + Fx, ay = m.jy + Fy, az = m.jz + Fz;
 
     const T base = m.drho - T(1.5) * (bxx + byy + bzz);
-    const T w0 = T(1) / T(3), w1 = T(1) / T(18), w2 = T(1) / T(36);
-    out[0] = w0 * base;
-    const T hx = base + T(4.5) * bxx, hy = base + T(4.5) * byy, hz = base + T(4.5) * bzz;
-    const T ax3 = T(3) * ax, ay3 = T(3) * ay, az3 = T(3) * az;
-    out[1] = w1 * (hx + ax3);
-    out[2] = w1 * (hx - ax3);
-    out[3] = w1 * (hy + ay3);
-    out[4] = w1 * (hy - ay3);
-    out[5] = w1 * (hz + az3);
-    out[6] = w1 * (hz - az3);
-    // (s1, s2) face diagonals in plane (a, b): base + 4.5 (Baa + Bbb) + 9 s1 s2 Bab + 3 (s1 Aa + s2 Ab)
+    out[0] = W::w0 * base;
+    // axis populations: w1 (base + 4.5 B_aa) + a1 (+-F_a) + a1 (+-j_a)
+    const T hx = W::w1 * (base + T(4.5) * bxx), hy = W::w1 * (base + T(4.5) * byy),
+            hz = W::w1 * (base + T(4.5) * bzz);
+    // force density plus the low part of j: both are far smaller than j
+    const T Gx = Fx + m.jx_lo, Gy = Fy + m.jy_lo, Gz = Fz + m.jz_lo;
+    const T fx = W::a1 * Gx, fy = W::a1 * Gy, fz = W::a1 * Gz;
+    out[1] = fma(W::a1, m.jx, hx + fx);
+    out[2] = fma(-W::a1, m.jx, hx - fx);
+    out[3] = fma(W::a1, m.jy, hy + fy);
+    out[4] = fma(-W::a1, m.jy, hy - fy);
+    out[5] = fma(W::a1, m.jz, hz + fz);
+    out[6] = fma(-W::a1, m.jz, hz - fz);
+    // face diagonals (s1, s2) in plane (a, b):
+    //   w2 (base + 4.5 (B_aa + B_bb) + 9 s1 s2 B_ab) + b1 (s1 F_a + s2 F_b) + b1 (s1 j_a + s2 j_b)
     const T pxy_ = base + T(4.5) * (bxx + byy), pxz_ = base + T(4.5) * (bxx + bzz), pyz_ = base + T(4.5) * (byy + bzz);
     const T qxy = T(9) * bxy, qxz = T(9) * bxz, qyz = T(9) * byz;
-    out[7] = w2 * (pxy_ + qxy + (ax3 + ay3));
-    out[8] = w2 * (pxy_ + qxy - (ax3 + ay3));
-    out[9] = w2 * (pxy_ - qxy + (ax3 - ay3));
-    out[10] = w2 * (pxy_ - qxy - (ax3 - ay3));
-    out[11] = w2 * (pxz_ + qxz + (ax3 + az3));
-    out[12] = w2 * (pxz_ + qxz - (ax3 + az3));
-    out[13] = w2 * (pxz_ - qxz + (ax3 - az3));
-    out[14] = w2 * (pxz_ - qxz - (ax3 - az3));
-    out[15] = w2 * (pyz_ + qyz + (ay3 + az3));
-    out[16] = w2 * (pyz_ + qyz - (ay3 + az3));
-    out[17] = w2 * (pyz_ - qyz + (ay3 - az3));
-    out[18] = w2 * (pyz_ - qyz - (ay3 - az3));
+    const T gpxy = W::w2 * (pxy_ + qxy), gmxy = W::w2 * (pxy_ - qxy);
+    const T gpxz = W::w2 * (pxz_ + qxz), gmxz = W::w2 * (pxz_ - qxz);
+    const T gpyz = W::w2 * (pyz_ + qyz), gmyz = W::w2 * (pyz_ - qyz);
+    const T Fpxy = W::b1 * (Gx + Gy), Fmxy = W::b1 * (Gx - Gy);
+    const T Fpxz = W::b1 * (Gx + Gz), Fmxz = W::b1 * (Gx - Gz);
+    const T Fpyz = W::b1 * (Gy + Gz), Fmyz = W::b1 * (Gy - Gz);
+    const T b = W::b1;
+    out[7] = fma(b, m.jx, fma(b, m.jy, gpxy + Fpxy));
+    out[8] = fma(-b, m.jx, fma(-b, m.jy, gpxy - Fpxy));
+    out[9] = fma(b, m.jx, fma(-b, m.jy, gmxy + Fmxy));
+    out[10] = fma(-b, m.jx, fma(b, m.jy, gmxy - Fmxy));
+    out[11] = fma(b, m.jx, fma(b, m.jz, gpxz + Fpxz));
+    out[12] = fma(-b, m.jx, fma(-b, m.jz, gpxz - Fpxz));
+    out[13] = fma(b, m.jx, fma(-b, m.jz, gmxz + Fmxz));
+    out[14] = fma(-b, m.jx, fma(b, m.jz, gmxz - Fmxz));
+    out[15] = fma(b, m.jy, fma(b, m.jz, gpyz + Fpyz));
+    out[16] = fma(-b, m.jy, fma(-b, m.jz, gpyz - Fpyz));
+    out[17] = fma(b, m.jy, fma(-b, m.jz, gmyz + Fmyz));
+    out[18] = fma(-b, m.jy, fma(b, m.jz, gmyz - Fmyz));
 }
 
 // drho = rho - 1 and v = (j + F/2) / rho, Eq. (macrovariables2).
@@ -242,9 +341,9 @@ __device__ __forceinline__ void macro19(const T f[NQ], T Fx, T Fy, T Fz, T& drho
     drho = m.drho;
     const T rho = T(1) + m.drho;
     const T irho = T(1) / rho;
-    vx = (m.jx + T(0.5) * Fx) * irho;
-    vy = (m.jy + T(0.5) * Fy) * irho;
-    vz = (m.jz + T(0.5) * Fz) * irho;
+    vx = (m.jx + (m.jx_lo + T(0.5) * Fx)) * irho;
+    vy = (m.jy + (m.jy_lo + T(0.5) * Fy)) * irho;
+    vz = (m.jz + (m.jz_lo + T(0.5) * Fz)) * irho;
 }
 
 // ------------------------------------------------------- Peskin kernel

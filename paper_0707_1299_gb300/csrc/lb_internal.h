@@ -33,12 +33,12 @@ struct lb_ctx {
     double* radius;           // > 0 for colloids, 0 for fixed points
     int* mobile;
     double* fsum;             // 3 doubles: net point force (device)
+    double fsum_host[3];      // its host copy, refreshed when the points change
     int* status;              // 1 int: device-side validation result
 
     // reductions
-    double* partials;         // 4 * red_blocks doubles
+    double* partials;         // 4 doubles per block of the moments kernel
     double* totals_dev;       // 4 doubles
-    int red_blocks;
 
     // staging for host pointers (grown on demand)
     void* stage;
@@ -51,11 +51,11 @@ struct lb_ctx {
 
 namespace lbk {
 
-// Coefficients passed to kernels that need the uniform force.
-struct ForceConst {
-    double g[3];
-    double inv_vfluid;   // 1 / number of fluid sites
-    int counter;
+// Uniform force density on fluid sites (body force + counter-force), in
+// the arithmetic type of the kernel.
+template <typename T>
+struct UForce {
+    T F[3];
 };
 
 cudaError_t launch_collide(lb_ctx* c);
@@ -73,6 +73,6 @@ cudaError_t compute_inv_aL(const int grid[3], const double R[3], const double di
 
 size_t storage_bytes(int prec);
 size_t arith_bytes(int prec);
-ForceConst force_const(const lb_ctx* c);
+long long moment_blocks(const Geom& g);
 
 }  // namespace lbk

@@ -35,61 +35,64 @@ size_t storage_bytes(int prec) {
 }
 size_t arith_bytes(int prec) { return prec == LB_F64 ? 8 : 4; }
 
-ForceConst force_const(const lb_ctx* c) {
-    ForceConst k;
-    for (int a = 0; a < 3; ++a) k.g[a] = c->g[a];
+double n_fluid(const lb_ctx* c) {
     long long nfluid = c->geom.V;
     const long long plane = (long long)c->geom.nx * c->geom.ny;
     if (c->geom.wall_lo >= 0) nfluid -= plane;
     if (c->geom.wall_hi >= 0 && c->geom.wall_hi != c->geom.wall_lo) nfluid -= plane;
-    k.inv_vfluid = nfluid > 0 ? 1.0 / (double)nfluid : 0.0;
-    k.counter = (c->counter && c->npts > 0) ? 1 : 0;
-    return k;
+    return (double)nfluid;
 }
 
-// Uniform part of the force density on a fluid site: g + counter-force.
-__device__ __forceinline__ void uniform_force(const ForceConst& k, const double* __restrict__ fsum, double F[3]) {
-    for (int a = 0; a < 3; ++a) F[a] = k.g[a];
-    if (k.counter)
-        for (int a = 0; a < 3; ++a) F[a] -= fsum[a] * k.inv_vfluid;
+// Uniform force density on fluid sites: g plus the counter-force
+// -sum F / V_fluid (evaluated on the host in FP64, passed in the arithmetic type).
+template <typename T>
+UForce<T> uniform_force(const lb_ctx* c) {
+    UForce<T> u;
+    const double nf = n_fluid(c);
+    for (int a = 0; a < 3; ++a) {
+        double F = c->g[a];
+        if (c->counter && c->npts > 0 && nf > 0) F -= c->fsum_host[a] / nf;
+        u.F[a] = (T)F;
+    }
+    return u;
 }
 
-// Decompose a warp's tile index into (x, y, z).
-__device__ __forceinline__ void tile_coords(const Geom& g, long long tile, int lane, int& x, int& y, int& z) {
-    const int tx = (int)(tile % g.ntx);
-    const long long r = tile / g.ntx;
-    y = (int)(r % g.ny);
-    z = (int)(r / g.ny);
-    x = tx * TILE_X + lane;
+template <typename S>
+static Pops<S> pops(void* base, long long V) {
+    Pops<S> p;
+    for (int i = 0; i < NQ; ++i) p.p[i] = (S*)base + (size_t)i * (size_t)V;
+    return p;
+}
+
+// Site kernels: block = 4 warps, one warp per 32-site x-row tile; grid =
+// (tiles per row, ceil(ny / 4), nz).  No division in the index math.
+static dim3 site_grid(const Geom& g) {
+    return dim3((unsigned)g.ntx, (unsigned)((g.ny + CS_WARPS - 1) / CS_WARPS), (unsigned)g.nz);
 }
 
 // ------------------------------------------------------------ k_collide
 template <typename S, bool WALLS>
-__global__ void __launch_bounds__(CS_THREADS)
-k_collide(const S* __restrict__ src, S* __restrict__ dst, typename Store<S>::T* __restrict__ floc,
-          unsigned char* __restrict__ flags, const double* __restrict__ fsum, Geom g,
-          Coef<typename Store<S>::T> k, ForceConst fk, float scale, float inv_scale) {
+__global__ void __launch_bounds__(CS_THREADS, 8)
+k_collide(const Pops<S> src, const Pops<S> dst, typename Store<S>::T* __restrict__ floc,
+          unsigned char* __restrict__ flags, Geom g, Coef<typename Store<S>::T> k,
+          UForce<typename Store<S>::T> fu, float scale, float inv_scale) {
     using T = typename Store<S>::T;
-    const long long tile = (long long)blockIdx.x * CS_WARPS + (threadIdx.x >> 5);
-    if (tile >= g.ntiles) return;  // uniform per warp
-    const int lane = threadIdx.x & 31;
-    int x, y, z;
-    tile_coords(g, tile, lane, x, y, z);
-    const bool active = x < g.nx;
+    const int y = blockIdx.y * CS_WARPS + threadIdx.y;
+    if (y >= g.ny) return;  // uniform per warp
+    const int z = blockIdx.z, lane = threadIdx.x;
+    const int x = blockIdx.x * TILE_X + lane;
+    const unsigned tile = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.ntx + blockIdx.x;
     const unsigned char fl = flags[tile];
-    const long long V = g.V;
+    const unsigned V = (unsigned)g.V;
 
-    if (active) {
+    if (x < g.nx) {
         const Nbr n = neighbours(g, x, y, z);
-        const long long site = n.c + x;
+        const unsigned site = n.c + n.x;
         if (WALLS && is_solid(g, z)) {
-            for (int i = 0; i < NQ; ++i) Store<S>::st(dst, i * V + site, T(0), scale);
-            if (fl)
-                for (int a = 0; a < 3; ++a) floc[a * V + site] = T(0);
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) Store<S>::st(dst.p[i], site, T(0), scale);
         } else {
-            double Fu[3];
-            uniform_force(fk, fsum, Fu);
-            T Fx = (T)Fu[0], Fy = (T)Fu[1], Fz = (T)Fu[2];
+            T Fx = fu.F[0], Fy = fu.F[1], Fz = fu.F[2];
             if (fl) {
                 Fx += floc[site];
                 Fy += floc[V + site];
@@ -99,10 +102,10 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, typename Store<S>::T* 
                 floc[2 * V + site] = T(0);
             }
             T f[NQ], o[NQ];
-            pull19<S, WALLS>(src, V, n, inv_scale, f);
+            pull19<S, WALLS>(src, n, inv_scale, f);
             collide19<T>(f, Fx, Fy, Fz, k, o);
 #pragma unroll
-            for (int i = 0; i < NQ; ++i) Store<S>::st(dst, i * V + site, o[i], scale);
+            for (int i = 0; i < NQ; ++i) Store<S>::st(dst.p[i], site, o[i], scale);
         }
     }
     if (fl) {
@@ -149,8 +152,8 @@ __device__ __forceinline__ double wrap_pos(double r, int n) {
 // update (update mode).  One warp per point.
 template <typename S, bool WALLS>
 __global__ void __launch_bounds__(128)
-k_gather(const S* __restrict__ src, const typename Store<S>::T* __restrict__ floc, const double* __restrict__ fsum,
-         Geom g, ForceConst fk, float inv_scale, int n, const double* __restrict__ qpos, double* __restrict__ vout,
+k_gather(const Pops<S> src, const typename Store<S>::T* __restrict__ floc, Geom g, UForce<typename Store<S>::T> fu,
+         float inv_scale, int n, const double* __restrict__ qpos, double* __restrict__ vout,
          double* __restrict__ upos, const double* __restrict__ force, const double* __restrict__ radius,
          const int* __restrict__ mobile, double inv_6pi_eta, double inv_aL) {
     using T = typename Store<S>::T;
@@ -162,8 +165,7 @@ k_gather(const S* __restrict__ src, const typename Store<S>::T* __restrict__ flo
     const double* P = update ? upos + 3 * s : qpos + 3 * s;
     const double X = wrap_pos(P[0], g.nx), Y = wrap_pos(P[1], g.ny), Z = wrap_pos(P[2], g.nz);
     const int bx = stencil_base(X), by = stencil_base(Y), bz = stencil_base(Z);
-    double Fu[3];
-    uniform_force(fk, fsum, Fu);
+    const unsigned V = (unsigned)g.V;
     T acc[3] = {T(0), T(0), T(0)};
     for (int h = 0; h < 2; ++h) {
         const int node = lane + 32 * h;
@@ -173,10 +175,10 @@ k_gather(const S* __restrict__ src, const typename Store<S>::T* __restrict__ flo
         const T w = peskin_phi((T)((double)(bx + i) - X)) * peskin_phi((T)((double)(by + j) - Y)) *
                     peskin_phi((T)((double)(bz + k) - Z));
         const Nbr nb = neighbours(g, x, y, z);
-        const long long site = nb.c + x;
+        const unsigned site = nb.c + nb.x;
         T f[NQ];
-        pull19<S, WALLS>(src, g.V, nb, inv_scale, f);
-        const T Fx = (T)Fu[0] + floc[site], Fy = (T)Fu[1] + floc[g.V + site], Fz = (T)Fu[2] + floc[2 * g.V + site];
+        pull19<S, WALLS>(src, nb, inv_scale, f);
+        const T Fx = fu.F[0] + floc[site], Fy = fu.F[1] + floc[V + site], Fz = fu.F[2] + floc[2 * V + site];
         T drho, vx, vy, vz;
         macro19<T>(f, Fx, Fy, Fz, drho, vx, vy, vz);
         acc[0] += w * vx;
@@ -193,9 +195,8 @@ k_gather(const S* __restrict__ src, const typename Store<S>::T* __restrict__ flo
     }
     const double c = (1.0 / radius[s] - inv_aL) * inv_6pi_eta;
     const int nn[3] = {g.nx, g.ny, g.nz};
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 0; a < 3; ++a)
         upos[3 * s + a] = wrap_pos(P[a] + (double)acc[a] + force[3 * s + a] * c, nn[a]);
-    }
 }
 
 // ------------------------------------------------------------ k_moments
@@ -203,65 +204,64 @@ k_gather(const S* __restrict__ src, const typename Store<S>::T* __restrict__ flo
 // (rho, rho u) in a fixed order, so the totals are deterministic.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int w = tid >> 5, lane = tid & 31;
+    const int nw = (int)(blockDim.x * blockDim.y) >> 5;
     __syncthreads();
     if (lane == 0) sh[w] = v;
     __syncthreads();
     double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+    if (tid == 0)
+        for (int i = 0; i < nw; ++i) t += sh[i];
     return t;  // valid in thread 0
 }
 
 template <typename S, bool WALLS>
 __global__ void __launch_bounds__(CS_THREADS)
-k_moments(const S* __restrict__ src, const typename Store<S>::T* __restrict__ floc, const double* __restrict__ fsum,
-          Geom g, ForceConst fk, float inv_scale, double* __restrict__ rho_out, double* __restrict__ u_out,
-          double* __restrict__ partials) {
+k_moments(const Pops<S> src, const typename Store<S>::T* __restrict__ floc, Geom g, UForce<typename Store<S>::T> fu,
+          float inv_scale, double* __restrict__ rho_out, double* __restrict__ u_out, double* __restrict__ partials) {
     using T = typename Store<S>::T;
     __shared__ double sh[CS_WARPS];
-    const int lane = threadIdx.x & 31;
-    double Fu[3];
-    uniform_force(fk, fsum, Fu);
+    const int y = blockIdx.y * CS_WARPS + threadIdx.y;
+    const int z = blockIdx.z, lane = threadIdx.x;
+    const int x = blockIdx.x * TILE_X + lane;
+    const unsigned V = (unsigned)g.V;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (long long tile = (long long)blockIdx.x * CS_WARPS + (threadIdx.x >> 5); tile < g.ntiles;
-         tile += (long long)gridDim.x * CS_WARPS) {
-        int x, y, z;
-        tile_coords(g, tile, lane, x, y, z);
-        if (x >= g.nx) continue;
+    if (y < g.ny && x < g.nx) {
         const Nbr nb = neighbours(g, x, y, z);
-        const long long site = nb.c + x;
+        const unsigned site = nb.c + nb.x;
         double r = 1.0, u[3] = {0.0, 0.0, 0.0};
         if (!(WALLS && is_solid(g, z))) {
             T f[NQ];
-            pull19<S, WALLS>(src, g.V, nb, inv_scale, f);
-            const T Fx = (T)Fu[0] + floc[site], Fy = (T)Fu[1] + floc[g.V + site], Fz = (T)Fu[2] + floc[2 * g.V + site];
+            pull19<S, WALLS>(src, nb, inv_scale, f);
+            const T Fx = fu.F[0] + floc[site], Fy = fu.F[1] + floc[V + site], Fz = fu.F[2] + floc[2 * V + site];
             T drho, vx, vy, vz;
             macro19<T>(f, Fx, Fy, Fz, drho, vx, vy, vz);
             r = 1.0 + (double)drho;
             u[0] = (double)vx;
             u[1] = (double)vy;
             u[2] = (double)vz;
-            acc[0] += r;
-            for (int a = 0; a < 3; ++a) acc[1 + a] += r * u[a];
+            acc[0] = r;
+            for (int a = 0; a < 3; ++a) acc[1 + a] = r * u[a];
         }
         if (rho_out) rho_out[site] = r;
         if (u_out)
-            for (int a = 0; a < 3; ++a) u_out[a * g.V + site] = u[a];
+            for (int a = 0; a < 3; ++a) u_out[(size_t)a * V + site] = u[a];
     }
     if (partials) {
+        const unsigned b = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
         for (int a = 0; a < 4; ++a) {
             const double t = block_sum(acc[a], sh);
-            if (threadIdx.x == 0) partials[4 * blockIdx.x + a] = t;
+            if (threadIdx.x == 0 && threadIdx.y == 0) partials[4 * (size_t)b + a] = t;
         }
     }
 }
 
-__global__ void k_reduce_partials(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
+__global__ void k_reduce_partials(const double* __restrict__ partials, long long nblocks, double* __restrict__ out) {
     __shared__ double sh[32];
     for (int a = 0; a < 4; ++a) {
         double v = 0.0;
-        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partials[4 * b + a];
+        for (long long b = threadIdx.x; b < nblocks; b += blockDim.x) v += partials[4 * b + a];
         const double t = block_sum(v, sh);
         if (threadIdx.x == 0) out[a] = t;
     }
@@ -439,7 +439,8 @@ __global__ void k_sum1(const double* __restrict__ partials, int n, double* __res
 }
 
 // ------------------------------------------------------------ launchers
-static unsigned int site_blocks(const Geom& g) { return (unsigned int)((g.ntiles + CS_WARPS - 1) / CS_WARPS); }
+static bool has_walls(const lb_ctx* c) { return c->geom.wall_lo >= 0 || c->geom.wall_hi >= 0; }
+static dim3 site_block() { return dim3(TILE_X, CS_WARPS, 1); }
 
 template <typename S>
 static cudaError_t collide_t(lb_ctx* c) {
@@ -449,16 +450,14 @@ static cudaError_t collide_t(lb_ctx* c) {
     k.tau_b = (T)c->tau_b;
     k.om_s = (T)(1.0 / (c->tau_s + 0.5));
     k.om_b = (T)(1.0 / (c->tau_b + 0.5));
-    const S* src = (const S*)c->f[c->cur];
-    S* dst = (S*)c->f[1 - c->cur];
-    const bool walls = c->geom.wall_lo >= 0 || c->geom.wall_hi >= 0;
-    const ForceConst fk = force_const(c);
-    if (walls)
-        k_collide<S, true><<<site_blocks(c->geom), CS_THREADS, 0, c->stream>>>(
-            src, dst, (T*)c->floc, c->flags, c->fsum, c->geom, k, fk, c->scale, c->inv_scale);
+    const Pops<S> src = pops<S>(c->f[c->cur], c->geom.V), dst = pops<S>(c->f[1 - c->cur], c->geom.V);
+    const UForce<T> fu = uniform_force<T>(c);
+    if (has_walls(c))
+        k_collide<S, true><<<site_grid(c->geom), site_block(), 0, c->stream>>>(
+            src, dst, (T*)c->floc, c->flags, c->geom, k, fu, c->scale, c->inv_scale);
     else
-        k_collide<S, false><<<site_blocks(c->geom), CS_THREADS, 0, c->stream>>>(
-            src, dst, (T*)c->floc, c->flags, c->fsum, c->geom, k, fk, c->scale, c->inv_scale);
+        k_collide<S, false><<<site_grid(c->geom), site_block(), 0, c->stream>>>(
+            src, dst, (T*)c->floc, c->flags, c->geom, k, fu, c->scale, c->inv_scale);
     c->launches++;
     return cudaGetLastError();
 }
@@ -476,8 +475,7 @@ template <typename T>
 static cudaError_t spread_t(lb_ctx* c) {
     const long long threads = (long long)c->npts * 64;
     const unsigned int blocks = (unsigned int)((threads + 255) / 256);
-    const bool walls = c->geom.wall_lo >= 0 || c->geom.wall_hi >= 0;
-    if (walls)
+    if (has_walls(c))
         k_spread<T, true><<<blocks, 256, 0, c->stream>>>(c->pos, c->force, c->npts, (T*)c->floc, c->flags, c->geom);
     else
         k_spread<T, false><<<blocks, 256, 0, c->stream>>>(c->pos, c->force, c->npts, (T*)c->floc, c->flags, c->geom);
@@ -493,22 +491,21 @@ cudaError_t launch_spread(lb_ctx* c) {
 template <typename S>
 static cudaError_t gather_t(lb_ctx* c, int n, const double* qpos, double* vout, bool update) {
     using T = typename Store<S>::T;
-    const bool walls = c->geom.wall_lo >= 0 || c->geom.wall_hi >= 0;
-    const ForceConst fk = force_const(c);
+    const UForce<T> fu = uniform_force<T>(c);
     const double eta = c->tau_s / 3.0;
     const double inv_6pi_eta = 1.0 / (6.0 * M_PI * eta);
     const double inv_aL = isinf(c->a_L) ? 0.0 : 1.0 / c->a_L;
     const unsigned int blocks = (unsigned int)((n + 3) / 4);
-    const S* src = (const S*)c->f[c->cur];
+    const Pops<S> src = pops<S>(c->f[c->cur], c->geom.V);
     double* upos = update ? c->pos : nullptr;
-    if (walls)
-        k_gather<S, true><<<blocks, 128, 0, c->stream>>>(src, (const T*)c->floc, c->fsum, c->geom, fk, c->inv_scale, n,
-                                                          qpos, vout, upos, c->force, c->radius, c->mobile,
-                                                          inv_6pi_eta, inv_aL);
+    if (has_walls(c))
+        k_gather<S, true><<<blocks, 128, 0, c->stream>>>(src, (const T*)c->floc, c->geom, fu, c->inv_scale, n, qpos,
+                                                          vout, upos, c->force, c->radius, c->mobile, inv_6pi_eta,
+                                                          inv_aL);
     else
-        k_gather<S, false><<<blocks, 128, 0, c->stream>>>(src, (const T*)c->floc, c->fsum, c->geom, fk, c->inv_scale, n,
-                                                           qpos, vout, upos, c->force, c->radius, c->mobile,
-                                                           inv_6pi_eta, inv_aL);
+        k_gather<S, false><<<blocks, 128, 0, c->stream>>>(src, (const T*)c->floc, c->geom, fu, c->inv_scale, n, qpos,
+                                                           vout, upos, c->force, c->radius, c->mobile, inv_6pi_eta,
+                                                           inv_aL);
     c->launches++;
     return cudaGetLastError();
 }
@@ -523,23 +520,27 @@ cudaError_t launch_gather(lb_ctx* c, int n, const double* qpos, double* vout, bo
     }
 }
 
+long long moment_blocks(const Geom& g) {
+    const dim3 gr = site_grid(g);
+    return (long long)gr.x * gr.y * gr.z;
+}
+
 template <typename S>
 static cudaError_t moments_t(lb_ctx* c, double* rho, double* u, bool want_totals) {
     using T = typename Store<S>::T;
-    const bool walls = c->geom.wall_lo >= 0 || c->geom.wall_hi >= 0;
-    const ForceConst fk = force_const(c);
-    const S* src = (const S*)c->f[c->cur];
+    const UForce<T> fu = uniform_force<T>(c);
+    const Pops<S> src = pops<S>(c->f[c->cur], c->geom.V);
     double* part = want_totals ? c->partials : nullptr;
-    if (walls)
-        k_moments<S, true><<<c->red_blocks, CS_THREADS, 0, c->stream>>>(src, (const T*)c->floc, c->fsum, c->geom, fk,
-                                                                         c->inv_scale, rho, u, part);
+    if (has_walls(c))
+        k_moments<S, true><<<site_grid(c->geom), site_block(), 0, c->stream>>>(src, (const T*)c->floc, c->geom, fu,
+                                                                               c->inv_scale, rho, u, part);
     else
-        k_moments<S, false><<<c->red_blocks, CS_THREADS, 0, c->stream>>>(src, (const T*)c->floc, c->fsum, c->geom, fk,
-                                                                          c->inv_scale, rho, u, part);
+        k_moments<S, false><<<site_grid(c->geom), site_block(), 0, c->stream>>>(src, (const T*)c->floc, c->geom, fu,
+                                                                                c->inv_scale, rho, u, part);
     c->launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !want_totals) return e;
-    k_reduce_partials<<<1, 256, 0, c->stream>>>(c->partials, c->red_blocks, c->totals_dev);
+    k_reduce_partials<<<1, 1024, 0, c->stream>>>(c->partials, moment_blocks(c->geom), c->totals_dev);
     c->launches++;
     return cudaGetLastError();
 }
