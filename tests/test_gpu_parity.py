@@ -139,7 +139,8 @@ def test_channel_256_full_size():
     uu = u.cpu().numpy()
     for (y, x) in [(0, 0), (17, 200), (255, 255), (128, 3)]:
         assert rel_err(uu[:, :, y, x], ref) < TOL["f32"]
-    assert np.abs(uu[1:]).max() < 1e-12 * np.abs(ref).max() + 1e-20
+    # no cross-flow beyond FP32 rounding
+    assert np.abs(uu[1:]).max() < TOL["f32"] * np.abs(ref).max()
     g.close()
 
 
