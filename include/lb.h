@@ -178,6 +178,38 @@ lb_status lb_synchronize(lb_ctx *ctx);
  * the current device (allocates temporary device memory). */
 lb_status lb_compute_aL(const int grid[3], const double R[3], const double dir[3], double *a_L);
 
+/* Totals {sum rho, sum rho u} over the fluid sites of a population array
+ * that the caller owns, computed without allocating any device memory.
+ * The paper has no counterpart to this call: it exists for callers that
+ * cannot use cudaMalloc -- code whose device memory belongs to its own pool
+ * allocator or fixed arena, and code that cannot tolerate cudaFree's
+ * device-wide wait or an out-of-memory failure in the middle of a run --
+ * and therefore cannot create an lb_ctx.
+ *   df        device pointer, 19 * V elements laid out as df[i][z][y][x]
+ *             (the order of lb_get_populations) in the storage format of
+ *             `precision`: double (LB_F64), float (LB_F32), half holding
+ *             df * 2^20 (LB_F16S) or bfloat16 (LB_BF16S).  It is read as
+ *             the post-collision state; the totals are those of the pulled
+ *             (streamed) state, as lb_moments reports them.
+ *   grid      nx, ny, nz >= 1 with nx * ny * nz < 2^32 (host).
+ *   z_lo, z_hi  solid z-planes with bounce-back, -1 for none.
+ *   F         uniform force density on fluid sites (3 doubles, host; NULL
+ *             for zero); it enters rho u = sum df c + F / 2.
+ *   totals    device pointer to 4 doubles, written.
+ *   stream    cudaStream_t the two kernels are launched on; the call does
+ *             not wait for them.
+ * Scratch: a library-wide static device array of 1024 x 4 doubles
+ * (32 KiB) that every GPU using the library keeps until the process
+ * exits.  The first call on a device looks its address up (with that
+ * device current) and should come before any stream capture.  All calls
+ * share the array; calls whose kernels overlap on the GPU race on it.
+ * Errors: LB_ERR_ARG (NULL pointer, bad precision, grid or plane, or a
+ * lattice beyond the limit above), LB_ERR_NONFINITE (F), LB_ERR_CUDA.
+ * Does not call cudaMalloc, cudaFree or any allocating routine, and does
+ * not touch lb_last_error. */
+lb_status lb_totals_noalloc(const void *df, int precision, const int grid[3], int z_lo, int z_hi,
+                            const double F[3], double *totals, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

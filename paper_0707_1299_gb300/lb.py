@@ -28,7 +28,7 @@ EXPORTS = ["lb_create", "lb_destroy", "lb_last_error", "lb_set_body_force", "lb_
            "lb_set_counterforce", "lb_set_colloid_aL", "lb_add_point_forces", "lb_clear_point_forces",
            "lb_num_points", "lb_set_positions", "lb_step", "lb_velocity_at", "lb_moments",
            "lb_particles", "lb_get_populations", "lb_set_populations", "lb_kernel_launches",
-           "lb_synchronize", "lb_compute_aL"]
+           "lb_synchronize", "lb_compute_aL", "lb_totals_noalloc"]
 
 _lib = None
 
@@ -70,6 +70,7 @@ def load():
         "lb_kernel_launches": ([vp, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
         "lb_synchronize": ([vp], ctypes.c_int),
         "lb_compute_aL": ([ip, dp, dp, dp], ctypes.c_int),
+        "lb_totals_noalloc": ([vp, ctypes.c_int, ip, ctypes.c_int, ctypes.c_int, dp, dp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -200,6 +201,23 @@ def lb_compute_aL(grid, R, direction=None):
     out = np.zeros(1)
     _check(None, load().lb_compute_aL(g, r.ctypes.data, None if d is None else d.ctypes.data, out.ctypes.data))
     return float(out[0])
+
+
+def lb_totals_noalloc(df, precision, grid, z_lo, z_hi, F, totals, stream=None):
+    """Totals of a caller-owned device population array without any device
+    allocation (see include/lb.h).  df: device tensor or address in the
+    storage format of `precision`; totals: device float64 tensor of 4."""
+    g = (ctypes.c_int * 3)(*[int(v) for v in grid])
+    f = None if F is None else np.ascontiguousarray(F, dtype=np.float64)
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    addr = df if isinstance(df, int) else df.data_ptr()
+    status = load().lb_totals_noalloc(addr, int(precision), g, int(z_lo), int(z_hi),
+                                      None if f is None else f.ctypes.data, _ptr(totals),
+                                      ctypes.c_void_p(stream))
+    if status != LB_OK:
+        raise LBError(status, "lb_totals_noalloc failed")
 
 
 # ------------------------------------------------------------- wrapper
