@@ -252,14 +252,7 @@ def run_gpu(args, rank, world):
     err = None
     nsteps_done = args.warmup + args.steps + e2e_steps
     if rank == 0 and not args.no_check:
-        import oracle
-        prob, g = lats[0]
-        _, u, _ = g.moments()
-        col = oracle.OracleLB((1, 1, L), prob.tau_s, prob.tau_b, g=prob.g, walls=prob.walls, counter=False)
-        col.step(nsteps_done)
-        ref = col.observe()["u"][0, :, 0, 0]
-        uu = u[0, :, :: max(1, L // 8), :: max(1, L // 8)].cpu().numpy()
-        err = float(np.abs(uu - ref[:, None, None]).max() / np.abs(ref).max())
+        err = channel_error(lats[0][0], lats[0][1], L, nsteps_done)
 
     peak, peak_kind = measured_peaks()
     b_alg = 2 * 19 * BYTES[prec] * V
@@ -267,6 +260,10 @@ def run_gpu(args, rank, world):
     traffic = committed_traffic(prec)
     for _, g in lats:
         g.close()
+    torch.cuda.empty_cache()
+    others = None
+    if rank == 0 and world == 1 and not args.no_per_precision:
+        others = per_precision(L, {p: (10 if p == "f64" else 100) for p in PREC_NAMES if p != prec})
     out = {
         "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True,
@@ -287,7 +284,63 @@ def run_gpu(args, rank, world):
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps},
         "gpu_launches": launches,
         "clocks": clk,
+        "per_precision": others,
     }
+    return out
+
+
+def channel_error(prob, g, L, nsteps):
+    """Channel lattice vs the exactly equivalent 1 x 1 x L FP64 oracle column."""
+    import oracle
+    _, u, _ = g.moments()
+    col = oracle.OracleLB((1, 1, L), prob.tau_s, prob.tau_b, g=prob.g, walls=prob.walls, counter=False)
+    col.step(nsteps)
+    ref = col.observe()["u"][0, :, 0, 0]
+    uu = u[0, :, :: max(1, L // 8), :: max(1, L // 8)].cpu().numpy()
+    return float(np.abs(uu - ref[:, None, None]).max() / np.abs(ref).max())
+
+
+def per_precision(L, steps_for):
+    """The same four-lattice step in the other storage formats: device-timed
+    (CUDA events around the collide launches, as for the headline line),
+    with the channel lattice's error against the FP64 oracle column."""
+    import torch
+    from paper_0707_1299_gb300 import lb
+    peak, peak_kind = measured_peaks()
+    stream = torch.cuda.current_stream()
+    out = {}
+    for prec, steps in steps_for.items():
+        lats = build_lattices(PREC_NAMES[prec], L)
+        warm = 3
+        for _ in range(warm):
+            for _, g in lats:
+                g.step(1)
+        torch.cuda.synchronize()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps * len(lats))]
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for s in range(steps):
+            for k, (_, g) in enumerate(lats):
+                e = ev[s * len(lats) + k]
+                e[0].record(stream)
+                g.step(1)
+                e[1].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        coll = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+        V = L ** 3
+        achieved = 2 * 19 * BYTES[prec] * V / (coll * 1e-3) / 1e9
+        err = channel_error(lats[0][0], lats[0][1], L, warm + steps)
+        out[prec] = {"value": round(4 * V * steps / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS", "steps": steps,
+                     "collide_ms": round(coll, 5), "bytes_per_site": 2 * 19 * BYTES[prec],
+                     "hbm_achieved_gbs": round(achieved, 1), "hbm_frac": round(achieved / peak, 4),
+                     "bound": "alu (FP64 pipe)" if prec == "f64" else "hbm / issue",
+                     "max_rel_velocity_vs_oracle": err, "error_steps": warm + steps}
+        for _, g in lats:
+            g.close()
+        torch.cuda.empty_cache()
     return out
 
 
@@ -363,6 +416,7 @@ def main():
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-per-precision", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 

@@ -183,6 +183,7 @@ lb_status lb_create(lb_ctx** out, const int grid[3], double tau_shear, double ta
     c->g[0] = c->g[1] = c->g[2] = 0.0;
     c->counter = 1;
     c->a_L = INFINITY;
+    c->seed = 0x2545F491u;
     c->scale = c->inv_scale = 1.0f;
     if (precision == LB_F16S) {
         c->scale = 1048576.0f;  // 2^20

@@ -40,34 +40,69 @@ __device__ __forceinline__ bool is_solid(const Geom& g, int z) {
 // df is stored as S and handled in arithmetic type T.  The half-precision
 // formats store df * scale (a power of two) to keep df out of subnormals.
 template <typename S> struct Store;
+// ld/st move the stored number without any scaling: for the half format
+// that is df * scale, and the kernels either work in those scaled units
+// (k_collide) or multiply by 1 / scale themselves.  st takes 32 random
+// bits `rnd`, used only by the 16-bit formats, which round stochastically:
+// a per-step change far below one unit in the last place would otherwise be
+// rounded away the same way every step.
 template <> struct Store<double> {
     using T = double;
-    static __device__ __forceinline__ double ld(const double* p, unsigned i, float) { return __ldg(p + i); }
-    static __device__ __forceinline__ void st(double* p, unsigned i, double v, float) { __stcs(p + i, v); }
+    static constexpr bool kCompensate = false;  // FP64 needs no compensated momentum sum
+    static constexpr bool kScaled = false;
+    static __device__ __forceinline__ double ld(const double* p, unsigned i) { return __ldg(p + i); }
+    static __device__ __forceinline__ void st(double* p, unsigned i, double v, unsigned) { __stcs(p + i, v); }
 };
 template <> struct Store<float> {
     using T = float;
-    static __device__ __forceinline__ float ld(const float* p, unsigned i, float) { return __ldg(p + i); }
-    static __device__ __forceinline__ void st(float* p, unsigned i, float v, float) { __stcs(p + i, v); }
+    static constexpr bool kCompensate = true;
+    static constexpr bool kScaled = false;
+    static __device__ __forceinline__ float ld(const float* p, unsigned i) { return __ldg(p + i); }
+    static __device__ __forceinline__ void st(float* p, unsigned i, float v, unsigned) { __stcs(p + i, v); }
 };
 template <> struct Store<__half> {
     using T = float;
-    static __device__ __forceinline__ float ld(const __half* p, unsigned i, float inv_scale) {
-        return __half2float(__ldg(p + i)) * inv_scale;
-    }
-    static __device__ __forceinline__ void st(__half* p, unsigned i, float v, float scale) {
-        p[i] = __float2half_rn(v * scale);
+    static constexpr bool kCompensate = false;  // storage rounding dominates
+    static constexpr bool kScaled = true;
+    static __device__ __forceinline__ float ld(const __half* p, unsigned i) { return __half2float(__ldg(p + i)); }
+    // Stochastic rounding to half: add 13 random bits below the 10-bit half
+    // mantissa to the float's magnitude, then truncate.  Values beyond the
+    // half range saturate to +-65504.
+    static __device__ __forceinline__ void st(__half* p, unsigned i, float v, unsigned rnd) {
+        const unsigned b = __float_as_uint(v) + (rnd >> 19);
+        p[i] = __float2half_rz(__uint_as_float(b));
     }
 };
 template <> struct Store<__nv_bfloat16> {
     using T = float;
-    static __device__ __forceinline__ float ld(const __nv_bfloat16* p, unsigned i, float inv_scale) {
-        return __bfloat162float(__ldg(p + i)) * inv_scale;
+    static constexpr bool kCompensate = false;
+    static constexpr bool kScaled = false;  // bfloat16 has the float exponent range
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p, unsigned i) {
+        return __bfloat162float(__ldg(p + i));
     }
-    static __device__ __forceinline__ void st(__nv_bfloat16* p, unsigned i, float v, float scale) {
-        p[i] = __float2bfloat16_rn(v * scale);
+    // Stochastic rounding to bfloat16: add 16 random bits to the dropped half
+    // of the float, keep the upper half.
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, unsigned i, float v, unsigned rnd) {
+        const unsigned b = __float_as_uint(v) + (rnd >> 16);
+        p[i] = __ushort_as_bfloat16((unsigned short)(b >> 16));
     }
 };
+
+// Counter-based random bits for stochastic rounding: a hash of the site and
+// the step seeds a linear congruential sequence, one draw per population.
+__device__ __forceinline__ unsigned rng_seed(unsigned site, unsigned step_seed) {
+    unsigned x = site * 0x9E3779B9u ^ step_seed;
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+__device__ __forceinline__ unsigned rng_next(unsigned& x) {
+    x = x * 1664525u + 1013904223u;
+    return x;
+}
 
 // ------------------------------------------------------------ pull stream
 // The 19 population arrays, one pointer each (kernel parameter space), so
@@ -106,46 +141,53 @@ __device__ __forceinline__ Nbr neighbours(const Geom& g, int x, int y, int z) {
 // df_i(x) = df*_i(x - c_i); where x - c_i is a solid node the population
 // bounces back: df_i(x) = df*_ibar(x).
 template <typename S, bool WALLS>
-__device__ __forceinline__ void pull19(const Pops<S>& src, const Nbr& n, float inv_scale,
-                                       typename Store<S>::T f[NQ]) {
+__device__ __forceinline__ void pull19(const Pops<S>& src, const Nbr& n, typename Store<S>::T f[NQ]) {
     using St = Store<S>;
     const unsigned own = n.c + n.x;
     const unsigned ym = n.c + n.dym, yp = n.c + n.dyp, zm = n.c + n.dzm, zp = n.c + n.dzp;
-    f[0] = St::ld(src.p[0], own, inv_scale);
-    f[1] = St::ld(src.p[1], n.c + n.xm, inv_scale);
-    f[2] = St::ld(src.p[2], n.c + n.xp, inv_scale);
-    f[3] = St::ld(src.p[3], ym + n.x, inv_scale);
-    f[4] = St::ld(src.p[4], yp + n.x, inv_scale);
-    f[7] = St::ld(src.p[7], ym + n.xm, inv_scale);
-    f[8] = St::ld(src.p[8], yp + n.xp, inv_scale);
-    f[9] = St::ld(src.p[9], yp + n.xm, inv_scale);
-    f[10] = St::ld(src.p[10], ym + n.xp, inv_scale);
+    f[0] = St::ld(src.p[0], own);
+    f[1] = St::ld(src.p[1], n.c + n.xm);
+    f[2] = St::ld(src.p[2], n.c + n.xp);
+    f[3] = St::ld(src.p[3], ym + n.x);
+    f[4] = St::ld(src.p[4], yp + n.x);
+    f[7] = St::ld(src.p[7], ym + n.xm);
+    f[8] = St::ld(src.p[8], yp + n.xp);
+    f[9] = St::ld(src.p[9], yp + n.xm);
+    f[10] = St::ld(src.p[10], ym + n.xp);
     if (!WALLS || !n.solid_zm) {
-        f[5] = St::ld(src.p[5], zm + n.x, inv_scale);
-        f[11] = St::ld(src.p[11], zm + n.xm, inv_scale);
-        f[14] = St::ld(src.p[14], zm + n.xp, inv_scale);
-        f[15] = St::ld(src.p[15], zm + n.dym + n.x, inv_scale);
-        f[18] = St::ld(src.p[18], zm + n.dyp + n.x, inv_scale);
+        f[5] = St::ld(src.p[5], zm + n.x);
+        f[11] = St::ld(src.p[11], zm + n.xm);
+        f[14] = St::ld(src.p[14], zm + n.xp);
+        f[15] = St::ld(src.p[15], zm + n.dym + n.x);
+        f[18] = St::ld(src.p[18], zm + n.dyp + n.x);
     } else {
-        f[5] = St::ld(src.p[6], own, inv_scale);
-        f[11] = St::ld(src.p[12], own, inv_scale);
-        f[14] = St::ld(src.p[13], own, inv_scale);
-        f[15] = St::ld(src.p[16], own, inv_scale);
-        f[18] = St::ld(src.p[17], own, inv_scale);
+        f[5] = St::ld(src.p[6], own);
+        f[11] = St::ld(src.p[12], own);
+        f[14] = St::ld(src.p[13], own);
+        f[15] = St::ld(src.p[16], own);
+        f[18] = St::ld(src.p[17], own);
     }
     if (!WALLS || !n.solid_zp) {
-        f[6] = St::ld(src.p[6], zp + n.x, inv_scale);
-        f[12] = St::ld(src.p[12], zp + n.xp, inv_scale);
-        f[13] = St::ld(src.p[13], zp + n.xm, inv_scale);
-        f[16] = St::ld(src.p[16], zp + n.dyp + n.x, inv_scale);
-        f[17] = St::ld(src.p[17], zp + n.dym + n.x, inv_scale);
+        f[6] = St::ld(src.p[6], zp + n.x);
+        f[12] = St::ld(src.p[12], zp + n.xp);
+        f[13] = St::ld(src.p[13], zp + n.xm);
+        f[16] = St::ld(src.p[16], zp + n.dyp + n.x);
+        f[17] = St::ld(src.p[17], zp + n.dym + n.x);
     } else {
-        f[6] = St::ld(src.p[5], own, inv_scale);
-        f[12] = St::ld(src.p[11], own, inv_scale);
-        f[13] = St::ld(src.p[14], own, inv_scale);
-        f[16] = St::ld(src.p[15], own, inv_scale);
-        f[17] = St::ld(src.p[18], own, inv_scale);
+        f[6] = St::ld(src.p[5], own);
+        f[12] = St::ld(src.p[11], own);
+        f[13] = St::ld(src.p[14], own);
+        f[16] = St::ld(src.p[15], own);
+        f[17] = St::ld(src.p[18], own);
     }
+}
+
+// Pulled populations in stored units -> df (only the half format is scaled).
+template <typename S>
+__device__ __forceinline__ void unscale19(typename Store<S>::T f[NQ], float inv_scale) {
+    if (Store<S>::kScaled)
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) f[i] *= inv_scale;
 }
 
 // ------------------------------------------------------------- moments
@@ -168,18 +210,17 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // j = sum df c would otherwise feed back into the populations every step:
 // when j changes by a nearly constant increment (a uniform body force) the
 // rounded increment is the same each step and the error grows linearly.
-template <typename T> struct MomentumSum;
-template <> struct MomentumSum<double> {
-    static __device__ __forceinline__ void eval(const double f[NQ], Moments<double>& m) {
-        const double e78 = f[7] - f[8], e910 = f[9] - f[10], e1112 = f[11] - f[12], e1314 = f[13] - f[14];
-        const double e1516 = f[15] - f[16], e1718 = f[17] - f[18];
+template <typename T, bool COMP> struct MomentumSum {
+    static __device__ __forceinline__ void eval(const T f[NQ], Moments<T>& m) {
+        const T e78 = f[7] - f[8], e910 = f[9] - f[10], e1112 = f[11] - f[12], e1314 = f[13] - f[14];
+        const T e1516 = f[15] - f[16], e1718 = f[17] - f[18];
         m.jx = (f[1] - f[2]) + e78 + e910 + e1112 + e1314;
         m.jy = (f[3] - f[4]) + e78 - e910 + e1516 + e1718;
         m.jz = (f[5] - f[6]) + e1112 - e1314 + e1516 - e1718;
-        m.jx_lo = m.jy_lo = m.jz_lo = 0.0;
+        m.jx_lo = m.jy_lo = m.jz_lo = T(0);
     }
 };
-template <> struct MomentumSum<float> {
+template <> struct MomentumSum<float, true> {
     static __device__ __forceinline__ void eval(const float f[NQ], Moments<float>& m) {
         float d12, d34, d56, d78, d910, d1112, d1314, d1516, d1718;
         float r12, r34, r56, r78, r910, r1112, r1314, r1516, r1718;
@@ -214,14 +255,14 @@ template <> struct MomentumSum<float> {
     }
 };
 
-template <typename T>
+template <typename T, bool COMP>
 __device__ __forceinline__ Moments<T> moments19(const T f[NQ]) {
     Moments<T> m;
     const T a12 = f[1] + f[2], a34 = f[3] + f[4], a56 = f[5] + f[6];
     const T d78 = f[7] + f[8], d910 = f[9] + f[10], d1112 = f[11] + f[12], d1314 = f[13] + f[14];
     const T d1516 = f[15] + f[16], d1718 = f[17] + f[18];
     m.drho = f[0] + a12 + a34 + a56 + d78 + d910 + d1112 + d1314 + d1516 + d1718;
-    MomentumSum<T>::eval(f, m);
+    MomentumSum<T, COMP>::eval(f, m);
     m.pxx = a12 + d78 + d910 + d1112 + d1314;
     m.pyy = a34 + d78 + d910 + d1516 + d1718;
     m.pzz = a56 + d1112 + d1314 + d1516 + d1718;
@@ -269,22 +310,29 @@ template <> struct Wts<double> {
 // last through fused multiply-adds, so it is rounded once; the force term
 // 3 w_i F.c_i is added to the small terms first, so a force much smaller
 // than j is not lost to the rounding of j + F.
-template <typename T>
-__device__ __forceinline__ void collide19(const T f[NQ], T Fx, T Fy, T Fz, const Coef<T>& k, T out[NQ]) {
+// With SCALED, f and F are in units of 1/scale (the half storage format)
+// and `is` = 1/scale: every term is linear in (f, F) except rho = 1 + drho,
+// rho vv and vF + Fv, which take one factor `is` each; the outputs come out
+// in the same scaled units.
+template <typename T, bool COMP, bool SCALED = false>
+__device__ __forceinline__ void collide19(const T f[NQ], T Fx, T Fy, T Fz, const Coef<T>& k, T out[NQ],
+                                          T is = T(1)) {
     using W = Wts<T>;
-    const Moments<T> m = moments19(f);
+    const Moments<T> m = moments19<T, COMP>(f);
     const T third = T(1) / T(3);
-    const T rho = T(1) + m.drho;
+    const T rho = T(1) + (SCALED ? m.drho * is : m.drho);
     const T irho = T(1) / rho;
     const T vx = (m.jx + T(0.5) * Fx) * irho;
     const T vy = (m.jy + T(0.5) * Fy) * irho;
     const T vz = (m.jz + T(0.5) * Fz) * irho;
+    const T rs = SCALED ? rho * is : rho;
+    const T Fxs = SCALED ? Fx * is : Fx, Fys = SCALED ? Fy * is : Fy, Fzs = SCALED ? Fz * is : Fz;
     // S = P - (drho/3) 1 ; X = S - rho vv ; Y = vF + Fv
     const T sxx = m.pxx - third * m.drho, syy = m.pyy - third * m.drho, szz = m.pzz - third * m.drho;
-    const T xxx = sxx - rho * vx * vx, xyy = syy - rho * vy * vy, xzz = szz - rho * vz * vz;
-    const T xxy = m.pxy - rho * vx * vy, xxz = m.pxz - rho * vx * vz, xyz = m.pyz - rho * vy * vz;
-    const T yxx = T(2) * vx * Fx, yyy = T(2) * vy * Fy, yzz = T(2) * vz * Fz;
-    const T yxy = vx * Fy + Fx * vy, yxz = vx * Fz + Fx * vz, yyz = vy * Fz + Fy * vz;
+    const T xxx = sxx - rs * vx * vx, xyy = syy - rs * vy * vy, xzz = szz - rs * vz * vz;
+    const T xxy = m.pxy - rs * vx * vy, xxz = m.pxz - rs * vx * vz, xyz = m.pyz - rs * vy * vz;
+    const T yxx = T(2) * vx * Fxs, yyy = T(2) * vy * Fys, yzz = T(2) * vz * Fzs;
+    const T yxy = vx * Fys + Fxs * vy, yxz = vx * Fzs + Fxs * vz, yyz = vy * Fzs + Fys * vz;
     const T trX = xxx + xyy + xzz, trY = yxx + yyy + yzz;
     const T dev_tr = third * (trX - k.tau_s * trY);
     const T iso = third * k.om_b * (trX - k.tau_b * trY);
@@ -335,9 +383,9 @@ __device__ __forceinline__ void collide19(const T f[NQ], T Fx, T Fy, T Fz, const
 }
 
 // drho = rho - 1 and v = (j + F/2) / rho, Eq. (macrovariables2).
-template <typename T>
+template <typename T, bool COMP = false>
 __device__ __forceinline__ void macro19(const T f[NQ], T Fx, T Fy, T Fz, T& drho, T& vx, T& vy, T& vz) {
-    const Moments<T> m = moments19(f);
+    const Moments<T> m = moments19<T, COMP>(f);
     drho = m.drho;
     const T rho = T(1) + m.drho;
     const T irho = T(1) / rho;

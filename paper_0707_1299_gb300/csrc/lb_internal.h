@@ -45,6 +45,7 @@ struct lb_ctx {
     size_t stage_bytes;
 
     long long launches;       // kernels launched so far
+    unsigned seed;            // seed of the stochastic rounding of the 16-bit formats
 
     std::string err;
 };

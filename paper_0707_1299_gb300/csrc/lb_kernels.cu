@@ -71,47 +71,74 @@ static dim3 site_grid(const Geom& g) {
 }
 
 // ------------------------------------------------------------ k_collide
-template <typename S, bool WALLS>
-__global__ void __launch_bounds__(CS_THREADS, 8)
+// NY consecutive y rows per thread (all loads of the NY sites issued
+// first).  The half format is handled in its scaled units throughout.
+template <typename S, bool WALLS, int NY>
+__global__ void __launch_bounds__(CS_THREADS, (NY == 1 ? 8 : 4))
 k_collide(const Pops<S> src, const Pops<S> dst, typename Store<S>::T* __restrict__ floc,
           unsigned char* __restrict__ flags, Geom g, Coef<typename Store<S>::T> k,
-          UForce<typename Store<S>::T> fu, float scale, float inv_scale) {
+          UForce<typename Store<S>::T> fu, float scale, float inv_scale, unsigned seed) {
     using T = typename Store<S>::T;
-    const int y = blockIdx.y * CS_WARPS + threadIdx.y;
-    if (y >= g.ny) return;  // uniform per warp
+    constexpr bool SC = Store<S>::kScaled;
+    const int y0 = (blockIdx.y * CS_WARPS + threadIdx.y) * NY;
+    if (y0 >= g.ny) return;  // uniform per warp
     const int z = blockIdx.z, lane = threadIdx.x;
     const int x = blockIdx.x * TILE_X + lane;
-    const unsigned tile = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.ntx + blockIdx.x;
-    const unsigned char fl = flags[tile];
     const unsigned V = (unsigned)g.V;
+    unsigned tile[NY];
+    unsigned char fl[NY];
+#pragma unroll
+    for (int r = 0; r < NY; ++r) {
+        tile[r] = ((unsigned)z * (unsigned)g.ny + (unsigned)(y0 + r)) * (unsigned)g.ntx + blockIdx.x;
+        fl[r] = (y0 + r < g.ny) ? flags[tile[r]] : (unsigned char)0;
+    }
 
     if (x < g.nx) {
-        const Nbr n = neighbours(g, x, y, z);
-        const unsigned site = n.c + n.x;
         if (WALLS && is_solid(g, z)) {
 #pragma unroll
-            for (int i = 0; i < NQ; ++i) Store<S>::st(dst.p[i], site, T(0), scale);
-        } else {
-            T Fx = fu.F[0], Fy = fu.F[1], Fz = fu.F[2];
-            if (fl) {
-                Fx += floc[site];
-                Fy += floc[V + site];
-                Fz += floc[2 * V + site];
-                floc[site] = T(0);
-                floc[V + site] = T(0);
-                floc[2 * V + site] = T(0);
-            }
-            T f[NQ], o[NQ];
-            pull19<S, WALLS>(src, n, inv_scale, f);
-            collide19<T>(f, Fx, Fy, Fz, k, o);
+            for (int r = 0; r < NY; ++r) {
+                if (y0 + r >= g.ny) break;
+                const unsigned site = (unsigned)z * g.plane + (unsigned)(y0 + r) * (unsigned)g.nx + (unsigned)x;
 #pragma unroll
-            for (int i = 0; i < NQ; ++i) Store<S>::st(dst.p[i], site, o[i], scale);
+                for (int i = 0; i < NQ; ++i) Store<S>::st(dst.p[i], site, T(0), 0u);
+            }
+        } else {
+            T f[NY][NQ];
+            Nbr n[NY];
+#pragma unroll
+            for (int r = 0; r < NY; ++r)  // every load of the NY sites first
+                if (y0 + r < g.ny) {
+                    n[r] = neighbours(g, x, y0 + r, z);
+                    pull19<S, WALLS>(src, n[r], f[r]);
+                }
+#pragma unroll
+            for (int r = 0; r < NY; ++r) {
+                if (y0 + r >= g.ny) break;
+                const unsigned site = n[r].c + n[r].x;
+                T Fx = fu.F[0], Fy = fu.F[1], Fz = fu.F[2];
+                if (fl[r]) {
+                    const T s = SC ? (T)scale : T(1);
+                    Fx += floc[site] * s;
+                    Fy += floc[V + site] * s;
+                    Fz += floc[2 * V + site] * s;
+                    floc[site] = T(0);
+                    floc[V + site] = T(0);
+                    floc[2 * V + site] = T(0);
+                }
+                T o[NQ];
+                collide19<T, Store<S>::kCompensate, SC>(f[r], Fx, Fy, Fz, k, o, (T)inv_scale);
+                unsigned rn = rng_seed(site, seed);
+#pragma unroll
+                for (int i = 0; i < NQ; ++i) Store<S>::st(dst.p[i], site, o[i], rng_next(rn));
+            }
         }
     }
-    if (fl) {
-        __syncwarp();
-        if (lane == 0) flags[tile] = 0;
-    }
+#pragma unroll
+    for (int r = 0; r < NY; ++r)
+        if (fl[r]) {
+            __syncwarp();
+            if (lane == 0) flags[tile[r]] = 0;
+        }
 }
 
 // ------------------------------------------------------------- k_spread
@@ -177,10 +204,11 @@ k_gather(const Pops<S> src, const typename Store<S>::T* __restrict__ floc, Geom 
         const Nbr nb = neighbours(g, x, y, z);
         const unsigned site = nb.c + nb.x;
         T f[NQ];
-        pull19<S, WALLS>(src, nb, inv_scale, f);
+        pull19<S, WALLS>(src, nb, f);
+        unscale19<S>(f, inv_scale);
         const T Fx = fu.F[0] + floc[site], Fy = fu.F[1] + floc[V + site], Fz = fu.F[2] + floc[2 * V + site];
         T drho, vx, vy, vz;
-        macro19<T>(f, Fx, Fy, Fz, drho, vx, vy, vz);
+        macro19<T, Store<S>::kCompensate>(f, Fx, Fy, Fz, drho, vx, vy, vz);
         acc[0] += w * vx;
         acc[1] += w * vy;
         acc[2] += w * vz;
@@ -233,10 +261,11 @@ k_moments(const Pops<S> src, const typename Store<S>::T* __restrict__ floc, Geom
         double r = 1.0, u[3] = {0.0, 0.0, 0.0};
         if (!(WALLS && is_solid(g, z))) {
             T f[NQ];
-            pull19<S, WALLS>(src, nb, inv_scale, f);
+            pull19<S, WALLS>(src, nb, f);
+            unscale19<S>(f, inv_scale);
             const T Fx = fu.F[0] + floc[site], Fy = fu.F[1] + floc[V + site], Fz = fu.F[2] + floc[2 * V + site];
             T drho, vx, vy, vz;
-            macro19<T>(f, Fx, Fy, Fz, drho, vx, vy, vz);
+            macro19<T, Store<S>::kCompensate>(f, Fx, Fy, Fz, drho, vx, vy, vz);
             r = 1.0 + (double)drho;
             u[0] = (double)vx;
             u[1] = (double)vy;
@@ -377,13 +406,16 @@ __global__ void k_set_positions(const double* __restrict__ in, int npts, Geom g,
 template <typename S>
 __global__ void k_convert_out(const S* __restrict__ src, long long count, float inv_scale, double* __restrict__ out) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
-        out[i] = (double)Store<S>::ld(src, i, inv_scale);
+        out[i] = (double)Store<S>::ld(src, (unsigned)i) * (double)inv_scale;
 }
 
 template <typename S>
-__global__ void k_convert_in(const double* __restrict__ in, long long count, float scale, S* __restrict__ dst) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
-        Store<S>::st(dst, i, (typename Store<S>::T)in[i], scale);
+__global__ void k_convert_in(const double* __restrict__ in, long long count, float scale, S* __restrict__ dst,
+                             unsigned seed) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+        unsigned r = rng_seed((unsigned)i, seed);
+        Store<S>::st(dst, (unsigned)i, (typename Store<S>::T)(in[i] * (double)scale), rng_next(r));
+    }
 }
 
 // -------------------------------------------------------------- a_L sum
@@ -451,13 +483,22 @@ static cudaError_t collide_t(lb_ctx* c) {
     k.om_s = (T)(1.0 / (c->tau_s + 0.5));
     k.om_b = (T)(1.0 / (c->tau_b + 0.5));
     const Pops<S> src = pops<S>(c->f[c->cur], c->geom.V), dst = pops<S>(c->f[1 - c->cur], c->geom.V);
-    const UForce<T> fu = uniform_force<T>(c);
+    UForce<T> fu = uniform_force<T>(c);
+    if (Store<S>::kScaled)
+        for (int a = 0; a < 3; ++a) fu.F[a] = (T)((double)fu.F[a] * (double)c->scale);
+    // one site per thread for every format: two rows per thread (more loads
+    // in flight for the 2-byte formats) measured slower on GB300 (fewer
+    // resident warps at 80-92 registers)
+    constexpr int NY = 1;
+    const dim3 grid((unsigned)c->geom.ntx, (unsigned)((c->geom.ny + CS_WARPS * NY - 1) / (CS_WARPS * NY)),
+                    (unsigned)c->geom.nz);
     if (has_walls(c))
-        k_collide<S, true><<<site_grid(c->geom), site_block(), 0, c->stream>>>(
-            src, dst, (T*)c->floc, c->flags, c->geom, k, fu, c->scale, c->inv_scale);
+        k_collide<S, true, NY><<<grid, site_block(), 0, c->stream>>>(src, dst, (T*)c->floc, c->flags, c->geom, k, fu,
+                                                                   c->scale, c->inv_scale, c->seed);
     else
-        k_collide<S, false><<<site_grid(c->geom), site_block(), 0, c->stream>>>(
-            src, dst, (T*)c->floc, c->flags, c->geom, k, fu, c->scale, c->inv_scale);
+        k_collide<S, false, NY><<<grid, site_block(), 0, c->stream>>>(src, dst, (T*)c->floc, c->flags, c->geom, k, fu,
+                                                                    c->scale, c->inv_scale, c->seed);
+    c->seed = c->seed * 747796405u + 2891336453u;  // next step's rounding seed
     c->launches++;
     return cudaGetLastError();
 }
@@ -584,7 +625,7 @@ static cudaError_t convert_t(lb_ctx* c, double* out, const double* in) {
     if (out)
         k_convert_out<S><<<blocks, 256, 0, c->stream>>>((const S*)c->f[c->cur], count, c->inv_scale, out);
     else
-        k_convert_in<S><<<blocks, 256, 0, c->stream>>>(in, count, c->scale, (S*)c->f[c->cur]);
+        k_convert_in<S><<<blocks, 256, 0, c->stream>>>(in, count, c->scale, (S*)c->f[c->cur], c->seed);
     c->launches++;
     return cudaGetLastError();
 }

@@ -69,9 +69,10 @@ k_totals_partials(const lbk::Pops<S> src, lbk::Geom g, lbk::UForce<typename lbk:
         if (x >= g.nx || (WALLS && lbk::is_solid(g, z))) continue;
         const lbk::Nbr nb = lbk::neighbours(g, x, y, z);
         T f[lbk::NQ];
-        lbk::pull19<S, WALLS>(src, nb, inv_scale, f);
+        lbk::pull19<S, WALLS>(src, nb, f);
+        lbk::unscale19<S>(f, inv_scale);
         T drho, vx, vy, vz;
-        lbk::macro19<T>(f, fu.F[0], fu.F[1], fu.F[2], drho, vx, vy, vz);
+        lbk::macro19<T, lbk::Store<S>::kCompensate>(f, fu.F[0], fu.F[1], fu.F[2], drho, vx, vy, vz);
         const double rho = 1.0 + (double)drho;
         acc[0] += rho;
         acc[1] += rho * (double)vx;

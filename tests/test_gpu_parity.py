@@ -79,13 +79,16 @@ def test_one_step_populations(prec, grid, walls, pts, ts, tb):
     g.close()
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+PREC_ID = {"f64": 0, "f32": 1, "f16s": 2, "bf16s": 3}
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16s", "bf16s"])
 def test_stokeslet_32_1000_steps(prec):
     # The 32^3 Stokeslet workload, 1000 steps, against the oracle within
     # the benchmark spec's tolerances (FP64 1e-12, FP32 1e-5).
     lb = _lb()
     prob = W.stokeslet_32()
-    g = gpu_lattice(prob, lb.LB_F64 if prec == "f64" else lb.LB_F32)
+    g = gpu_lattice(prob, PREC_ID[prec])
     g.step(prob.steps)
     rho, u, tot = g.moments()
     o = oracle_lattice(prob)
@@ -93,7 +96,8 @@ def test_stokeslet_32_1000_steps(prec):
     ref = o.observe()
     err = rel_err(u.cpu().numpy(), ref["u"])
     assert err < TOL[prec], err
-    assert rel_err(rho.cpu().numpy() - 1.0, ref["rho"] - 1.0) < (1e-10 if prec == "f64" else 1e-3)
+    if prec in ("f64", "f32"):
+        assert rel_err(rho.cpu().numpy() - 1.0, ref["rho"] - 1.0) < (1e-10 if prec == "f64" else 1e-3)
     t = tot.cpu().numpy()
     assert abs(t[0] - 32 ** 3) < (1e-9 if prec == "f64" else 1e-3)
     # total momentum stays zero under the counter-force: within the
@@ -123,13 +127,14 @@ def test_multipole_recipe_reduced(prec):
         g.close()
 
 
-def test_channel_256_full_size():
-    # The wall-bounded channel at its full 256^3 size, FP32, 2000 steps, as
-    # the benchmark runs it.  The flow is invariant in x and y, so a
+@pytest.mark.parametrize("prec", ["f32", "f16s", "bf16s"])
+def test_channel_256_full_size(prec):
+    # The wall-bounded channel at its full 256^3 size, 2000 steps, as the
+    # benchmark runs it.  The flow is invariant in x and y, so a
     # 1 x 1 x 256 oracle lattice is exactly equivalent.
     lb = _lb()
     prob = W.channel_256()[0]
-    g = gpu_lattice(prob, lb.LB_F32)
+    g = gpu_lattice(prob, PREC_ID[prec])
     g.step(prob.steps)
     _, u, _ = g.moments()
     col = W.Problem("col", (1, 1, 256), 0.5, 0.5, g=prob.g, walls=prob.walls, counter=False)
@@ -138,9 +143,9 @@ def test_channel_256_full_size():
     ref = o.observe()["u"][:, :, 0, 0]
     uu = u.cpu().numpy()
     for (y, x) in [(0, 0), (17, 200), (255, 255), (128, 3)]:
-        assert rel_err(uu[:, :, y, x], ref) < TOL["f32"]
-    # no cross-flow beyond FP32 rounding
-    assert np.abs(uu[1:]).max() < TOL["f32"] * np.abs(ref).max()
+        assert rel_err(uu[:, :, y, x], ref) < TOL[prec]
+    # no cross-flow beyond rounding
+    assert np.abs(uu[1:]).max() < TOL[prec] * np.abs(ref).max()
     g.close()
 
 
@@ -174,7 +179,7 @@ def test_multipoles_256_full_size_light_cone(which):
     g.close()
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16s", "bf16s"])
 def test_colloids_reduced(prec):
     # The colloid recipe (uniform random colloids at the 1e5-in-512^3
     # number density, force 1e-6, radius 0.117) at 40^3 for 300 steps:
@@ -184,7 +189,7 @@ def test_colloids_reduced(prec):
     n = int(round(1e5 * (L / 512) ** 3))
     aL = oracle.aL_along((L, L, L), [L / 2] * 3, [0, 0, 1])
     prob = W.colloids(L=L, n=n, steps=300, a_L=aL)
-    g = gpu_lattice(prob, lb.LB_F64 if prec == "f64" else lb.LB_F32)
+    g = gpu_lattice(prob, PREC_ID[prec])
     p0, _ = g.particles()
     p0 = p0.cpu().numpy()
     g.step(prob.steps)
