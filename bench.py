@@ -264,6 +264,9 @@ def run_gpu(args, rank, world):
     others = None
     if rank == 0 and world == 1 and not args.no_per_precision:
         others = per_precision(L, {p: (10 if p == "f64" else 100) for p in PREC_NAMES if p != prec})
+    batched = None
+    if rank == 0 and world == 1 and not args.no_batched:
+        batched = batched_replicas()
     out = {
         "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True,
@@ -285,6 +288,7 @@ def run_gpu(args, rank, world):
         "gpu_launches": launches,
         "clocks": clk,
         "per_precision": others,
+        "batched": batched,
     }
     return out
 
@@ -342,6 +346,60 @@ def per_precision(L, steps_for):
             g.close()
         torch.cuda.empty_cache()
     return out
+
+
+def batched_replicas(steps=50, seq_steps=10):
+    """64 independent sedimentation boxes of uneven sizes (48^3-128^3, 100-2000
+    colloids each, FP32) advanced by one batch (a launch per phase over all
+    boxes, graph-replayed steps, tuned persistent grid) against the same boxes
+    stepped one after another with lb_step."""
+    import torch
+    from paper_0707_1299_gb300 import lb, workloads as W
+    probs = W.replicas()
+    lats = []
+    for p in probs:
+        g = lb.Lattice(p.grid, p.tau_s, p.tau_b, lb.LB_F32)
+        g.set_colloid_aL(lb.lb_compute_aL(p.grid, [p.grid[0] / 2] * 3, [0, 0, 1]))
+        for ps in p.points:
+            g.add_point_forces(ps.kind, ps.pos, ps.F, ps.param)
+        lats.append(g)
+    sites = sum(g.V for g in lats)
+    stream = torch.cuda.current_stream()
+    batch = lb.lb_batch_create([g.ctx for g in lats])
+    blocks = lb.lb_batch_tune(batch)
+    lb.lb_batch_step(batch, 4)
+    torch.cuda.synchronize()
+    l0 = lb.lb_batch_info(batch)["launches"]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    lb.lb_batch_step(batch, steps)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = t0.elapsed_time(t1) / steps
+    launches = lb.lb_batch_info(batch)["launches"] - l0
+    lb.lb_batch_destroy(batch)
+    for g in lats:
+        g.step(1)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(seq_steps):
+        for g in lats:
+            g.step(1)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms_s = t0.elapsed_time(t1) / seq_steps
+    peak, _ = measured_peaks()
+    npts = sum(g.num_points() for g in lats)
+    for g in lats:
+        g.close()
+    torch.cuda.empty_cache()
+    return {"replicas": len(probs), "sites_per_step": sites, "colloids": npts, "precision": "f32",
+            "value": round(sites / (ms_b * 1e-3) / 1e6, 1), "unit": "MLUPS", "ms_per_step": round(ms_b, 4),
+            "hbm_frac_of_step": round(152 * sites / (ms_b * 1e-3) / 1e9 / peak, 4),
+            "launches_per_step": launches / steps, "collide_blocks": blocks, "steps": steps,
+            "sequential_lb_step": {"value": round(sites / (ms_s * 1e-3) / 1e6, 1), "ms_per_step": round(ms_s, 4),
+                                   "steps": seq_steps}}
 
 
 # ---------------------------------------------------------- oracle (CPU)
@@ -417,6 +475,7 @@ def main():
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-precision", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 

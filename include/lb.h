@@ -178,6 +178,43 @@ lb_status lb_synchronize(lb_ctx *ctx);
  * the current device (allocates temporary device memory). */
 lb_status lb_compute_aL(const int grid[3], const double R[3], const double dir[3], double *a_L);
 
+/* ------------------------------------------------------------------------
+ * Batches: independent lattices (replicas of uneven sizes, e.g. many small
+ * sedimentation boxes) advanced together.  Each phase of a time step
+ * (spreading, colloid update, collide + stream) is one launch over all
+ * members -- the collide + stream phase walks one work list of 4 x 32-site
+ * tiles over every member, in a grid shape picked by lb_batch_tune -- and
+ * two steps are replayed
+ * from a CUDA graph.  The method per member is exactly that of lb_step.
+ * --------------------------------------------------------------------- */
+typedef struct lb_batch lb_batch;
+
+/* Group n contexts (same device and precision) into a batch.  The batch
+ * snapshots each member's configuration (points, forces, walls, body
+ * force, relaxation times, a_L); the members keep their memory and every
+ * per-context call (lb_moments, lb_particles, lb_velocity_at, ...) still
+ * works between batch steps.  Reconfiguring or stepping a member on its own
+ * makes the next lb_batch_step fail with LB_ERR_STATE: recreate the batch.
+ * The batch orders its work after `stream` and every member's stream and
+ * makes them wait for it.  Allocates a private stream and small tables. */
+lb_status lb_batch_create(lb_batch **out, int n, lb_ctx *const *ctxs, void *stream);
+void lb_batch_destroy(lb_batch *batch);
+const char *lb_batch_last_error(const lb_batch *batch);
+
+/* Time the collide kernel of this batch for several grid sizes (persistent
+ * grids of 2 to 16 blocks of 128 threads per SM, and one block per work
+ * item), keep the fastest, report its block count in *blocks (may be NULL).  Leaves every member's state unchanged (it clears
+ * a spread force field, which the next step spreads again). */
+lb_status lb_batch_tune(lb_batch *batch, int *blocks);
+
+/* Advance every member nsteps >= 0 time steps (Sec. II-IV, as lb_step). */
+lb_status lb_batch_step(lb_batch *batch, int nsteps);
+
+/* Sites and points over all members, the collide grid size and the number
+ * of kernels launched by the batch so far (any pointer may be NULL). */
+lb_status lb_batch_info(const lb_batch *batch, long long *sites, long long *points, int *blocks,
+                        long long *launches);
+
 /* Totals {sum rho, sum rho u} over the fluid sites of a population array
  * that the caller owns, computed without allocating any device memory.
  * The paper has no counterpart to this call: it exists for callers that

@@ -1,0 +1,563 @@
+// lb_batch.cu -- many independent lattices (replicas of uneven sizes)
+// advanced together: every phase of a time step is one launch over all
+// replicas, the collide+stream phase a persistent kernel that walks a work
+// list of 4-tile groups spanning every replica, and a CUDA graph replays the
+// step so a short lattice costs no launch overhead.  The launch shape of
+// the persistent kernel is picked by timing candidates on the batch itself.
+//
+// The method per replica is exactly that of lb_step (same device helpers:
+// Sec. II collision, Sec. III spreading, Sec. IV colloid update).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/lb.h"
+#include "lb_internal.h"
+
+namespace {
+
+using namespace lbk;
+
+constexpr int BW = 4;  // warps (tiles) per work item of the collide kernel
+
+// One replica as the batched kernels see it.
+struct Entry {
+    void* pop[2];              // population buffers: index = parity ^ cur0
+    void* floc;
+    unsigned char* flags;
+    double* pos;
+    double* force;
+    double* radius;
+    int* mobile;
+    Geom g;
+    int npts;
+    int cur0;                  // buffer holding the state when the batch step starts
+    double coef[4];            // tau_s, tau_b, om_s, om_b
+    double uf[3];              // uniform force density on fluid sites (unscaled)
+    float coef_f[4];           // the same in float, for the float-arithmetic formats
+    float ufs_f[3];            // uniform force in the stored units (scaled for half), float
+    double inv_6pi_eta, inv_aL;
+    float scale, inv_scale;
+};
+
+struct Work {
+    long long group_begin;     // first collide work item of the replica
+    int groups_x, groups_y;    // ntx, ceil(ny / BW)
+    long long pt_begin;        // first point of the replica in the batch order
+};
+
+__device__ __forceinline__ int find_entry(const long long* __restrict__ begin, int n, long long w) {
+    int lo = 0, hi = n - 1;  // last e with begin[e] <= w
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (begin[mid] <= w) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// -------------------------------------------------------------- kernels
+template <typename T> struct EP;  // per-replica parameters in the arithmetic type
+template <> struct EP<float> {
+    static __device__ __forceinline__ float coef(const Entry& E, int i) { return E.coef_f[i]; }
+    static __device__ __forceinline__ float uf(const Entry& E, int a) { return E.ufs_f[a]; }
+};
+template <> struct EP<double> {
+    static __device__ __forceinline__ double coef(const Entry& E, int i) { return E.coef[i]; }
+    static __device__ __forceinline__ double uf(const Entry& E, int a) { return E.uf[a]; }
+};
+
+template <typename S>
+__global__ void __launch_bounds__(BW * 32, 8)
+kb_collide(const Entry* __restrict__ ent, const long long* __restrict__ gbegin, const Work* __restrict__ wk, int nrep,
+           long long total_groups, int parity, const unsigned* __restrict__ step_counter) {
+    using T = typename Store<S>::T;
+    constexpr bool SC = Store<S>::kScaled;
+    const int lane = threadIdx.x, warp = threadIdx.y;
+    // rounding seed of this step (the 16-bit formats): read from device
+    // memory so that graph replays draw new bits every step
+    const unsigned seed = Store<S>::kScaled || sizeof(S) == 2 ? rng_seed(*step_counter, 0xB5297A4Du) : 0u;
+    // each block takes a contiguous chunk of work items and walks it with
+    // incremental coordinates: one search per block, none per item
+    const long long chunk = (total_groups + gridDim.x - 1) / gridDim.x;
+    const long long w0 = (long long)blockIdx.x * chunk;
+    const long long w1 = w0 + chunk < total_groups ? w0 + chunk : total_groups;
+    if (w0 >= w1) return;
+    int e = find_entry(gbegin, nrep, w0);
+    int tx, yg, zz;
+    {
+        const long long local = w0 - wk[e].group_begin;
+        tx = (int)(local % wk[e].groups_x);
+        const long long r = local / wk[e].groups_x;
+        yg = (int)(r % wk[e].groups_y);
+        zz = (int)(r / wk[e].groups_y);
+    }
+    for (long long w = w0; w < w1; ++w) {
+        if (w > w0) {  // advance (tx, yg, z, entry)
+            if (++tx == wk[e].groups_x) {
+                tx = 0;
+                if (++yg == wk[e].groups_y) {
+                    yg = 0;
+                    if (++zz == ent[e].g.nz) {
+                        zz = 0;
+                        ++e;
+                    }
+                }
+            }
+        }
+        const Entry& E = ent[e];
+        const Geom& g = E.g;
+        const int y = yg * BW + warp;
+        const int z = zz;
+        const int x = tx * TILE_X + lane;
+        if (y >= g.ny) continue;  // uniform per warp
+        const unsigned tile = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.ntx + (unsigned)tx;
+        const unsigned char fl = E.flags[tile];
+        const unsigned V = (unsigned)g.V;
+        const int b = parity ^ E.cur0;
+        if (x < g.nx) {
+            Pops<S> src, dst;
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) {
+                src.p[i] = (S*)E.pop[b] + (size_t)i * V;
+                dst.p[i] = (S*)E.pop[b ^ 1] + (size_t)i * V;
+            }
+            const Nbr n = neighbours(g, x, y, z);
+            const unsigned site = n.c + n.x;
+            T* floc = (T*)E.floc;
+            if (is_solid(g, z)) {
+#pragma unroll
+                for (int i = 0; i < NQ; ++i) Store<S>::st(dst.p[i], site, T(0), 0u);
+            } else {
+                T f[NQ], o[NQ];
+                pull19<S, true>(src, n, f);  // populations first: in flight with the force loads below
+                T Fx = EP<T>::uf(E, 0), Fy = EP<T>::uf(E, 1), Fz = EP<T>::uf(E, 2);
+                if (fl) {
+                    const T s = SC ? (T)E.scale : T(1);
+                    Fx += floc[site] * s;
+                    Fy += floc[V + site] * s;
+                    Fz += floc[2 * V + site] * s;
+                }
+                Coef<T> k;
+                k.tau_s = EP<T>::coef(E, 0);
+                k.tau_b = EP<T>::coef(E, 1);
+                k.om_s = EP<T>::coef(E, 2);
+                k.om_b = EP<T>::coef(E, 3);
+                collide19<T, Store<S>::kCompensate, SC>(f, Fx, Fy, Fz, k, o, (T)E.inv_scale);
+                unsigned rn = rng_seed(site ^ (unsigned)(e * 0x27d4eb2d), seed);
+#pragma unroll
+                for (int i = 0; i < NQ; ++i) Store<S>::st(dst.p[i], site, o[i], rng_next(rn));
+                // clear the field only now: a store to a line whose load is
+                // still in flight would hold the warp until that load returns
+                if (fl) {
+                    floc[site] = T(0);
+                    floc[V + site] = T(0);
+                    floc[2 * V + site] = T(0);
+                }
+            }
+        }
+        if (fl) {
+            __syncwarp();
+            if (lane == 0) E.flags[tile] = 0;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+kb_spread(const Entry* __restrict__ ent, const long long* __restrict__ pbegin, int nrep, long long total_pts) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total_pts * 64) return;
+    const long long gp = t >> 6;
+    const int node = (int)(t & 63);
+    const int e = find_entry(pbegin, nrep, gp);
+    const Entry& E = ent[e];
+    const Geom& g = E.g;
+    const int s = (int)(gp - pbegin[e]);
+    const int i = node & 3, j = (node >> 2) & 3, k = node >> 4;
+    const double X = E.pos[3 * s], Y = E.pos[3 * s + 1], Z = E.pos[3 * s + 2];
+    const int nxg = stencil_base(X) + i, nyg = stencil_base(Y) + j, nzg = stencil_base(Z) + k;
+    const int z = wrap_node(nzg, g.nz);
+    if (is_solid(g, z)) return;
+    const int x = wrap_node(nxg, g.nx), y = wrap_node(nyg, g.ny);
+    const T w = peskin_phi((T)((double)nxg - X)) * peskin_phi((T)((double)nyg - Y)) * peskin_phi((T)((double)nzg - Z));
+    const long long site = ((long long)z * g.ny + y) * g.nx + x;
+    T* floc = (T*)E.floc;
+    atomicAdd(floc + site, (T)E.force[3 * s] * w);
+    atomicAdd(floc + g.V + site, (T)E.force[3 * s + 1] * w);
+    atomicAdd(floc + 2 * g.V + site, (T)E.force[3 * s + 2] * w);
+    E.flags[((long long)z * g.ny + y) * g.ntx + x / TILE_X] = 1;
+}
+
+__global__ void kb_tick(unsigned* step_counter) { *step_counter += 1u; }
+
+// Interpolated velocity and Faxen update of every colloid, one warp each.
+template <typename S>
+__global__ void __launch_bounds__(128)
+kb_gather(const Entry* __restrict__ ent, const long long* __restrict__ pbegin, int nrep, long long total_pts,
+          int parity) {
+    using T = typename Store<S>::T;
+    const long long gp = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (gp >= total_pts) return;
+    const int e = find_entry(pbegin, nrep, gp);
+    const Entry& E = ent[e];
+    const int s = (int)(gp - pbegin[e]);
+    if (!E.mobile[s]) return;
+    const Geom& g = E.g;
+    const int lane = threadIdx.x & 31;
+    const unsigned V = (unsigned)g.V;
+    const int b = parity ^ E.cur0;
+    Pops<S> src;
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) src.p[i] = (S*)E.pop[b] + (size_t)i * V;
+    const T* floc = (const T*)E.floc;
+    const double X = E.pos[3 * s], Y = E.pos[3 * s + 1], Z = E.pos[3 * s + 2];
+    const int bx = stencil_base(X), by = stencil_base(Y), bz = stencil_base(Z);
+    T acc[3] = {T(0), T(0), T(0)};
+    for (int h = 0; h < 2; ++h) {
+        const int node = lane + 32 * h;
+        const int i = node & 3, j = (node >> 2) & 3, k = node >> 4;
+        const int x = wrap_node(bx + i, g.nx), y = wrap_node(by + j, g.ny), z = wrap_node(bz + k, g.nz);
+        if (is_solid(g, z)) continue;
+        const T w = peskin_phi((T)((double)(bx + i) - X)) * peskin_phi((T)((double)(by + j) - Y)) *
+                    peskin_phi((T)((double)(bz + k) - Z));
+        const Nbr nb = neighbours(g, x, y, z);
+        const unsigned site = nb.c + nb.x;
+        T f[NQ];
+        pull19<S, true>(src, nb, f);
+        unscale19<S>(f, E.inv_scale);
+        const T Fx = (T)E.uf[0] + floc[site], Fy = (T)E.uf[1] + floc[V + site], Fz = (T)E.uf[2] + floc[2 * V + site];
+        T drho, vx, vy, vz;
+        macro19<T, Store<S>::kCompensate>(f, Fx, Fy, Fz, drho, vx, vy, vz);
+        acc[0] += w * vx;
+        acc[1] += w * vy;
+        acc[2] += w * vz;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+        for (int a = 0; a < 3; ++a) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], off);
+    if (lane != 0) return;
+    const double c = (1.0 / E.radius[s] - E.inv_aL) * E.inv_6pi_eta;
+    const int nn[3] = {g.nx, g.ny, g.nz};
+    for (int a = 0; a < 3; ++a) {
+        const double L = (double)nn[a];
+        double r = E.pos[3 * s + a] + (double)acc[a] + E.force[3 * s + a] * c;
+        r = r - L * floor(r / L);
+        if (r >= L || r < 0.0) r = 0.0;
+        E.pos[3 * s + a] = r;
+    }
+}
+
+}  // namespace
+
+struct lb_batch {
+    int n;
+    int prec;
+    std::vector<lb_ctx*> ctx;
+    cudaStream_t user_stream;
+    cudaStream_t stream;       // private stream: graphs cannot capture the legacy stream
+    cudaEvent_t ev_in, ev_out;
+    Entry* d_ent;
+    long long* d_gbegin;
+    long long* d_pbegin;
+    Work* d_work;
+    long long total_groups, total_pts, n_mobile;
+    int blocks;                // persistent grid of the collide kernel
+    unsigned* d_step;          // step counter seeding the stochastic rounding
+    int parity;                // batch steps taken since creation, mod 2
+    std::vector<int> cur0;     // each member's current buffer at creation
+    std::vector<unsigned> version;  // each member's configuration version at creation
+    cudaGraphExec_t graph2;    // two steps (parity 0, 1)
+    bool graph_ready;
+    long long launches;
+    std::string err;
+};
+
+namespace {
+
+lb_status bfail(lb_batch* b, lb_status s, const std::string& m) {
+    if (b) b->err = m;
+    return s;
+}
+
+#define LB_BCUDA(call, where)                                                                     \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return bfail(b, e_ == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA,           \
+                         std::string(where) + ": " + cudaGetErrorString(e_));                     \
+    } while (0)
+
+// Launch the three phases of one step (parity p) on the batch stream.
+template <typename S>
+cudaError_t launch_step(lb_batch* b, int p, int blocks) {
+    using T = typename Store<S>::T;
+    if (b->total_pts > 0) {
+        const long long th = b->total_pts * 64;
+        kb_spread<T><<<(unsigned)((th + 255) / 256), 256, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->n, b->total_pts);
+        if (b->n_mobile > 0)
+            kb_gather<S><<<(unsigned)((b->total_pts + 3) / 4), 128, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->n,
+                                                                                   b->total_pts, p);
+    }
+    kb_collide<S><<<blocks, dim3(32, BW), 0, b->stream>>>(b->d_ent, b->d_gbegin, b->d_work, b->n, b->total_groups, p,
+                                                          b->d_step);
+    if (sizeof(S) == 2) kb_tick<<<1, 1, 0, b->stream>>>(b->d_step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_any(lb_batch* b, int p, int blocks) {
+    switch (b->prec) {
+        case LB_F64: return launch_step<double>(b, p, blocks);
+        case LB_F32: return launch_step<float>(b, p, blocks);
+        case LB_F16S: return launch_step<__half>(b, p, blocks);
+        default: return launch_step<__nv_bfloat16>(b, p, blocks);
+    }
+}
+
+template <typename S>
+cudaError_t launch_collide_only(lb_batch* b, int blocks) {
+    kb_collide<S><<<blocks, dim3(32, BW), 0, b->stream>>>(b->d_ent, b->d_gbegin, b->d_work, b->n, b->total_groups,
+                                                          b->parity, b->d_step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_collide_any(lb_batch* b, int blocks) {
+    switch (b->prec) {
+        case LB_F64: return launch_collide_only<double>(b, blocks);
+        case LB_F32: return launch_collide_only<float>(b, blocks);
+        case LB_F16S: return launch_collide_only<__half>(b, blocks);
+        default: return launch_collide_only<__nv_bfloat16>(b, blocks);
+    }
+}
+
+int launches_per_step(const lb_batch* b) {
+    return 1 + (b->total_pts > 0 ? 1 : 0) + (b->n_mobile > 0 ? 1 : 0) + (b->prec >= LB_F16S ? 1 : 0);
+}
+
+}  // namespace
+
+extern "C" {
+
+lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stream) {
+    if (!out || n < 1 || !ctxs) return LB_ERR_ARG;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i)
+        if (!ctxs[i] || ctxs[i]->prec != ctxs[0]->prec || ctxs[i]->device != ctxs[0]->device) return LB_ERR_ARG;
+    lb_batch* b = new (std::nothrow) lb_batch();
+    if (!b) return LB_ERR_OOM;
+    b->n = n;
+    b->prec = ctxs[0]->prec;
+    b->ctx.assign(ctxs, ctxs + n);
+    b->user_stream = (cudaStream_t)stream;
+    b->parity = 0;
+    std::vector<Entry> ent(n);
+    std::vector<long long> gbegin(n), pbegin(n);
+    std::vector<Work> work(n);
+    long long groups = 0, pts = 0, mob = 0;
+    for (int i = 0; i < n; ++i) {
+        lb_ctx* c = ctxs[i];
+        Entry& E = ent[i];
+        E.pop[0] = c->f[0];
+        E.pop[1] = c->f[1];
+        E.floc = c->floc;
+        E.flags = c->flags;
+        E.pos = c->pos;
+        E.force = c->force;
+        E.radius = c->radius;
+        E.mobile = c->mobile;
+        E.g = c->geom;
+        E.npts = c->npts;
+        E.cur0 = c->cur;
+        b->cur0.push_back(c->cur);
+        b->version.push_back(c->version);
+        E.coef[0] = c->tau_s;
+        E.coef[1] = c->tau_b;
+        E.coef[2] = 1.0 / (c->tau_s + 0.5);
+        E.coef[3] = 1.0 / (c->tau_b + 0.5);
+        const UForce<double> u = uniform_force<double>(c);
+        for (int a = 0; a < 3; ++a) {
+            E.uf[a] = u.F[a];
+            E.ufs_f[a] = (float)(u.F[a] * (double)c->scale);
+        }
+        for (int a = 0; a < 4; ++a) E.coef_f[a] = (float)E.coef[a];
+        E.inv_6pi_eta = 1.0 / (6.0 * M_PI * (c->tau_s / 3.0));
+        E.inv_aL = isinf(c->a_L) ? 0.0 : 1.0 / c->a_L;
+        E.scale = c->scale;
+        E.inv_scale = c->inv_scale;
+        work[i].groups_x = c->geom.ntx;
+        work[i].groups_y = (c->geom.ny + BW - 1) / BW;
+        work[i].group_begin = groups;
+        work[i].pt_begin = pts;
+        gbegin[i] = groups;
+        pbegin[i] = pts;
+        groups += (long long)work[i].groups_x * work[i].groups_y * c->geom.nz;
+        pts += c->npts;
+        mob += c->n_mobile;
+    }
+    b->total_groups = groups;
+    b->total_pts = pts;
+    b->n_mobile = mob;
+    b->blocks = (int)std::min<long long>(std::max<long long>(groups, 1), 0x7fffffffLL);  // untuned: one per item
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_ent, sizeof(Entry) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_gbegin, sizeof(long long) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_pbegin, sizeof(long long) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_work, sizeof(Work) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_step, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(b->d_step, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_ent, ent.data(), sizeof(Entry) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_gbegin, gbegin.data(), sizeof(long long) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_pbegin, pbegin.data(), sizeof(long long) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_work, work.data(), sizeof(Work) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        lb_batch_destroy(b);
+        return e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA;
+    }
+    *out = b;
+    return LB_OK;
+}
+
+void lb_batch_destroy(lb_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->graph_ready) cudaGraphExecDestroy(b->graph2);
+    cudaFree(b->d_ent);
+    cudaFree(b->d_gbegin);
+    cudaFree(b->d_pbegin);
+    cudaFree(b->d_work);
+    cudaFree(b->d_step);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+const char* lb_batch_last_error(const lb_batch* b) { return b ? b->err.c_str() : ""; }
+
+lb_status lb_batch_tune(lb_batch* b, int* blocks_out) {
+    if (!b) return LB_ERR_ARG;
+    // Side-effect free: the member fields are cleared first, so the collide
+    // kernel reads and writes no force tiles; it writes the spare buffer of
+    // every replica and leaves the state (current buffer) untouched.
+    for (lb_ctx* c : b->ctx) {
+        if (c->field_ready) {
+            LB_BCUDA(lbk::launch_clear_field(c), "clear force field");
+            c->field_ready = false;
+        }
+        LB_BCUDA(cudaStreamSynchronize(c->stream), "member stream");
+    }
+    int best = b->blocks;
+    float best_ms = 1e30f;
+    cudaEvent_t t0, t1;
+    LB_BCUDA(cudaEventCreate(&t0), "event");
+    LB_BCUDA(cudaEventCreate(&t1), "event");
+    // candidates: persistent grids of 2-16 blocks per SM (contiguous chunks of
+    // work items per block), and one block per work item (no persistence)
+    const long long per_sm[] = {2, 4, 8, 16, 0};
+    for (long long k : per_sm) {
+        const long long want = k ? 152LL * k : std::min<long long>(b->total_groups, 0x7fffffffLL);
+        const int blocks = (int)std::min<long long>(want, std::max<long long>(1, b->total_groups));
+        LB_BCUDA(launch_collide_any(b, blocks), "tune launch");  // warm
+        LB_BCUDA(cudaEventRecord(t0, b->stream), "event");
+        for (int r = 0; r < 3; ++r) LB_BCUDA(launch_collide_any(b, blocks), "tune launch");
+        LB_BCUDA(cudaEventRecord(t1, b->stream), "event");
+        LB_BCUDA(cudaEventSynchronize(t1), "event");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t0, t1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = blocks;
+        }
+        b->launches += 4;
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (best != b->blocks && b->graph_ready) {
+        cudaGraphExecDestroy(b->graph2);
+        b->graph_ready = false;
+    }
+    b->blocks = best;
+    if (blocks_out) *blocks_out = best;
+    return LB_OK;
+}
+
+lb_status lb_batch_step(lb_batch* b, int nsteps) {
+    if (!b) return LB_ERR_ARG;
+    if (nsteps < 0) return bfail(b, LB_ERR_ARG, "lb_batch_step: nsteps < 0");
+    if (nsteps == 0) return LB_OK;
+    for (int i = 0; i < b->n; ++i) {
+        lb_ctx* c = b->ctx[i];
+        if (c->version != b->version[i] || c->cur != (b->cur0[i] ^ b->parity))
+            return bfail(b, LB_ERR_STATE,
+                         "lb_batch_step: a member was reconfigured or stepped on its own since lb_batch_create");
+    }
+    // order after the caller's stream and the member contexts' work
+    LB_BCUDA(cudaEventRecord(b->ev_in, b->user_stream), "event record");
+    LB_BCUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0), "stream wait");
+    for (lb_ctx* c : b->ctx) {
+        if (c->stream != b->user_stream) {
+            LB_BCUDA(cudaEventRecord(b->ev_in, c->stream), "event record");
+            LB_BCUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0), "stream wait");
+        }
+        if (c->field_ready) {  // forces already spread by a query: clear, the step spreads again
+            LB_BCUDA(lbk::launch_clear_field(c), "clear force field");
+            LB_BCUDA(cudaEventRecord(b->ev_in, c->stream), "event record");
+            LB_BCUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0), "stream wait");
+            c->field_ready = false;
+        }
+    }
+    if (!b->graph_ready && nsteps >= 2) {
+        cudaGraph_t g;
+        LB_BCUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        cudaError_t e = launch_step_any(b, 0, b->blocks);
+        if (e == cudaSuccess) e = launch_step_any(b, 1, b->blocks);
+        cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess)
+            return bfail(b, LB_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+        e = cudaGraphInstantiate(&b->graph2, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return bfail(b, LB_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        b->graph_ready = true;
+    }
+    // The graph holds two steps starting at parity 0: a batch at odd parity
+    // takes one plain step first.
+    int done = 0;
+    while (done < nsteps) {
+        if (b->graph_ready && b->parity == 0 && nsteps - done >= 2) {
+            LB_BCUDA(cudaGraphLaunch(b->graph2, b->stream), "graph launch");
+            done += 2;
+        } else {
+            LB_BCUDA(launch_step_any(b, b->parity, b->blocks), "batched step");
+            b->parity ^= 1;
+            done += 1;
+        }
+    }
+    b->launches += (long long)nsteps * launches_per_step(b);
+    for (lb_ctx* c : b->ctx) {
+        c->cur ^= (nsteps & 1);
+        c->field_ready = false;
+    }
+    LB_BCUDA(cudaEventRecord(b->ev_out, b->stream), "event record");
+    LB_BCUDA(cudaStreamWaitEvent(b->user_stream, b->ev_out, 0), "stream wait");
+    for (lb_ctx* c : b->ctx)
+        if (c->stream != b->user_stream) LB_BCUDA(cudaStreamWaitEvent(c->stream, b->ev_out, 0), "stream wait");
+    return LB_OK;
+}
+
+lb_status lb_batch_info(const lb_batch* b, long long* sites, long long* points, int* blocks, long long* launches) {
+    if (!b) return LB_ERR_ARG;
+    long long s = 0;
+    for (lb_ctx* c : b->ctx) s += c->geom.V;
+    if (sites) *sites = s;
+    if (points) *points = b->total_pts;
+    if (blocks) *blocks = b->blocks;
+    if (launches) *launches = b->launches;
+    return LB_OK;
+}
+
+}  // extern "C"

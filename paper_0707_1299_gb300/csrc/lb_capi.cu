@@ -257,6 +257,7 @@ lb_status lb_set_body_force(lb_ctx* c, const double g[3]) {
     for (int a = 0; a < 3; ++a)
         if (!isfinite(g[a])) return fail(c, LB_ERR_NONFINITE, "lb_set_body_force: non-finite g");
     for (int a = 0; a < 3; ++a) c->g[a] = g[a];
+    c->version++;
     return LB_OK;
 }
 
@@ -268,12 +269,14 @@ lb_status lb_set_walls_z(lb_ctx* c, int z_lo, int z_hi) {
     if (s != LB_OK) return s;
     c->geom.wall_lo = z_lo;
     c->geom.wall_hi = z_hi;
+    c->version++;
     return LB_OK;
 }
 
 lb_status lb_set_counterforce(lb_ctx* c, int enabled) {
     if (!c) return LB_ERR_ARG;
     c->counter = enabled ? 1 : 0;
+    c->version++;
     return LB_OK;
 }
 
@@ -281,6 +284,7 @@ lb_status lb_set_colloid_aL(lb_ctx* c, double a_L) {
     if (!c) return LB_ERR_ARG;
     if (!(a_L > 0) || isnan(a_L)) return fail(c, LB_ERR_ARG, "lb_set_colloid_aL: a_L must be > 0");
     c->a_L = a_L;
+    c->version++;
     return LB_OK;
 }
 
@@ -314,6 +318,7 @@ lb_status lb_add_point_forces(lb_ctx* c, int n, const double* pos, const double*
     if (status & 2)
         return fail(c, LB_ERR_ARG, "lb_add_point_forces: parameter must be > 0 (and |F| > 0 for stresslet/rotlet)");
     c->npts = (int)total;
+    c->version++;
     if (kind == LB_COLLOID) c->n_mobile += n;
     LB_CUDA(lbk::launch_fsum(c), "force sum");
     LB_CUDA(cudaMemcpyAsync(c->fsum_host, c->fsum, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream),
@@ -328,6 +333,7 @@ lb_status lb_clear_point_forces(lb_ctx* c) {
     if (s != LB_OK) return s;
     c->npts = 0;
     c->n_mobile = 0;
+    c->version++;
     for (int a = 0; a < 3; ++a) c->fsum_host[a] = 0.0;
     LB_CUDA(cudaMemsetAsync(c->fsum, 0, sizeof(double) * 3, c->stream), "force sum reset");
     return LB_OK;

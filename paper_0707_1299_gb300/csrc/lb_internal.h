@@ -46,6 +46,7 @@ struct lb_ctx {
 
     long long launches;       // kernels launched so far
     unsigned seed;            // seed of the stochastic rounding of the 16-bit formats
+    unsigned version;         // bumped by every configuration change (batches check it)
 
     std::string err;
 };
@@ -70,6 +71,8 @@ cudaError_t launch_set_positions(lb_ctx* c, const double* pos);
 cudaError_t launch_convert_out(lb_ctx* c, double* df);
 cudaError_t launch_convert_in(lb_ctx* c, const double* df);
 cudaError_t launch_clear_field(lb_ctx* c);
+template <typename T>
+UForce<T> uniform_force(const lb_ctx* c);
 cudaError_t compute_inv_aL(const int grid[3], const double R[3], const double dir[3], double* inv_aL);
 
 size_t storage_bytes(int prec);

@@ -46,7 +46,7 @@ double n_fluid(const lb_ctx* c) {
 // Uniform force density on fluid sites: g plus the counter-force
 // -sum F / V_fluid (evaluated on the host in FP64, passed in the arithmetic type).
 template <typename T>
-UForce<T> uniform_force(const lb_ctx* c) {
+UForce<T> uniform_force(const lb_ctx* c) {  // instantiated for float and double below
     UForce<T> u;
     const double nf = n_fluid(c);
     for (int a = 0; a < 3; ++a) {
@@ -56,6 +56,9 @@ UForce<T> uniform_force(const lb_ctx* c) {
     }
     return u;
 }
+
+template UForce<float> uniform_force<float>(const lb_ctx*);
+template UForce<double> uniform_force<double>(const lb_ctx*);
 
 template <typename S>
 static Pops<S> pops(void* base, long long V) {
@@ -116,20 +119,24 @@ k_collide(const Pops<S> src, const Pops<S> dst, typename Store<S>::T* __restrict
                 if (y0 + r >= g.ny) break;
                 const unsigned site = n[r].c + n[r].x;
                 T Fx = fu.F[0], Fy = fu.F[1], Fz = fu.F[2];
-                if (fl[r]) {
+                if (fl[r]) {  // after the population loads, so both are in flight together
                     const T s = SC ? (T)scale : T(1);
                     Fx += floc[site] * s;
                     Fy += floc[V + site] * s;
                     Fz += floc[2 * V + site] * s;
-                    floc[site] = T(0);
-                    floc[V + site] = T(0);
-                    floc[2 * V + site] = T(0);
                 }
                 T o[NQ];
                 collide19<T, Store<S>::kCompensate, SC>(f[r], Fx, Fy, Fz, k, o, (T)inv_scale);
                 unsigned rn = rng_seed(site, seed);
 #pragma unroll
                 for (int i = 0; i < NQ; ++i) Store<S>::st(dst.p[i], site, o[i], rng_next(rn));
+                // clear the field only now: a store to a line whose load is
+                // still in flight would hold the warp until that load returns
+                if (fl[r]) {
+                    floc[site] = T(0);
+                    floc[V + site] = T(0);
+                    floc[2 * V + site] = T(0);
+                }
             }
         }
     }

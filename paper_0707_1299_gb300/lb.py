@@ -28,7 +28,8 @@ EXPORTS = ["lb_create", "lb_destroy", "lb_last_error", "lb_set_body_force", "lb_
            "lb_set_counterforce", "lb_set_colloid_aL", "lb_add_point_forces", "lb_clear_point_forces",
            "lb_num_points", "lb_set_positions", "lb_step", "lb_velocity_at", "lb_moments",
            "lb_particles", "lb_get_populations", "lb_set_populations", "lb_kernel_launches",
-           "lb_synchronize", "lb_compute_aL", "lb_totals_noalloc"]
+           "lb_synchronize", "lb_compute_aL", "lb_totals_noalloc", "lb_batch_create",
+           "lb_batch_destroy", "lb_batch_last_error", "lb_batch_tune", "lb_batch_step", "lb_batch_info"]
 
 _lib = None
 
@@ -71,6 +72,14 @@ def load():
         "lb_synchronize": ([vp], ctypes.c_int),
         "lb_compute_aL": ([ip, dp, dp, dp], ctypes.c_int),
         "lb_totals_noalloc": ([vp, ctypes.c_int, ip, ctypes.c_int, ctypes.c_int, dp, dp, vp], ctypes.c_int),
+        "lb_batch_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), vp],
+                            ctypes.c_int),
+        "lb_batch_destroy": ([vp], None),
+        "lb_batch_last_error": ([vp], ctypes.c_char_p),
+        "lb_batch_tune": ([vp, ip], ctypes.c_int),
+        "lb_batch_step": ([vp, ctypes.c_int], ctypes.c_int),
+        "lb_batch_info": ([vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), ip,
+                           ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -218,6 +227,47 @@ def lb_totals_noalloc(df, precision, grid, z_lo, z_hi, F, totals, stream=None):
                                       ctypes.c_void_p(stream))
     if status != LB_OK:
         raise LBError(status, "lb_totals_noalloc failed")
+
+
+def _bcheck(batch, status):
+    if status != LB_OK:
+        msg = load().lb_batch_last_error(batch)
+        raise LBError(status, msg.decode() if msg else "")
+
+
+def lb_batch_create(ctxs, stream=None):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    arr = (ctypes.c_void_p * len(ctxs))(*ctxs)
+    out = ctypes.c_void_p()
+    _bcheck(None, load().lb_batch_create(ctypes.byref(out), len(ctxs), arr, ctypes.c_void_p(stream)))
+    return out.value
+
+
+def lb_batch_destroy(batch):
+    load().lb_batch_destroy(batch)
+
+
+def lb_batch_last_error(batch):
+    return load().lb_batch_last_error(batch).decode()
+
+
+def lb_batch_tune(batch):
+    n = ctypes.c_int()
+    _bcheck(batch, load().lb_batch_tune(batch, ctypes.byref(n)))
+    return n.value
+
+
+def lb_batch_step(batch, nsteps):
+    _bcheck(batch, load().lb_batch_step(batch, int(nsteps)))
+
+
+def lb_batch_info(batch):
+    s, p, l = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+    b = ctypes.c_int()
+    _bcheck(batch, load().lb_batch_info(batch, ctypes.byref(s), ctypes.byref(p), ctypes.byref(b), ctypes.byref(l)))
+    return {"sites": s.value, "points": p.value, "blocks": b.value, "launches": l.value}
 
 
 # ------------------------------------------------------------- wrapper

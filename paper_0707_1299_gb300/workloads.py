@@ -20,6 +20,9 @@ Workloads (lattice units, rho0 = 1):
                     [L/4, 3L/4)^3 from seed 2.
   colloids_512   -- 512^3, 1e5 colloids uniform in the box (seed 3), force
                     (0, 0, -1e-6), radius a = 0.117 (Table I), counter-force.
+  replicas       -- 64 independent periodic boxes, sides uniform in
+                    {48, 56, ..., 128} (seed 4), 100-2000 colloids each,
+                    force 1e-6, 5000 steps.
 Every workload takes a size argument so that the same recipe runs at
 sizes a CPU oracle finishes in seconds.
 """
@@ -97,11 +100,30 @@ def colloids(L: int = 512, n: int = 100000, seed: int = 3, force: float = 1e-6, 
                    points=[PointSet(COLLOID, pos, F, prm)], steps=steps)
 
 
+def replicas(n: int = 64, seed: int = 4, L_min: int = 48, L_max: int = 128, L_step: int = 8,
+             n_min: int = 100, n_max: int = 2000, force: float = 1e-6, steps: int = 5000):
+    """Independent periodic sedimentation boxes of seeded uneven sizes: side
+    uniform in {L_min, L_min + L_step, ..., L_max}, colloid count uniform in
+    [n_min, n_max], colloids uniform in the box with force (0, 0, -force),
+    radius a = 0.117, counter-force on."""
+    r = rng(seed)
+    sides = np.arange(L_min, L_max + 1, L_step)
+    out = []
+    for k in range(n):
+        L = int(r.choice(sides))
+        m = int(r.integers(n_min, n_max + 1))
+        pos = r.uniform(0, L, size=(m, 3))
+        F = np.tile([0.0, 0.0, -force], (m, 1))
+        out.append(Problem(f"replica{k}", (L, L, L), 0.5, 0.5,
+                           points=[PointSet(COLLOID, pos, F, np.full(m, A_TABLE1))], steps=steps))
+    return out
+
+
 def random_state(grid, seed: int, amp: float = 1e-4) -> np.ndarray:
     """A seeded non-equilibrium initial population deviation df[19][z][y][x]."""
     r = rng(seed)
     return r.normal(0.0, amp, size=(19, grid[2], grid[1], grid[0]))
 
 
-__all__ = ["Problem", "PointSet", "stokeslet_32", "channel_256", "colloids", "random_state", "rng",
+__all__ = ["Problem", "PointSet", "stokeslet_32", "channel_256", "colloids", "replicas", "random_state", "rng",
            "STOKESLET", "STRESSLET", "ROTLET", "COLLOID", "A_TABLE1"]
