@@ -178,6 +178,48 @@ lb_status lb_synchronize(lb_ctx *ctx);
  * the current device (allocates temporary device memory). */
 lb_status lb_compute_aL(const int grid[3], const double R[3], const double dir[3], double *a_L);
 
+/* Colloid velocity of Sec. IV at n query points: the interpolated fluid
+ * velocity plus the Faxen term with the a_L subtraction,
+ *   U = v(R) + F (1/a - 1/a_L) / (6 pi eta),
+ * for forces F (3n doubles) and radii a (n doubles); host or device
+ * pointers.  lb_step moves colloids with exactly this velocity. */
+lb_status lb_colloid_velocity(lb_ctx *ctx, int n, const double *pos, const double *F, const double *radius,
+                              double *U_out);
+
+/* ------------------------------------------------------------------------
+ * Learned correction of the colloid velocity: a 27 -> 64 -> 64 -> 3
+ * perceptron with SiLU activations in bfloat16 (FP32 accumulation and
+ * master weights), trained on pairs of runs of the method at two lattice
+ * resolutions.  Input of a colloid: its fractional lattice offset and the
+ * minimum-image vectors to its 8 nearest others within 8 lattice units
+ * (nearest first, in units of 4 lattice spacings, zero where absent).
+ * Parameters: one float vector, W1[64][27] b1[64] W2[64][64] b2[64]
+ * W3[3][64] b3[3] (lb_mlp_num_params() floats).  n-sized arrays are device
+ * pointers; parameter vectors host or device.  Work runs on the stream
+ * given at creation.  Not part of the paper: the method itself stays the
+ * reference the correction is judged against.
+ * --------------------------------------------------------------------- */
+typedef struct lb_mlp lb_mlp;
+int lb_mlp_num_params(void);
+lb_status lb_mlp_create(lb_mlp **out, const float *init_params, void *stream);
+void lb_mlp_destroy(lb_mlp *net);
+const char *lb_mlp_last_error(const lb_mlp *net);
+lb_status lb_mlp_get_params(lb_mlp *net, float *out);
+lb_status lb_mlp_set_params(lb_mlp *net, const float *in);  /* also resets Adam */
+/* feat[n][27] (float) from positions pos[n][3] (double) in a periodic box */
+lb_status lb_mlp_features(lb_mlp *net, long long n, const double *pos, const int box[3], float *feat);
+/* out[n][3] = network(feat) */
+lb_status lb_mlp_forward(lb_mlp *net, long long n, const float *feat, float *out);
+/* gradient of (1/3n) sum (y - target)^2 (grad: num_params floats, host or
+ * device, may be NULL) and the sum of squared errors (*sse, may be NULL);
+ * waits for completion */
+lb_status lb_mlp_grad(lb_mlp *net, long long n, const float *feat, const float *target, float *grad,
+                      float *sse);
+/* one Adam step (beta 0.9 / 0.999, eps 1e-8) on that gradient; *sse (may
+ * be NULL) receives the sum of squared errors before the step */
+lb_status lb_mlp_train_step(lb_mlp *net, long long n, const float *feat, const float *target, float lr,
+                            float *sse);
+
 /* ------------------------------------------------------------------------
  * Batches: independent lattices (replicas of uneven sizes, e.g. many small
  * sedimentation boxes) advanced together.  Each phase of a time step

@@ -393,6 +393,26 @@ lb_status lb_velocity_at(lb_ctx* c, int n, const double* pos, double* v_out) {
     return finish(c, args, 2, any_host);
 }
 
+lb_status lb_colloid_velocity(lb_ctx* c, int n, const double* pos, const double* F, const double* radius,
+                              double* U_out) {
+    if (!c) return LB_ERR_ARG;
+    if (n < 0) return fail(c, LB_ERR_ARG, "lb_colloid_velocity: n < 0");
+    if (n == 0) return LB_OK;
+    if (!pos || !F || !radius || !U_out) return fail(c, LB_ERR_ARG, "lb_colloid_velocity: NULL argument");
+    Arg args[4] = {{pos, sizeof(double) * 3 * n, false, nullptr, false},
+                   {F, sizeof(double) * 3 * n, false, nullptr, false},
+                   {radius, sizeof(double) * n, false, nullptr, false},
+                   {U_out, sizeof(double) * 3 * n, true, nullptr, false}};
+    bool any_host;
+    lb_status s = resolve(c, args, 4, &any_host);
+    if (s == LB_OK) s = ensure_field(c);
+    if (s != LB_OK) return s;
+    LB_CUDA(lbk::launch_gather(c, n, (const double*)args[0].dev, (double*)args[3].dev, false), "gather kernel");
+    LB_CUDA(lbk::launch_faxen(c, n, (const double*)args[1].dev, (const double*)args[2].dev, (double*)args[3].dev),
+            "faxen kernel");
+    return finish(c, args, 4, any_host);
+}
+
 lb_status lb_moments(lb_ctx* c, double* rho, double* u, double* totals) {
     if (!c) return LB_ERR_ARG;
     const size_t V = (size_t)c->geom.V;

@@ -67,6 +67,7 @@ cudaError_t launch_moments(lb_ctx* c, double* rho, double* u, bool want_totals);
 cudaError_t launch_expand(lb_ctx* c, int n, const double* pos, const double* F, const double* param, int kind,
                           int mult);
 cudaError_t launch_fsum(lb_ctx* c);
+cudaError_t launch_faxen(lb_ctx* c, int n, const double* F, const double* a, double* U);
 cudaError_t launch_set_positions(lb_ctx* c, const double* pos);
 cudaError_t launch_convert_out(lb_ctx* c, double* df);
 cudaError_t launch_convert_in(lb_ctx* c, const double* df);

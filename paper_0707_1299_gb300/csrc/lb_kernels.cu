@@ -303,6 +303,16 @@ __global__ void k_reduce_partials(const double* __restrict__ partials, long long
     }
 }
 
+// U = v(R) + F (1/a - 1/a_L) / (6 pi eta): the colloid velocity of Sec. IV
+// from the interpolated fluid velocity v (in place).
+__global__ void k_faxen(int n, const double* __restrict__ F, const double* __restrict__ a, double inv_aL,
+                        double inv_6pi_eta, double* __restrict__ U) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const double c = (1.0 / a[t] - inv_aL) * inv_6pi_eta;
+    for (int k = 0; k < 3; ++k) U[3 * t + k] += F[3 * t + k] * c;
+}
+
 // ---------------------------------------------------- point bookkeeping
 
 // Expand n records of one kind into monopoles at out offset `base`
@@ -600,6 +610,15 @@ cudaError_t launch_moments(lb_ctx* c, double* rho, double* u, bool want_totals) 
         case LB_F16S: return moments_t<__half>(c, rho, u, want_totals);
         default: return moments_t<__nv_bfloat16>(c, rho, u, want_totals);
     }
+}
+
+cudaError_t launch_faxen(lb_ctx* c, int n, const double* F, const double* a, double* U) {
+    if (n == 0) return cudaSuccess;
+    const double eta = c->tau_s / 3.0;
+    const double inv_aL = isinf(c->a_L) ? 0.0 : 1.0 / c->a_L;
+    k_faxen<<<(n + 127) / 128, 128, 0, c->stream>>>(n, F, a, inv_aL, 1.0 / (6.0 * M_PI * eta), U);
+    c->launches++;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_expand(lb_ctx* c, int n, const double* pos, const double* F, const double* param, int kind,

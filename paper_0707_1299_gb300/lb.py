@@ -29,7 +29,10 @@ EXPORTS = ["lb_create", "lb_destroy", "lb_last_error", "lb_set_body_force", "lb_
            "lb_num_points", "lb_set_positions", "lb_step", "lb_velocity_at", "lb_moments",
            "lb_particles", "lb_get_populations", "lb_set_populations", "lb_kernel_launches",
            "lb_synchronize", "lb_compute_aL", "lb_totals_noalloc", "lb_batch_create",
-           "lb_batch_destroy", "lb_batch_last_error", "lb_batch_tune", "lb_batch_step", "lb_batch_info"]
+           "lb_batch_destroy", "lb_batch_last_error", "lb_batch_tune", "lb_batch_step", "lb_batch_info",
+           "lb_colloid_velocity", "lb_mlp_num_params", "lb_mlp_create", "lb_mlp_destroy", "lb_mlp_last_error",
+           "lb_mlp_get_params", "lb_mlp_set_params", "lb_mlp_features", "lb_mlp_forward", "lb_mlp_grad",
+           "lb_mlp_train_step"]
 
 _lib = None
 
@@ -72,6 +75,17 @@ def load():
         "lb_synchronize": ([vp], ctypes.c_int),
         "lb_compute_aL": ([ip, dp, dp, dp], ctypes.c_int),
         "lb_totals_noalloc": ([vp, ctypes.c_int, ip, ctypes.c_int, ctypes.c_int, dp, dp, vp], ctypes.c_int),
+        "lb_colloid_velocity": ([vp, ctypes.c_int, dp, dp, dp, dp], ctypes.c_int),
+        "lb_mlp_num_params": ([], ctypes.c_int),
+        "lb_mlp_create": ([ctypes.POINTER(ctypes.c_void_p), vp, vp], ctypes.c_int),
+        "lb_mlp_destroy": ([vp], None),
+        "lb_mlp_last_error": ([vp], ctypes.c_char_p),
+        "lb_mlp_get_params": ([vp, vp], ctypes.c_int),
+        "lb_mlp_set_params": ([vp, vp], ctypes.c_int),
+        "lb_mlp_features": ([vp, ctypes.c_longlong, vp, ip, vp], ctypes.c_int),
+        "lb_mlp_forward": ([vp, ctypes.c_longlong, vp, vp], ctypes.c_int),
+        "lb_mlp_grad": ([vp, ctypes.c_longlong, vp, vp, vp, vp], ctypes.c_int),
+        "lb_mlp_train_step": ([vp, ctypes.c_longlong, vp, vp, ctypes.c_float, vp], ctypes.c_int),
         "lb_batch_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), vp],
                             ctypes.c_int),
         "lb_batch_destroy": ([vp], None),
@@ -227,6 +241,76 @@ def lb_totals_noalloc(df, precision, grid, z_lo, z_hi, F, totals, stream=None):
                                       ctypes.c_void_p(stream))
     if status != LB_OK:
         raise LBError(status, "lb_totals_noalloc failed")
+
+
+def lb_colloid_velocity(ctx, n, pos, F, radius, U_out):
+    _check(ctx, load().lb_colloid_velocity(ctx, int(n), _ptr(pos), _ptr(F), _ptr(radius), _ptr(U_out)))
+
+
+# ---------------------------------------------------------- learned part
+def _addr(x):
+    """Address of a tensor/array of any dtype (device or host)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return x.data_ptr()
+    assert isinstance(x, np.ndarray) and x.flags["C_CONTIGUOUS"]
+    return x.ctypes.data
+
+
+def _mcheck(net, status):
+    if status != LB_OK:
+        msg = load().lb_mlp_last_error(net)
+        raise LBError(status, msg.decode() if msg else "")
+
+
+def lb_mlp_num_params():
+    return load().lb_mlp_num_params()
+
+
+def lb_mlp_create(init_params, stream=None):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    out = ctypes.c_void_p()
+    _mcheck(None, load().lb_mlp_create(ctypes.byref(out), _addr(init_params), ctypes.c_void_p(stream)))
+    return out.value
+
+
+def lb_mlp_destroy(net):
+    load().lb_mlp_destroy(net)
+
+
+def lb_mlp_last_error(net):
+    return load().lb_mlp_last_error(net).decode()
+
+
+def lb_mlp_get_params(net, out):
+    _mcheck(net, load().lb_mlp_get_params(net, _addr(out)))
+
+
+def lb_mlp_set_params(net, params):
+    _mcheck(net, load().lb_mlp_set_params(net, _addr(params)))
+
+
+def lb_mlp_features(net, n, pos, box, feat):
+    b = (ctypes.c_int * 3)(*[int(v) for v in box])
+    _mcheck(net, load().lb_mlp_features(net, int(n), _addr(pos), b, _addr(feat)))
+
+
+def lb_mlp_forward(net, n, feat, out):
+    _mcheck(net, load().lb_mlp_forward(net, int(n), _addr(feat), _addr(out)))
+
+
+def lb_mlp_grad(net, n, feat, target, grad=None, sse=None):
+    _mcheck(net, load().lb_mlp_grad(net, int(n), _addr(feat), _addr(target), _addr(grad), _addr(sse)))
+
+
+def lb_mlp_train_step(net, n, feat, target, lr, sse=None):
+    _mcheck(net, load().lb_mlp_train_step(net, int(n), _addr(feat), _addr(target), float(lr), _addr(sse)))
 
 
 def _bcheck(batch, status):

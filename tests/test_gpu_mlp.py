@@ -1,0 +1,123 @@
+"""The learned-correction kernels (features, bfloat16 forward, fused
+backward, Adam) against the oracle MLP, and what the trained network gains
+over the plain method on held-out 1x/2x run pairs."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0707_1299_gb300 import build, lb
+    build.build()
+    lb.load()
+    torch.cuda.set_device(0)
+    yield
+
+
+def _lb():
+    from paper_0707_1299_gb300 import lb
+    return lb
+
+
+def test_features_match_brute_force():
+    lb = _lb()
+    rng = np.random.default_rng(5)
+    for box, n in (((20, 24, 30), 300), ((9, 9, 9), 40), ((40, 17, 33), 700)):
+        pos = rng.uniform(0, 1, (n, 3)) * np.asarray(box, float)
+        pos[:5] = np.asarray(box) - 1e-3 * rng.uniform(size=(5, 3))  # near the periodic boundary
+        net = lb.lb_mlp_create(np.zeros(lb.lb_mlp_num_params(), dtype=np.float32))
+        P = torch.as_tensor(pos, device="cuda").contiguous()
+        f = torch.empty((n, 27), dtype=torch.float32, device="cuda")
+        lb.lb_mlp_features(net, n, P, box, f)
+        ref = mlp.features(pos, box)
+        assert np.abs(f.cpu().numpy() - ref).max() < 1e-6
+        lb.lb_mlp_destroy(net)
+
+
+def _random_problem(n, seed):
+    rng = np.random.default_rng(seed)
+    P = mlp.init_params(seed)
+    for k in P:
+        P[k] = P[k] + rng.normal(0, 0.05, P[k].shape)
+    x = rng.normal(0, 1, (n, 27))
+    t = rng.normal(0, 0.5, (n, 3))
+    return P, x, t
+
+
+def test_forward_and_gradient_match_oracle():
+    # bfloat16 rounding points as in the kernels; FP32 accumulation on the
+    # GPU against FP64 in the oracle.  A pre-activation that lies within the
+    # FP32 error of a bfloat16 rounding boundary may round the other way, so
+    # single outputs may differ by one bfloat16 unit of an activation; the
+    # bulk agrees to FP32 accuracy.
+    lb = _lb()
+    for n in (200, 64, 1):
+        P, x, t = _random_problem(n, 11 + n)
+        v = mlp.flatten(P).astype(np.float32)
+        P32 = mlp.unflatten(v.astype(np.float64))
+        net = lb.lb_mlp_create(v)
+        X = torch.as_tensor(x, dtype=torch.float32, device="cuda").contiguous()
+        T = torch.as_tensor(t, dtype=torch.float32, device="cuda").contiguous()
+        y = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+        lb.lb_mlp_forward(net, n, X, y)
+        xr = x.astype(np.float32).astype(np.float64)
+        tr = t.astype(np.float32).astype(np.float64)
+        yref, _ = mlp.forward(P32, xr, bf16_round=True)
+        err = np.abs(y.cpu().numpy() - yref).max(axis=1) / np.abs(yref).max()
+        assert np.quantile(err, 0.98) < 1e-5 and err.max() < 2e-2
+        g = np.zeros(lb.lb_mlp_num_params(), dtype=np.float32)
+        sse = np.zeros(1, dtype=np.float32)
+        lb.lb_mlp_grad(net, n, X, T, g, sse)
+        gref = mlp.flatten(mlp.backward(P32, xr, tr, bf16_round=True))
+        assert np.abs(g - gref).max() < 3e-3 * np.abs(gref).max()
+        assert abs(sse[0] / (3 * n) - np.mean((yref - tr) ** 2)) < 1e-3 * np.mean((yref - tr) ** 2)
+        lb.lb_mlp_destroy(net)
+
+
+def test_adam_steps_match_oracle():
+    lb = _lb()
+    n, lr = 256, 1e-3
+    P, x, t = _random_problem(n, 3)
+    v = mlp.flatten(P).astype(np.float32)
+    net = lb.lb_mlp_create(v)
+    X = torch.as_tensor(x, dtype=torch.float32, device="cuda").contiguous()
+    T = torch.as_tensor(t, dtype=torch.float32, device="cuda").contiguous()
+    xr = x.astype(np.float32).astype(np.float64)
+    tr = t.astype(np.float32).astype(np.float64)
+    vr = v.astype(np.float64)
+    m = np.zeros_like(vr)
+    s = np.zeros_like(vr)
+    for step in range(1, 4):
+        g = mlp.flatten(mlp.backward(mlp.unflatten(vr), xr, tr, bf16_round=True))
+        vr, m, s = mlp.adam(vr, g, m, s, step, lr)
+        lb.lb_mlp_train_step(net, n, X, T, lr)
+    out = np.zeros_like(v)
+    lb.lb_mlp_get_params(net, out)
+    moved = np.abs(vr - v) > 0.5 * lr  # entries whose gradient sign is not in doubt
+    assert moved.mean() > 0.5
+    assert np.abs(out - vr)[moved].max() < 0.05 * lr
+    lb.lb_mlp_destroy(net)
+
+
+def test_trained_network_reduces_subgrid_error():
+    # Pairs of runs of the method at 1x and 2x resolution (48^3 boxes at the
+    # number density of the 2e5-colloids-in-256^3 workload): train on 10
+    # boxes, judge on 3 held-out boxes.  The corrected colloid velocity is
+    # closer to the resolved one than the plain method's.
+    from paper_0707_1299_gb300 import learned
+    data = [learned.pair_samples(L=48, seed=s, T=400) for s in range(13)]
+    ftr = torch.cat([d[0] for d in data[:10]]).contiguous()
+    ltr = torch.cat([d[1] for d in data[:10]]).contiguous()
+    fte = torch.cat([d[0] for d in data[10:]]).contiguous()
+    lte = torch.cat([d[1] for d in data[10:]]).contiguous()
+    net, hist = learned.train(ftr, ltr, steps=1500, batch=2048, lr=2e-3)
+    assert hist[-1] < 0.9
+    ev = learned.evaluate(net, fte, lte)
+    assert ev["rms_corrected"] < 0.9 * ev["rms_plain"], ev
