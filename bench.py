@@ -211,11 +211,13 @@ def run_gpu(args, rank, world):
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    # each lattice's lb_step(1) launches exactly one kernel, k_collide (the
-    # points were spread by the preceding lb_velocity_at)
+    # lb_step(1) of the channel lattice (no points) launches exactly one
+    # kernel, k_collide: its events time that kernel alone.  The point
+    # lattices' lb_step(1) also clears their force tiles (their points were
+    # spread by the preceding lb_velocity_at), reported beside it.
     per_lat = [float(np.mean([ev[s][k][0].elapsed_time(ev[s][k][1]) for s in range(args.steps)]))
                for k in range(len(lats))]
-    coll_ms = float(np.mean(per_lat))
+    coll_ms = per_lat[0]
     step_ms = ms / args.steps
     mlups = world * 4 * V * args.steps / (ms * 1e-3) / 1e6
 
@@ -267,6 +269,9 @@ def run_gpu(args, rank, world):
     batched = None
     if rank == 0 and world == 1 and not args.no_batched:
         batched = batched_replicas()
+    learned = None
+    if rank == 0 and world == 1 and not args.no_learned:
+        learned = learned_correction()
     out = {
         "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True,
@@ -277,8 +282,8 @@ def run_gpu(args, rank, world):
                    "parallelism": f"replicas{world}"},
         "error": {"max_rel_velocity_vs_oracle": err, "steps": nsteps_done,
                   "case": "channel lattice vs exactly equivalent 1x1xL FP64 oracle column"},
-        "roofline": {"bound": "hbm", "kernel": f"k_collide<{prec}> (mean over the four lattices)",
-                     "launch_ms_per_lattice": {p.name: round(t, 5) for (p, _), t in zip(lats, per_lat)},
+        "roofline": {"bound": "hbm", "kernel": f"k_collide<{prec}> (channel lattice: 256^3, walls, one launch per lb_step)",
+                     "lb_step_ms_per_lattice": {p.name: round(t, 5) for (p, _), t in zip(lats, per_lat)},
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                      "bytes_per_site": 2 * 19 * BYTES[prec], "launch_ms": round(coll_ms, 5),
@@ -289,6 +294,7 @@ def run_gpu(args, rank, world):
         "clocks": clk,
         "per_precision": others,
         "batched": batched,
+        "learned": learned,
     }
     return out
 
@@ -402,6 +408,62 @@ def batched_replicas(steps=50, seq_steps=10):
                                    "steps": seq_steps}}
 
 
+def learned_correction(train_pairs=32, test_pairs=4, L_pair=64, T_pair=1000, steps=20):
+    """The learned correction of the colloid velocity: trained on ~1e5
+    samples of 1x/2x run pairs of the method (64^3 / 128^3 boxes at the
+    number density of the workload below), judged on held-out pairs; then
+    the 256^3 FP32 box with 2e5 colloids (seed 5, force 1e-6, a = 0.117)
+    stepped with the plain update and with the corrected one."""
+    import torch
+    from paper_0707_1299_gb300 import lb, learned, workloads as W
+    t0 = time.perf_counter()
+    data = [learned.pair_samples(L=L_pair, seed=s, T=T_pair) for s in range(train_pairs + test_pairs)]
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    ftr = torch.cat([d[0] for d in data[:train_pairs]]).contiguous()
+    ltr = torch.cat([d[1] for d in data[:train_pairs]]).contiguous()
+    fte = torch.cat([d[0] for d in data[train_pairs:]]).contiguous()
+    lte = torch.cat([d[1] for d in data[train_pairs:]]).contiguous()
+    t0 = time.perf_counter()
+    net, hist = learned.train(ftr, ltr, steps=4000, batch=4096, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    ev = learned.evaluate(net, fte, lte)
+    prob = W.colloids(L=256, n=200000, seed=5, force=1e-6)
+    g = lb.Lattice(prob.grid, prob.tau_s, prob.tau_b, lb.LB_F32)
+    g.set_colloid_aL(lb.lb_compute_aL(prob.grid, [128.5] * 3, [0, 0, 1]))
+    ps = prob.points[0]
+    g.add_point_forces(ps.kind, ps.pos, ps.F, ps.param)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    out = {}
+    for name, attach in (("plain", None), ("corrected", net)):
+        lb.lb_set_colloid_correction(g.ctx, attach)
+        g.step(3)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        g.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"ms_per_step": round(ms, 4), "value": round(256 ** 3 / (ms * 1e-3) / 1e6, 1)}
+    lb.lb_set_colloid_correction(g.ctx, None)
+    g.close()
+    lb.lb_mlp_destroy(net)
+    torch.cuda.empty_cache()
+    return {"workload": "256^3 FP32, 2e5 colloids (seed 5), force 1e-6, a = 0.117", "unit": "MLUPS",
+            "plain": out["plain"], "corrected": out["corrected"],
+            "training": {"samples": int(ftr.shape[0]), "pairs": f"{train_pairs} x ({L_pair}^3 T={T_pair}, "
+                                                                 f"{2 * L_pair}^3 T={4 * T_pair})",
+                         "adam_steps": 4000, "generation_s": round(t_gen, 2), "train_s": round(t_train, 2),
+                         "final_loss_rel": round(hist[-1], 4)},
+            "velocity_error_vs_2x": {"held_out_samples": int(fte.shape[0]),
+                                     "rms_plain_over_v0": round(ev["rms_plain"], 6),
+                                     "rms_corrected_over_v0": round(ev["rms_corrected"], 6),
+                                     "gain": round(ev["gain"], 3)}}
+
+
 # ---------------------------------------------------------- oracle (CPU)
 def oracle_sample_step(lats):
     for o in lats:
@@ -476,6 +538,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-precision", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 

@@ -220,6 +220,14 @@ lb_status lb_mlp_grad(lb_mlp *net, long long n, const float *feat, const float *
 lb_status lb_mlp_train_step(lb_mlp *net, long long n, const float *feat, const float *target, float lr,
                             float *sse);
 
+/* Attach (net != NULL) or detach the learned correction to the colloid
+ * update of lb_step: each mobile colloid then moves by
+ *   U + y |F| / (6 pi eta a),  y = net(features of all points),
+ * U the colloid velocity of lb_colloid_velocity.  The network is used, not
+ * owned (keep it alive while attached; do not use it concurrently on
+ * another stream).  Without a network the plain method of Sec. IV runs. */
+lb_status lb_set_colloid_correction(lb_ctx *ctx, lb_mlp *net);
+
 /* ------------------------------------------------------------------------
  * Batches: independent lattices (replicas of uneven sizes, e.g. many small
  * sedimentation boxes) advanced together.  Each phase of a time step

@@ -27,7 +27,9 @@ constexpr int BW = 4;  // warps (tiles) per work item of the collide kernel
 struct Entry {
     void* pop[2];              // population buffers: index = parity ^ cur0
     void* floc;
-    unsigned char* flags;
+    unsigned* flags;
+    unsigned* tile_list;
+    unsigned* tile_ctr;
     double* pos;
     double* force;
     double* radius;
@@ -115,7 +117,7 @@ kb_collide(const Entry* __restrict__ ent, const long long* __restrict__ gbegin, 
         const int x = tx * TILE_X + lane;
         if (y >= g.ny) continue;  // uniform per warp
         const unsigned tile = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.ntx + (unsigned)tx;
-        const unsigned char fl = E.flags[tile];
+        const unsigned fl = __ldg(E.flags + tile);
         const unsigned V = (unsigned)g.V;
         const int b = parity ^ E.cur0;
         if (x < g.nx) {
@@ -127,7 +129,7 @@ kb_collide(const Entry* __restrict__ ent, const long long* __restrict__ gbegin, 
             }
             const Nbr n = neighbours(g, x, y, z);
             const unsigned site = n.c + n.x;
-            T* floc = (T*)E.floc;
+            const T* floc = (const T*)E.floc;
             if (is_solid(g, z)) {
 #pragma unroll
                 for (int i = 0; i < NQ; ++i) Store<S>::st(dst.p[i], site, T(0), 0u);
@@ -150,18 +152,24 @@ kb_collide(const Entry* __restrict__ ent, const long long* __restrict__ gbegin, 
                 unsigned rn = rng_seed(site ^ (unsigned)(e * 0x27d4eb2d), seed);
 #pragma unroll
                 for (int i = 0; i < NQ; ++i) Store<S>::st(dst.p[i], site, o[i], rng_next(rn));
-                // clear the field only now: a store to a line whose load is
-                // still in flight would hold the warp until that load returns
-                if (fl) {
-                    floc[site] = T(0);
-                    floc[V + site] = T(0);
-                    floc[2 * V + site] = T(0);
-                }
             }
         }
-        if (fl) {
-            __syncwarp();
-            if (lane == 0) E.flags[tile] = 0;
+    }
+}
+
+// Clear every member's consumed force tiles: grid (blocks per member,
+// members); the last block of a member resets that member's list.
+template <typename T>
+__global__ void __launch_bounds__(256) kb_clear(const Entry* __restrict__ ent) {
+    const Entry& E = ent[blockIdx.y];
+    clear_listed_tiles<T>(E.g, (T*)E.floc, E.flags, E.tile_list, E.tile_ctr, blockIdx.x * blockDim.x + threadIdx.x,
+                          gridDim.x * blockDim.x);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&E.tile_ctr[1], 1u) == gridDim.x - 1) {
+            E.tile_ctr[0] = 0u;
+            E.tile_ctr[1] = 0u;
         }
     }
 }
@@ -189,7 +197,7 @@ kb_spread(const Entry* __restrict__ ent, const long long* __restrict__ pbegin, i
     atomicAdd(floc + site, (T)E.force[3 * s] * w);
     atomicAdd(floc + g.V + site, (T)E.force[3 * s + 1] * w);
     atomicAdd(floc + 2 * g.V + site, (T)E.force[3 * s + 2] * w);
-    E.flags[((long long)z * g.ny + y) * g.ntx + x / TILE_X] = 1;
+    mark_tile(E.flags, E.tile_list, E.tile_ctr, (unsigned)(((long long)z * g.ny + y) * g.ntx + x / TILE_X));
 }
 
 __global__ void kb_tick(unsigned* step_counter) { *step_counter += 1u; }
@@ -304,6 +312,7 @@ cudaError_t launch_step(lb_batch* b, int p, int blocks) {
     }
     kb_collide<S><<<blocks, dim3(32, BW), 0, b->stream>>>(b->d_ent, b->d_gbegin, b->d_work, b->n, b->total_groups, p,
                                                           b->d_step);
+    if (b->total_pts > 0) kb_clear<T><<<dim3(8, b->n), 256, 0, b->stream>>>(b->d_ent);
     if (sizeof(S) == 2) kb_tick<<<1, 1, 0, b->stream>>>(b->d_step);
     return cudaGetLastError();
 }
@@ -334,7 +343,7 @@ cudaError_t launch_collide_any(lb_batch* b, int blocks) {
 }
 
 int launches_per_step(const lb_batch* b) {
-    return 1 + (b->total_pts > 0 ? 1 : 0) + (b->n_mobile > 0 ? 1 : 0) + (b->prec >= LB_F16S ? 1 : 0);
+    return 1 + (b->total_pts > 0 ? 2 : 0) + (b->n_mobile > 0 ? 1 : 0) + (b->prec >= LB_F16S ? 1 : 0);
 }
 
 }  // namespace
@@ -364,6 +373,8 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
         E.pop[1] = c->f[1];
         E.floc = c->floc;
         E.flags = c->flags;
+        E.tile_list = c->tile_list;
+        E.tile_ctr = c->tile_ctr;
         E.pos = c->pos;
         E.force = c->force;
         E.radius = c->radius;

@@ -204,14 +204,17 @@ lb_status lb_create(lb_ctx** out, const int grid[3], double tau_shear, double ta
     if (e == cudaSuccess) e = cudaMalloc(&c->f[0], sb * lbk::NQ * (size_t)V);
     if (e == cudaSuccess) e = cudaMalloc(&c->f[1], sb * lbk::NQ * (size_t)V);
     if (e == cudaSuccess) e = cudaMalloc(&c->floc, ab * 3 * (size_t)V);
-    if (e == cudaSuccess) e = cudaMalloc(&c->flags, (size_t)c->geom.ntiles);
+    if (e == cudaSuccess) e = cudaMalloc(&c->flags, sizeof(unsigned) * (size_t)c->geom.ntiles);
+    if (e == cudaSuccess) e = cudaMalloc(&c->tile_list, sizeof(unsigned) * (size_t)c->geom.ntiles);
+    if (e == cudaSuccess) e = cudaMalloc(&c->tile_ctr, sizeof(unsigned) * 2);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->tile_ctr, 0, sizeof(unsigned) * 2, c->stream);
     if (e == cudaSuccess) e = cudaMalloc(&c->fsum, sizeof(double) * 3);
     if (e == cudaSuccess) e = cudaMalloc(&c->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->partials, sizeof(double) * 4 * (size_t)lbk::moment_blocks(c->geom));
     if (e == cudaSuccess) e = cudaMalloc(&c->totals_dev, sizeof(double) * 4);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->f[0], 0, sb * lbk::NQ * (size_t)V, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->floc, 0, ab * 3 * (size_t)V, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, (size_t)c->geom.ntiles, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, sizeof(unsigned) * (size_t)c->geom.ntiles, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->fsum, 0, sizeof(double) * 3, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -237,6 +240,8 @@ void lb_destroy(lb_ctx* c) {
     cudaFree(c->f[1]);
     cudaFree(c->floc);
     cudaFree(c->flags);
+    cudaFree(c->tile_list);
+    cudaFree(c->tile_ctr);
     cudaFree(c->pos);
     cudaFree(c->force);
     cudaFree(c->radius);
@@ -246,6 +251,10 @@ void lb_destroy(lb_ctx* c) {
     cudaFree(c->partials);
     cudaFree(c->totals_dev);
     cudaFree(c->stage);
+    cudaFree(c->corr_v);
+    cudaFree(c->corr_feat);
+    cudaFree(c->corr_y);
+    cudaFree(c->corr_ws);
     delete c;
 }
 
@@ -364,14 +373,66 @@ lb_status lb_set_positions(lb_ctx* c, const double* pos) {
     return LB_OK;
 }
 
+namespace {
+lb_status ensure_corr_buffers(lb_ctx* c) {
+    const int box[3] = {c->geom.nx, c->geom.ny, c->geom.nz};
+    const size_t ws = lbk::mlp_features_ws_ints(c->npts, box);
+    if ((size_t)c->npts > c->corr_cap) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->corr_v);
+        cudaFree(c->corr_feat);
+        cudaFree(c->corr_y);
+        c->corr_v = nullptr;
+        c->corr_feat = nullptr;
+        c->corr_y = nullptr;
+        c->corr_cap = 0;
+        const size_t n = (size_t)c->npts;
+        LB_CUDA(cudaMalloc(&c->corr_v, sizeof(double) * 3 * n), "correction buffers");
+        LB_CUDA(cudaMalloc(&c->corr_feat, sizeof(float) * 27 * n), "correction buffers");
+        LB_CUDA(cudaMalloc(&c->corr_y, sizeof(float) * 3 * n), "correction buffers");
+        c->corr_cap = n;
+    }
+    if (ws > c->corr_ws_ints) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->corr_ws);
+        c->corr_ws = nullptr;
+        c->corr_ws_ints = 0;
+        LB_CUDA(cudaMalloc(&c->corr_ws, sizeof(int) * ws), "correction workspace");
+        c->corr_ws_ints = ws;
+    }
+    return LB_OK;
+}
+}  // namespace
+
+lb_status lb_set_colloid_correction(lb_ctx* c, lb_mlp* net) {
+    if (!c) return LB_ERR_ARG;
+    c->corr = net;
+    c->version++;
+    return LB_OK;
+}
+
 lb_status lb_step(lb_ctx* c, int nsteps) {
     if (!c) return LB_ERR_ARG;
     if (nsteps < 0) return fail(c, LB_ERR_ARG, "lb_step: nsteps < 0");
+    if (c->corr && c->n_mobile > 0) {
+        lb_status st = ensure_corr_buffers(c);
+        if (st != LB_OK) return st;
+    }
+    const int box[3] = {c->geom.nx, c->geom.ny, c->geom.nz};
     for (int s = 0; s < nsteps; ++s) {
         lb_status st = ensure_field(c);
         if (st != LB_OK) return st;
-        if (c->n_mobile > 0) LB_CUDA(lbk::launch_gather(c, c->npts, nullptr, nullptr, true), "gather/update kernel");
+        if (c->n_mobile > 0 && c->corr) {  // colloid update with the learned correction
+            LB_CUDA(lbk::launch_gather(c, c->npts, c->pos, c->corr_v, false), "gather kernel");
+            LB_CUDA(lbk::mlp_features(c->npts, c->pos, box, c->corr_feat, c->corr_ws, c->stream), "feature kernels");
+            LB_CUDA(lbk::mlp_forward(c->corr, c->npts, c->corr_feat, c->corr_y, c->stream), "forward kernel");
+            LB_CUDA(lbk::launch_corrected_update(c), "corrected update kernel");
+            c->launches += 5;
+        } else if (c->n_mobile > 0) {
+            LB_CUDA(lbk::launch_gather(c, c->npts, nullptr, nullptr, true), "gather/update kernel");
+        }
         LB_CUDA(lbk::launch_collide(c), "collide-stream kernel");
+        if (c->field_ready) LB_CUDA(lbk::launch_clear_tiles(c), "tile clearing kernel");
         c->cur ^= 1;
         c->field_ready = false;
     }

@@ -36,6 +36,37 @@ __device__ __forceinline__ bool is_solid(const Geom& g, int z) {
     return z == g.wall_lo || z == g.wall_hi;
 }
 
+// Mark the tile of a site as holding spread force; the first marker also
+// appends the tile to the list that the clearing kernel walks.
+__device__ __forceinline__ void mark_tile(unsigned* __restrict__ flags, unsigned* __restrict__ list,
+                                          unsigned* __restrict__ ctr, unsigned tile) {
+    if (flags[tile] == 0u && atomicExch(&flags[tile], 1u) == 0u) list[atomicAdd(&ctr[0], 1u)] = tile;
+}
+
+// Zero the force field of every listed tile and its flag; the last block to
+// finish resets the list.  Runs after the collide kernel has consumed the
+// field, so no load of the field is in flight anywhere.
+template <typename T>
+__device__ __forceinline__ void clear_listed_tiles(const Geom& g, T* __restrict__ floc, unsigned* __restrict__ flags,
+                                                   const unsigned* __restrict__ list, unsigned* __restrict__ ctr,
+                                                   unsigned first, unsigned stride) {
+    const unsigned n = *(volatile unsigned*)&ctr[0];
+    const unsigned V = (unsigned)g.V;
+    for (unsigned i = first; i < n * 32u; i += stride) {
+        const unsigned tile = list[i >> 5], lane = i & 31u;
+        const unsigned tx = tile % (unsigned)g.ntx, r = tile / (unsigned)g.ntx;
+        const unsigned y = r % (unsigned)g.ny, z = r / (unsigned)g.ny;
+        const unsigned x = tx * TILE_X + lane;
+        if (x < (unsigned)g.nx) {
+            const unsigned site = z * g.plane + y * (unsigned)g.nx + x;
+            floc[site] = T(0);
+            floc[V + site] = T(0);
+            floc[2 * V + site] = T(0);
+        }
+        if (lane == 0) flags[tile] = 0u;
+    }
+}
+
 // ----------------------------------------------------------- storage types
 // df is stored as S and handled in arithmetic type T.  The half-precision
 // formats store df * scale (a power of two) to keep df out of subnormals.
@@ -154,31 +185,31 @@ __device__ __forceinline__ void pull19(const Pops<S>& src, const Nbr& n, typenam
     f[8] = St::ld(src.p[8], yp + n.xp);
     f[9] = St::ld(src.p[9], yp + n.xm);
     f[10] = St::ld(src.p[10], ym + n.xp);
-    if (!WALLS || !n.solid_zm) {
+    if (!WALLS) {
         f[5] = St::ld(src.p[5], zm + n.x);
         f[11] = St::ld(src.p[11], zm + n.xm);
         f[14] = St::ld(src.p[14], zm + n.xp);
         f[15] = St::ld(src.p[15], zm + n.dym + n.x);
         f[18] = St::ld(src.p[18], zm + n.dyp + n.x);
-    } else {
-        f[5] = St::ld(src.p[6], own);
-        f[11] = St::ld(src.p[12], own);
-        f[14] = St::ld(src.p[13], own);
-        f[15] = St::ld(src.p[16], own);
-        f[18] = St::ld(src.p[17], own);
-    }
-    if (!WALLS || !n.solid_zp) {
         f[6] = St::ld(src.p[6], zp + n.x);
         f[12] = St::ld(src.p[12], zp + n.xp);
         f[13] = St::ld(src.p[13], zp + n.xm);
         f[16] = St::ld(src.p[16], zp + n.dyp + n.x);
         f[17] = St::ld(src.p[17], zp + n.dym + n.x);
     } else {
-        f[6] = St::ld(src.p[5], own);
-        f[12] = St::ld(src.p[11], own);
-        f[13] = St::ld(src.p[14], own);
-        f[16] = St::ld(src.p[15], own);
-        f[17] = St::ld(src.p[18], own);
+        // one load per population: a solid source selects the opposite
+        // population of the site itself (uniform across the warp)
+        const bool bm = n.solid_zm, bp = n.solid_zp;
+        f[5] = St::ld(bm ? src.p[6] : src.p[5], bm ? own : zm + n.x);
+        f[11] = St::ld(bm ? src.p[12] : src.p[11], bm ? own : zm + n.xm);
+        f[14] = St::ld(bm ? src.p[13] : src.p[14], bm ? own : zm + n.xp);
+        f[15] = St::ld(bm ? src.p[16] : src.p[15], bm ? own : zm + n.dym + n.x);
+        f[18] = St::ld(bm ? src.p[17] : src.p[18], bm ? own : zm + n.dyp + n.x);
+        f[6] = St::ld(bp ? src.p[5] : src.p[6], bp ? own : zp + n.x);
+        f[12] = St::ld(bp ? src.p[11] : src.p[12], bp ? own : zp + n.xp);
+        f[13] = St::ld(bp ? src.p[14] : src.p[13], bp ? own : zp + n.xm);
+        f[16] = St::ld(bp ? src.p[15] : src.p[16], bp ? own : zp + n.dyp + n.x);
+        f[17] = St::ld(bp ? src.p[18] : src.p[17], bp ? own : zp + n.dym + n.x);
     }
 }
 

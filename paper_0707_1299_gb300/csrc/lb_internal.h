@@ -9,6 +9,8 @@
 
 #include "lb_device.cuh"
 
+struct lb_mlp;
+
 struct lb_ctx {
     lbk::Geom geom;
     int prec;                 // lb_precision
@@ -23,7 +25,9 @@ struct lb_ctx {
     void* f[2];               // population buffers (19 V elements of the storage type)
     int cur;                  // index of the buffer holding the current state
     void* floc;               // localised force field, 3 V elements of the arithmetic type
-    unsigned char* flags;     // one flag per 32-site x-row tile: tile holds nonzero floc
+    unsigned* flags;          // one flag per 32-site x-row tile: tile holds nonzero floc
+    unsigned* tile_list;      // the flagged tiles, in the order they were flagged
+    unsigned* tile_ctr;       // [number of listed tiles, blocks of the clearing kernel done]
     bool field_ready;         // floc holds the forces at the current positions
 
     // monopoles after expansion (device, xyz interleaved)
@@ -43,6 +47,14 @@ struct lb_ctx {
     // staging for host pointers (grown on demand)
     void* stage;
     size_t stage_bytes;
+
+    // learned correction of the colloid velocity (optional)
+    lb_mlp* corr;
+    double* corr_v;           // interpolated velocity at every point (3 npts)
+    float* corr_feat;         // features (27 npts)
+    float* corr_y;            // network output (3 npts)
+    int* corr_ws;             // feature workspace
+    size_t corr_cap, corr_ws_ints;
 
     long long launches;       // kernels launched so far
     unsigned seed;            // seed of the stochastic rounding of the 16-bit formats
@@ -72,8 +84,13 @@ cudaError_t launch_set_positions(lb_ctx* c, const double* pos);
 cudaError_t launch_convert_out(lb_ctx* c, double* df);
 cudaError_t launch_convert_in(lb_ctx* c, const double* df);
 cudaError_t launch_clear_field(lb_ctx* c);
+cudaError_t launch_clear_tiles(lb_ctx* c);
 template <typename T>
 UForce<T> uniform_force(const lb_ctx* c);
+cudaError_t launch_corrected_update(lb_ctx* c);
+size_t mlp_features_ws_ints(long long n, const int box[3]);
+cudaError_t mlp_features(long long n, const double* pos, const int box[3], float* feat, int* ws, cudaStream_t st);
+cudaError_t mlp_forward(const lb_mlp* net, long long n, const float* feat, float* out, cudaStream_t st);
 cudaError_t compute_inv_aL(const int grid[3], const double R[3], const double dir[3], double* inv_aL);
 
 size_t storage_bytes(int prec);

@@ -76,10 +76,14 @@ static dim3 site_grid(const Geom& g) {
 // ------------------------------------------------------------ k_collide
 // NY consecutive y rows per thread (all loads of the NY sites issued
 // first).  The half format is handled in its scaled units throughout.
-template <typename S, bool WALLS, int NY>
-__global__ void __launch_bounds__(CS_THREADS, (NY == 1 ? 8 : 4))
-k_collide(const Pops<S> src, const Pops<S> dst, typename Store<S>::T* __restrict__ floc,
-          unsigned char* __restrict__ flags, Geom g, Coef<typename Store<S>::T> k,
+// Occupancy bound (blocks of 128 threads per SM), swept on GB300 at 256^3:
+// the 4- and 2-byte formats are fastest at 12 (42 registers; 8-10 were
+// 2-10 % slower, 14 spills); FP64 at 8.
+// FIELD = false: a lattice without point forces (no flag or field access).
+template <typename S, bool WALLS, int NY, bool FIELD>
+__global__ void __launch_bounds__(CS_THREADS, (NY == 1 ? (sizeof(S) == 8 ? 8 : 12) : 4))
+k_collide(const Pops<S> src, const Pops<S> dst, const typename Store<S>::T* __restrict__ floc,
+          const unsigned* __restrict__ flags, Geom g, Coef<typename Store<S>::T> k,
           UForce<typename Store<S>::T> fu, float scale, float inv_scale, unsigned seed) {
     using T = typename Store<S>::T;
     constexpr bool SC = Store<S>::kScaled;
@@ -88,12 +92,11 @@ k_collide(const Pops<S> src, const Pops<S> dst, typename Store<S>::T* __restrict
     const int z = blockIdx.z, lane = threadIdx.x;
     const int x = blockIdx.x * TILE_X + lane;
     const unsigned V = (unsigned)g.V;
-    unsigned tile[NY];
-    unsigned char fl[NY];
+    unsigned fl[NY];
 #pragma unroll
     for (int r = 0; r < NY; ++r) {
-        tile[r] = ((unsigned)z * (unsigned)g.ny + (unsigned)(y0 + r)) * (unsigned)g.ntx + blockIdx.x;
-        fl[r] = (y0 + r < g.ny) ? flags[tile[r]] : (unsigned char)0;
+        const unsigned tile = ((unsigned)z * (unsigned)g.ny + (unsigned)(y0 + r)) * (unsigned)g.ntx + blockIdx.x;
+        fl[r] = (FIELD && y0 + r < g.ny) ? __ldg(flags + tile) : 0u;
     }
 
     if (x < g.nx) {
@@ -119,7 +122,7 @@ k_collide(const Pops<S> src, const Pops<S> dst, typename Store<S>::T* __restrict
                 if (y0 + r >= g.ny) break;
                 const unsigned site = n[r].c + n[r].x;
                 T Fx = fu.F[0], Fy = fu.F[1], Fz = fu.F[2];
-                if (fl[r]) {  // after the population loads, so both are in flight together
+                if (FIELD && fl[r]) {  // after the population loads, so both are in flight together
                     const T s = SC ? (T)scale : T(1);
                     Fx += floc[site] * s;
                     Fy += floc[V + site] * s;
@@ -130,29 +133,34 @@ k_collide(const Pops<S> src, const Pops<S> dst, typename Store<S>::T* __restrict
                 unsigned rn = rng_seed(site, seed);
 #pragma unroll
                 for (int i = 0; i < NQ; ++i) Store<S>::st(dst.p[i], site, o[i], rng_next(rn));
-                // clear the field only now: a store to a line whose load is
-                // still in flight would hold the warp until that load returns
-                if (fl[r]) {
-                    floc[site] = T(0);
-                    floc[V + site] = T(0);
-                    floc[2 * V + site] = T(0);
-                }
             }
         }
     }
-#pragma unroll
-    for (int r = 0; r < NY; ++r)
-        if (fl[r]) {
-            __syncwarp();
-            if (lane == 0) flags[tile[r]] = 0;
+}
+
+// Clear the consumed force tiles (k_clear_tiles runs after k_collide): the
+// collide kernel only reads the field, so it never stores to a line whose
+// load may still be in flight.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_clear_tiles(Geom g, T* __restrict__ floc, unsigned* __restrict__ flags, const unsigned* __restrict__ list,
+              unsigned* __restrict__ ctr) {
+    clear_listed_tiles<T>(g, floc, flags, list, ctr, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&ctr[1], 1u) == gridDim.x - 1) {  // last block: reset the list
+            ctr[0] = 0u;
+            ctr[1] = 0u;
         }
+    }
 }
 
 // ------------------------------------------------------------- k_spread
 template <typename T, bool WALLS>
 __global__ void __launch_bounds__(256)
 k_spread(const double* __restrict__ pos, const double* __restrict__ force, int npts, T* __restrict__ floc,
-         unsigned char* __restrict__ flags, Geom g) {
+         unsigned* __restrict__ flags, unsigned* __restrict__ list, unsigned* __restrict__ ctr, Geom g) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)npts * 64) return;
     const int s = (int)(t >> 6), node = (int)(t & 63);
@@ -170,7 +178,7 @@ k_spread(const double* __restrict__ pos, const double* __restrict__ force, int n
     atomicAdd(floc + site, (T)force[3 * s] * w);
     atomicAdd(floc + g.V + site, (T)force[3 * s + 1] * w);
     atomicAdd(floc + 2 * g.V + site, (T)force[3 * s + 2] * w);
-    flags[((long long)z * g.ny + y) * g.ntx + x / TILE_X] = 1;
+    mark_tile(flags, list, ctr, (unsigned)(((long long)z * g.ny + y) * g.ntx + x / TILE_X));
 }
 
 // Position wrapped into [0, n).
@@ -311,6 +319,23 @@ __global__ void k_faxen(int n, const double* __restrict__ F, const double* __res
     if (t >= n) return;
     const double c = (1.0 / a[t] - inv_aL) * inv_6pi_eta;
     for (int k = 0; k < 3; ++k) U[3 * t + k] += F[3 * t + k] * c;
+}
+
+// Colloid update with the learned correction: R += v(R) + F (1/a - 1/a_L) /
+// (6 pi eta) + y |F| / (6 pi eta a), y the network output in units of the
+// Stokes velocity of the colloid.
+__global__ void k_corrected_update(int n, const double* __restrict__ v, const float* __restrict__ y,
+                                   const double* __restrict__ F, const double* __restrict__ a,
+                                   const int* __restrict__ mobile, double inv_aL, double inv_6pi_eta, Geom g,
+                                   double* __restrict__ pos) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n || !mobile[t]) return;
+    const double f0 = F[3 * t], f1 = F[3 * t + 1], f2 = F[3 * t + 2];
+    const double c = (1.0 / a[t] - inv_aL) * inv_6pi_eta;
+    const double v0 = sqrt(f0 * f0 + f1 * f1 + f2 * f2) * inv_6pi_eta / a[t];
+    const int nn[3] = {g.nx, g.ny, g.nz};
+    for (int k = 0; k < 3; ++k)
+        pos[3 * t + k] = wrap_pos(pos[3 * t + k] + v[3 * t + k] + F[3 * t + k] * c + (double)y[3 * t + k] * v0, nn[k]);
 }
 
 // ---------------------------------------------------- point bookkeeping
@@ -509,12 +534,19 @@ static cudaError_t collide_t(lb_ctx* c) {
     constexpr int NY = 1;
     const dim3 grid((unsigned)c->geom.ntx, (unsigned)((c->geom.ny + CS_WARPS * NY - 1) / (CS_WARPS * NY)),
                     (unsigned)c->geom.nz);
-    if (has_walls(c))
-        k_collide<S, true, NY><<<grid, site_block(), 0, c->stream>>>(src, dst, (T*)c->floc, c->flags, c->geom, k, fu,
-                                                                   c->scale, c->inv_scale, c->seed);
-    else
-        k_collide<S, false, NY><<<grid, site_block(), 0, c->stream>>>(src, dst, (T*)c->floc, c->flags, c->geom, k, fu,
-                                                                    c->scale, c->inv_scale, c->seed);
+    const T* floc = (const T*)c->floc;
+    const bool field = c->npts > 0;
+#define LB_COLLIDE(W, FD)                                                                                       \
+    k_collide<S, W, NY, FD><<<grid, site_block(), 0, c->stream>>>(src, dst, floc, c->flags, c->geom, k, fu, c->scale, \
+                                                                c->inv_scale, c->seed)
+    if (has_walls(c)) {
+        if (field) LB_COLLIDE(true, true);
+        else LB_COLLIDE(true, false);
+    } else {
+        if (field) LB_COLLIDE(false, true);
+        else LB_COLLIDE(false, false);
+    }
+#undef LB_COLLIDE
     c->seed = c->seed * 747796405u + 2891336453u;  // next step's rounding seed
     c->launches++;
     return cudaGetLastError();
@@ -534,9 +566,11 @@ static cudaError_t spread_t(lb_ctx* c) {
     const long long threads = (long long)c->npts * 64;
     const unsigned int blocks = (unsigned int)((threads + 255) / 256);
     if (has_walls(c))
-        k_spread<T, true><<<blocks, 256, 0, c->stream>>>(c->pos, c->force, c->npts, (T*)c->floc, c->flags, c->geom);
+        k_spread<T, true><<<blocks, 256, 0, c->stream>>>(c->pos, c->force, c->npts, (T*)c->floc, c->flags,
+                                                          c->tile_list, c->tile_ctr, c->geom);
     else
-        k_spread<T, false><<<blocks, 256, 0, c->stream>>>(c->pos, c->force, c->npts, (T*)c->floc, c->flags, c->geom);
+        k_spread<T, false><<<blocks, 256, 0, c->stream>>>(c->pos, c->force, c->npts, (T*)c->floc, c->flags,
+                                                           c->tile_list, c->tile_ctr, c->geom);
     c->launches++;
     return cudaGetLastError();
 }
@@ -612,6 +646,16 @@ cudaError_t launch_moments(lb_ctx* c, double* rho, double* u, bool want_totals) 
     }
 }
 
+cudaError_t launch_corrected_update(lb_ctx* c) {
+    const double eta = c->tau_s / 3.0;
+    const double inv_aL = isinf(c->a_L) ? 0.0 : 1.0 / c->a_L;
+    k_corrected_update<<<(c->npts + 127) / 128, 128, 0, c->stream>>>(c->npts, c->corr_v, c->corr_y, c->force,
+                                                                    c->radius, c->mobile, inv_aL,
+                                                                    1.0 / (6.0 * M_PI * eta), c->geom, c->pos);
+    c->launches++;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_faxen(lb_ctx* c, int n, const double* F, const double* a, double* U) {
     if (n == 0) return cudaSuccess;
     const double eta = c->tau_s / 3.0;
@@ -676,8 +720,24 @@ cudaError_t launch_convert_in(lb_ctx* c, const double* df) {
 
 cudaError_t launch_clear_field(lb_ctx* c) {
     cudaError_t e = cudaMemsetAsync(c->floc, 0, 3 * (size_t)c->geom.V * arith_bytes(c->prec), c->stream);
-    if (e != cudaSuccess) return e;
-    return cudaMemsetAsync(c->flags, 0, (size_t)c->geom.ntiles, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, sizeof(unsigned) * (size_t)c->geom.ntiles, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->tile_ctr, 0, sizeof(unsigned) * 2, c->stream);
+    return e;
+}
+
+cudaError_t launch_clear_tiles(lb_ctx* c) {
+    // a point flags at most 32 tiles (4 x 4 node rows, two x-tiles each):
+    // size the grid for that many 32-site tiles, at most 2 blocks per SM
+    const long long lanes = std::min<long long>((long long)c->npts * 32 * 32, c->geom.ntiles * 32);
+    const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>(152 * 2, (lanes + 255) / 256));
+    if (c->prec == LB_F64)
+        k_clear_tiles<double><<<blocks, 256, 0, c->stream>>>(c->geom, (double*)c->floc, c->flags, c->tile_list,
+                                                             c->tile_ctr);
+    else
+        k_clear_tiles<float><<<blocks, 256, 0, c->stream>>>(c->geom, (float*)c->floc, c->flags, c->tile_list,
+                                                            c->tile_ctr);
+    c->launches++;
+    return cudaGetLastError();
 }
 
 cudaError_t compute_inv_aL(const int grid[3], const double R[3], const double dir[3], double* inv_aL) {

@@ -371,6 +371,47 @@ int grid_for(long long n) {
 
 }  // namespace
 
+namespace lbk {
+
+size_t mlp_features_ws_ints(long long n, const int box[3]) {
+    long long m = 1;
+    for (int a = 0; a < 3; ++a) m *= (box[a] / (int)R_CUT > 0 ? box[a] / (int)R_CUT : 1);
+    return (size_t)(m + (m + 1) + m + 2 * n);  // count, start, cursor, cell, sorted
+}
+
+cudaError_t mlp_features(long long n, const double* pos, const int box[3], float* feat, int* ws, cudaStream_t st) {
+    int3 nc;
+    nc.x = box[0] / (int)R_CUT > 0 ? box[0] / (int)R_CUT : 1;
+    nc.y = box[1] / (int)R_CUT > 0 ? box[1] / (int)R_CUT : 1;
+    nc.z = box[2] / (int)R_CUT > 0 ? box[2] / (int)R_CUT : 1;
+    const long long m = (long long)nc.x * nc.y * nc.z;
+    int* count = ws;
+    int* start = count + m;
+    int* cursor = start + m + 1;
+    int* cell = cursor + m;
+    int* sorted = cell + n;
+    Geom g{};
+    g.nx = box[0];
+    g.ny = box[1];
+    g.nz = box[2];
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * m, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, sizeof(int) * m, st);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    kf_count<<<blocks, 256, 0, st>>>(pos, n, g, nc, count, cell);
+    kf_scan<<<1, 1024, 0, st>>>(count, (int)m, start);
+    kf_fill<<<blocks, 256, 0, st>>>(n, cell, start, cursor, sorted);
+    kf_knn<<<blocks, 256, 0, st>>>(pos, n, g, nc, start, sorted, feat);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_forward(const lb_mlp* net, long long n, const float* feat, float* out, cudaStream_t st) {
+    km_forward<<<grid_for(n), NT, net->smem_fwd, st>>>(net->p, n, feat, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbk
+
 extern "C" {
 
 int lb_mlp_num_params(void) { return NPARAM; }
@@ -433,12 +474,7 @@ lb_status lb_mlp_features(lb_mlp* net, long long n, const double* pos, const int
     if (!net || n < 0 || (n && (!pos || !feat)) || !box) return mfail(net, LB_ERR_ARG, "lb_mlp_features: bad argument");
     if (box[0] < 1 || box[1] < 1 || box[2] < 1) return mfail(net, LB_ERR_ARG, "lb_mlp_features: bad box");
     if (n == 0) return LB_OK;
-    int3 nc;
-    nc.x = box[0] / (int)R_CUT > 0 ? box[0] / (int)R_CUT : 1;
-    nc.y = box[1] / (int)R_CUT > 0 ? box[1] / (int)R_CUT : 1;
-    nc.z = box[2] / (int)R_CUT > 0 ? box[2] / (int)R_CUT : 1;
-    const long long m = (long long)nc.x * nc.y * nc.z;
-    const size_t need = (size_t)(m + (m + 1) + m + 2 * n);  // count, start, cursor, cell, sorted
+    const size_t need = lbk::mlp_features_ws_ints(n, box);
     if (need > net->ws_ints) {
         cudaFree(net->ws);
         net->ws = nullptr;
@@ -446,31 +482,14 @@ lb_status lb_mlp_features(lb_mlp* net, long long n, const double* pos, const int
         LB_MCUDA(cudaMalloc(&net->ws, sizeof(int) * need), "feature workspace");
         net->ws_ints = need;
     }
-    int* count = net->ws;
-    int* start = count + m;
-    int* cursor = start + m + 1;
-    int* cell = cursor + m;
-    int* sorted = cell + n;
-    Geom g{};
-    g.nx = box[0];
-    g.ny = box[1];
-    g.nz = box[2];
-    LB_MCUDA(cudaMemsetAsync(count, 0, sizeof(int) * m, net->stream), "memset");
-    LB_MCUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * m, net->stream), "memset");
-    const unsigned blocks = (unsigned)((n + 255) / 256);
-    kf_count<<<blocks, 256, 0, net->stream>>>(pos, n, g, nc, count, cell);
-    kf_scan<<<1, 1024, 0, net->stream>>>(count, (int)m, start);
-    kf_fill<<<blocks, 256, 0, net->stream>>>(n, cell, start, cursor, sorted);
-    kf_knn<<<blocks, 256, 0, net->stream>>>(pos, n, g, nc, start, sorted, feat);
-    LB_MCUDA(cudaGetLastError(), "feature kernels");
+    LB_MCUDA(lbk::mlp_features(n, pos, box, feat, net->ws, net->stream), "feature kernels");
     return LB_OK;
 }
 
 lb_status lb_mlp_forward(lb_mlp* net, long long n, const float* feat, float* out) {
     if (!net || n < 0 || (n && (!feat || !out))) return mfail(net, LB_ERR_ARG, "lb_mlp_forward: bad argument");
     if (n == 0) return LB_OK;
-    km_forward<<<grid_for(n), NT, net->smem_fwd, net->stream>>>(net->p, n, feat, out);
-    LB_MCUDA(cudaGetLastError(), "forward kernel");
+    LB_MCUDA(lbk::mlp_forward(net, n, feat, out, net->stream), "forward kernel");
     return LB_OK;
 }
 

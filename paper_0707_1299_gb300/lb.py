@@ -32,7 +32,7 @@ EXPORTS = ["lb_create", "lb_destroy", "lb_last_error", "lb_set_body_force", "lb_
            "lb_batch_destroy", "lb_batch_last_error", "lb_batch_tune", "lb_batch_step", "lb_batch_info",
            "lb_colloid_velocity", "lb_mlp_num_params", "lb_mlp_create", "lb_mlp_destroy", "lb_mlp_last_error",
            "lb_mlp_get_params", "lb_mlp_set_params", "lb_mlp_features", "lb_mlp_forward", "lb_mlp_grad",
-           "lb_mlp_train_step"]
+           "lb_mlp_train_step", "lb_set_colloid_correction"]
 
 _lib = None
 
@@ -77,6 +77,7 @@ def load():
         "lb_totals_noalloc": ([vp, ctypes.c_int, ip, ctypes.c_int, ctypes.c_int, dp, dp, vp], ctypes.c_int),
         "lb_colloid_velocity": ([vp, ctypes.c_int, dp, dp, dp, dp], ctypes.c_int),
         "lb_mlp_num_params": ([], ctypes.c_int),
+        "lb_set_colloid_correction": ([vp, vp], ctypes.c_int),
         "lb_mlp_create": ([ctypes.POINTER(ctypes.c_void_p), vp, vp], ctypes.c_int),
         "lb_mlp_destroy": ([vp], None),
         "lb_mlp_last_error": ([vp], ctypes.c_char_p),
@@ -265,6 +266,10 @@ def _mcheck(net, status):
     if status != LB_OK:
         msg = load().lb_mlp_last_error(net)
         raise LBError(status, msg.decode() if msg else "")
+
+
+def lb_set_colloid_correction(ctx, net):
+    _check(ctx, load().lb_set_colloid_correction(ctx, net))
 
 
 def lb_mlp_num_params():

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from oracle import mlp
+from _harness import periodic_diff
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -121,3 +122,50 @@ def test_trained_network_reduces_subgrid_error():
     assert hist[-1] < 0.9
     ev = learned.evaluate(net, fte, lte)
     assert ev["rms_corrected"] < 0.9 * ev["rms_plain"], ev
+
+
+def test_corrected_step_moves_colloids_by_network_output():
+    # With a network attached, one lb_step moves each colloid by
+    # U + y |F| / (6 pi eta a): rebuild that from the pieces (interpolated
+    # velocity, features, forward) and compare; detached, the plain update.
+    lb = _lb()
+    from paper_0707_1299_gb300 import learned, workloads as W
+    prob = W.colloids(L=20, n=30, seed=9, force=1e-5, a_L=1.6)
+    rng = np.random.default_rng(4)
+    params = (learned.initial_params(7) * 0.3).astype(np.float32)
+    net = lb.lb_mlp_create(params)
+    g = lb.Lattice(prob.grid, 0.6, 0.6, lb.LB_F64)
+    g.set_colloid_aL(1.6)
+    ps = prob.points[0]
+    g.add_point_forces(ps.kind, ps.pos, ps.F, ps.param)
+    g.step(3)
+    lb.lb_set_colloid_correction(g.ctx, net)
+    R0, F = g.particles()
+    n = R0.shape[0]
+    v = g.velocity_at(R0)
+    feat = torch.empty((n, 27), dtype=torch.float32, device="cuda")
+    lb.lb_mlp_features(net, n, R0, prob.grid, feat)
+    y = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    lb.lb_mlp_forward(net, n, feat, y)
+    torch.cuda.synchronize()
+    g.step(1)
+    R1, _ = g.particles()
+    eta = 0.6 / 3
+    a = 0.117
+    Fn = F.cpu().numpy()
+    c = (1 / a - 1 / 1.6) / (6 * np.pi * eta)
+    v0 = np.linalg.norm(Fn, axis=1, keepdims=True) / (6 * np.pi * eta * a)
+    expect = R0.cpu().numpy() + v.cpu().numpy() + Fn * c + y.cpu().numpy().astype(np.float64) * v0
+    expect %= np.asarray(prob.grid, float)
+    assert np.abs(periodic_diff(R1.cpu().numpy(), expect, prob.grid)).max() < 1e-12
+    assert np.abs(y.cpu().numpy()).max() > 1e-3  # the correction did move them
+    # detached: the plain Faxen update of Sec. IV
+    lb.lb_set_colloid_correction(g.ctx, None)
+    v = g.velocity_at(R1)
+    torch.cuda.synchronize()
+    g.step(1)
+    R2, _ = g.particles()
+    expect = (R1.cpu().numpy() + v.cpu().numpy() + Fn * c) % np.asarray(prob.grid, float)
+    assert np.abs(periodic_diff(R2.cpu().numpy(), expect, prob.grid)).max() < 1e-12
+    g.close()
+    lb.lb_mlp_destroy(net)
