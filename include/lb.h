@@ -60,7 +60,8 @@ typedef enum {
     LB_ERR_CUDA = 2,       /* a CUDA call failed; see lb_last_error */
     LB_ERR_OOM = 3,        /* device allocation failed */
     LB_ERR_NONFINITE = 4,  /* a non-finite value was found in an input */
-    LB_ERR_STATE = 5       /* call not valid in the context's state */
+    LB_ERR_STATE = 5,      /* call not valid in the context's state */
+    LB_ERR_TIMEOUT = 6     /* a bounded device-side wait ran out; see lb_mlp_last_error */
 } lb_status;
 
 /* Storage precision of the populations.  F64: double storage and
@@ -208,7 +209,10 @@ lb_status lb_mlp_get_params(lb_mlp *net, float *out);
 lb_status lb_mlp_set_params(lb_mlp *net, const float *in);  /* also resets Adam */
 /* feat[n][27] (float) from positions pos[n][3] (double) in a periodic box */
 lb_status lb_mlp_features(lb_mlp *net, long long n, const double *pos, const int box[3], float *feat);
-/* out[n][3] = network(feat) */
+/* out[n][3] = network(feat); the two hidden layers run on the tensor cores
+ * (tcgen05, bfloat16 operands, FP32 accumulation).  Waits for completion;
+ * LB_ERR_TIMEOUT if the tensor-core pipeline did not complete within its
+ * bounded wait (out is then incomplete). */
 lb_status lb_mlp_forward(lb_mlp *net, long long n, const float *feat, float *out);
 /* gradient of (1/3n) sum (y - target)^2 (grad: num_params floats, host or
  * device, may be NULL) and the sum of squared errors (*sse, may be NULL);

@@ -27,9 +27,8 @@ constexpr int BW = 4;  // warps (tiles) per work item of the collide kernel
 struct Entry {
     void* pop[2];              // population buffers: index = parity ^ cur0
     void* floc;
-    unsigned* flags;
-    unsigned* tile_list;
-    unsigned* tile_ctr;
+    flag_t* flags;
+    void* vel;                 // velocity field written by the collide (replicas with colloids), or null
     double* pos;
     double* force;
     double* radius;
@@ -134,7 +133,7 @@ kb_collide(const Entry* __restrict__ ent, const long long* __restrict__ gbegin, 
 #pragma unroll
                 for (int i = 0; i < NQ; ++i) Store<S>::st(dst.p[i], site, T(0), 0u);
             } else {
-                T f[NQ], o[NQ];
+                T f[NQ], o[NQ], v3[3];
                 pull19<S, true>(src, n, f);  // populations first: in flight with the force loads below
                 T Fx = EP<T>::uf(E, 0), Fy = EP<T>::uf(E, 1), Fz = EP<T>::uf(E, 2);
                 if (fl) {
@@ -148,115 +147,121 @@ kb_collide(const Entry* __restrict__ ent, const long long* __restrict__ gbegin, 
                 k.tau_b = EP<T>::coef(E, 1);
                 k.om_s = EP<T>::coef(E, 2);
                 k.om_b = EP<T>::coef(E, 3);
-                collide19<T, Store<S>::kCompensate, SC>(f, Fx, Fy, Fz, k, o, (T)E.inv_scale);
+                collide19<T, Store<S>::kCompensate, SC, true>(f, Fx, Fy, Fz, k, o, (T)E.inv_scale, v3);
                 unsigned rn = rng_seed(site ^ (unsigned)(e * 0x27d4eb2d), seed);
 #pragma unroll
                 for (int i = 0; i < NQ; ++i) Store<S>::st(dst.p[i], site, o[i], rng_next(rn));
+                if (fl && E.vel) {  // v at the stencil nodes of the replica's colloids
+                    T* vel = (T*)E.vel;
+                    vel[site] = v3[0];
+                    vel[V + site] = v3[1];
+                    vel[2 * V + site] = v3[2];
+                }
             }
         }
     }
 }
 
 // Clear every member's consumed force tiles: grid (blocks per member,
-// members); the last block of a member resets that member's list.
+// members), each member's flags scanned by its blocks' warps.
 template <typename T>
 __global__ void __launch_bounds__(256) kb_clear(const Entry* __restrict__ ent) {
     const Entry& E = ent[blockIdx.y];
-    clear_listed_tiles<T>(E.g, (T*)E.floc, E.flags, E.tile_list, E.tile_ctr, blockIdx.x * blockDim.x + threadIdx.x,
-                          gridDim.x * blockDim.x);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(&E.tile_ctr[1], 1u) == gridDim.x - 1) {
-            E.tile_ctr[0] = 0u;
-            E.tile_ctr[1] = 0u;
-        }
-    }
+    clear_flagged_tiles<T>(E.g, (T*)E.floc, E.flags, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                           (gridDim.x * blockDim.x) >> 5);
 }
 
+// Spreading, one warp per point (the stencil scheme of k_spread).
 template <typename T>
 __global__ void __launch_bounds__(256)
 kb_spread(const Entry* __restrict__ ent, const long long* __restrict__ pbegin, int nrep, long long total_pts) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= total_pts * 64) return;
-    const long long gp = t >> 6;
-    const int node = (int)(t & 63);
+    const long long gp = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (gp >= total_pts) return;  // uniform per warp
+    const int lane = threadIdx.x & 31;
     const int e = find_entry(pbegin, nrep, gp);
     const Entry& E = ent[e];
     const Geom& g = E.g;
     const int s = (int)(gp - pbegin[e]);
-    const int i = node & 3, j = (node >> 2) & 3, k = node >> 4;
     const double X = E.pos[3 * s], Y = E.pos[3 * s + 1], Z = E.pos[3 * s + 2];
-    const int nxg = stencil_base(X) + i, nyg = stencil_base(Y) + j, nzg = stencil_base(Z) + k;
-    const int z = wrap_node(nzg, g.nz);
-    if (is_solid(g, z)) return;
-    const int x = wrap_node(nxg, g.nx), y = wrap_node(nyg, g.ny);
-    const T w = peskin_phi((T)((double)nxg - X)) * peskin_phi((T)((double)nyg - Y)) * peskin_phi((T)((double)nzg - Z));
-    const long long site = ((long long)z * g.ny + y) * g.nx + x;
+    const StencilLane<T> st = stencil_lane<T>(X, Y, Z, lane);
+    const unsigned FULL = 0xffffffffu;
+    const int bx = __shfl_sync(FULL, st.base, 0), by = __shfl_sync(FULL, st.base, 4), bz = __shfl_sync(FULL, st.base, 8);
+    const int i = lane & 3, j = (lane >> 2) & 3;
+    const T wxy = __shfl_sync(FULL, st.phi, i) * __shfl_sync(FULL, st.phi, 4 + j);
+    const T F0 = (T)E.force[3 * s], F1 = (T)E.force[3 * s + 1], F2 = (T)E.force[3 * s + 2];
+    const int x = wrap_node(bx + i, g.nx), y = wrap_node(by + j, g.ny);
+    const bool marker = (i == 0) || ((x & (TILE_X - 1)) == 0);
+    const unsigned V = (unsigned)g.V;
     T* floc = (T*)E.floc;
-    atomicAdd(floc + site, (T)E.force[3 * s] * w);
-    atomicAdd(floc + g.V + site, (T)E.force[3 * s + 1] * w);
-    atomicAdd(floc + 2 * g.V + site, (T)E.force[3 * s + 2] * w);
-    mark_tile(E.flags, E.tile_list, E.tile_ctr, (unsigned)(((long long)z * g.ny + y) * g.ntx + x / TILE_X));
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int k = (lane >> 4) + 2 * h;
+        const T wz = __shfl_sync(FULL, st.phi, 8 + k);
+        const int z = wrap_node(bz + k, g.nz);
+        if (is_solid(g, z)) continue;
+        const T w = wxy * wz;
+        const unsigned row = (unsigned)z * (unsigned)g.ny + (unsigned)y;
+        const unsigned site = row * (unsigned)g.nx + (unsigned)x;
+        atomicAdd(floc + site, F0 * w);
+        atomicAdd(floc + V + site, F1 * w);
+        atomicAdd(floc + 2 * V + site, F2 * w);
+        if (marker) E.flags[row * (unsigned)g.ntx + (unsigned)(x / TILE_X)] = 1;
+    }
 }
 
 __global__ void kb_tick(unsigned* step_counter) { *step_counter += 1u; }
 
-// Interpolated velocity and Faxen update of every colloid, one warp each.
-template <typename S>
-__global__ void __launch_bounds__(128)
-kb_gather(const Entry* __restrict__ ent, const long long* __restrict__ pbegin, int nrep, long long total_pts,
-          int parity) {
-    using T = typename Store<S>::T;
-    const long long gp = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
-    if (gp >= total_pts) return;
+// Interpolated velocity (from the velocity field the collide wrote) and
+// the Faxen update of every colloid, one warp each (the scheme of k_interp).
+template <typename T>
+__global__ void __launch_bounds__(256)
+kb_interp(const Entry* __restrict__ ent, const long long* __restrict__ pbegin, int nrep, long long total_pts) {
+    const long long gp = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (gp >= total_pts) return;  // uniform per warp
     const int e = find_entry(pbegin, nrep, gp);
     const Entry& E = ent[e];
     const int s = (int)(gp - pbegin[e]);
-    if (!E.mobile[s]) return;
+    if (!E.mobile[s]) return;  // uniform per warp
     const Geom& g = E.g;
     const int lane = threadIdx.x & 31;
-    const unsigned V = (unsigned)g.V;
-    const int b = parity ^ E.cur0;
-    Pops<S> src;
-#pragma unroll
-    for (int i = 0; i < NQ; ++i) src.p[i] = (S*)E.pop[b] + (size_t)i * V;
-    const T* floc = (const T*)E.floc;
+    const T* vel = (const T*)E.vel;
     const double X = E.pos[3 * s], Y = E.pos[3 * s + 1], Z = E.pos[3 * s + 2];
-    const int bx = stencil_base(X), by = stencil_base(Y), bz = stencil_base(Z);
+    const StencilLane<T> st = stencil_lane<T>(X, Y, Z, lane);
+    const unsigned FULL = 0xffffffffu;
+    const int bx = __shfl_sync(FULL, st.base, 0), by = __shfl_sync(FULL, st.base, 4), bz = __shfl_sync(FULL, st.base, 8);
+    const int i = lane & 3, j = (lane >> 2) & 3;
+    const T wxy = __shfl_sync(FULL, st.phi, i) * __shfl_sync(FULL, st.phi, 4 + j);
+    const int x = wrap_node(bx + i, g.nx), y = wrap_node(by + j, g.ny);
+    const unsigned V = (unsigned)g.V;
     T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const int node = lane + 32 * h;
-        const int i = node & 3, j = (node >> 2) & 3, k = node >> 4;
-        const int x = wrap_node(bx + i, g.nx), y = wrap_node(by + j, g.ny), z = wrap_node(bz + k, g.nz);
-        if (is_solid(g, z)) continue;
-        const T w = peskin_phi((T)((double)(bx + i) - X)) * peskin_phi((T)((double)(by + j) - Y)) *
-                    peskin_phi((T)((double)(bz + k) - Z));
-        const Nbr nb = neighbours(g, x, y, z);
-        const unsigned site = nb.c + nb.x;
-        T f[NQ];
-        pull19<S, true>(src, nb, f);
-        unscale19<S>(f, E.inv_scale);
-        const T Fx = (T)E.uf[0] + floc[site], Fy = (T)E.uf[1] + floc[V + site], Fz = (T)E.uf[2] + floc[2 * V + site];
-        T drho, vx, vy, vz;
-        macro19<T, Store<S>::kCompensate>(f, Fx, Fy, Fz, drho, vx, vy, vz);
-        acc[0] += w * vx;
-        acc[1] += w * vy;
-        acc[2] += w * vz;
+        const int k = (lane >> 4) + 2 * h;
+        const T wz = __shfl_sync(FULL, st.phi, 8 + k);
+        const int z = wrap_node(bz + k, g.nz);
+        if (is_solid(g, z)) continue;  // v = 0 on solid nodes
+        const T w = wxy * wz;
+        const unsigned site = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.nx + (unsigned)x;
+        acc[0] += w * vel[site];
+        acc[1] += w * vel[V + site];
+        acc[2] += w * vel[2 * V + site];
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
-        for (int a = 0; a < 3; ++a) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], off);
-    if (lane != 0) return;
+        for (int a = 0; a < 3; ++a) acc[a] += __shfl_xor_sync(FULL, acc[a], off);
+    if (lane >= 3) return;  // lanes 0-2 finish one axis each
+    const double v = (double)(lane == 0 ? acc[0] : (lane == 1 ? acc[1] : acc[2]));
     const double c = (1.0 / E.radius[s] - E.inv_aL) * E.inv_6pi_eta;
-    const int nn[3] = {g.nx, g.ny, g.nz};
-    for (int a = 0; a < 3; ++a) {
-        const double L = (double)nn[a];
-        double r = E.pos[3 * s + a] + (double)acc[a] + E.force[3 * s + a] * c;
+    const double P = lane == 0 ? X : (lane == 1 ? Y : Z);
+    const double L = (double)(lane == 0 ? g.nx : (lane == 1 ? g.ny : g.nz));
+    double r = P + v + E.force[3 * s + lane] * c;
+    if (r < 0.0) r += L;
+    else if (r >= L) r -= L;
+    if (!(r >= 0.0 && r < L)) {  // moved by a period or more
         r = r - L * floor(r / L);
         if (r >= L || r < 0.0) r = 0.0;
-        E.pos[3 * s + a] = r;
     }
+    E.pos[3 * s + lane] = r;
 }
 
 }  // namespace
@@ -299,19 +304,17 @@ lb_status bfail(lb_batch* b, lb_status s, const std::string& m) {
                          std::string(where) + ": " + cudaGetErrorString(e_));                     \
     } while (0)
 
-// Launch the three phases of one step (parity p) on the batch stream.
+// Launch the phases of one step (parity p) on the batch stream: spread,
+// collide (writing v at the colloids' stencil nodes), colloid update, tile
+// clearing, and the rounding-seed counter of the 16-bit formats.
 template <typename S>
 cudaError_t launch_step(lb_batch* b, int p, int blocks) {
     using T = typename Store<S>::T;
-    if (b->total_pts > 0) {
-        const long long th = b->total_pts * 64;
-        kb_spread<T><<<(unsigned)((th + 255) / 256), 256, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->n, b->total_pts);
-        if (b->n_mobile > 0)
-            kb_gather<S><<<(unsigned)((b->total_pts + 3) / 4), 128, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->n,
-                                                                                   b->total_pts, p);
-    }
+    const unsigned pblocks = (unsigned)((b->total_pts + 7) / 8);
+    if (b->total_pts > 0) kb_spread<T><<<pblocks, 256, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->n, b->total_pts);
     kb_collide<S><<<blocks, dim3(32, BW), 0, b->stream>>>(b->d_ent, b->d_gbegin, b->d_work, b->n, b->total_groups, p,
                                                           b->d_step);
+    if (b->n_mobile > 0) kb_interp<T><<<pblocks, 256, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->n, b->total_pts);
     if (b->total_pts > 0) kb_clear<T><<<dim3(8, b->n), 256, 0, b->stream>>>(b->d_ent);
     if (sizeof(S) == 2) kb_tick<<<1, 1, 0, b->stream>>>(b->d_step);
     return cudaGetLastError();
@@ -373,8 +376,15 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
         E.pop[1] = c->f[1];
         E.floc = c->floc;
         E.flags = c->flags;
-        E.tile_list = c->tile_list;
-        E.tile_ctr = c->tile_ctr;
+        E.vel = nullptr;
+        if (c->n_mobile > 0) {
+            const cudaError_t ev = lbk::ensure_velocity_field(c);
+            if (ev != cudaSuccess) {
+                delete b;
+                return ev == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA;
+            }
+            E.vel = c->vel;
+        }
         E.pos = c->pos;
         E.force = c->force;
         E.radius = c->radius;

@@ -151,10 +151,60 @@ lb_status invalidate_field(lb_ctx* c) {
     return LB_OK;
 }
 
+// Cell order of the points (the work order of the spread and the
+// interpolation): recomputed when the points change and, for moving
+// colloids, every SORT_INTERVAL steps.  Correctness never depends on it.
+constexpr int SORT_INTERVAL = 64;
+
+// Per-point buffers (order, sort workspace, stencil rows, velocities),
+// grown with the point capacity.
+lb_status ensure_point_buffers(lb_ctx* c) {
+    const size_t ws = lbk::sort_ws_ints(c->geom, c->npts);
+    if ((size_t)c->npts <= c->pt_cap && ws <= c->sort_ws_ints) return LB_OK;
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->order);
+    cudaFree(c->sort_ws);
+    cudaFree(c->stencil);
+    cudaFree(c->pt_v);
+    c->order = nullptr;
+    c->sort_ws = nullptr;
+    c->stencil = nullptr;
+    c->pt_v = nullptr;
+    c->pt_cap = c->sort_ws_ints = 0;
+    const size_t cap = std::max<size_t>((size_t)c->npts, (size_t)c->cap);
+    const size_t wcap = lbk::sort_ws_ints(c->geom, (long long)cap);
+    LB_CUDA(cudaMalloc(&c->order, sizeof(int) * cap), "point order");
+    LB_CUDA(cudaMalloc(&c->sort_ws, sizeof(int) * wcap), "point order workspace");
+    LB_CUDA(cudaMalloc(&c->stencil, lbk::arith_bytes(c->prec) * lbk::ST_W * cap), "stencil rows");
+    LB_CUDA(cudaMalloc(&c->pt_v, sizeof(double) * 3 * cap), "point velocities");
+    c->pt_cap = cap;
+    c->sort_ws_ints = wcap;
+    c->order_stale = c->npts > 0;
+    c->stencil_ready = false;
+    return LB_OK;
+}
+
 lb_status ensure_field(lb_ctx* c) {
     if (c->field_ready || c->npts == 0) return LB_OK;
+    lb_status s = ensure_point_buffers(c);
+    if (s != LB_OK) return s;
+    if (c->order_stale) {
+        LB_CUDA(lbk::launch_sort_points(c), "point order kernels");
+        c->order_stale = false;
+        c->steps_since_sort = 0;
+    }
+    if (!c->stencil_ready) {
+        LB_CUDA(lbk::launch_stencil(c), "stencil kernel");
+        c->stencil_ready = true;
+    }
     LB_CUDA(lbk::launch_spread(c), "spread kernel");
     c->field_ready = true;
+    return LB_OK;
+}
+
+// Velocity field of the collide kernel (lattices with colloids).
+lb_status ensure_vel(lb_ctx* c) {
+    LB_CUDA(lbk::ensure_velocity_field(c), "velocity field");
     return LB_OK;
 }
 
@@ -204,17 +254,14 @@ lb_status lb_create(lb_ctx** out, const int grid[3], double tau_shear, double ta
     if (e == cudaSuccess) e = cudaMalloc(&c->f[0], sb * lbk::NQ * (size_t)V);
     if (e == cudaSuccess) e = cudaMalloc(&c->f[1], sb * lbk::NQ * (size_t)V);
     if (e == cudaSuccess) e = cudaMalloc(&c->floc, ab * 3 * (size_t)V);
-    if (e == cudaSuccess) e = cudaMalloc(&c->flags, sizeof(unsigned) * (size_t)c->geom.ntiles);
-    if (e == cudaSuccess) e = cudaMalloc(&c->tile_list, sizeof(unsigned) * (size_t)c->geom.ntiles);
-    if (e == cudaSuccess) e = cudaMalloc(&c->tile_ctr, sizeof(unsigned) * 2);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->tile_ctr, 0, sizeof(unsigned) * 2, c->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&c->flags, sizeof(lbk::flag_t) * (size_t)c->geom.ntiles);
     if (e == cudaSuccess) e = cudaMalloc(&c->fsum, sizeof(double) * 3);
     if (e == cudaSuccess) e = cudaMalloc(&c->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->partials, sizeof(double) * 4 * (size_t)lbk::moment_blocks(c->geom));
     if (e == cudaSuccess) e = cudaMalloc(&c->totals_dev, sizeof(double) * 4);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->f[0], 0, sb * lbk::NQ * (size_t)V, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->floc, 0, ab * 3 * (size_t)V, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, sizeof(unsigned) * (size_t)c->geom.ntiles, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, sizeof(lbk::flag_t) * (size_t)c->geom.ntiles, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->fsum, 0, sizeof(double) * 3, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -240,8 +287,11 @@ void lb_destroy(lb_ctx* c) {
     cudaFree(c->f[1]);
     cudaFree(c->floc);
     cudaFree(c->flags);
-    cudaFree(c->tile_list);
-    cudaFree(c->tile_ctr);
+    cudaFree(c->vel);
+    cudaFree(c->order);
+    cudaFree(c->sort_ws);
+    cudaFree(c->stencil);
+    cudaFree(c->pt_v);
     cudaFree(c->pos);
     cudaFree(c->force);
     cudaFree(c->radius);
@@ -251,7 +301,6 @@ void lb_destroy(lb_ctx* c) {
     cudaFree(c->partials);
     cudaFree(c->totals_dev);
     cudaFree(c->stage);
-    cudaFree(c->corr_v);
     cudaFree(c->corr_feat);
     cudaFree(c->corr_y);
     cudaFree(c->corr_ws);
@@ -328,6 +377,8 @@ lb_status lb_add_point_forces(lb_ctx* c, int n, const double* pos, const double*
         return fail(c, LB_ERR_ARG, "lb_add_point_forces: parameter must be > 0 (and |F| > 0 for stresslet/rotlet)");
     c->npts = (int)total;
     c->version++;
+    c->order_stale = true;
+    c->stencil_ready = false;
     if (kind == LB_COLLOID) c->n_mobile += n;
     LB_CUDA(lbk::launch_fsum(c), "force sum");
     LB_CUDA(cudaMemcpyAsync(c->fsum_host, c->fsum, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream),
@@ -370,6 +421,8 @@ lb_status lb_set_positions(lb_ctx* c, const double* pos) {
     LB_CUDA(cudaMemcpyAsync(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "status read");
     LB_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
     if (status) return fail(c, LB_ERR_NONFINITE, "lb_set_positions: non-finite position");
+    c->order_stale = true;
+    c->stencil_ready = false;
     return LB_OK;
 }
 
@@ -379,15 +432,12 @@ lb_status ensure_corr_buffers(lb_ctx* c) {
     const size_t ws = lbk::mlp_features_ws_ints(c->npts, box);
     if ((size_t)c->npts > c->corr_cap) {
         cudaStreamSynchronize(c->stream);
-        cudaFree(c->corr_v);
         cudaFree(c->corr_feat);
         cudaFree(c->corr_y);
-        c->corr_v = nullptr;
         c->corr_feat = nullptr;
         c->corr_y = nullptr;
         c->corr_cap = 0;
         const size_t n = (size_t)c->npts;
-        LB_CUDA(cudaMalloc(&c->corr_v, sizeof(double) * 3 * n), "correction buffers");
         LB_CUDA(cudaMalloc(&c->corr_feat, sizeof(float) * 27 * n), "correction buffers");
         LB_CUDA(cudaMalloc(&c->corr_y, sizeof(float) * 3 * n), "correction buffers");
         c->corr_cap = n;
@@ -418,23 +468,35 @@ lb_status lb_step(lb_ctx* c, int nsteps) {
         lb_status st = ensure_corr_buffers(c);
         if (st != LB_OK) return st;
     }
+    {
+        lb_status st = ensure_vel(c);
+        if (st != LB_OK) return st;
+    }
     const int box[3] = {c->geom.nx, c->geom.ny, c->geom.nz};
+    // Step n (Sec. IV with forward Euler): spread F^n at R^n; collide and
+    // stream with F^n, writing v^n = (j + F^n/2) / rho at the stencil nodes;
+    // interpolate v^n at R^n and move the colloids (plus the learned
+    // correction when a network is attached), which also prepares the
+    // stencil rows of R^{n+1}; clear the consumed force tiles.  Fixed points
+    // keep their field from step to step.
     for (int s = 0; s < nsteps; ++s) {
         lb_status st = ensure_field(c);
         if (st != LB_OK) return st;
-        if (c->n_mobile > 0 && c->corr) {  // colloid update with the learned correction
-            LB_CUDA(lbk::launch_gather(c, c->npts, c->pos, c->corr_v, false), "gather kernel");
+        const bool corrected = c->n_mobile > 0 && c->corr;
+        if (corrected) {  // the network's inputs depend on R^n only
             LB_CUDA(lbk::mlp_features(c->npts, c->pos, box, c->corr_feat, c->corr_ws, c->stream), "feature kernels");
             LB_CUDA(lbk::mlp_forward(c->corr, c->npts, c->corr_feat, c->corr_y, c->stream), "forward kernel");
-            LB_CUDA(lbk::launch_corrected_update(c), "corrected update kernel");
-            c->launches += 5;
-        } else if (c->n_mobile > 0) {
-            LB_CUDA(lbk::launch_gather(c, c->npts, nullptr, nullptr, true), "gather/update kernel");
+            c->launches += lbk::MLP_FEATURE_LAUNCHES + 1;
         }
         LB_CUDA(lbk::launch_collide(c), "collide-stream kernel");
-        if (c->field_ready) LB_CUDA(lbk::launch_clear_tiles(c), "tile clearing kernel");
         c->cur ^= 1;
-        c->field_ready = false;
+        if (c->n_mobile > 0) {
+            LB_CUDA(lbk::launch_interp(c), "interpolation kernel");
+            LB_CUDA(lbk::launch_update(c, corrected ? c->corr_y : nullptr), "colloid update kernel");
+            LB_CUDA(lbk::launch_clear_tiles(c), "tile clearing kernel");
+            c->field_ready = false;
+            if (++c->steps_since_sort >= SORT_INTERVAL) c->order_stale = true;
+        }
     }
     return LB_OK;
 }
@@ -450,7 +512,7 @@ lb_status lb_velocity_at(lb_ctx* c, int n, const double* pos, double* v_out) {
     lb_status s = resolve(c, args, 2, &any_host);
     if (s == LB_OK) s = ensure_field(c);
     if (s != LB_OK) return s;
-    LB_CUDA(lbk::launch_gather(c, n, (const double*)args[0].dev, (double*)args[1].dev, false), "gather kernel");
+    LB_CUDA(lbk::launch_gather(c, n, (const double*)args[0].dev, (double*)args[1].dev), "gather kernel");
     return finish(c, args, 2, any_host);
 }
 
@@ -468,7 +530,7 @@ lb_status lb_colloid_velocity(lb_ctx* c, int n, const double* pos, const double*
     lb_status s = resolve(c, args, 4, &any_host);
     if (s == LB_OK) s = ensure_field(c);
     if (s != LB_OK) return s;
-    LB_CUDA(lbk::launch_gather(c, n, (const double*)args[0].dev, (double*)args[3].dev, false), "gather kernel");
+    LB_CUDA(lbk::launch_gather(c, n, (const double*)args[0].dev, (double*)args[3].dev), "gather kernel");
     LB_CUDA(lbk::launch_faxen(c, n, (const double*)args[1].dev, (const double*)args[2].dev, (double*)args[3].dev),
             "faxen kernel");
     return finish(c, args, 4, any_host);

@@ -36,34 +36,39 @@ __device__ __forceinline__ bool is_solid(const Geom& g, int z) {
     return z == g.wall_lo || z == g.wall_hi;
 }
 
-// Mark the tile of a site as holding spread force; the first marker also
-// appends the tile to the list that the clearing kernel walks.
-__device__ __forceinline__ void mark_tile(unsigned* __restrict__ flags, unsigned* __restrict__ list,
-                                          unsigned* __restrict__ ctr, unsigned tile) {
-    if (flags[tile] == 0u && atomicExch(&flags[tile], 1u) == 0u) list[atomicAdd(&ctr[0], 1u)] = tile;
-}
+// Force tiles.  Spreading sets the byte flag of every 32-site x-row tile it
+// adds force to (a plain store: any number of writers store the same
+// value); the collide kernel reads the field only in flagged tiles; after
+// the collide a clearing pass zeroes the flagged tiles and their flags.
+using flag_t = unsigned char;
 
-// Zero the force field of every listed tile and its flag; the last block to
-// finish resets the list.  Runs after the collide kernel has consumed the
-// field, so no load of the field is in flight anywhere.
+// Zero the field and the flag of every flagged tile: each warp takes
+// groups of 32 tiles (one flag per lane), then clears the flagged ones of
+// its group one after the other, one site per lane.  Runs after the
+// collide kernel has consumed the field, so no load of it is in flight.
 template <typename T>
-__device__ __forceinline__ void clear_listed_tiles(const Geom& g, T* __restrict__ floc, unsigned* __restrict__ flags,
-                                                   const unsigned* __restrict__ list, unsigned* __restrict__ ctr,
-                                                   unsigned first, unsigned stride) {
-    const unsigned n = *(volatile unsigned*)&ctr[0];
-    const unsigned V = (unsigned)g.V;
-    for (unsigned i = first; i < n * 32u; i += stride) {
-        const unsigned tile = list[i >> 5], lane = i & 31u;
-        const unsigned tx = tile % (unsigned)g.ntx, r = tile / (unsigned)g.ntx;
-        const unsigned y = r % (unsigned)g.ny, z = r / (unsigned)g.ny;
-        const unsigned x = tx * TILE_X + lane;
-        if (x < (unsigned)g.nx) {
-            const unsigned site = z * g.plane + y * (unsigned)g.nx + x;
-            floc[site] = T(0);
-            floc[V + site] = T(0);
-            floc[2 * V + site] = T(0);
+__device__ __forceinline__ void clear_flagged_tiles(const Geom& g, T* __restrict__ floc, flag_t* __restrict__ flags,
+                                                    unsigned warp0, unsigned nwarps) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned V = (unsigned)g.V, ntiles = (unsigned)g.ntiles, ntx = (unsigned)g.ntx;
+    const unsigned ngroups = (ntiles + 31u) >> 5;
+    for (unsigned grp = warp0; grp < ngroups; grp += nwarps) {
+        const unsigned t = (grp << 5) + lane;
+        const bool mine = t < ntiles && flags[t] != 0;
+        unsigned m = __ballot_sync(0xffffffffu, mine);
+        if (mine) flags[t] = 0;
+        while (m) {
+            const unsigned tile = (grp << 5) + (unsigned)(__ffs(m) - 1);
+            m &= m - 1u;
+            const unsigned row = tile / ntx;               // z * ny + y
+            const unsigned x = (tile - row * ntx) * TILE_X + lane;
+            if (x < (unsigned)g.nx) {
+                const unsigned site = row * (unsigned)g.nx + x;
+                floc[site] = T(0);
+                floc[V + site] = T(0);
+                floc[2 * V + site] = T(0);
+            }
         }
-        if (lane == 0) flags[tile] = 0u;
     }
 }
 
@@ -345,14 +350,23 @@ template <> struct Wts<double> {
 // and `is` = 1/scale: every term is linear in (f, F) except rho = 1 + drho,
 // rho vv and vF + Fv, which take one factor `is` each; the outputs come out
 // in the same scaled units.
-template <typename T, bool COMP, bool SCALED = false>
+// With VOUT the fluid velocity v = (j + F/2) / rho of Eq. (macrovariables2)
+// is also returned in v3, in physical units (the same expression, rounding
+// for rounding, as macro19).
+template <typename T, bool COMP, bool SCALED = false, bool VOUT = false>
 __device__ __forceinline__ void collide19(const T f[NQ], T Fx, T Fy, T Fz, const Coef<T>& k, T out[NQ],
-                                          T is = T(1)) {
+                                          T is = T(1), T* v3 = nullptr) {
     using W = Wts<T>;
     const Moments<T> m = moments19<T, COMP>(f);
     const T third = T(1) / T(3);
     const T rho = T(1) + (SCALED ? m.drho * is : m.drho);
     const T irho = T(1) / rho;
+    if (VOUT) {
+        const T iv = SCALED ? is * irho : irho;
+        v3[0] = (m.jx + (m.jx_lo + T(0.5) * Fx)) * iv;
+        v3[1] = (m.jy + (m.jy_lo + T(0.5) * Fy)) * iv;
+        v3[2] = (m.jz + (m.jz_lo + T(0.5) * Fz)) * iv;
+    }
     const T vx = (m.jx + T(0.5) * Fx) * irho;
     const T vy = (m.jy + T(0.5) * Fy) * irho;
     const T vz = (m.jz + T(0.5) * Fz) * irho;
@@ -444,9 +458,60 @@ __device__ __forceinline__ float peskin_phi(float r) {
 // floor(X)+2; node k's offset from X is (floor(X) - 1 + k) - X.
 __device__ __forceinline__ int stencil_base(double X) { return (int)floor(X) - 1; }
 __device__ __forceinline__ int wrap_node(int k, int n) {
-    // k in [-1, n + 2); also correct for n < 4 where it may wrap twice
+    // k in [-1, n + 2): one correction suffices for n >= 3; the modulo
+    // covers the smaller lattices, where a stencil may wrap twice
+    if (n >= 3) return k < 0 ? k + n : (k >= n ? k - n : k);
     int r = k % n;
     return r < 0 ? r + n : r;
+}
+
+// The 4 x 4 x 4 stencil of one point, evaluated by a warp: lane 4a + i
+// (lanes 0-11) holds the base node of axis a and the one-dimensional weight
+// phi(b_a + i - X_a) of Eq. (deltadef), from FP64 position arithmetic; every
+// lane reads the weights of its nodes by shuffle, so the 64 nodes cost 12
+// evaluations of phi.  The weight of node (i, j, k) is
+// (phi_x[i] phi_y[j]) phi_z[k].
+template <typename T>
+struct StencilLane {
+    T phi;
+    int base;
+};
+template <typename T>
+__device__ __forceinline__ StencilLane<T> stencil_lane(double X, double Y, double Z, int lane) {
+    StencilLane<T> s;
+    s.phi = T(0);
+    s.base = 0;
+    if (lane < 12) {
+        const int a = lane >> 2, i = lane & 3;
+        const double P = a == 0 ? X : (a == 1 ? Y : Z);
+        s.base = stencil_base(P);
+        s.phi = peskin_phi((T)((double)(s.base + i) - P));
+    }
+    return s;
+}
+
+// Stencil row of a point, computed once per position by a thread per point
+// and read by the warp-per-point kernels: elements 0-11 hold phi(b_a + i -
+// X_a) (axis a, node i at 4a + i), elements 12-14 the base nodes b_a as int
+// bits, element 15 is unused; 16 elements of the arithmetic type, so a
+// warp reads a row with one coalesced load.
+constexpr int ST_W = 16;
+__device__ __forceinline__ float int_bits(int v, float) { return __int_as_float(v); }
+__device__ __forceinline__ double int_bits(int v, double) { return __longlong_as_double((long long)v); }
+__device__ __forceinline__ int bits_int(float v) { return __float_as_int(v); }
+__device__ __forceinline__ int bits_int(double v) { return (int)__double_as_longlong(v); }
+
+template <typename T>
+__device__ __forceinline__ void write_stencil(T* __restrict__ row, double X, double Y, double Z) {
+    const double P[3] = {X, Y, Z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int b = stencil_base(P[a]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) row[4 * a + i] = peskin_phi((T)((double)(b + i) - P[a]));
+        row[12 + a] = int_bits(b, T(0));
+    }
+    row[15] = T(0);
 }
 
 }  // namespace lbk

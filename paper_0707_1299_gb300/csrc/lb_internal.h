@@ -25,9 +25,9 @@ struct lb_ctx {
     void* f[2];               // population buffers (19 V elements of the storage type)
     int cur;                  // index of the buffer holding the current state
     void* floc;               // localised force field, 3 V elements of the arithmetic type
-    unsigned* flags;          // one flag per 32-site x-row tile: tile holds nonzero floc
-    unsigned* tile_list;      // the flagged tiles, in the order they were flagged
-    unsigned* tile_ctr;       // [number of listed tiles, blocks of the clearing kernel done]
+    lbk::flag_t* flags;       // one byte per 32-site x-row tile: the tile holds spread force
+    void* vel;                // fluid velocity in the flagged tiles, 3 V elements of the
+                              // arithmetic type (lattices with colloids only)
     bool field_ready;         // floc holds the forces at the current positions
 
     // monopoles after expansion (device, xyz interleaved)
@@ -39,6 +39,15 @@ struct lb_ctx {
     double* fsum;             // 3 doubles: net point force (device)
     double fsum_host[3];      // its host copy, refreshed when the points change
     int* status;              // 1 int: device-side validation result
+    // per-point work buffers of the spread and the interpolation
+    int* order;               // the points in cell order
+    int* sort_ws;
+    void* stencil;            // stencil rows (ST_W elements of the arithmetic type per point)
+    double* pt_v;             // interpolated velocity at every point (3 npts)
+    size_t pt_cap, sort_ws_ints;
+    bool order_stale;         // positions changed since the last sort
+    bool stencil_ready;       // stencil rows match the positions
+    int steps_since_sort;
 
     // reductions
     double* partials;         // 4 doubles per block of the moments kernel
@@ -50,7 +59,6 @@ struct lb_ctx {
 
     // learned correction of the colloid velocity (optional)
     lb_mlp* corr;
-    double* corr_v;           // interpolated velocity at every point (3 npts)
     float* corr_feat;         // features (27 npts)
     float* corr_y;            // network output (3 npts)
     int* corr_ws;             // feature workspace
@@ -74,7 +82,15 @@ struct UForce {
 
 cudaError_t launch_collide(lb_ctx* c);
 cudaError_t launch_spread(lb_ctx* c);
-cudaError_t launch_gather(lb_ctx* c, int n, const double* qpos, double* vout, bool update);
+cudaError_t launch_gather(lb_ctx* c, int n, const double* qpos, double* vout);
+cudaError_t launch_interp(lb_ctx* c);
+cudaError_t launch_update(lb_ctx* c, const float* y);
+cudaError_t launch_stencil(lb_ctx* c);
+cudaError_t launch_sort_points(lb_ctx* c);
+cudaError_t ensure_velocity_field(lb_ctx* c);
+size_t sort_ws_ints(const Geom& g, long long npts);
+size_t scan_ws_ints(long long m);
+cudaError_t scan_exclusive(const int* in, long long m, int* out, int* bsum, cudaStream_t st);
 cudaError_t launch_moments(lb_ctx* c, double* rho, double* u, bool want_totals);
 cudaError_t launch_expand(lb_ctx* c, int n, const double* pos, const double* F, const double* param, int kind,
                           int mult);
@@ -87,7 +103,7 @@ cudaError_t launch_clear_field(lb_ctx* c);
 cudaError_t launch_clear_tiles(lb_ctx* c);
 template <typename T>
 UForce<T> uniform_force(const lb_ctx* c);
-cudaError_t launch_corrected_update(lb_ctx* c);
+constexpr int MLP_FEATURE_LAUNCHES = 6;  // kernels of one mlp_features call
 size_t mlp_features_ws_ints(long long n, const int box[3]);
 cudaError_t mlp_features(long long n, const double* pos, const int box[3], float* feat, int* ws, cudaStream_t st);
 cudaError_t mlp_forward(const lb_mlp* net, long long n, const float* feat, float* out, cudaStream_t st);

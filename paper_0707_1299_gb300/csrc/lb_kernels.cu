@@ -4,15 +4,18 @@
 //   k_collide   fused pull-stream + moment-space collision with the
 //               second-order forcing term (Sec. II, Eq. fiexp); one thread
 //               per site, one warp per 32-site x-row tile; reads the
-//               localised force only in tiles flagged by k_spread, then
-//               clears them.
+//               localised force only in tiles flagged by k_spread and, for
+//               lattices with colloids, writes the fluid velocity there.
+//   k_clear_tiles  zeroes the flagged tiles once the collide has read them.
 //   k_spread    regularised point forces onto the lattice (Sec. III,
-//               Eq. deltadef): one thread per (point, stencil node),
-//               atomic accumulation.
-//   k_gather    velocity interpolated with the same kernel (Sec. IV);
-//               one warp per point, two stencil nodes per lane, each node
-//               rebuilt from its pulled populations; optionally the Faxen
-//               update with the a_L subtraction (Eq. a_Ldefn).
+//               Eq. deltadef): one warp per point in cell order, the 12
+//               one-dimensional weights evaluated once and shuffled,
+//               atomic accumulation into the field.
+//   k_interp    colloid velocity interpolated with the same kernel from the
+//               velocity the collide wrote (Sec. IV), with the update
+//               R += v(R) + F (1/a - 1/a_L) / (6 pi eta) (Eq. a_Ldefn).
+//   k_gather    velocity at arbitrary query points, each stencil node
+//               rebuilt from its pulled populations.
 //   k_moments   rho, u fields and FP64 totals (Eq. macrovariables2).
 #include <math.h>
 
@@ -79,14 +82,19 @@ static dim3 site_grid(const Geom& g) {
 // Occupancy bound (blocks of 128 threads per SM), swept on GB300 at 256^3:
 // the 4- and 2-byte formats are fastest at 12 (42 registers; 8-10 were
 // 2-10 % slower, 14 spills); FP64 at 8.
-// FIELD = false: a lattice without point forces (no flag or field access).
-template <typename S, bool WALLS, int NY, bool FIELD>
+// FMODE: FM_NONE a lattice without point forces (no flag or field access);
+// FM_FIELD the force field is read in flagged tiles; FM_VEL also writes the
+// fluid velocity v = (j + F/2) / rho there, for the colloid update.
+enum { FM_NONE = 0, FM_FIELD = 1, FM_VEL = 2 };
+template <typename S, bool WALLS, int NY, int FMODE>
 __global__ void __launch_bounds__(CS_THREADS, (NY == 1 ? (sizeof(S) == 8 ? 8 : 12) : 4))
 k_collide(const Pops<S> src, const Pops<S> dst, const typename Store<S>::T* __restrict__ floc,
-          const unsigned* __restrict__ flags, Geom g, Coef<typename Store<S>::T> k,
-          UForce<typename Store<S>::T> fu, float scale, float inv_scale, unsigned seed) {
+          const flag_t* __restrict__ flags, typename Store<S>::T* __restrict__ vel, Geom g,
+          Coef<typename Store<S>::T> k, UForce<typename Store<S>::T> fu, float scale, float inv_scale,
+          unsigned seed) {
     using T = typename Store<S>::T;
     constexpr bool SC = Store<S>::kScaled;
+    constexpr bool FIELD = FMODE != FM_NONE, VOUT = FMODE == FM_VEL;
     const int y0 = (blockIdx.y * CS_WARPS + threadIdx.y) * NY;
     if (y0 >= g.ny) return;  // uniform per warp
     const int z = blockIdx.z, lane = threadIdx.x;
@@ -128,11 +136,16 @@ k_collide(const Pops<S> src, const Pops<S> dst, const typename Store<S>::T* __re
                     Fy += floc[V + site] * s;
                     Fz += floc[2 * V + site] * s;
                 }
-                T o[NQ];
-                collide19<T, Store<S>::kCompensate, SC>(f[r], Fx, Fy, Fz, k, o, (T)inv_scale);
+                T o[NQ], v3[3];
+                collide19<T, Store<S>::kCompensate, SC, VOUT>(f[r], Fx, Fy, Fz, k, o, (T)inv_scale, v3);
                 unsigned rn = rng_seed(site, seed);
 #pragma unroll
                 for (int i = 0; i < NQ; ++i) Store<S>::st(dst.p[i], site, o[i], rng_next(rn));
+                if (VOUT && fl[r]) {
+                    vel[site] = v3[0];
+                    vel[V + site] = v3[1];
+                    vel[2 * V + site] = v3[2];
+                }
             }
         }
     }
@@ -142,43 +155,8 @@ k_collide(const Pops<S> src, const Pops<S> dst, const typename Store<S>::T* __re
 // collide kernel only reads the field, so it never stores to a line whose
 // load may still be in flight.
 template <typename T>
-__global__ void __launch_bounds__(256)
-k_clear_tiles(Geom g, T* __restrict__ floc, unsigned* __restrict__ flags, const unsigned* __restrict__ list,
-              unsigned* __restrict__ ctr) {
-    clear_listed_tiles<T>(g, floc, flags, list, ctr, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(&ctr[1], 1u) == gridDim.x - 1) {  // last block: reset the list
-            ctr[0] = 0u;
-            ctr[1] = 0u;
-        }
-    }
-}
-
-// ------------------------------------------------------------- k_spread
-template <typename T, bool WALLS>
-__global__ void __launch_bounds__(256)
-k_spread(const double* __restrict__ pos, const double* __restrict__ force, int npts, T* __restrict__ floc,
-         unsigned* __restrict__ flags, unsigned* __restrict__ list, unsigned* __restrict__ ctr, Geom g) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)npts * 64) return;
-    const int s = (int)(t >> 6), node = (int)(t & 63);
-    const int i = node & 3, j = (node >> 2) & 3, k = node >> 4;
-    const double X = pos[3 * s], Y = pos[3 * s + 1], Z = pos[3 * s + 2];
-    const int nxg = stencil_base(X) + i, nyg = stencil_base(Y) + j, nzg = stencil_base(Z) + k;
-    const int z = wrap_node(nzg, g.nz);
-    if (WALLS && is_solid(g, z)) return;
-    const int x = wrap_node(nxg, g.nx), y = wrap_node(nyg, g.ny);
-    const T wx = peskin_phi((T)((double)nxg - X));
-    const T wy = peskin_phi((T)((double)nyg - Y));
-    const T wz = peskin_phi((T)((double)nzg - Z));
-    const T w = wx * wy * wz;
-    const long long site = ((long long)z * g.ny + y) * g.nx + x;
-    atomicAdd(floc + site, (T)force[3 * s] * w);
-    atomicAdd(floc + g.V + site, (T)force[3 * s + 1] * w);
-    atomicAdd(floc + 2 * g.V + site, (T)force[3 * s + 2] * w);
-    mark_tile(flags, list, ctr, (unsigned)(((long long)z * g.ny + y) * g.ntx + x / TILE_X));
+__global__ void __launch_bounds__(256) k_clear_tiles(Geom g, T* __restrict__ floc, flag_t* __restrict__ flags) {
+    clear_flagged_tiles<T>(g, floc, flags, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5);
 }
 
 // Position wrapped into [0, n).
@@ -189,33 +167,159 @@ __device__ __forceinline__ double wrap_pos(double r, int n) {
     return r;
 }
 
+// The same after a step that moved the point by less than one period: one
+// addition instead of a division, except in the cases wrap_pos settles.
+__device__ __forceinline__ double wrap_step(double r, int n) {
+    const double L = (double)n;
+    if (r < 0.0) r += L;
+    else if (r >= L) r -= L;
+    return (r >= 0.0 && r < L) ? r : wrap_pos(r, n);
+}
+
+// ------------------------------------------------------------- k_spread
+// One warp per point, taken in the cell order of `order`; the point's
+// stencil row (12 weights, 3 base nodes) is read once and shuffled; lane l
+// adds the force to nodes l and l + 32 (node = i + 4 j + 16 k: i along x, j
+// along y, k along z) and flags their tiles (the lane of the first node of
+// a tile in the row: i = 0, or x at a tile start).
+template <typename T, bool WALLS>
+__global__ void __launch_bounds__(256)
+k_spread(const T* __restrict__ st, const double* __restrict__ force, const int* __restrict__ order, int npts,
+         T* __restrict__ floc, flag_t* __restrict__ flags, Geom g) {
+    const int q = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (q >= npts) return;  // uniform per warp
+    const int lane = threadIdx.x & 31;
+    const int s = order[q];
+    const unsigned FULL = 0xffffffffu;
+    const T r = lane < ST_W ? st[(size_t)s * ST_W + lane] : T(0);
+    const T fl = lane < 3 ? (T)force[3 * s + lane] : T(0);
+    const int bx = bits_int(__shfl_sync(FULL, r, 12)), by = bits_int(__shfl_sync(FULL, r, 13)),
+              bz = bits_int(__shfl_sync(FULL, r, 14));
+    const T F0 = __shfl_sync(FULL, fl, 0), F1 = __shfl_sync(FULL, fl, 1), F2 = __shfl_sync(FULL, fl, 2);
+    const int i = lane & 3, j = (lane >> 2) & 3;
+    const T wxy = __shfl_sync(FULL, r, i) * __shfl_sync(FULL, r, 4 + j);
+    const int x = wrap_node(bx + i, g.nx), y = wrap_node(by + j, g.ny);
+    const bool marker = (i == 0) || ((x & (TILE_X - 1)) == 0);
+    const unsigned V = (unsigned)g.V;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int k = (lane >> 4) + 2 * h;
+        const T wz = __shfl_sync(FULL, r, 8 + k);
+        const int z = wrap_node(bz + k, g.nz);
+        if (WALLS && is_solid(g, z)) continue;
+        const T w = wxy * wz;
+        const unsigned row = (unsigned)z * (unsigned)g.ny + (unsigned)y;
+        const unsigned site = row * (unsigned)g.nx + (unsigned)x;
+        atomicAdd(floc + site, F0 * w);
+        atomicAdd(floc + V + site, F1 * w);
+        atomicAdd(floc + 2 * V + site, F2 * w);
+        if (marker) flags[row * (unsigned)g.ntx + (unsigned)(x / TILE_X)] = 1;
+    }
+}
+
+// Stencil rows of n points.
+template <typename T>
+__global__ void k_stencil(int n, const double* __restrict__ pos, T* __restrict__ st) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    write_stencil<T>(st + (size_t)t * ST_W, pos[3 * t], pos[3 * t + 1], pos[3 * t + 2]);
+}
+
+// ------------------------------------------------------------- k_interp
+// Velocity at every point, v(R) = sum over the 64 stencil nodes of phi phi
+// phi v (Sec. IV), from the velocity field the collide kernel wrote in the
+// flagged tiles (every fluid stencil node of a point lies in one: the
+// spread flagged it).  One warp per point, in cell order; lane l takes
+// nodes l and l + 32; lanes 0-2 write v[3 s + a] (FP64).
+template <typename T, bool WALLS>
+__global__ void __launch_bounds__(256)
+k_interp(const T* __restrict__ vel, Geom g, int n, const int* __restrict__ order, const T* __restrict__ st,
+         double* __restrict__ vout) {
+    const int q = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (q >= n) return;  // uniform per warp
+    const int lane = threadIdx.x & 31;
+    const int s = order[q];
+    const unsigned FULL = 0xffffffffu;
+    const T r = lane < ST_W ? st[(size_t)s * ST_W + lane] : T(0);
+    const int bx = bits_int(__shfl_sync(FULL, r, 12)), by = bits_int(__shfl_sync(FULL, r, 13)),
+              bz = bits_int(__shfl_sync(FULL, r, 14));
+    const int i = lane & 3, j = (lane >> 2) & 3;
+    const T wxy = __shfl_sync(FULL, r, i) * __shfl_sync(FULL, r, 4 + j);
+    const int x = wrap_node(bx + i, g.nx), y = wrap_node(by + j, g.ny);
+    const unsigned V = (unsigned)g.V;
+    T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int k = (lane >> 4) + 2 * h;
+        const T wz = __shfl_sync(FULL, r, 8 + k);
+        const int z = wrap_node(bz + k, g.nz);
+        if (WALLS && is_solid(g, z)) continue;  // v = 0 on solid nodes
+        const T w = wxy * wz;
+        const unsigned site = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.nx + (unsigned)x;
+        acc[0] += w * vel[site];
+        acc[1] += w * vel[V + site];
+        acc[2] += w * vel[2 * V + site];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+        for (int a = 0; a < 3; ++a) acc[a] += __shfl_xor_sync(FULL, acc[a], off);
+    if (lane < 3) vout[3 * s + lane] = (double)(lane == 0 ? acc[0] : (lane == 1 ? acc[1] : acc[2]));
+}
+
+// Colloid update, one thread per point (Sec. IV, forward Euler, unit time
+// step): a mobile point moves by
+//   R <- R + v(R) + F (1/a - 1/a_L) / (6 pi eta)          (Eq. a_Ldefn)
+// plus, with a network output y, y |F| / (6 pi eta a); wrapped
+// periodically.  The stencil row of the new position is written for the
+// next step's spread and interpolation.
+template <typename T>
+__global__ void k_update(int n, double* __restrict__ pos, const double* __restrict__ v, const float* __restrict__ y,
+                         const double* __restrict__ F, const double* __restrict__ a, const int* __restrict__ mobile,
+                         double inv_aL, double inv_6pi_eta, Geom g, T* __restrict__ st) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    double P[3] = {pos[3 * t], pos[3 * t + 1], pos[3 * t + 2]};
+    if (mobile[t]) {
+        const int nn[3] = {g.nx, g.ny, g.nz};
+        const double c = (1.0 / a[t] - inv_aL) * inv_6pi_eta;
+        if (y) {
+            const double f0 = F[3 * t], f1 = F[3 * t + 1], f2 = F[3 * t + 2];
+            const double v0 = sqrt(f0 * f0 + f1 * f1 + f2 * f2) * inv_6pi_eta / a[t];
+            for (int k = 0; k < 3; ++k)
+                P[k] = wrap_step(P[k] + v[3 * t + k] + F[3 * t + k] * c + (double)y[3 * t + k] * v0, nn[k]);
+        } else {
+            for (int k = 0; k < 3; ++k) P[k] = wrap_step(P[k] + v[3 * t + k] + F[3 * t + k] * c, nn[k]);
+        }
+        for (int k = 0; k < 3; ++k) pos[3 * t + k] = P[k];
+    }
+    write_stencil<T>(st + (size_t)t * ST_W, P[0], P[1], P[2]);
+}
+
 // ------------------------------------------------------------- k_gather
-// v at the n points (query mode) or at every colloid with the position
-// update (update mode).  One warp per point.
+// v at n query points (Sec. IV interpolation), one warp per point, two
+// stencil nodes per lane, each node's v rebuilt from its pulled populations
+// and the force at time n (Eq. macrovariables2).
 template <typename S, bool WALLS>
 __global__ void __launch_bounds__(128)
 k_gather(const Pops<S> src, const typename Store<S>::T* __restrict__ floc, Geom g, UForce<typename Store<S>::T> fu,
-         float inv_scale, int n, const double* __restrict__ qpos, double* __restrict__ vout,
-         double* __restrict__ upos, const double* __restrict__ force, const double* __restrict__ radius,
-         const int* __restrict__ mobile, double inv_6pi_eta, double inv_aL) {
+         float inv_scale, int n, const double* __restrict__ qpos, double* __restrict__ vout) {
     using T = typename Store<S>::T;
     const int s = blockIdx.x * 4 + (threadIdx.x >> 5);
     if (s >= n) return;
-    const bool update = (upos != nullptr);
-    if (update && !mobile[s]) return;
     const int lane = threadIdx.x & 31;
-    const double* P = update ? upos + 3 * s : qpos + 3 * s;
+    const double* P = qpos + 3 * s;
     const double X = wrap_pos(P[0], g.nx), Y = wrap_pos(P[1], g.ny), Z = wrap_pos(P[2], g.nz);
-    const int bx = stencil_base(X), by = stencil_base(Y), bz = stencil_base(Z);
+    const StencilLane<T> st = stencil_lane<T>(X, Y, Z, lane);
+    const unsigned FULL = 0xffffffffu;
+    const int bx = __shfl_sync(FULL, st.base, 0), by = __shfl_sync(FULL, st.base, 4), bz = __shfl_sync(FULL, st.base, 8);
     const unsigned V = (unsigned)g.V;
     T acc[3] = {T(0), T(0), T(0)};
     for (int h = 0; h < 2; ++h) {
         const int node = lane + 32 * h;
         const int i = node & 3, j = (node >> 2) & 3, k = node >> 4;
+        const T w = __shfl_sync(FULL, st.phi, i) * __shfl_sync(FULL, st.phi, 4 + j) * __shfl_sync(FULL, st.phi, 8 + k);
         const int x = wrap_node(bx + i, g.nx), y = wrap_node(by + j, g.ny), z = wrap_node(bz + k, g.nz);
         if (WALLS && is_solid(g, z)) continue;  // v = 0 on solid nodes
-        const T w = peskin_phi((T)((double)(bx + i) - X)) * peskin_phi((T)((double)(by + j) - Y)) *
-                    peskin_phi((T)((double)(bz + k) - Z));
         const Nbr nb = neighbours(g, x, y, z);
         const unsigned site = nb.c + nb.x;
         T f[NQ];
@@ -230,16 +334,9 @@ k_gather(const Pops<S> src, const typename Store<S>::T* __restrict__ floc, Geom 
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
-        for (int a = 0; a < 3; ++a) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], off);
-    if (lane != 0) return;
-    if (!update) {
+        for (int a = 0; a < 3; ++a) acc[a] += __shfl_xor_sync(FULL, acc[a], off);
+    if (lane == 0)
         for (int a = 0; a < 3; ++a) vout[3 * s + a] = (double)acc[a];
-        return;
-    }
-    const double c = (1.0 / radius[s] - inv_aL) * inv_6pi_eta;
-    const int nn[3] = {g.nx, g.ny, g.nz};
-    for (int a = 0; a < 3; ++a)
-        upos[3 * s + a] = wrap_pos(P[a] + (double)acc[a] + force[3 * s + a] * c, nn[a]);
 }
 
 // ------------------------------------------------------------ k_moments
@@ -321,22 +418,6 @@ __global__ void k_faxen(int n, const double* __restrict__ F, const double* __res
     for (int k = 0; k < 3; ++k) U[3 * t + k] += F[3 * t + k] * c;
 }
 
-// Colloid update with the learned correction: R += v(R) + F (1/a - 1/a_L) /
-// (6 pi eta) + y |F| / (6 pi eta a), y the network output in units of the
-// Stokes velocity of the colloid.
-__global__ void k_corrected_update(int n, const double* __restrict__ v, const float* __restrict__ y,
-                                   const double* __restrict__ F, const double* __restrict__ a,
-                                   const int* __restrict__ mobile, double inv_aL, double inv_6pi_eta, Geom g,
-                                   double* __restrict__ pos) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n || !mobile[t]) return;
-    const double f0 = F[3 * t], f1 = F[3 * t + 1], f2 = F[3 * t + 2];
-    const double c = (1.0 / a[t] - inv_aL) * inv_6pi_eta;
-    const double v0 = sqrt(f0 * f0 + f1 * f1 + f2 * f2) * inv_6pi_eta / a[t];
-    const int nn[3] = {g.nx, g.ny, g.nz};
-    for (int k = 0; k < 3; ++k)
-        pos[3 * t + k] = wrap_pos(pos[3 * t + k] + v[3 * t + k] + F[3 * t + k] * c + (double)y[3 * t + k] * v0, nn[k]);
-}
 
 // ---------------------------------------------------- point bookkeeping
 
@@ -512,6 +593,176 @@ __global__ void k_sum1(const double* __restrict__ partials, int n, double* __res
     if (threadIdx.x == 0) out[0] = t;
 }
 
+// ----------------------------------------------------------- cell order
+// The points ordered by the 8^3 brick that holds them (a counting sort), so
+// that warps next to each other in a launch work on nearby stencils: the
+// spread's atomics and the interpolation's loads then find their lines in
+// L2.  Only the order of the work depends on it, never a result.
+constexpr int BRICK = 8;
+
+__global__ void k_brick_count(const double* __restrict__ pos, int n, Geom g, int3 nb, int* __restrict__ count,
+                              int* __restrict__ key) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int bx = min(max((int)pos[3 * t] / BRICK, 0), nb.x - 1);
+    const int by = min(max((int)pos[3 * t + 1] / BRICK, 0), nb.y - 1);
+    const int bz = min(max((int)pos[3 * t + 2] / BRICK, 0), nb.z - 1);
+    const int b = (bz * nb.y + by) * nb.x + bx;
+    key[t] = b;
+    atomicAdd(&count[b], 1);
+}
+
+__global__ void k_brick_fill(int n, const int* __restrict__ key, const int* __restrict__ start,
+                             int* __restrict__ cursor, int* __restrict__ order) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int b = key[t];
+    order[start[b] + atomicAdd(&cursor[b], 1)] = t;
+}
+
+// ---------------------------------------------------- exclusive int scan
+// Three passes: tile sums, a one-block scan of the tile sums, and the scan
+// of each tile offset by its prefix.  Tiles of 2048 ints; at most 8192 tiles.
+constexpr int SCAN_T = 256, SCAN_PER = 8, SCAN_TILE = SCAN_T * SCAN_PER, SCAN_MAX_TILES = 8192;
+
+__device__ __forceinline__ int warp_inclusive_scan(int v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// Exclusive prefix of v over the block (blockDim.x a multiple of 32);
+// *total gets the block's sum.  sh: 33 ints of shared memory.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* sh, int* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (int)blockDim.x >> 5;
+    const int inc = warp_inclusive_scan(v);
+    __syncthreads();
+    if (lane == 31) sh[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const int x = lane < nw ? sh[lane] : 0;
+        const int xi = warp_inclusive_scan(x);
+        if (lane < nw) sh[lane] = xi - x;
+        if (lane == 31) sh[32] = xi;
+    }
+    __syncthreads();
+    *total = sh[32];
+    return sh[w] + inc - v;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const int* __restrict__ in, long long m, int* __restrict__ bsum) {
+    __shared__ int sh[33];
+    const long long base = (long long)blockIdx.x * SCAN_TILE;
+    int v = 0;
+#pragma unroll
+    for (int r = 0; r < SCAN_PER; ++r) {
+        const long long i = base + r * SCAN_T + threadIdx.x;
+        if (i < m) v += in[i];
+    }
+    int total;
+    block_exclusive_scan(v, sh, &total);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+// One block of 1024 threads: exclusive scan of the nt tile sums in place,
+// the grand total in bsum[nt].
+__global__ void __launch_bounds__(1024) k_scan_top(int* __restrict__ bsum, int nt) {
+    __shared__ int sh[33];
+    const int per = (nt + 1023) / 1024;  // at most 8
+    const int b = threadIdx.x * per;
+    int loc[8];
+    int v = 0;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        loc[r] = (r < per && b + r < nt) ? bsum[b + r] : 0;
+        v += loc[r];
+    }
+    int total;
+    int run = block_exclusive_scan(v, sh, &total);
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+        if (r < per && b + r < nt) {
+            bsum[b + r] = run;
+            run += loc[r];
+        }
+    if (threadIdx.x == 0) bsum[nt] = total;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_apply(const int* __restrict__ in, long long m,
+                                                       const int* __restrict__ bsum, int nt, int* __restrict__ out) {
+    __shared__ int sh[33];
+    const long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_PER;
+    int loc[SCAN_PER];
+    int v = 0;
+#pragma unroll
+    for (int r = 0; r < SCAN_PER; ++r) {
+        loc[r] = base + r < m ? in[base + r] : 0;
+        v += loc[r];
+    }
+    int total;
+    int run = block_exclusive_scan(v, sh, &total) + bsum[blockIdx.x];
+#pragma unroll
+    for (int r = 0; r < SCAN_PER; ++r)
+        if (base + r < m) {
+            out[base + r] = run;
+            run += loc[r];
+        }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[m] = bsum[nt];
+}
+
+size_t scan_ws_ints(long long m) { return (size_t)((m + SCAN_TILE - 1) / SCAN_TILE) + 1; }
+
+cudaError_t scan_exclusive(const int* in, long long m, int* out, int* bsum, cudaStream_t st) {
+    const long long nt = (m + SCAN_TILE - 1) / SCAN_TILE;
+    if (nt > SCAN_MAX_TILES) return cudaErrorInvalidValue;
+    if (nt == 0) return cudaMemsetAsync(out, 0, sizeof(int), st);
+    k_scan_reduce<<<(unsigned)nt, SCAN_T, 0, st>>>(in, m, bsum);
+    k_scan_top<<<1, 1024, 0, st>>>(bsum, (int)nt);
+    k_scan_apply<<<(unsigned)nt, SCAN_T, 0, st>>>(in, m, bsum, (int)nt, out);
+    return cudaGetLastError();
+}
+
+static int3 brick_dims(const Geom& g) {
+    return make_int3((g.nx + BRICK - 1) / BRICK, (g.ny + BRICK - 1) / BRICK, (g.nz + BRICK - 1) / BRICK);
+}
+
+// Workspace of the cell-order sort, in ints: count and cursor (nb each),
+// start (nb + 1), the tile sums of the scan, and one key per point.
+size_t sort_ws_ints(const Geom& g, long long npts) {
+    const int3 d = brick_dims(g);
+    const long long nb = (long long)d.x * d.y * d.z;
+    return (size_t)(3 * nb + 1) + scan_ws_ints(nb) + (size_t)npts;
+}
+
+cudaError_t ensure_velocity_field(lb_ctx* c) {
+    if (c->vel || c->n_mobile == 0) return cudaSuccess;
+    return cudaMalloc(&c->vel, arith_bytes(c->prec) * 3 * (size_t)c->geom.V);
+}
+
+cudaError_t launch_sort_points(lb_ctx* c) {
+    if (c->npts == 0) return cudaSuccess;
+    const int3 d = brick_dims(c->geom);
+    const long long nb = (long long)d.x * d.y * d.z;
+    int* count = c->sort_ws;
+    int* cursor = count + nb;
+    int* start = cursor + nb;
+    int* bsum = start + nb + 1;
+    int* key = bsum + scan_ws_ints(nb);
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * 2 * (size_t)nb, c->stream);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)((c->npts + 255) / 256);
+    k_brick_count<<<blocks, 256, 0, c->stream>>>(c->pos, c->npts, c->geom, d, count, key);
+    e = scan_exclusive(count, nb, start, bsum, c->stream);
+    if (e != cudaSuccess) return e;
+    k_brick_fill<<<blocks, 256, 0, c->stream>>>(c->npts, key, start, cursor, c->order);
+    c->launches += 5;
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ launchers
 static bool has_walls(const lb_ctx* c) { return c->geom.wall_lo >= 0 || c->geom.wall_hi >= 0; }
 static dim3 site_block() { return dim3(TILE_X, CS_WARPS, 1); }
@@ -535,16 +786,19 @@ static cudaError_t collide_t(lb_ctx* c) {
     const dim3 grid((unsigned)c->geom.ntx, (unsigned)((c->geom.ny + CS_WARPS * NY - 1) / (CS_WARPS * NY)),
                     (unsigned)c->geom.nz);
     const T* floc = (const T*)c->floc;
-    const bool field = c->npts > 0;
-#define LB_COLLIDE(W, FD)                                                                                       \
-    k_collide<S, W, NY, FD><<<grid, site_block(), 0, c->stream>>>(src, dst, floc, c->flags, c->geom, k, fu, c->scale, \
-                                                                c->inv_scale, c->seed)
+    T* vel = (T*)c->vel;
+    const int mode = c->npts == 0 ? FM_NONE : (c->n_mobile > 0 ? FM_VEL : FM_FIELD);
+#define LB_COLLIDE(W, FM)                                                                                     \
+    k_collide<S, W, NY, FM><<<grid, site_block(), 0, c->stream>>>(src, dst, floc, c->flags, vel, c->geom, k, fu, \
+                                                                c->scale, c->inv_scale, c->seed)
     if (has_walls(c)) {
-        if (field) LB_COLLIDE(true, true);
-        else LB_COLLIDE(true, false);
+        if (mode == FM_VEL) LB_COLLIDE(true, FM_VEL);
+        else if (mode == FM_FIELD) LB_COLLIDE(true, FM_FIELD);
+        else LB_COLLIDE(true, FM_NONE);
     } else {
-        if (field) LB_COLLIDE(false, true);
-        else LB_COLLIDE(false, false);
+        if (mode == FM_VEL) LB_COLLIDE(false, FM_VEL);
+        else if (mode == FM_FIELD) LB_COLLIDE(false, FM_FIELD);
+        else LB_COLLIDE(false, FM_NONE);
     }
 #undef LB_COLLIDE
     c->seed = c->seed * 747796405u + 2891336453u;  // next step's rounding seed
@@ -563,14 +817,14 @@ cudaError_t launch_collide(lb_ctx* c) {
 
 template <typename T>
 static cudaError_t spread_t(lb_ctx* c) {
-    const long long threads = (long long)c->npts * 64;
-    const unsigned int blocks = (unsigned int)((threads + 255) / 256);
+    const unsigned blocks = (unsigned)((c->npts + 7) / 8);  // 8 warps per block, one point each
+    const T* st = (const T*)c->stencil;
     if (has_walls(c))
-        k_spread<T, true><<<blocks, 256, 0, c->stream>>>(c->pos, c->force, c->npts, (T*)c->floc, c->flags,
-                                                          c->tile_list, c->tile_ctr, c->geom);
+        k_spread<T, true><<<blocks, 256, 0, c->stream>>>(st, c->force, c->order, c->npts, (T*)c->floc, c->flags,
+                                                          c->geom);
     else
-        k_spread<T, false><<<blocks, 256, 0, c->stream>>>(c->pos, c->force, c->npts, (T*)c->floc, c->flags,
-                                                           c->tile_list, c->tile_ctr, c->geom);
+        k_spread<T, false><<<blocks, 256, 0, c->stream>>>(st, c->force, c->order, c->npts, (T*)c->floc, c->flags,
+                                                           c->geom);
     c->launches++;
     return cudaGetLastError();
 }
@@ -581,35 +835,72 @@ cudaError_t launch_spread(lb_ctx* c) {
 }
 
 template <typename S>
-static cudaError_t gather_t(lb_ctx* c, int n, const double* qpos, double* vout, bool update) {
+static cudaError_t gather_t(lb_ctx* c, int n, const double* qpos, double* vout) {
     using T = typename Store<S>::T;
     const UForce<T> fu = uniform_force<T>(c);
-    const double eta = c->tau_s / 3.0;
-    const double inv_6pi_eta = 1.0 / (6.0 * M_PI * eta);
-    const double inv_aL = isinf(c->a_L) ? 0.0 : 1.0 / c->a_L;
     const unsigned int blocks = (unsigned int)((n + 3) / 4);
     const Pops<S> src = pops<S>(c->f[c->cur], c->geom.V);
-    double* upos = update ? c->pos : nullptr;
     if (has_walls(c))
         k_gather<S, true><<<blocks, 128, 0, c->stream>>>(src, (const T*)c->floc, c->geom, fu, c->inv_scale, n, qpos,
-                                                          vout, upos, c->force, c->radius, c->mobile, inv_6pi_eta,
-                                                          inv_aL);
+                                                          vout);
     else
         k_gather<S, false><<<blocks, 128, 0, c->stream>>>(src, (const T*)c->floc, c->geom, fu, c->inv_scale, n, qpos,
-                                                           vout, upos, c->force, c->radius, c->mobile, inv_6pi_eta,
-                                                           inv_aL);
+                                                           vout);
     c->launches++;
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather(lb_ctx* c, int n, const double* qpos, double* vout, bool update) {
+cudaError_t launch_gather(lb_ctx* c, int n, const double* qpos, double* vout) {
     if (n == 0) return cudaSuccess;
     switch (c->prec) {
-        case LB_F64: return gather_t<double>(c, n, qpos, vout, update);
-        case LB_F32: return gather_t<float>(c, n, qpos, vout, update);
-        case LB_F16S: return gather_t<__half>(c, n, qpos, vout, update);
-        default: return gather_t<__nv_bfloat16>(c, n, qpos, vout, update);
+        case LB_F64: return gather_t<double>(c, n, qpos, vout);
+        case LB_F32: return gather_t<float>(c, n, qpos, vout);
+        case LB_F16S: return gather_t<__half>(c, n, qpos, vout);
+        default: return gather_t<__nv_bfloat16>(c, n, qpos, vout);
     }
+}
+
+template <typename T>
+static cudaError_t interp_t(lb_ctx* c) {
+    const unsigned blocks = (unsigned)((c->npts + 7) / 8);
+    const T* vel = (const T*)c->vel;
+    const T* st = (const T*)c->stencil;
+    if (has_walls(c))
+        k_interp<T, true><<<blocks, 256, 0, c->stream>>>(vel, c->geom, c->npts, c->order, st, c->pt_v);
+    else
+        k_interp<T, false><<<blocks, 256, 0, c->stream>>>(vel, c->geom, c->npts, c->order, st, c->pt_v);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interp(lb_ctx* c) {
+    if (c->npts == 0) return cudaSuccess;
+    return c->prec == LB_F64 ? interp_t<double>(c) : interp_t<float>(c);
+}
+
+template <typename T>
+static cudaError_t update_t(lb_ctx* c, const float* y) {
+    const double eta = c->tau_s / 3.0;
+    const double inv_aL = isinf(c->a_L) ? 0.0 : 1.0 / c->a_L;
+    k_update<T><<<(c->npts + 127) / 128, 128, 0, c->stream>>>(c->npts, c->pos, c->pt_v, y, c->force, c->radius,
+                                                              c->mobile, inv_aL, 1.0 / (6.0 * M_PI * eta), c->geom,
+                                                              (T*)c->stencil);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update(lb_ctx* c, const float* y) {
+    if (c->npts == 0) return cudaSuccess;
+    return c->prec == LB_F64 ? update_t<double>(c, y) : update_t<float>(c, y);
+}
+
+cudaError_t launch_stencil(lb_ctx* c) {
+    if (c->npts == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((c->npts + 127) / 128);
+    if (c->prec == LB_F64) k_stencil<double><<<blocks, 128, 0, c->stream>>>(c->npts, c->pos, (double*)c->stencil);
+    else k_stencil<float><<<blocks, 128, 0, c->stream>>>(c->npts, c->pos, (float*)c->stencil);
+    c->launches++;
+    return cudaGetLastError();
 }
 
 long long moment_blocks(const Geom& g) {
@@ -644,16 +935,6 @@ cudaError_t launch_moments(lb_ctx* c, double* rho, double* u, bool want_totals) 
         case LB_F16S: return moments_t<__half>(c, rho, u, want_totals);
         default: return moments_t<__nv_bfloat16>(c, rho, u, want_totals);
     }
-}
-
-cudaError_t launch_corrected_update(lb_ctx* c) {
-    const double eta = c->tau_s / 3.0;
-    const double inv_aL = isinf(c->a_L) ? 0.0 : 1.0 / c->a_L;
-    k_corrected_update<<<(c->npts + 127) / 128, 128, 0, c->stream>>>(c->npts, c->corr_v, c->corr_y, c->force,
-                                                                    c->radius, c->mobile, inv_aL,
-                                                                    1.0 / (6.0 * M_PI * eta), c->geom, c->pos);
-    c->launches++;
-    return cudaGetLastError();
 }
 
 cudaError_t launch_faxen(lb_ctx* c, int n, const double* F, const double* a, double* U) {
@@ -719,23 +1000,20 @@ cudaError_t launch_convert_in(lb_ctx* c, const double* df) {
 }
 
 cudaError_t launch_clear_field(lb_ctx* c) {
-    cudaError_t e = cudaMemsetAsync(c->floc, 0, 3 * (size_t)c->geom.V * arith_bytes(c->prec), c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, sizeof(unsigned) * (size_t)c->geom.ntiles, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->tile_ctr, 0, sizeof(unsigned) * 2, c->stream);
+    cudaError_t e = cudaMemsetAsync(c->floc, 0, arith_bytes(c->prec) * 3 * (size_t)c->geom.V, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, sizeof(flag_t) * (size_t)c->geom.ntiles, c->stream);
     return e;
 }
 
 cudaError_t launch_clear_tiles(lb_ctx* c) {
-    // a point flags at most 32 tiles (4 x 4 node rows, two x-tiles each):
-    // size the grid for that many 32-site tiles, at most 2 blocks per SM
-    const long long lanes = std::min<long long>((long long)c->npts * 32 * 32, c->geom.ntiles * 32);
-    const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>(152 * 2, (lanes + 255) / 256));
+    // one warp per group of 32 tiles, grid-strided, at most 4 blocks of 256
+    // threads per SM: the flags (one byte per tile) are read once
+    const long long warps = (c->geom.ntiles + 31) / 32;
+    const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>(152 * 4, (warps + 7) / 8));
     if (c->prec == LB_F64)
-        k_clear_tiles<double><<<blocks, 256, 0, c->stream>>>(c->geom, (double*)c->floc, c->flags, c->tile_list,
-                                                             c->tile_ctr);
+        k_clear_tiles<double><<<blocks, 256, 0, c->stream>>>(c->geom, (double*)c->floc, c->flags);
     else
-        k_clear_tiles<float><<<blocks, 256, 0, c->stream>>>(c->geom, (float*)c->floc, c->flags, c->tile_list,
-                                                            c->tile_ctr);
+        k_clear_tiles<float><<<blocks, 256, 0, c->stream>>>(c->geom, (float*)c->floc, c->flags);
     c->launches++;
     return cudaGetLastError();
 }

@@ -11,6 +11,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 
@@ -20,6 +21,7 @@
 namespace {
 
 using lbk::Geom;
+using lbk::wrap_node;
 
 constexpr int D0 = 27, D1 = 64, D2 = 64, D3 = 3;
 constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + D1 * D0, OFF_W2 = OFF_B1 + D1, OFF_B2 = OFF_W2 + D2 * D1,
@@ -53,7 +55,6 @@ struct Smem {
     static constexpr int GZ2 = GY + TS * D3;        // [64][65]
     static constexpr int GZ1 = GZ2 + TS * P2;       // [64][65]
     static constexpr int END = GZ1 + TS * P2;
-    static constexpr int FWD_END = GY + TS * D3;    // forward-only kernels stop here (tile_forward stages y in GY)
 };
 
 __device__ void load_weights(const float* __restrict__ p, float* sm) {
@@ -99,16 +100,238 @@ __device__ void tile_forward(const float* __restrict__ feat, long long s0, int n
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(NT) km_forward(const float* __restrict__ params, long long n,
-                                                 const float* __restrict__ feat, float* __restrict__ out) {
-    extern __shared__ float sm[];
-    load_weights(params, sm);
-    __syncthreads();
-    for (long long t = blockIdx.x; t * TS < n; t += gridDim.x) {
-        const long long s0 = t * TS;
-        const int ns = (int)(n - s0 < TS ? n - s0 : TS);
-        tile_forward(feat, s0, ns, sm, out);
+// ------------------------------------------------- tensor-core forward
+// The two 64-wide layers on the 5th-generation tensor cores: a CTA of 128
+// threads takes tiles of 128 samples; per layer one thread issues
+// tcgen05.mma (kind::f16, bfloat16 operands from shared memory, FP32
+// accumulator in 64 tensor-memory columns, M = 128, N = 64, K = 16 per
+// instruction) and commits to an mbarrier; thread r then reads row r of the
+// accumulator (tcgen05.ld) and applies bias and SiLU, rounding to bfloat16
+// for the next layer.  The 64 -> 3 output layer runs on the CUDA cores.
+//
+// Operands use the K-major layout without swizzle: 8 x 16-byte core
+// matrices (8 rows of 8 bfloat16), core matrices along K 128 bytes apart
+// (leading byte offset), 8-row groups K/8 * 128 bytes apart (stride byte
+// offset).
+namespace tc {
+
+constexpr int M = 128;          // samples per tile = threads per CTA
+constexpr int K1 = 32;          // 27 inputs padded to two K = 16 steps
+constexpr int NCOL = 64;        // tensor-memory columns (both layers reuse them)
+// shared-memory layout (bytes)
+constexpr int B1 = 0;                       // W1 [64][32] bf16
+constexpr int B2 = B1 + D1 * K1 * 2;        // W2 [64][64] bf16
+constexpr int A1 = B2 + D2 * D1 * 2;        // x  [128][32] bf16
+constexpr int A2 = A1 + M * K1 * 2;         // h1 [128][64] bf16
+constexpr int W3S = A2 + M * D1 * 2;        // W3 [3][64] float (bf16-rounded)
+constexpr int BIAS = W3S + D3 * D2 * 4;     // b1 b2 b3 float
+constexpr int MBAR = BIAS + 132 * 4;        // mbarrier (8 bytes)
+constexpr int TADDR = MBAR + 8;             // tensor-memory address from tcgen05.alloc
+constexpr int USED = TADDR + 8;
+// requested dynamic shared memory: at most 4 CTAs per SM, so 4 x 64 of the
+// 512 tensor-memory columns are ever allocated at once (alloc never waits)
+constexpr int SMEM = 56 * 1024;
+static_assert(USED <= SMEM, "shared layout");
+
+// byte offset of element (row, k) in a K-major no-swizzle operand with K columns
+__host__ __device__ constexpr int kmajor_off(int row, int k, int K) {
+    return (row >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);  // version 1, no swizzle
+}
+
+// instruction descriptor: D FP32, A and B bfloat16, both K-major, N, M
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(D1 >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(IDESC), "r"(accumulate));
+}
+
+__device__ __forceinline__ void commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+// Bounded wait for phase `parity` of the mbarrier; false on timeout.
+__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity) {
+    for (long long it = 0; it < (1LL << 26); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
     }
+    return false;
+}
+
+// 64 consecutive FP32 columns of this thread's accumulator row
+__device__ __forceinline__ void load_row64(uint32_t taddr, float (&v)[64]) {
+    uint32_t r[64];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,"
+        "%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+          "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+          "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+          "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+          "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 64; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+    const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+    return a | (b << 16);
+}
+
+}  // namespace tc
+
+// Forward pass on the tensor cores; status[0] is set to 1 if a wait on the
+// tensor-core pipeline timed out (the kernel then stops early).
+__global__ void __launch_bounds__(tc::M) km_forward_tc(const float* __restrict__ params, long long n,
+                                                       const float* __restrict__ feat, float* __restrict__ out,
+                                                       int* __restrict__ status) {
+    using namespace tc;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t mbar = smem_u32(smem + MBAR);
+    float* w3 = (float*)(smem + W3S);
+    float* bias = (float*)(smem + BIAS);
+
+    // weights, rounded to bfloat16, in the K-major layout
+    for (int i = tid; i < D1 * K1; i += M) {
+        const int r = i / K1, k = i % K1;
+        const float w = k < D0 ? params[OFF_W1 + r * D0 + k] : 0.0f;
+        *(__nv_bfloat16*)(smem + B1 + kmajor_off(r, k, K1)) = __float2bfloat16_rn(w);
+    }
+    for (int i = tid; i < D2 * D1; i += M) {
+        const int r = i / D1, k = i % D1;
+        *(__nv_bfloat16*)(smem + B2 + kmajor_off(r, k, D1)) = __float2bfloat16_rn(params[OFF_W2 + i]);
+    }
+    for (int i = tid; i < D3 * D2; i += M) w3[i] = bf16r(params[OFF_W3 + i]);
+    for (int i = tid; i < D1; i += M) bias[i] = params[OFF_B1 + i];
+    for (int i = tid; i < D2; i += M) bias[D1 + i] = params[OFF_B2 + i];
+    if (tid < D3) bias[D1 + D2 + tid] = params[OFF_B3 + tid];
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(smem + TADDR)),
+                     "r"(NCOL)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tbase = *(volatile uint32_t*)(smem + TADDR);
+    const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);  // this warp's 32 lanes
+    const uint32_t a1 = smem_u32(smem + A1), a2 = smem_u32(smem + A2);
+    const uint32_t b1 = smem_u32(smem + B1), b2 = smem_u32(smem + B2);
+    uint32_t phase = 0;
+    bool ok = true;
+
+    for (long long t = blockIdx.x; t * M < n && ok; t += gridDim.x) {
+        const long long s = t * M + tid;  // this thread's sample
+        // x: 27 features rounded to bfloat16, zero-padded to 32
+        {
+            float x[K1];
+#pragma unroll
+            for (int k = 0; k < K1; ++k) x[k] = (s < n && k < D0) ? feat[s * D0 + k] : 0.0f;
+#pragma unroll
+            for (int kg = 0; kg < K1 / 8; ++kg) {
+                uint4 v;
+                v.x = pack_bf16(x[8 * kg + 0], x[8 * kg + 1]);
+                v.y = pack_bf16(x[8 * kg + 2], x[8 * kg + 3]);
+                v.z = pack_bf16(x[8 * kg + 4], x[8 * kg + 5]);
+                v.w = pack_bf16(x[8 * kg + 6], x[8 * kg + 7]);
+                *(uint4*)(smem + A1 + kmajor_off(tid, 8 * kg, K1)) = v;
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int ks = 0; ks < K1 / 16; ++ks)
+                mma(tbase, smem_desc(a1 + ks * 256, 128, (K1 / 8) * 128), smem_desc(b1 + ks * 256, 128, (K1 / 8) * 128),
+                    ks > 0);
+            commit(mbar);
+        }
+        ok = __syncthreads_and(wait_phase(mbar, phase));  // uniform across the CTA
+        phase ^= 1u;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float z[64];
+        load_row64(trow, z);
+        // h1 = bf16(silu(z1 + b1)) into the layer-2 operand
+#pragma unroll
+        for (int kg = 0; kg < D1 / 8; ++kg) {
+            float h[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) h[e] = silu(z[8 * kg + e] + bias[8 * kg + e]);
+            uint4 v;
+            v.x = pack_bf16(h[0], h[1]);
+            v.y = pack_bf16(h[2], h[3]);
+            v.z = pack_bf16(h[4], h[5]);
+            v.w = pack_bf16(h[6], h[7]);
+            *(uint4*)(smem + A2 + kmajor_off(tid, 8 * kg, D1)) = v;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int ks = 0; ks < D1 / 16; ++ks)
+                mma(tbase, smem_desc(a2 + ks * 256, 128, (D1 / 8) * 128), smem_desc(b2 + ks * 256, 128, (D1 / 8) * 128),
+                    ks > 0);
+            commit(mbar);
+        }
+        ok = __syncthreads_and(wait_phase(mbar, phase));
+        phase ^= 1u;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        load_row64(trow, z);
+        // h2 = bf16(silu(z2 + b2)); y = W3 h2 + b3 on the CUDA cores
+        float y0 = bias[D1 + D2], y1 = bias[D1 + D2 + 1], y2 = bias[D1 + D2 + 2];
+#pragma unroll
+        for (int k = 0; k < D2; ++k) {
+            const float h = bf16r(silu(z[k] + bias[D1 + k]));
+            y0 = fmaf(h, w3[k], y0);
+            y1 = fmaf(h, w3[D2 + k], y1);
+            y2 = fmaf(h, w3[2 * D2 + k], y2);
+        }
+        if (s < n) {
+            out[s * D3] = y0;
+            out[s * D3 + 1] = y1;
+            out[s * D3 + 2] = y2;
+        }
+        // every thread's accumulator reads are complete before the next tile's MMA
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    if (!ok) {
+        if (tid == 0) atomicExch(status, 1);
+        wait_phase(mbar, phase ^ 1u);  // bounded: let the tensor-core work in flight finish
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(NCOL) : "memory");
 }
 
 // Forward + backward of the mean squared error (1 / 3n) sum (y - t)^2 over
@@ -224,6 +447,9 @@ __global__ void km_adam(float* __restrict__ p, const float* __restrict__ g, floa
 }
 
 // --------------------------------------------------------- features
+// Cell list with cells of at least R_CUT (nc = floor(box / R_CUT) per
+// axis), so that the 27 cells around a point's cell hold every other point
+// within R_CUT.
 __device__ __forceinline__ int cell_of(double X, double box, int nc) {
     int c = (int)(X / box * nc);
     return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
@@ -240,101 +466,201 @@ __global__ void kf_count(const double* __restrict__ pos, long long n, Geom g, in
     atomicAdd(&count[c], 1);
 }
 
-// exclusive scan of count[0..m) into start[0..m], one block
-__global__ void kf_scan(const int* __restrict__ count, int m, int* __restrict__ start) {
-    __shared__ int part[1024];
-    const int per = (m + blockDim.x - 1) / blockDim.x;
-    const int b = threadIdx.x * per;
-    int s = 0;
-    for (int i = b; i < b + per && i < m; ++i) s += count[i];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        for (int i = 0; i < (int)blockDim.x; ++i) {
-            const int t = part[i];
-            part[i] = acc;
-            acc += t;
-        }
-        start[m] = acc;
-    }
-    __syncthreads();
-    int acc = part[threadIdx.x];
-    for (int i = b; i < b + per && i < m; ++i) {
-        start[i] = acc;
-        acc += count[i];
-    }
-}
-
-__global__ void kf_fill(long long n, const int* __restrict__ cell, const int* __restrict__ start,
-                        int* __restrict__ cursor, int* __restrict__ sorted) {
+// Points in cell order: their indices, and their positions rounded to float
+// with the index in w (the candidate filter of kf_knn reads these).
+__global__ void kf_fill(const double* __restrict__ pos, long long n, const int* __restrict__ cell,
+                        const int* __restrict__ start, int* __restrict__ cursor, int* __restrict__ sorted,
+                        float4* __restrict__ spos) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int c = cell[i];
-    sorted[start[c] + atomicAdd(&cursor[c], 1)] = (int)i;
+    const int slot = start[c] + atomicAdd(&cursor[c], 1);
+    sorted[slot] = (int)i;
+    spos[slot] = make_float4((float)pos[3 * i], (float)pos[3 * i + 1], (float)pos[3 * i + 2], __int_as_float((int)i));
 }
 
-// 27 features per colloid: fractional offset, then the 8 nearest others
-// within R_CUT (minimum image), nearest first, equal distances by index.
-__global__ void kf_knn(const double* __restrict__ pos, long long n, Geom g, int3 nc, const int* __restrict__ start,
-                       const int* __restrict__ sorted, float* __restrict__ feat) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double box[3] = {(double)g.nx, (double)g.ny, (double)g.nz};
-    const double P[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
-    double bd[NNB];
-    int bj[NNB];
-    float bv[NNB][3];
-    for (int q = 0; q < NNB; ++q) {
-        bd[q] = 1.0e300;
-        bj[q] = 0x7fffffff;
+// Minimum-image difference, exactly as d - box * rint(d / box) (rint = 0
+// for |d| <= box / 4, where the division is skipped).
+__device__ __forceinline__ double min_image(double d, double box) {
+    return fabs(d) > 0.25 * box ? d - box * rint(d / box) : d;
+}
+
+// Squared distance summed in the order ((dx^2 + dy^2) + dz^2), each step
+// rounded once.
+__device__ __forceinline__ double dist2(const double d[3]) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+}
+
+// Exact top-8 insertion of candidate (ck, cj): ck is the bit pattern of a
+// non-negative FP64 squared distance (ordered as the distances are, so the
+// comparisons run on the integer pipe), equal distances by lower index; the
+// last entry drops out.
+__device__ __forceinline__ void insert_exact(unsigned long long (&bk)[NNB], int (&bj)[NNB], unsigned long long ck,
+                                             int cj) {
+#pragma unroll
+    for (int k = 0; k < NNB; ++k) {
+        const bool lt = ck < bk[k] || (ck == bk[k] && cj < bj[k]);
+        const unsigned long long tk = bk[k];
+        const int tj = bj[k];
+        bk[k] = lt ? ck : tk;
+        bj[k] = lt ? cj : tj;
+        ck = lt ? tk : ck;
+        cj = lt ? tj : cj;
     }
-    const int c0[3] = {cell_of(P[0], box[0], nc.x), cell_of(P[1], box[1], nc.y), cell_of(P[2], box[2], nc.z)};
-    const int ncs[3] = {nc.x, nc.y, nc.z};
-    int lo[3], hi[3];
-    for (int a = 0; a < 3; ++a) {  // neighbouring cells, each visited once
-        if (ncs[a] >= 3) {
-            lo[a] = -1;
-            hi[a] = 1;
-        } else {
-            lo[a] = 0;
-            hi[a] = ncs[a] - 1;
+}
+
+// Minimum-image difference along one axis, d = x_j - x_i, exactly as
+// min_image; the float difference df of the same pair (within 1 of d)
+// settles the common case |d| < box / 4, where no image shift applies.
+__device__ __forceinline__ double min_image_hint(double xj, double xi, float df, double box) {
+    const double d = xj - xi;
+    return fabsf(df) < 0.25f * (float)box - 1.0f ? d : min_image(d, box);
+}
+
+// The 27 cells around cell c0 (each visited once when an axis has fewer
+// than 3 cells), as a flat index for step t = 0 .. ncells - 1.
+struct CellWalk {
+    int c0[3], nc[3], lo[3], span[3], count;
+    __device__ CellWalk(int ci, int3 n) {
+        nc[0] = n.x;
+        nc[1] = n.y;
+        nc[2] = n.z;
+        c0[0] = ci % n.x;
+        c0[1] = (ci / n.x) % n.y;
+        c0[2] = ci / (n.x * n.y);
+        count = 1;
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = nc[a] >= 3 ? -1 : 0;
+            span[a] = nc[a] >= 3 ? 3 : nc[a];
+            count *= span[a];
         }
     }
+    __device__ int cell(int t) const {
+        const int dx = t % span[0] + lo[0], dy = (t / span[0]) % span[1] + lo[1], dz = t / (span[0] * span[1]) + lo[2];
+        const int cx = nc[0] >= 3 ? wrap_node(c0[0] + dx, nc[0]) : dx;
+        const int cy = nc[1] >= 3 ? wrap_node(c0[1] + dy, nc[1]) : dy;
+        const int cz = nc[2] >= 3 ? wrap_node(c0[2] + dz, nc[2]) : dz;
+        return (cz * nc[1] + cy) * nc[0] + cx;
+    }
+};
+
+// 27 features per point: fractional offset, then the 8 nearest others
+// within R_CUT (minimum image), nearest first, equal distances by lower
+// index.  One thread per point, the points taken in cell order so that a
+// warp's threads walk the same cells.
+//
+// Which 8, and in which order, is decided in FP64 exactly as the definition
+// states, but FP64 arithmetic is kept off the per-candidate loop:
+//   1. float pass: squared distances r2f from float positions, whose error
+//      is below `margin`; the KF = 16 smallest r2f <= R_CUT^2 + margin are
+//      kept (registers);
+//   2. window: with F8 the 8th smallest r2f kept, every candidate of the
+//      exact top 8 has r2f <= W = F8 + 2 margin (W = R_CUT^2 + margin when
+//      fewer than 8 were kept), so the FP64 distances of the kept entries
+//      with r2f <= W decide.  If all KF kept entries lie within W an entry
+//      may have been dropped: that thread repeats the search in FP64.
+constexpr int KF = 16;
+
+__global__ void __launch_bounds__(256)
+kf_knn(const double* __restrict__ pos, long long n, Geom g, int3 nc, const int* __restrict__ start,
+       const int* __restrict__ sorted, const int* __restrict__ cell, const float4* __restrict__ spos, float margin,
+       float* __restrict__ feat) {
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int i = sorted[q];
+    const float4 me = spos[q];
+    const double box[3] = {(double)g.nx, (double)g.ny, (double)g.nz};
+    const float boxf[3] = {(float)g.nx, (float)g.ny, (float)g.nz};
+    const float halff[3] = {0.5f * (float)g.nx, 0.5f * (float)g.ny, 0.5f * (float)g.nz};
+    const double P[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
     const double rc2 = (double)R_CUT * (double)R_CUT;
-    for (int dz = lo[2]; dz <= hi[2]; ++dz)
-        for (int dy = lo[1]; dy <= hi[1]; ++dy)
-            for (int dx = lo[0]; dx <= hi[0]; ++dx) {
-                const int cx = (c0[0] + dx + ncs[0]) % ncs[0], cy = (c0[1] + dy + ncs[1]) % ncs[1],
-                          cz = (c0[2] + dz + ncs[2]) % ncs[2];
-                const int c = (cz * ncs[1] + cy) * ncs[0] + cx;
-                for (int q = start[c]; q < start[c + 1]; ++q) {
-                    const int jn = sorted[q];
-                    if (jn == i) continue;
-                    double d[3];
-                    for (int a = 0; a < 3; ++a) {
-                        d[a] = pos[3 * (long long)jn + a] - P[a];
-                        d[a] -= box[a] * rint(d[a] / box[a]);
-                    }
-                    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                    if (r2 > rc2) continue;
-                    if (r2 > bd[NNB - 1] || (r2 == bd[NNB - 1] && jn > bj[NNB - 1])) continue;
-                    int p = NNB - 1;  // insertion into the sorted list
-                    while (p > 0 && (r2 < bd[p - 1] || (r2 == bd[p - 1] && jn < bj[p - 1]))) {
-                        bd[p] = bd[p - 1];
-                        bj[p] = bj[p - 1];
-                        for (int a = 0; a < 3; ++a) bv[p][a] = bv[p - 1][a];
-                        --p;
-                    }
-                    bd[p] = r2;
-                    bj[p] = jn;
-                    for (int a = 0; a < 3; ++a) bv[p][a] = (float)(d[a] / (double)FEAT_LENGTH);
-                }
+    const CellWalk walk(cell[i], nc);
+
+    // 1. float pass
+    float fr[KF];
+    int fq[KF];  // slot in cell order (index = spos[slot].w)
+#pragma unroll
+    for (int k = 0; k < KF; ++k) {
+        fr[k] = 3.0e38f;
+        fq[k] = -1;
+    }
+    int kept = 0;
+    float lim = (float)rc2 + margin;
+    for (int t = 0; t < walk.count; ++t) {
+        const int c = walk.cell(t);
+        const int e = start[c + 1];
+        for (int qq = start[c]; qq < e; ++qq) {
+            const float4 o = spos[qq];
+            float df[3] = {o.x - me.x, o.y - me.y, o.z - me.z};
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                df[a] = df[a] > halff[a] ? df[a] - boxf[a] : (df[a] < -halff[a] ? df[a] + boxf[a] : df[a]);
+            float cr = df[0] * df[0] + df[1] * df[1] + df[2] * df[2];
+            if (qq == q || !(cr <= lim)) continue;
+            int cq = qq;
+#pragma unroll
+            for (int k = 0; k < KF; ++k) {  // sorted insertion; the last entry drops out
+                const bool lt = cr < fr[k];
+                const float tr = fr[k];
+                const int tq = fq[k];
+                fr[k] = lt ? cr : tr;
+                fq[k] = lt ? cq : tq;
+                cr = lt ? tr : cr;
+                cq = lt ? tq : cq;
             }
-    float* f = feat + i * D0;
+            if (++kept >= KF) lim = fminf(lim, fr[KF - 1]);
+        }
+    }
+
+    // 2. exact decision over the window
+    const float W = kept >= NNB ? fr[NNB - 1] + 2.0f * margin : (float)rc2 + margin;
+    const unsigned long long krc2 = (unsigned long long)__double_as_longlong(rc2);
+    unsigned long long bk[NNB];
+    int bj[NNB];
+#pragma unroll
+    for (int k = 0; k < NNB; ++k) {
+        bk[k] = ~0ull;
+        bj[k] = 0x7fffffff;
+    }
+    if (kept >= KF && fr[KF - 1] <= W) {  // window not held in full: search again in FP64
+        for (int t = 0; t < walk.count; ++t) {
+            const int c = walk.cell(t);
+            for (int qq = start[c]; qq < start[c + 1]; ++qq) {
+                const int jn = sorted[qq];
+                if (jn == i) continue;
+                double d[3];
+                for (int a = 0; a < 3; ++a) d[a] = min_image(pos[3 * (long long)jn + a] - P[a], box[a]);
+                const unsigned long long ck = (unsigned long long)__double_as_longlong(dist2(d));
+                if (ck <= krc2) insert_exact(bk, bj, ck, jn);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < KF; ++k) {
+            if (fq[k] >= 0 && fr[k] <= W) {
+                const float4 o = spos[fq[k]];
+                const int jn = __float_as_int(o.w);
+                const float dfx[3] = {o.x - me.x, o.y - me.y, o.z - me.z};
+                double d[3];
+                for (int a = 0; a < 3; ++a) d[a] = min_image_hint(pos[3 * (long long)jn + a], P[a], dfx[a], box[a]);
+                const unsigned long long ck = (unsigned long long)__double_as_longlong(dist2(d));
+                if (ck <= krc2) insert_exact(bk, bj, ck, jn);
+            }
+        }
+    }
+    // outputs: float(d / 4) = float(d) / 4 exactly
+    float* f = feat + (long long)i * D0;
     for (int a = 0; a < 3; ++a) f[a] = (float)(P[a] - floor(P[a]));
-    for (int q = 0; q < NNB; ++q)
-        for (int a = 0; a < 3; ++a) f[3 + 3 * q + a] = bd[q] < 1.0e299 ? bv[q][a] : 0.0f;
+#pragma unroll
+    for (int k = 0; k < NNB; ++k) {
+        if (bk[k] != ~0ull) {
+            const int jn = bj[k];
+            for (int a = 0; a < 3; ++a)
+                f[3 + 3 * k + a] = __double2float_rn(min_image(pos[3 * (long long)jn + a] - P[a], box[a])) * (1.0f / FEAT_LENGTH);
+        } else {
+            for (int a = 0; a < 3; ++a) f[3 + 3 * k + a] = 0.0f;
+        }
+    }
 }
 
 }  // namespace
@@ -342,10 +668,11 @@ __global__ void kf_knn(const double* __restrict__ pos, long long n, Geom g, int3
 struct lb_mlp {
     cudaStream_t stream;
     float *p, *g, *m, *v, *sse;
+    int* status;              // set by the tensor-core forward kernel on a timed-out wait
     long long t;              // Adam steps taken
     int *ws;                  // feature workspace (cell lists), grown on demand
     size_t ws_ints;
-    int smem_fwd, smem_grad, blocks;
+    int smem_grad, blocks;
     std::string err;
 };
 
@@ -364,6 +691,18 @@ lb_status mfail(lb_mlp* net, lb_status s, const std::string& m) {
                          std::string(where) + ": " + cudaGetErrorString(e_));                     \
     } while (0)
 
+// Wait for the network's stream and report a timed-out tensor-core wait.
+lb_status check_status(lb_mlp* net) {
+    int st = 0;
+    LB_MCUDA(cudaMemcpyAsync(&st, net->status, sizeof(int), cudaMemcpyDeviceToHost, net->stream), "status read");
+    LB_MCUDA(cudaStreamSynchronize(net->stream), "stream synchronize");
+    if (st) {
+        LB_MCUDA(cudaMemsetAsync(net->status, 0, sizeof(int), net->stream), "status reset");
+        return mfail(net, LB_ERR_TIMEOUT, "forward kernel: a tensor-core wait timed out");
+    }
+    return LB_OK;
+}
+
 int grid_for(long long n) {
     const long long tiles = (n + TS - 1) / TS;
     return (int)(tiles < 152LL * 2 ? (tiles > 0 ? tiles : 1) : 152LL * 2);
@@ -373,40 +712,58 @@ int grid_for(long long n) {
 
 namespace lbk {
 
-size_t mlp_features_ws_ints(long long n, const int box[3]) {
-    long long m = 1;
-    for (int a = 0; a < 3; ++a) m *= (box[a] / (int)R_CUT > 0 ? box[a] / (int)R_CUT : 1);
-    return (size_t)(m + (m + 1) + m + 2 * n);  // count, start, cursor, cell, sorted
-}
-
-cudaError_t mlp_features(long long n, const double* pos, const int box[3], float* feat, int* ws, cudaStream_t st) {
+static int3 feature_cells(const int box[3]) {
     int3 nc;
     nc.x = box[0] / (int)R_CUT > 0 ? box[0] / (int)R_CUT : 1;
     nc.y = box[1] / (int)R_CUT > 0 ? box[1] / (int)R_CUT : 1;
     nc.z = box[2] / (int)R_CUT > 0 ? box[2] / (int)R_CUT : 1;
+    return nc;
+}
+
+// Workspace in ints: the float4 positions in cell order (4 n, first, so
+// 16-byte aligned), count, cursor, start (m + 1), cell and sorted index per
+// point, the scan's tile sums.
+size_t mlp_features_ws_ints(long long n, const int box[3]) {
+    const int3 nc = feature_cells(box);
     const long long m = (long long)nc.x * nc.y * nc.z;
-    int* count = ws;
-    int* start = count + m;
-    int* cursor = start + m + 1;
-    int* cell = cursor + m;
+    return (size_t)(4 * n + 3 * m + 1 + 2 * n) + scan_ws_ints(m);
+}
+
+cudaError_t mlp_features(long long n, const double* pos, const int box[3], float* feat, int* ws, cudaStream_t st) {
+    const int3 nc = feature_cells(box);
+    const long long m = (long long)nc.x * nc.y * nc.z;
+    float4* spos = (float4*)ws;
+    int* count = ws + 4 * n;
+    int* cursor = count + m;
+    int* start = cursor + m;
+    int* cell = start + m + 1;
     int* sorted = cell + n;
+    int* bsum = sorted + n;
     Geom g{};
     g.nx = box[0];
     g.ny = box[1];
     g.nz = box[2];
-    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * m, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, sizeof(int) * m, st);
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * 2 * m, st);
     if (e != cudaSuccess) return e;
+    // float error of a coordinate difference <= box 2^-22 + |d| 2^-23; the
+    // margin bounds the error of |d|^2 near the cutoff with a factor 4 to spare
+    const double bmax = (double)std::max(box[0], std::max(box[1], box[2]));
+    const double ea = bmax * 0x1p-20 + 0x1p-18;
+    const float margin = (float)(2.0 * ea * 1.7320508075688772 * (R_CUT + 1.0) + 3.0 * ea * ea + 1e-5);
     const unsigned blocks = (unsigned)((n + 255) / 256);
     kf_count<<<blocks, 256, 0, st>>>(pos, n, g, nc, count, cell);
-    kf_scan<<<1, 1024, 0, st>>>(count, (int)m, start);
-    kf_fill<<<blocks, 256, 0, st>>>(n, cell, start, cursor, sorted);
-    kf_knn<<<blocks, 256, 0, st>>>(pos, n, g, nc, start, sorted, feat);
+    e = scan_exclusive(count, m, start, bsum, st);
+    if (e != cudaSuccess) return e;
+    kf_fill<<<blocks, 256, 0, st>>>(pos, n, cell, start, cursor, sorted, spos);
+    kf_knn<<<blocks, 256, 0, st>>>(pos, n, g, nc, start, sorted, cell, spos, margin, feat);
     return cudaGetLastError();
 }
 
 cudaError_t mlp_forward(const lb_mlp* net, long long n, const float* feat, float* out, cudaStream_t st) {
-    km_forward<<<grid_for(n), NT, net->smem_fwd, st>>>(net->p, n, feat, out);
+    const long long tiles = (n + tc::M - 1) / tc::M;
+    const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(tiles, 152LL * 4));
+    km_forward_tc<<<grid, tc::M, tc::SMEM, st>>>(net->p, n, feat, out, net->status);
     return cudaGetLastError();
 }
 
@@ -422,7 +779,6 @@ lb_status lb_mlp_create(lb_mlp** out, const float* init, void* stream) {
     lb_mlp* net = new (std::nothrow) lb_mlp();
     if (!net) return LB_ERR_OOM;
     net->stream = (cudaStream_t)stream;
-    net->smem_fwd = Smem::FWD_END * (int)sizeof(float);
     net->smem_grad = Smem::END * (int)sizeof(float);
     cudaError_t e = cudaMalloc(&net->p, sizeof(float) * (4 * NPARAM + 1));
     if (e == cudaSuccess) {
@@ -434,7 +790,9 @@ lb_status lb_mlp_create(lb_mlp** out, const float* init, void* stream) {
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(net->p, init, sizeof(float) * NPARAM, cudaMemcpyDefault, net->stream);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(km_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, net->smem_grad);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(km_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, net->smem_fwd);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(km_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM);
+    if (e == cudaSuccess) e = cudaMalloc(&net->status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(net->status, 0, sizeof(int), net->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
     if (e != cudaSuccess) {
         lb_mlp_destroy(net);
@@ -449,6 +807,7 @@ void lb_mlp_destroy(lb_mlp* net) {
     cudaStreamSynchronize(net->stream);
     cudaFree(net->p);
     cudaFree(net->ws);
+    cudaFree(net->status);
     delete net;
 }
 
@@ -490,7 +849,7 @@ lb_status lb_mlp_forward(lb_mlp* net, long long n, const float* feat, float* out
     if (!net || n < 0 || (n && (!feat || !out))) return mfail(net, LB_ERR_ARG, "lb_mlp_forward: bad argument");
     if (n == 0) return LB_OK;
     LB_MCUDA(lbk::mlp_forward(net, n, feat, out, net->stream), "forward kernel");
-    return LB_OK;
+    return check_status(net);
 }
 
 static lb_status run_grad(lb_mlp* net, long long n, const float* feat, const float* target) {

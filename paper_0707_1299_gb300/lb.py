@@ -19,7 +19,7 @@ import numpy as np
 
 from .build import LIB
 
-LB_OK, LB_ERR_ARG, LB_ERR_CUDA, LB_ERR_OOM, LB_ERR_NONFINITE, LB_ERR_STATE = range(6)
+LB_OK, LB_ERR_ARG, LB_ERR_CUDA, LB_ERR_OOM, LB_ERR_NONFINITE, LB_ERR_STATE, LB_ERR_TIMEOUT = range(7)
 LB_F64, LB_F32, LB_F16S, LB_BF16S = range(4)
 LB_STOKESLET, LB_STRESSLET, LB_ROTLET, LB_COLLOID = range(4)
 NQ = 19

@@ -42,6 +42,59 @@ def test_features_match_brute_force():
         lb.lb_mlp_destroy(net)
 
 
+def _features(lb, pos, box):
+    n = len(pos)
+    net = lb.lb_mlp_create(np.zeros(lb.lb_mlp_num_params(), dtype=np.float32))
+    P = torch.as_tensor(pos, device="cuda").contiguous()
+    f = torch.empty((n, 27), dtype=torch.float32, device="cuda")
+    lb.lb_mlp_features(net, n, P, box, f)
+    lb.lb_mlp_destroy(net)
+    return f.cpu().numpy()
+
+
+def test_features_dense_and_near_ties():
+    # (a) the number density of the 2e5-colloid 256^3 workload in a 64^3
+    # box: about 25 others within the cutoff, so the kept list of the
+    # float pass is full and the FP64 window decides;
+    # (b) points on a grid of spacing (2, 2.5, 3) jittered by 1e-9, far
+    # below float resolution: the four next-nearest at sqrt(10.25) tie in
+    # float and the FP64 distances decide which two enter, by lower index
+    # on an exact tie;
+    # (c) a cubic grid of spacing 2 (exact ties everywhere): 18 entries
+    # share the window, more than the float pass keeps, so the FP64
+    # search repeats for every point.
+    lb = _lb()
+    rng = np.random.default_rng(21)
+    box = (64, 64, 64)
+    pos = rng.uniform(0, 64, (int(round(2e5 / 256 ** 3 * 64 ** 3)), 3))
+    assert np.abs(_features(lb, pos, box) - mlp.features(pos, box)).max() < 1e-6
+    g = np.stack(np.meshgrid(np.arange(8) * 2.0, np.arange(8) * 2.5, np.arange(8) * 3.0, indexing="ij"), -1)
+    pos = g.reshape(-1, 3) + 0.25 + rng.uniform(-1e-9, 1e-9, (512, 3))
+    box = (16, 20, 24)
+    assert np.abs(_features(lb, pos, box) - mlp.features(pos, box)).max() < 1e-6
+    g = np.stack(np.meshgrid(*[np.arange(8) * 2.0] * 3, indexing="ij"), -1)
+    pos = g.reshape(-1, 3) + 0.5
+    box = (16, 16, 16)
+    assert np.abs(_features(lb, pos, box) - mlp.features(pos, box)).max() < 1e-6
+
+
+def test_forward_many_tiles():
+    # the tensor-core forward over 157 tiles of 128 samples (ragged last
+    # tile) at the scale of the corrected step's inputs
+    lb = _lb()
+    n = 128 * 156 + 37
+    P, x, _ = _random_problem(n, 4)
+    v = mlp.flatten(P).astype(np.float32)
+    net = lb.lb_mlp_create(v)
+    X = torch.as_tensor(x, dtype=torch.float32, device="cuda").contiguous()
+    y = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    lb.lb_mlp_forward(net, n, X, y)
+    yref, _ = mlp.forward(mlp.unflatten(v.astype(np.float64)), x.astype(np.float32).astype(np.float64), bf16_round=True)
+    err = np.abs(y.cpu().numpy() - yref).max(axis=1) / np.abs(yref).max()
+    assert np.quantile(err, 0.98) < 1e-5 and err.max() < 2e-2
+    lb.lb_mlp_destroy(net)
+
+
 def _random_problem(n, seed):
     rng = np.random.default_rng(seed)
     P = mlp.init_params(seed)
