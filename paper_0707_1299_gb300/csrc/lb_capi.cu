@@ -145,6 +145,7 @@ lb_status grow_points(lb_ctx* c, int need) {
 }
 
 lb_status invalidate_field(lb_ctx* c) {
+    c->fix_ok = false;
     if (!c->field_ready) return LB_OK;
     LB_CUDA(lbk::launch_clear_field(c), "clear force field");
     c->field_ready = false;
@@ -199,6 +200,8 @@ lb_status ensure_field(lb_ctx* c) {
     }
     LB_CUDA(lbk::launch_spread(c), "spread kernel");
     c->field_ready = true;
+    // fixed points keep this field: list its tiles once for the fix-up path
+    if (c->n_mobile == 0) LB_CUDA(lbk::list_fixed_tiles(c), "tile list");
     return LB_OK;
 }
 
@@ -292,6 +295,7 @@ void lb_destroy(lb_ctx* c) {
     cudaFree(c->sort_ws);
     cudaFree(c->stencil);
     cudaFree(c->pt_v);
+    cudaFree(c->fix_list);
     cudaFree(c->pos);
     cudaFree(c->force);
     cudaFree(c->radius);

@@ -29,6 +29,9 @@ struct lb_ctx {
     void* vel;                // fluid velocity in the flagged tiles, 3 V elements of the
                               // arithmetic type (lattices with colloids only)
     bool field_ready;         // floc holds the forces at the current positions
+    unsigned* fix_list;       // flagged tiles of a field of fixed points (then a count)
+    int fix_count;
+    bool fix_ok;              // the list holds every flagged tile: collide field-free + fix-up
 
     // monopoles after expansion (device, xyz interleaved)
     int npts, cap, n_mobile;
@@ -88,6 +91,7 @@ cudaError_t launch_update(lb_ctx* c, const float* y);
 cudaError_t launch_stencil(lb_ctx* c);
 cudaError_t launch_sort_points(lb_ctx* c);
 cudaError_t ensure_velocity_field(lb_ctx* c);
+cudaError_t list_fixed_tiles(lb_ctx* c);
 size_t sort_ws_ints(const Geom& g, long long npts);
 size_t scan_ws_ints(long long m);
 cudaError_t scan_exclusive(const int* in, long long m, int* out, int* bsum, cudaStream_t st);

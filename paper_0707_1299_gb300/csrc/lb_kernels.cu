@@ -76,6 +76,37 @@ static dim3 site_grid(const Geom& g) {
     return dim3((unsigned)g.ntx, (unsigned)((g.ny + CS_WARPS - 1) / CS_WARPS), (unsigned)g.nz);
 }
 
+// Collision and store of one site from its pulled populations f: force =
+// uniform + (field ? localised : 0), in the stored units of the format;
+// with VOUT and a field, v = (j + F/2) / rho is written to vel as well.
+template <typename S, bool VOUT>
+__device__ __forceinline__ void finish_site(const typename Store<S>::T (&f)[NQ], const Pops<S>& dst,
+                                            const typename Store<S>::T* __restrict__ floc,
+                                            typename Store<S>::T* __restrict__ vel, unsigned V, unsigned site,
+                                            bool field, const Coef<typename Store<S>::T>& k,
+                                            const UForce<typename Store<S>::T>& fu, float scale, float inv_scale,
+                                            unsigned seed) {
+    using T = typename Store<S>::T;
+    constexpr bool SC = Store<S>::kScaled;
+    T Fx = fu.F[0], Fy = fu.F[1], Fz = fu.F[2];
+    if (field) {
+        const T s = SC ? (T)scale : T(1);
+        Fx += floc[site] * s;
+        Fy += floc[V + site] * s;
+        Fz += floc[2 * V + site] * s;
+    }
+    T o[NQ], v3[3];
+    collide19<T, Store<S>::kCompensate, SC, VOUT>(f, Fx, Fy, Fz, k, o, (T)inv_scale, v3);
+    unsigned rn = rng_seed(site, seed);
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) Store<S>::st(dst.p[i], site, o[i], rng_next(rn));
+    if (VOUT && field) {
+        vel[site] = v3[0];
+        vel[V + site] = v3[1];
+        vel[2 * V + site] = v3[2];
+    }
+}
+
 // ------------------------------------------------------------ k_collide
 // NY consecutive y rows per thread (all loads of the NY sites issued
 // first).  The half format is handled in its scaled units throughout.
@@ -128,26 +159,52 @@ k_collide(const Pops<S> src, const Pops<S> dst, const typename Store<S>::T* __re
 #pragma unroll
             for (int r = 0; r < NY; ++r) {
                 if (y0 + r >= g.ny) break;
-                const unsigned site = n[r].c + n[r].x;
-                T Fx = fu.F[0], Fy = fu.F[1], Fz = fu.F[2];
-                if (FIELD && fl[r]) {  // after the population loads, so both are in flight together
-                    const T s = SC ? (T)scale : T(1);
-                    Fx += floc[site] * s;
-                    Fy += floc[V + site] * s;
-                    Fz += floc[2 * V + site] * s;
-                }
-                T o[NQ], v3[3];
-                collide19<T, Store<S>::kCompensate, SC, VOUT>(f[r], Fx, Fy, Fz, k, o, (T)inv_scale, v3);
-                unsigned rn = rng_seed(site, seed);
-#pragma unroll
-                for (int i = 0; i < NQ; ++i) Store<S>::st(dst.p[i], site, o[i], rng_next(rn));
-                if (VOUT && fl[r]) {
-                    vel[site] = v3[0];
-                    vel[V + site] = v3[1];
-                    vel[2 * V + site] = v3[2];
-                }
+                // the field loads come after the population loads, so both are in flight together
+                finish_site<S, VOUT>(f[r], dst, floc, vel, V, n[r].c + n[r].x, FIELD && fl[r], k, fu, scale, inv_scale,
+                                     seed);
             }
         }
+    }
+}
+
+// Fix-up for a few fixed points: the collide ran with the uniform force at
+// every site (FM_NONE); one warp per listed tile recomputes its sites with
+// the localised force added and overwrites them, with the same arithmetic
+// and the same rounding bits as the field-aware collide.  Solid sites carry
+// no force (the spread skips them), so they are left as they are.
+template <typename S, bool WALLS>
+__global__ void __launch_bounds__(CS_THREADS)
+k_fixup(const Pops<S> src, const Pops<S> dst, const typename Store<S>::T* __restrict__ floc,
+        const unsigned* __restrict__ list, int count, Geom g, Coef<typename Store<S>::T> k,
+        UForce<typename Store<S>::T> fu, float scale, float inv_scale, unsigned seed) {
+    using T = typename Store<S>::T;
+    const int w = blockIdx.x * CS_WARPS + threadIdx.y;
+    if (w >= count) return;
+    const unsigned tile = list[w];
+    const unsigned row = tile / (unsigned)g.ntx;
+    const int x = (int)(tile - row * (unsigned)g.ntx) * TILE_X + threadIdx.x;
+    const int y = (int)(row % (unsigned)g.ny), z = (int)(row / (unsigned)g.ny);
+    if (x >= g.nx || (WALLS && is_solid(g, z))) return;
+    const Nbr n = neighbours(g, x, y, z);
+    T f[NQ];
+    pull19<S, WALLS>(src, n, f);
+    finish_site<S, false>(f, dst, floc, nullptr, (unsigned)g.V, n.c + n.x, true, k, fu, scale, inv_scale, seed);
+}
+
+// Compact list of the flagged tiles (at most cap written; *count gets the
+// total).  One warp per 32 flags.
+__global__ void k_list_tiles(const flag_t* __restrict__ flags, long long ntiles, unsigned* __restrict__ list,
+                             unsigned cap, unsigned* __restrict__ count) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool mine = t < ntiles && flags[t] != 0;
+    const unsigned m = __ballot_sync(0xffffffffu, mine);
+    const int lane = threadIdx.x & 31;
+    unsigned base = 0;
+    if (lane == 0 && m) base = atomicAdd(count, (unsigned)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (mine) {
+        const unsigned idx = base + (unsigned)__popc(m & ((1u << lane) - 1u));
+        if (idx < cap) list[idx] = (unsigned)t;
     }
 }
 
@@ -738,6 +795,30 @@ size_t sort_ws_ints(const Geom& g, long long npts) {
     return (size_t)(3 * nb + 1) + scan_ws_ints(nb) + (size_t)npts;
 }
 
+// The flagged tiles of a field of fixed points, listed for the fix-up when
+// they are few (at most 1/64 of all tiles): reads the count back (waits).
+cudaError_t list_fixed_tiles(lb_ctx* c) {
+    c->fix_ok = false;
+    const unsigned cap = (unsigned)std::max<long long>(1024, c->geom.ntiles / 64);
+    if (!c->fix_list) {
+        cudaError_t e = cudaMalloc(&c->fix_list, sizeof(unsigned) * (cap + 1));
+        if (e != cudaSuccess) return e;
+    }
+    unsigned* count = c->fix_list + cap;
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned), c->stream);
+    if (e != cudaSuccess) return e;
+    k_list_tiles<<<(unsigned)((c->geom.ntiles + 255) / 256), 256, 0, c->stream>>>(c->flags, c->geom.ntiles, c->fix_list,
+                                                                                 cap, count);
+    c->launches++;
+    unsigned n = 0;
+    e = cudaMemcpyAsync(&n, count, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return e;
+    c->fix_count = (int)n;
+    c->fix_ok = n <= cap;
+    return cudaSuccess;
+}
+
 cudaError_t ensure_velocity_field(lb_ctx* c) {
     if (c->vel || c->n_mobile == 0) return cudaSuccess;
     return cudaMalloc(&c->vel, arith_bytes(c->prec) * 3 * (size_t)c->geom.V);
@@ -787,7 +868,9 @@ static cudaError_t collide_t(lb_ctx* c) {
                     (unsigned)c->geom.nz);
     const T* floc = (const T*)c->floc;
     T* vel = (T*)c->vel;
-    const int mode = c->npts == 0 ? FM_NONE : (c->n_mobile > 0 ? FM_VEL : FM_FIELD);
+    // a few fixed points: field-free collide plus the fix-up of their tiles
+    const bool fixup = c->npts > 0 && c->n_mobile == 0 && c->fix_ok;
+    const int mode = (c->npts == 0 || fixup) ? FM_NONE : (c->n_mobile > 0 ? FM_VEL : FM_FIELD);
 #define LB_COLLIDE(W, FM)                                                                                     \
     k_collide<S, W, NY, FM><<<grid, site_block(), 0, c->stream>>>(src, dst, floc, c->flags, vel, c->geom, k, fu, \
                                                                 c->scale, c->inv_scale, c->seed)
@@ -801,8 +884,18 @@ static cudaError_t collide_t(lb_ctx* c) {
         else LB_COLLIDE(false, FM_NONE);
     }
 #undef LB_COLLIDE
-    c->seed = c->seed * 747796405u + 2891336453u;  // next step's rounding seed
     c->launches++;
+    if (fixup && c->fix_count > 0) {
+        const unsigned blocks = (unsigned)((c->fix_count + CS_WARPS - 1) / CS_WARPS);
+        if (has_walls(c))
+            k_fixup<S, true><<<blocks, site_block(), 0, c->stream>>>(src, dst, floc, c->fix_list, c->fix_count, c->geom,
+                                                                     k, fu, c->scale, c->inv_scale, c->seed);
+        else
+            k_fixup<S, false><<<blocks, site_block(), 0, c->stream>>>(src, dst, floc, c->fix_list, c->fix_count,
+                                                                      c->geom, k, fu, c->scale, c->inv_scale, c->seed);
+        c->launches++;
+    }
+    c->seed = c->seed * 747796405u + 2891336453u;  // next step's rounding seed
     return cudaGetLastError();
 }
 

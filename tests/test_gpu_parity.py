@@ -127,6 +127,30 @@ def test_multipole_recipe_reduced(prec):
         g.close()
 
 
+@pytest.mark.parametrize("npts", [6, 400])
+def test_fixed_points_fixup_and_field_paths(npts):
+    # Fixed Stokeslets on 64^3 (8192 force tiles): a few flag fewer than
+    # 1024 tiles and take the field-free collide plus the fix-up of their
+    # tiles; 400 flag several thousand and take the field-aware collide.
+    # Both against the oracle after 60 steps (FP64 and FP32).
+    lb = _lb()
+    r = W.rng(77 + npts)
+    pos = r.uniform(0, 64, (npts, 3))
+    F = r.normal(0, 1e-5, (npts, 3))
+    prob = W.Problem(f"stokeslets{npts}", (64, 64, 64), 0.5, 0.7, steps=60,
+                     points=[W.PointSet(W.STOKESLET, pos, F, None)])
+    o = oracle_lattice(prob)
+    o.step(prob.steps)
+    ref = o.observe()
+    for prec in ("f64", "f32"):
+        g = gpu_lattice(prob, lb.LB_F64 if prec == "f64" else lb.LB_F32)
+        g.step(prob.steps)
+        _, u, _ = g.moments()
+        err = rel_err(u.cpu().numpy(), ref["u"])
+        assert err < TOL[prec], (prec, err)
+        g.close()
+
+
 @pytest.mark.parametrize("prec", ["f32", "f16s", "bf16s"])
 def test_channel_256_full_size(prec):
     # The wall-bounded channel at its full 256^3 size, 2000 steps, as the
