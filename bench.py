@@ -266,6 +266,9 @@ def run_gpu(args, rank, world):
     others = None
     if rank == 0 and world == 1 and not args.no_per_precision:
         others = per_precision(L, {p: (10 if p == "f64" else 100) for p in PREC_NAMES if p != prec})
+    c512 = None
+    if rank == 0 and world == 1 and not args.no_colloids512:
+        c512 = colloids_512()
     batched = None
     if rank == 0 and world == 1 and not args.no_batched:
         batched = batched_replicas()
@@ -293,6 +296,7 @@ def run_gpu(args, rank, world):
         "gpu_launches": launches,
         "clocks": clk,
         "per_precision": others,
+        "colloids_512": c512,
         "batched": batched,
         "learned": learned,
     }
@@ -351,6 +355,61 @@ def per_precision(L, steps_for):
         for _, g in lats:
             g.close()
         torch.cuda.empty_cache()
+    return out
+
+
+def colloids_512(L=512, n=100000, steps=100, timed=40):
+    """The 512^3 sedimentation box: 1e5 colloids (seed 3) with force 1e-6
+    and radius 0.117, counter-force, a_L along z; every storage format
+    stepped `steps` times, the last `timed` device-timed with CUDA events.
+    Velocity field and colloid displacements are compared with the FP64
+    run of the same configuration (the FP64 CUDA path is checked against
+    the oracle on this recipe at 40^3 by the parity tests); FP64 mass and
+    momentum totals are reported beside it."""
+    import torch
+    from paper_0707_1299_gb300 import lb, workloads as W
+    peak, _ = measured_peaks()
+    prob = W.colloids(L=L, n=n, seed=3, force=1e-6)
+    aL = lb.lb_compute_aL(prob.grid, [L / 2 + 0.5] * 3, [0, 0, 1])
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    V = L ** 3
+    ref = None
+    out = {"workload": f"{L}^3 periodic, {n} colloids (seed 3), force 1e-6, a = 0.117, counter-force, a_L = {aL:.4g}",
+           "steps": steps, "timed_steps": timed}
+    for prec in ("f64", "f32", "f16s", "bf16s"):
+        g = lb.Lattice(prob.grid, prob.tau_s, prob.tau_b, PREC_NAMES[prec])
+        g.set_colloid_aL(aL)
+        ps = prob.points[0]
+        g.add_point_forces(ps.kind, ps.pos, ps.F, ps.param)
+        p0, _ = g.particles()
+        g.step(steps - timed)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        g.step(timed)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / timed
+        _, u, tot = g.moments()
+        p1, _ = g.particles()
+        disp = p1 - p0
+        disp -= L * torch.round(disp / L)
+        row = {"value": round(V / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS", "ms_per_step": round(ms, 4),
+               "hbm_frac_of_step": round(2 * 19 * BYTES[prec] * V / (ms * 1e-3) / 1e9 / peak, 4)}
+        if ref is None:
+            ref = (u, disp)
+            t = tot.cpu().numpy()
+            row["totals"] = {"mass_minus_V": float(t[0] - V), "momentum": [float(x) for x in t[1:]]}
+        else:
+            row["max_rel_velocity_vs_f64"] = float((u - ref[0]).abs().max() / ref[0].abs().max())
+            row["max_rel_displacement_vs_f64"] = float((disp - ref[1]).abs().max() / ref[1].abs().max())
+            del u
+        out[prec] = row
+        g.close()
+        torch.cuda.empty_cache()
+    del ref
+    torch.cuda.empty_cache()
     return out
 
 
@@ -538,6 +597,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-precision", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-colloids512", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

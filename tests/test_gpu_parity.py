@@ -229,6 +229,39 @@ def test_colloids_reduced(prec):
     g.close()
 
 
+def test_colloids_512_full_size():
+    # The 512^3 sedimentation box at full size (1e5 colloids, seed 3), in
+    # the launch configuration the benchmark times, 30 steps: FP64 mass and
+    # momentum totals (the counter-force keeps the momentum at zero), and
+    # the FP32 velocity field and colloid displacements against the FP64
+    # run (the FP64 path is checked against the oracle on this recipe at
+    # 40^3 above).
+    lb = _lb()
+    L, steps = 512, 30
+    prob = W.colloids(L=L, n=100000, seed=3, force=1e-6)
+    aL = lb.lb_compute_aL(prob.grid, [L / 2 + 0.5] * 3, [0, 0, 1])
+    res = {}
+    for prec in ("f64", "f32"):
+        g = gpu_lattice(prob, PREC_ID[prec])
+        g.set_colloid_aL(aL)
+        p0, _ = g.particles()
+        g.step(steps)
+        _, u, tot = g.moments()
+        p1, _ = g.particles()
+        d = p1 - p0
+        d -= L * torch.round(d / L)
+        res[prec] = (u, d, tot.cpu().numpy())
+        g.close()
+        torch.cuda.empty_cache()
+    t = res["f64"][2]
+    assert abs(t[0] - L ** 3) < 1e-12 * L ** 3
+    assert np.abs(t[1:]).max() < TOL["f64"] * steps * 0.1  # impulse of the point forces: 0.1 per step
+    u64, d64, _ = res["f64"]
+    u32, d32, _ = res["f32"]
+    assert float((u32 - u64).abs().max() / u64.abs().max()) < TOL["f32"]
+    assert float((d32 - d64).abs().max() / d64.abs().max()) < TOL["f32"]
+
+
 def test_aL_kernel_matches_oracle():
     lb = _lb()
     for n, R, d in [((16, 16, 16), [8.3, 7.6, 8.45], [0, 0, 1]), ((12, 20, 9), [1.1, 19.7, 4.0], None),
