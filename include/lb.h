@@ -169,6 +169,22 @@ lb_status lb_set_populations(lb_ctx *ctx, const double *df);
  * count kept on the host; copies and memsets are not counted). */
 lb_status lb_kernel_launches(const lb_ctx *ctx, long long *count);
 
+/* Checkpoint of the whole state of a context: lattice parameters, the
+ * expanded point list (positions, forces, radii, mobility), the populations
+ * of the current step in the storage format (raw bytes: the restored state
+ * is the saved one bit for bit), and the stochastic-rounding seed, followed
+ * by a 64-bit FNV-1a hash of the file.  The continued run equals the
+ * uninterrupted one bit for bit wherever no two stencils overlap (where
+ * they do, the order of the spreading atomics may change the last bits).  lb_save waits for the context's stream
+ * and writes `path` (LB_ERR_ARG if it cannot be written).  lb_load reads a
+ * checkpoint into a context of the same grid and precision and replaces
+ * its state; LB_ERR_ARG for a missing, foreign, truncated or corrupt file
+ * or a grid or precision mismatch (the context is then unchanged).  Host
+ * memory of one population buffer is used while loading.  Not part of the
+ * paper: restart support for long runs. */
+lb_status lb_save(lb_ctx *ctx, const char *path);
+lb_status lb_load(lb_ctx *ctx, const char *path);
+
 /* Wait for all work issued on the context's stream. */
 lb_status lb_synchronize(lb_ctx *ctx);
 

@@ -593,6 +593,179 @@ lb_status lb_set_populations(lb_ctx* c, const double* df) {
     return finish(c, args, 1, any_host);
 }
 
+// ------------------------------------------------------------ checkpoints
+// File layout (host byte order): a fixed header, then the expanded point
+// arrays, then the populations of the current step in the storage format
+// (raw bytes: a restart continues bit for bit), then a 64-bit FNV-1a hash
+// of everything before it.
+namespace {
+
+struct CkptHeader {
+    char magic[8];            // "LBCKPT1\0"
+    int grid[3], prec;
+    double tau_s, tau_b, g[3], a_L;
+    int counter, wall_lo, wall_hi;
+    unsigned seed;
+    float scale, inv_scale;
+    int npts, n_mobile;
+    long long pop_bytes;
+};
+
+struct Fnv {
+    unsigned long long h = 1469598103934665603ull;
+    void add(const void* p, size_t n) {
+        const unsigned char* b = (const unsigned char*)p;
+        for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    }
+};
+
+constexpr size_t CKPT_CHUNK = (size_t)64 << 20;
+
+bool write_all(FILE* f, const void* p, size_t n, Fnv& h) {
+    h.add(p, n);
+    return fwrite(p, 1, n, f) == n;
+}
+
+bool read_all(FILE* f, void* p, size_t n, Fnv& h) {
+    if (fread(p, 1, n, f) != n) return false;
+    h.add(p, n);
+    return true;
+}
+
+}  // namespace
+
+lb_status lb_save(lb_ctx* c, const char* path) {
+    if (!c) return LB_ERR_ARG;
+    if (!path) return fail(c, LB_ERR_ARG, "lb_save: path is NULL");
+    CkptHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, "LBCKPT1", 8);
+    h.grid[0] = c->geom.nx;
+    h.grid[1] = c->geom.ny;
+    h.grid[2] = c->geom.nz;
+    h.prec = c->prec;
+    h.tau_s = c->tau_s;
+    h.tau_b = c->tau_b;
+    for (int a = 0; a < 3; ++a) h.g[a] = c->g[a];
+    h.a_L = c->a_L;
+    h.counter = c->counter;
+    h.wall_lo = c->geom.wall_lo;
+    h.wall_hi = c->geom.wall_hi;
+    h.seed = c->seed;
+    h.scale = c->scale;
+    h.inv_scale = c->inv_scale;
+    h.npts = c->npts;
+    h.n_mobile = c->n_mobile;
+    h.pop_bytes = (long long)(lbk::storage_bytes(c->prec) * lbk::NQ * (size_t)c->geom.V);
+    const size_t n = (size_t)c->npts;
+    std::string pts;
+    pts.resize(n * (sizeof(double) * 7 + sizeof(int)));
+    char* q = &pts[0];
+    if (n) {
+        LB_CUDA(cudaMemcpyAsync(q, c->pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream), "copy");
+        LB_CUDA(cudaMemcpyAsync(q + sizeof(double) * 3 * n, c->force, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost,
+                                c->stream),
+                "copy");
+        LB_CUDA(cudaMemcpyAsync(q + sizeof(double) * 6 * n, c->radius, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                                c->stream),
+                "copy");
+        LB_CUDA(cudaMemcpyAsync(q + sizeof(double) * 7 * n, c->mobile, sizeof(int) * n, cudaMemcpyDeviceToHost,
+                                c->stream),
+                "copy");
+    }
+    LB_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+    FILE* f = fopen(path, "wb");
+    if (!f) return fail(c, LB_ERR_ARG, std::string("lb_save: cannot open ") + path);
+    Fnv hash;
+    bool ok = write_all(f, &h, sizeof(h), hash) && write_all(f, pts.data(), pts.size(), hash);
+    std::string buf;
+    buf.resize(std::min<size_t>(CKPT_CHUNK, (size_t)h.pop_bytes));
+    const char* src = (const char*)c->f[c->cur];
+    for (size_t off = 0; ok && off < (size_t)h.pop_bytes; off += buf.size()) {
+        const size_t len = std::min(buf.size(), (size_t)h.pop_bytes - off);
+        cudaError_t e = cudaMemcpyAsync(&buf[0], src + off, len, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            fclose(f);
+            return cuda_fail(c, e, "lb_save: population copy");
+        }
+        ok = write_all(f, buf.data(), len, hash);
+    }
+    const unsigned long long digest = hash.h;
+    ok = ok && fwrite(&digest, sizeof(digest), 1, f) == 1;
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) return fail(c, LB_ERR_ARG, std::string("lb_save: write failed: ") + path);
+    return LB_OK;
+}
+
+lb_status lb_load(lb_ctx* c, const char* path) {
+    if (!c) return LB_ERR_ARG;
+    if (!path) return fail(c, LB_ERR_ARG, "lb_load: path is NULL");
+    FILE* f = fopen(path, "rb");
+    if (!f) return fail(c, LB_ERR_ARG, std::string("lb_load: cannot open ") + path);
+    Fnv hash;
+    CkptHeader h;
+    const long long pop_bytes = (long long)(lbk::storage_bytes(c->prec) * lbk::NQ * (size_t)c->geom.V);
+    if (!read_all(f, &h, sizeof(h), hash) || memcmp(h.magic, "LBCKPT1", 8) != 0) {
+        fclose(f);
+        return fail(c, LB_ERR_ARG, "lb_load: not a checkpoint file");
+    }
+    if (h.grid[0] != c->geom.nx || h.grid[1] != c->geom.ny || h.grid[2] != c->geom.nz || h.prec != c->prec ||
+        h.pop_bytes != pop_bytes || h.npts < 0 || h.n_mobile < 0 || h.n_mobile > h.npts) {
+        fclose(f);
+        return fail(c, LB_ERR_ARG, "lb_load: checkpoint of another grid or precision");
+    }
+    const size_t n = (size_t)h.npts;
+    std::string pts;
+    pts.resize(n * (sizeof(double) * 7 + sizeof(int)));
+    std::string pops;
+    pops.resize((size_t)pop_bytes);
+    unsigned long long digest = 0;
+    const bool ok = read_all(f, &pts[0], pts.size(), hash) && read_all(f, &pops[0], pops.size(), hash) &&
+                    fread(&digest, sizeof(digest), 1, f) == 1 && digest == hash.h;
+    fclose(f);
+    if (!ok) return fail(c, LB_ERR_ARG, "lb_load: truncated or corrupt checkpoint");
+    // the file is complete and intact: replace the state
+    lb_status s = invalidate_field(c);
+    if (s == LB_OK) s = grow_points(c, std::max(h.npts, 1));
+    if (s != LB_OK) return s;
+    const char* q = pts.data();
+    if (n) {
+        LB_CUDA(cudaMemcpyAsync(c->pos, q, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream), "copy");
+        LB_CUDA(cudaMemcpyAsync(c->force, q + sizeof(double) * 3 * n, sizeof(double) * 3 * n, cudaMemcpyHostToDevice,
+                                c->stream),
+                "copy");
+        LB_CUDA(cudaMemcpyAsync(c->radius, q + sizeof(double) * 6 * n, sizeof(double) * n, cudaMemcpyHostToDevice,
+                                c->stream),
+                "copy");
+        LB_CUDA(cudaMemcpyAsync(c->mobile, q + sizeof(double) * 7 * n, sizeof(int) * n, cudaMemcpyHostToDevice,
+                                c->stream),
+                "copy");
+    }
+    LB_CUDA(cudaMemcpyAsync(c->f[c->cur], pops.data(), (size_t)pop_bytes, cudaMemcpyHostToDevice, c->stream),
+            "population copy");
+    c->tau_s = h.tau_s;
+    c->tau_b = h.tau_b;
+    for (int a = 0; a < 3; ++a) c->g[a] = h.g[a];
+    c->a_L = h.a_L;
+    c->counter = h.counter;
+    c->geom.wall_lo = h.wall_lo;
+    c->geom.wall_hi = h.wall_hi;
+    c->seed = h.seed;
+    c->scale = h.scale;
+    c->inv_scale = h.inv_scale;
+    c->npts = h.npts;
+    c->n_mobile = h.n_mobile;
+    c->order_stale = true;
+    c->stencil_ready = false;
+    c->version++;
+    LB_CUDA(lbk::launch_fsum(c), "force sum");
+    LB_CUDA(cudaMemcpyAsync(c->fsum_host, c->fsum, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream),
+            "force sum read");
+    LB_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+    return LB_OK;
+}
+
 lb_status lb_kernel_launches(const lb_ctx* c, long long* count) {
     if (!c || !count) return LB_ERR_ARG;
     *count = c->launches;

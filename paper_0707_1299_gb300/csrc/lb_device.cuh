@@ -15,6 +15,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 namespace lbk {
 
@@ -104,9 +105,31 @@ template <> struct Store<__half> {
     // Stochastic rounding to half: add 13 random bits below the 10-bit half
     // mantissa to the float's magnitude, then truncate.  Values beyond the
     // half range saturate to +-65504.
-    static __device__ __forceinline__ void st(__half* p, unsigned i, float v, unsigned rnd) {
+    static __device__ __forceinline__ unsigned short bits(float v, unsigned rnd) {
         const unsigned b = __float_as_uint(v) + (rnd >> 19);
-        p[i] = __float2half_rz(__uint_as_float(b));
+        return __half_as_ushort(__float2half_rz(__uint_as_float(b)));
+    }
+    static __device__ __forceinline__ void st(__half* p, unsigned i, float v, unsigned rnd) {
+        p[i] = __ushort_as_half(bits(v, rnd));
+    }
+    // element h (0: low, 1: high half) of a 32-bit word holding two values
+    static __device__ __forceinline__ float unpack(unsigned w, int h) {
+        return __half2float(__ushort_as_half((unsigned short)(h ? w >> 16 : w & 0xFFFFu)));
+    }
+    // both elements of a word
+    static __device__ __forceinline__ float2 unpack2(unsigned w) {
+        __half2 h;
+        memcpy(&h, &w, sizeof(w));
+        return __half22float2(h);
+    }
+    // stochastic rounding of two values into one word (lo: low half), one
+    // round-toward-zero conversion for the pair
+    static __device__ __forceinline__ unsigned bits2(float lo, float hi, unsigned rlo, unsigned rhi) {
+        const float a = __uint_as_float(__float_as_uint(lo) + (rlo >> 19));
+        const float b = __uint_as_float(__float_as_uint(hi) + (rhi >> 19));
+        unsigned r;
+        asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+        return r;
     }
 };
 template <> struct Store<__nv_bfloat16> {
@@ -118,9 +141,21 @@ template <> struct Store<__nv_bfloat16> {
     }
     // Stochastic rounding to bfloat16: add 16 random bits to the dropped half
     // of the float, keep the upper half.
+    static __device__ __forceinline__ unsigned short bits(float v, unsigned rnd) {
+        return (unsigned short)((__float_as_uint(v) + (rnd >> 16)) >> 16);
+    }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, unsigned i, float v, unsigned rnd) {
-        const unsigned b = __float_as_uint(v) + (rnd >> 16);
-        p[i] = __ushort_as_bfloat16((unsigned short)(b >> 16));
+        p[i] = __ushort_as_bfloat16(bits(v, rnd));
+    }
+    static __device__ __forceinline__ float unpack(unsigned w, int h) {
+        return __uint_as_float(h ? (w & 0xFFFF0000u) : (w << 16));
+    }
+    static __device__ __forceinline__ float2 unpack2(unsigned w) {
+        return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u));
+    }
+    static __device__ __forceinline__ unsigned bits2(float lo, float hi, unsigned rlo, unsigned rhi) {
+        const unsigned a = __float_as_uint(lo) + (rlo >> 16), b = __float_as_uint(hi) + (rhi >> 16);
+        return __byte_perm(a, b, 0x7632);  // the upper halves: (a >> 16) | (b & 0xffff0000)
     }
 };
 
@@ -216,6 +251,115 @@ __device__ __forceinline__ void pull19(const Pops<S>& src, const Nbr& n, typenam
         f[16] = St::ld(bp ? src.p[15] : src.p[16], bp ? own : zp + n.dyp + n.x);
         f[17] = St::ld(bp ? src.p[18] : src.p[17], bp ? own : zp + n.dym + n.x);
     }
+}
+
+// ------------------------------------------- pull stream, two sites a thread
+// The 16-bit formats with nx even: a thread takes the x-adjacent sites x0,
+// x0 + 1 (x0 even), whose values of one population share a 32-bit word.
+// A population pulled from x - 1 or x + 1 straddles two words: the
+// neighbouring lane's word arrives by shuffle (the lane at a warp or row
+// edge loads it, wrapping periodically), and a byte permute joins the
+// halves.  Inactive lanes (x0 >= nx) load nothing but take part in the
+// shuffles; only a lane whose neighbour is active reads the shuffled word.
+template <typename S>
+__device__ __forceinline__ unsigned ldw(const S* p, unsigned e) {
+    return __ldg((const unsigned*)(p + e));
+}
+
+// Which neighbour word a population's pair needs: 0 none, -1 the word
+// before (pulled from x - 1: c_x = +1), +1 the word after (c_x = -1).
+__host__ __device__ constexpr int pair_shift(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? -1
+         : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? 1 : 0;
+}
+
+// The pulls of pull19 for the pair (x0, x0 + 1); n holds the rows of (y, z)
+// (its x fields are not used).  With walls a solid source selects the
+// opposite population of the site itself, unshifted (uniform per warp).
+// Every load is issued first (the own-row word of each population, and the
+// edge lanes' words beyond the warp), then the shuffles and permutes.
+template <typename S, bool BOUNCE>
+__device__ __forceinline__ void pull19_pair_impl(const Pops<S>& src, const Nbr& n, unsigned x0, unsigned nx, int lane,
+                                                 bool active, unsigned w[NQ]) {
+    const unsigned c = n.c, ym = n.c + n.dym, yp = n.c + n.dyp, zm = n.c + n.dzm, zp = n.c + n.dzp;
+    const bool bm = BOUNCE && n.solid_zm, bp = BOUNCE && n.solid_zp;
+    // source population and row of each pull; a bounced pull is unshifted
+    const S* ptr[NQ];
+    unsigned row[NQ];
+    bool shifted[NQ];
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+        ptr[i] = src.p[i];
+        shifted[i] = pair_shift(i) != 0;
+    }
+    row[0] = c;
+    row[1] = c;
+    row[2] = c;
+    row[3] = ym;
+    row[4] = yp;
+    row[7] = ym;
+    row[8] = yp;
+    row[9] = yp;
+    row[10] = ym;
+    row[5] = zm;
+    row[11] = zm;
+    row[14] = zm;
+    row[15] = zm + n.dym;
+    row[18] = zm + n.dyp;
+    row[6] = zp;
+    row[12] = zp;
+    row[13] = zp;
+    row[16] = zp + n.dyp;
+    row[17] = zp + n.dym;
+    if (bm) {
+        ptr[5] = src.p[6];
+        ptr[11] = src.p[12];
+        ptr[14] = src.p[13];
+        ptr[15] = src.p[16];
+        ptr[18] = src.p[17];
+        row[5] = row[11] = row[14] = row[15] = row[18] = c;
+        shifted[11] = shifted[14] = false;
+    }
+    if (bp) {
+        ptr[6] = src.p[5];
+        ptr[12] = src.p[11];
+        ptr[13] = src.p[14];
+        ptr[16] = src.p[15];
+        ptr[17] = src.p[18];
+        row[6] = row[12] = row[13] = row[16] = row[17] = c;
+        shifted[12] = shifted[13] = false;
+    }
+    const bool first = lane == 0, last = lane == 31 || x0 + 2 >= nx;
+    const unsigned xb = x0 == 0 ? nx - 2 : x0 - 2, xa = x0 + 2 >= nx ? 0 : x0 + 2;
+    unsigned edge[NQ];
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+        w[i] = active ? ldw(ptr[i], row[i] + x0) : 0u;
+        edge[i] = 0u;
+        if (pair_shift(i) < 0 && shifted[i] && active && first) edge[i] = ldw(ptr[i], row[i] + xb);
+        if (pair_shift(i) > 0 && shifted[i] && active && last) edge[i] = ldw(ptr[i], row[i] + xa);
+    }
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+        if (pair_shift(i) < 0 && shifted[i]) {  // (element x0 - 1, element x0)
+            unsigned prev = __shfl_up_sync(0xffffffffu, w[i], 1);
+            if (first) prev = edge[i];
+            w[i] = __byte_perm(prev, w[i], 0x5432);
+        } else if (pair_shift(i) > 0 && shifted[i]) {  // (element x0 + 1, element x0 + 2)
+            unsigned next = __shfl_down_sync(0xffffffffu, w[i], 1);
+            if (last) next = edge[i];
+            w[i] = __byte_perm(w[i], next, 0x5432);
+        }
+    }
+}
+
+// A plane next to a solid one takes the bounce-back selections; every other
+// plane (uniform per warp) the plain pulls.
+template <typename S, bool WALLS>
+__device__ __forceinline__ void pull19_pair(const Pops<S>& src, const Nbr& n, unsigned x0, unsigned nx, int lane,
+                                            bool active, unsigned w[NQ]) {
+    if (WALLS && (n.solid_zm || n.solid_zp)) pull19_pair_impl<S, true>(src, n, x0, nx, lane, active, w);
+    else pull19_pair_impl<S, false>(src, n, x0, nx, lane, active, w);
 }
 
 // Pulled populations in stored units -> df (only the half format is scaled).
@@ -336,6 +480,26 @@ template <> struct Wts<double> {
     static constexpr double a1 = 6004799503160660.0 * 0x1p-55;
     static constexpr double b1 = 6004799503160662.0 * 0x1p-56;
 };
+
+// Two sites at once on the packed FP32 datapath of sm_100 and later: F2
+// holds one float of each site; every operation is the IEEE round-to-
+// nearest float operation on both halves (one instruction for the pair).
+// collide19 and moments19 instantiated with F2 compute two independent
+// sites; products and sums are not contracted unless written as fma.
+struct F2 {
+    float2 v;
+    __device__ __forceinline__ F2() {}
+    __device__ __forceinline__ F2(float s) : v(make_float2(s, s)) {}
+    __device__ __forceinline__ explicit F2(float2 a) : v(a) {}
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(__ffma2_rn(b.v, make_float2(-1.0f, -1.0f), a.v)); }
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(__fmul2_rn(a.v, make_float2(-1.0f, -1.0f))); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator/(F2 a, F2 b) { return F2(make_float2(a.v.x / b.v.x, a.v.y / b.v.y)); }
+using ::fma;  // the float and double overloads stay visible beside F2's
+__device__ __forceinline__ F2 fma(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
+template <> struct Wts<F2> : Wts<float> {};
 
 // Post-collision df* from the pulled df and the local force density F:
 //   A = j + F,  v = (j + F/2) / rho,  S = sum df Q,

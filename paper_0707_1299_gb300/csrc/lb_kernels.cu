@@ -124,7 +124,6 @@ k_collide(const Pops<S> src, const Pops<S> dst, const typename Store<S>::T* __re
           Coef<typename Store<S>::T> k, UForce<typename Store<S>::T> fu, float scale, float inv_scale,
           unsigned seed) {
     using T = typename Store<S>::T;
-    constexpr bool SC = Store<S>::kScaled;
     constexpr bool FIELD = FMODE != FM_NONE, VOUT = FMODE == FM_VEL;
     const int y0 = (blockIdx.y * CS_WARPS + threadIdx.y) * NY;
     if (y0 >= g.ny) return;  // uniform per warp
@@ -164,6 +163,72 @@ k_collide(const Pops<S> src, const Pops<S> dst, const typename Store<S>::T* __re
                                      seed);
             }
         }
+    }
+}
+
+// The collide for the 16-bit formats with nx even: two x-adjacent sites
+// per thread, one 32-bit word per population and site pair, and the two
+// sites' arithmetic on the packed FP32x2 datapath (F2), so a site costs
+// half the load, store and floating-point instructions of k_collide (the
+// instruction count, not the bytes, bounds these formats).  The rounding
+// bits are drawn per site as in k_collide; the arithmetic differs from it
+// only where k_collide's compiler contracts a product and a sum.
+// Grid: (ceil(nx / 64), ceil(ny / 4), nz).  Occupancy bound (blocks of 128
+// threads per SM), swept on GB300 at 256^3: 8 for half (64 registers), 10
+// for bfloat16 (51); 6 was slower for both.
+template <typename S, bool WALLS, int FMODE>
+__global__ void __launch_bounds__(CS_THREADS, (sizeof(S) == 2 && Store<S>::kScaled) ? 8 : 10)
+k_collide_pair(const Pops<S> src, const Pops<S> dst, const float* __restrict__ floc, const flag_t* __restrict__ flags,
+               float* __restrict__ vel, Geom g, Coef<float> k, UForce<float> fu, float scale, float inv_scale,
+               unsigned seed) {
+    using St = Store<S>;
+    constexpr bool SC = St::kScaled, FIELD = FMODE != FM_NONE, VOUT = FMODE == FM_VEL;
+    const int y = blockIdx.y * CS_WARPS + threadIdx.y;
+    if (y >= g.ny) return;  // uniform per warp
+    const int z = blockIdx.z, lane = threadIdx.x;
+    const unsigned nx = (unsigned)g.nx;
+    const unsigned x0 = (blockIdx.x * 32u + (unsigned)lane) * 2u;
+    const bool active = x0 < nx;
+    const unsigned row = (unsigned)z * g.plane + (unsigned)y * nx;
+    if (WALLS && is_solid(g, z)) {  // uniform per warp
+        if (active)
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) *(unsigned*)(dst.p[i] + row + x0) = 0u;
+        return;
+    }
+    const unsigned fl =
+        (FIELD && active) ? __ldg(flags + ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.ntx + x0 / TILE_X) : 0u;
+    const Nbr n = neighbours(g, 0, y, z);
+    unsigned w[NQ];
+    pull19_pair<S, WALLS>(src, n, x0, nx, lane, active, w);
+    const unsigned V = (unsigned)g.V;
+    F2 f[NQ];
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) f[i] = F2(St::unpack2(w[i]));
+    F2 Fx(fu.F[0]), Fy(fu.F[1]), Fz(fu.F[2]);
+    if (FIELD && fl) {  // after the population loads, so both are in flight together
+        const F2 sc(SC ? scale : 1.0f);
+        Fx = fma(F2(*(const float2*)(floc + row + x0)), sc, Fx);
+        Fy = fma(F2(*(const float2*)(floc + V + row + x0)), sc, Fy);
+        Fz = fma(F2(*(const float2*)(floc + 2 * V + row + x0)), sc, Fz);
+    }
+    Coef<F2> k2;
+    k2.tau_s = F2(k.tau_s);
+    k2.tau_b = F2(k.tau_b);
+    k2.om_s = F2(k.om_s);
+    k2.om_b = F2(k.om_b);
+    F2 o[NQ], v3[3];
+    collide19<F2, false, SC, VOUT>(f, Fx, Fy, Fz, k2, o, F2(inv_scale), v3);
+    unsigned r0 = rng_seed(row + x0, seed), r1 = rng_seed(row + x0 + 1, seed);
+    if (active) {
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) {
+            const unsigned d0 = rng_next(r0), d1 = rng_next(r1);
+            *(unsigned*)(dst.p[i] + row + x0) = St::bits2(o[i].v.x, o[i].v.y, d0, d1);
+        }
+        if (VOUT && fl)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) *(float2*)(vel + a * V + row + x0) = v3[a].v;
     }
 }
 
@@ -848,6 +913,25 @@ cudaError_t launch_sort_points(lb_ctx* c) {
 static bool has_walls(const lb_ctx* c) { return c->geom.wall_lo >= 0 || c->geom.wall_hi >= 0; }
 static dim3 site_block() { return dim3(TILE_X, CS_WARPS, 1); }
 
+// The pair kernel exists for the 16-bit formats; for the others PairS maps
+// to a 16-bit type only to keep the dead branch of LB_COLLIDE compilable.
+template <typename S> struct PairSel { using type = __half; };
+template <> struct PairSel<__nv_bfloat16> { using type = __nv_bfloat16; };
+template <typename S> using PairS = typename PairSel<S>::type;
+template <typename T> static Coef<float> coef_f(const Coef<T>& k) {
+    Coef<float> r;
+    r.tau_s = (float)k.tau_s;
+    r.tau_b = (float)k.tau_b;
+    r.om_s = (float)k.om_s;
+    r.om_b = (float)k.om_b;
+    return r;
+}
+template <typename T> static UForce<float> uforce_f(const UForce<T>& u) {
+    UForce<float> r;
+    for (int a = 0; a < 3; ++a) r.F[a] = (float)u.F[a];
+    return r;
+}
+
 template <typename S>
 static cudaError_t collide_t(lb_ctx* c) {
     using T = typename Store<S>::T;
@@ -871,9 +955,21 @@ static cudaError_t collide_t(lb_ctx* c) {
     // a few fixed points: field-free collide plus the fix-up of their tiles
     const bool fixup = c->npts > 0 && c->n_mobile == 0 && c->fix_ok;
     const int mode = (c->npts == 0 || fixup) ? FM_NONE : (c->n_mobile > 0 ? FM_VEL : FM_FIELD);
-#define LB_COLLIDE(W, FM)                                                                                     \
-    k_collide<S, W, NY, FM><<<grid, site_block(), 0, c->stream>>>(src, dst, floc, c->flags, vel, c->geom, k, fu, \
-                                                                c->scale, c->inv_scale, c->seed)
+    // the 16-bit formats take two sites a thread when the rows pair up
+    constexpr bool PAIRABLE = sizeof(S) == 2;
+    const bool pair = PAIRABLE && (c->geom.nx % 2) == 0;
+    const dim3 pgrid((unsigned)((c->geom.nx + 63) / 64), grid.y, grid.z);
+#define LB_COLLIDE(W, FM)                                                                                          \
+    do {                                                                                                           \
+        if (PAIRABLE && pair)                                                                                      \
+            k_collide_pair<PairS<S>, W, FM><<<pgrid, site_block(), 0, c->stream>>>(                                \
+                pops<PairS<S>>(c->f[c->cur], c->geom.V), pops<PairS<S>>(c->f[1 - c->cur], c->geom.V),              \
+                (const float*)floc, c->flags, (float*)vel, c->geom, coef_f(k), uforce_f(fu), c->scale, c->inv_scale, \
+                c->seed);                                                                                          \
+        else                                                                                                       \
+            k_collide<S, W, NY, FM><<<grid, site_block(), 0, c->stream>>>(src, dst, floc, c->flags, vel, c->geom,  \
+                                                                        k, fu, c->scale, c->inv_scale, c->seed);   \
+    } while (0)
     if (has_walls(c)) {
         if (mode == FM_VEL) LB_COLLIDE(true, FM_VEL);
         else if (mode == FM_FIELD) LB_COLLIDE(true, FM_FIELD);

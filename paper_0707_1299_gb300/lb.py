@@ -32,7 +32,7 @@ EXPORTS = ["lb_create", "lb_destroy", "lb_last_error", "lb_set_body_force", "lb_
            "lb_batch_destroy", "lb_batch_last_error", "lb_batch_tune", "lb_batch_step", "lb_batch_info",
            "lb_colloid_velocity", "lb_mlp_num_params", "lb_mlp_create", "lb_mlp_destroy", "lb_mlp_last_error",
            "lb_mlp_get_params", "lb_mlp_set_params", "lb_mlp_features", "lb_mlp_forward", "lb_mlp_grad",
-           "lb_mlp_train_step", "lb_set_colloid_correction"]
+           "lb_mlp_train_step", "lb_set_colloid_correction", "lb_save", "lb_load"]
 
 _lib = None
 
@@ -73,6 +73,8 @@ def load():
         "lb_set_populations": ([vp, dp], ctypes.c_int),
         "lb_kernel_launches": ([vp, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
         "lb_synchronize": ([vp], ctypes.c_int),
+        "lb_save": ([vp, ctypes.c_char_p], ctypes.c_int),
+        "lb_load": ([vp, ctypes.c_char_p], ctypes.c_int),
         "lb_compute_aL": ([ip, dp, dp, dp], ctypes.c_int),
         "lb_totals_noalloc": ([vp, ctypes.c_int, ip, ctypes.c_int, ctypes.c_int, dp, dp, vp], ctypes.c_int),
         "lb_colloid_velocity": ([vp, ctypes.c_int, dp, dp, dp, dp], ctypes.c_int),
@@ -216,6 +218,14 @@ def lb_kernel_launches(ctx):
 
 def lb_synchronize(ctx):
     _check(ctx, load().lb_synchronize(ctx))
+
+
+def lb_save(ctx, path):
+    _check(ctx, load().lb_save(ctx, os.fsencode(path)))
+
+
+def lb_load(ctx, path):
+    _check(ctx, load().lb_load(ctx, os.fsencode(path)))
 
 
 def lb_compute_aL(grid, R, direction=None):
@@ -413,6 +423,12 @@ class Lattice:
 
     def set_positions(self, pos):
         lb_set_positions(self.ctx, self._dev(pos, (-1, 3)))
+
+    def save(self, path):
+        lb_save(self.ctx, path)
+
+    def load(self, path):
+        lb_load(self.ctx, path)
 
     def step(self, nsteps=1):
         lb_step(self.ctx, nsteps)
