@@ -230,6 +230,13 @@ lb_status lb_mlp_features(lb_mlp *net, long long n, const double *pos, const int
  * LB_ERR_TIMEOUT if the tensor-core pipeline did not complete within its
  * bounded wait (out is then incomplete). */
 lb_status lb_mlp_forward(lb_mlp *net, long long n, const float *feat, float *out);
+/* Bound of every wait of the tensor-core kernels on their own pipeline, in
+ * polls of an mbarrier (default 2^26, far beyond any completion).  0 makes
+ * the waits time out at once, which drives the timeout path: the forward
+ * stops, waits with the default bound for the work it issued, frees its
+ * tensor memory and returns LB_ERR_TIMEOUT; the network stays usable.
+ * LB_ERR_ARG for polls < 0. */
+lb_status lb_mlp_set_wait_limit(lb_mlp *net, long long polls);
 /* gradient of (1/3n) sum (y - target)^2 (grad: num_params floats, host or
  * device, may be NULL) and the sum of squared errors (*sse, may be NULL);
  * waits for completion */

@@ -159,9 +159,11 @@ __device__ __forceinline__ void commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
 
+constexpr long long WAIT_POLLS = 1LL << 26;  // default bound of a wait (polls of the mbarrier)
+
 // Bounded wait for phase `parity` of the mbarrier; false on timeout.
-__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity) {
-    for (long long it = 0; it < (1LL << 26); ++it) {
+__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity, long long polls) {
+    for (long long it = 0; it < polls; ++it) {
         uint32_t done;
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
@@ -202,11 +204,13 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 
 }  // namespace tc
 
-// Forward pass on the tensor cores; status[0] is set to 1 if a wait on the
-// tensor-core pipeline timed out (the kernel then stops early).
+// Forward pass on the tensor cores; each wait on the tensor-core pipeline
+// polls at most `polls` times.  On a timeout status[0] is set to 1 and the
+// kernel stops: it first waits (default bound) for the work it issued, then
+// frees its tensor memory.
 __global__ void __launch_bounds__(tc::M) km_forward_tc(const float* __restrict__ params, long long n,
                                                        const float* __restrict__ feat, float* __restrict__ out,
-                                                       int* __restrict__ status) {
+                                                       int* __restrict__ status, long long polls) {
     using namespace tc;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -273,7 +277,7 @@ __global__ void __launch_bounds__(tc::M) km_forward_tc(const float* __restrict__
                     ks > 0);
             commit(mbar);
         }
-        ok = __syncthreads_and(wait_phase(mbar, phase));  // uniform across the CTA
+        ok = __syncthreads_and(wait_phase(mbar, phase, polls));  // uniform across the CTA
         phase ^= 1u;
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -302,7 +306,7 @@ __global__ void __launch_bounds__(tc::M) km_forward_tc(const float* __restrict__
                     ks > 0);
             commit(mbar);
         }
-        ok = __syncthreads_and(wait_phase(mbar, phase));
+        ok = __syncthreads_and(wait_phase(mbar, phase, polls));
         phase ^= 1u;
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -327,7 +331,7 @@ __global__ void __launch_bounds__(tc::M) km_forward_tc(const float* __restrict__
     }
     if (!ok) {
         if (tid == 0) atomicExch(status, 1);
-        wait_phase(mbar, phase ^ 1u);  // bounded: let the tensor-core work in flight finish
+        wait_phase(mbar, phase ^ 1u, WAIT_POLLS);  // bounded: let the tensor-core work in flight finish
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -669,6 +673,7 @@ struct lb_mlp {
     cudaStream_t stream;
     float *p, *g, *m, *v, *sse;
     int* status;              // set by the tensor-core forward kernel on a timed-out wait
+    long long wait_polls;     // bound of the tensor-core kernels' waits
     long long t;              // Adam steps taken
     int *ws;                  // feature workspace (cell lists), grown on demand
     size_t ws_ints;
@@ -763,7 +768,7 @@ cudaError_t mlp_features(long long n, const double* pos, const int box[3], float
 cudaError_t mlp_forward(const lb_mlp* net, long long n, const float* feat, float* out, cudaStream_t st) {
     const long long tiles = (n + tc::M - 1) / tc::M;
     const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(tiles, 152LL * 4));
-    km_forward_tc<<<grid, tc::M, tc::SMEM, st>>>(net->p, n, feat, out, net->status);
+    km_forward_tc<<<grid, tc::M, tc::SMEM, st>>>(net->p, n, feat, out, net->status, net->wait_polls);
     return cudaGetLastError();
 }
 
@@ -780,6 +785,7 @@ lb_status lb_mlp_create(lb_mlp** out, const float* init, void* stream) {
     if (!net) return LB_ERR_OOM;
     net->stream = (cudaStream_t)stream;
     net->smem_grad = Smem::END * (int)sizeof(float);
+    net->wait_polls = tc::WAIT_POLLS;
     cudaError_t e = cudaMalloc(&net->p, sizeof(float) * (4 * NPARAM + 1));
     if (e == cudaSuccess) {
         net->g = net->p + NPARAM;
@@ -842,6 +848,13 @@ lb_status lb_mlp_features(lb_mlp* net, long long n, const double* pos, const int
         net->ws_ints = need;
     }
     LB_MCUDA(lbk::mlp_features(n, pos, box, feat, net->ws, net->stream), "feature kernels");
+    return LB_OK;
+}
+
+lb_status lb_mlp_set_wait_limit(lb_mlp* net, long long polls) {
+    if (!net) return LB_ERR_ARG;
+    if (polls < 0) return mfail(net, LB_ERR_ARG, "lb_mlp_set_wait_limit: polls < 0");
+    net->wait_polls = polls;
     return LB_OK;
 }
 

@@ -32,7 +32,8 @@ EXPORTS = ["lb_create", "lb_destroy", "lb_last_error", "lb_set_body_force", "lb_
            "lb_batch_destroy", "lb_batch_last_error", "lb_batch_tune", "lb_batch_step", "lb_batch_info",
            "lb_colloid_velocity", "lb_mlp_num_params", "lb_mlp_create", "lb_mlp_destroy", "lb_mlp_last_error",
            "lb_mlp_get_params", "lb_mlp_set_params", "lb_mlp_features", "lb_mlp_forward", "lb_mlp_grad",
-           "lb_mlp_train_step", "lb_set_colloid_correction", "lb_save", "lb_load"]
+           "lb_mlp_train_step", "lb_set_colloid_correction", "lb_save", "lb_load",
+           "lb_mlp_set_wait_limit"]
 
 _lib = None
 
@@ -87,6 +88,7 @@ def load():
         "lb_mlp_set_params": ([vp, vp], ctypes.c_int),
         "lb_mlp_features": ([vp, ctypes.c_longlong, vp, ip, vp], ctypes.c_int),
         "lb_mlp_forward": ([vp, ctypes.c_longlong, vp, vp], ctypes.c_int),
+        "lb_mlp_set_wait_limit": ([vp, ctypes.c_longlong], ctypes.c_int),
         "lb_mlp_grad": ([vp, ctypes.c_longlong, vp, vp, vp, vp], ctypes.c_int),
         "lb_mlp_train_step": ([vp, ctypes.c_longlong, vp, vp, ctypes.c_float, vp], ctypes.c_int),
         "lb_batch_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), vp],
@@ -318,6 +320,10 @@ def lb_mlp_features(net, n, pos, box, feat):
 
 def lb_mlp_forward(net, n, feat, out):
     _mcheck(net, load().lb_mlp_forward(net, int(n), _addr(feat), _addr(out)))
+
+
+def lb_mlp_set_wait_limit(net, polls):
+    _mcheck(net, load().lb_mlp_set_wait_limit(net, int(polls)))
 
 
 def lb_mlp_grad(net, n, feat, target, grad=None, sse=None):

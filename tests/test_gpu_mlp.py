@@ -95,6 +95,32 @@ def test_forward_many_tiles():
     lb.lb_mlp_destroy(net)
 
 
+def test_forward_timeout_is_reported_and_recovers():
+    # Every wait of the tensor-core forward is bounded.  A bound of 0 polls
+    # makes the first one run out: the call returns LB_ERR_TIMEOUT (the
+    # kernel drained the work it issued and freed its tensor memory), and
+    # with the default bound restored the same network computes correctly.
+    lb = _lb()
+    n = 1000
+    P, x, _ = _random_problem(n, 6)
+    v = mlp.flatten(P).astype(np.float32)
+    net = lb.lb_mlp_create(v)
+    X = torch.as_tensor(x, dtype=torch.float32, device="cuda").contiguous()
+    y = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    lb.lb_mlp_set_wait_limit(net, 0)
+    with pytest.raises(lb.LBError) as e:
+        lb.lb_mlp_forward(net, n, X, y)
+    assert e.value.status == lb.LB_ERR_TIMEOUT
+    lb.lb_mlp_set_wait_limit(net, 1 << 26)
+    lb.lb_mlp_forward(net, n, X, y)
+    yref, _ = mlp.forward(mlp.unflatten(v.astype(np.float64)), x.astype(np.float32).astype(np.float64), bf16_round=True)
+    err = np.abs(y.cpu().numpy() - yref).max(axis=1) / np.abs(yref).max()
+    assert np.quantile(err, 0.98) < 1e-5 and err.max() < 2e-2
+    with pytest.raises(lb.LBError):
+        lb.lb_mlp_set_wait_limit(net, -1)
+    lb.lb_mlp_destroy(net)
+
+
 def _random_problem(n, seed):
     rng = np.random.default_rng(seed)
     P = mlp.init_params(seed)
