@@ -189,8 +189,8 @@ lb_status ensure_field(lb_ctx* c) {
     if (c->field_ready || c->npts == 0) return LB_OK;
     lb_status s = ensure_point_buffers(c);
     if (s != LB_OK) return s;
-    if (c->order_stale) {
-        LB_CUDA(lbk::launch_sort_points(c), "point order kernels");
+    if (c->order_stale) {  // a few points are taken in their own order
+        if (c->npts > lbk::SORT_MIN_POINTS) LB_CUDA(lbk::launch_sort_points(c), "point order kernels");
         c->order_stale = false;
         c->steps_since_sort = 0;
     }
@@ -202,6 +202,7 @@ lb_status ensure_field(lb_ctx* c) {
     c->field_ready = true;
     // fixed points keep this field: list its tiles once for the fix-up path
     if (c->n_mobile == 0) LB_CUDA(lbk::list_fixed_tiles(c), "tile list");
+    else c->fix_ok = false;
     return LB_OK;
 }
 
@@ -413,20 +414,28 @@ lb_status lb_set_positions(lb_ctx* c, const double* pos) {
     if (!c) return LB_ERR_ARG;
     if (c->npts == 0) return LB_OK;
     if (!pos) return fail(c, LB_ERR_ARG, "lb_set_positions: pos is NULL");
+    // host positions are checked on the host, so the call need not wait for
+    // the device; device positions are checked by the kernel
+    const bool on_device = is_device_ptr(pos);
+    if (!on_device)
+        for (long long i = 0; i < 3LL * c->npts; ++i)
+            if (!isfinite(pos[i])) return fail(c, LB_ERR_NONFINITE, "lb_set_positions: non-finite position");
     lb_status s = invalidate_field(c);
     if (s != LB_OK) return s;
     Arg args[1] = {{pos, sizeof(double) * 3 * c->npts, false, nullptr, false}};
     bool any_host;
     s = resolve(c, args, 1, &any_host);
     if (s != LB_OK) return s;
-    LB_CUDA(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "status reset");
+    if (on_device) LB_CUDA(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "status reset");
     LB_CUDA(lbk::launch_set_positions(c, (const double*)args[0].dev), "position kernel");
-    int status = 0;
-    LB_CUDA(cudaMemcpyAsync(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "status read");
-    LB_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
-    if (status) return fail(c, LB_ERR_NONFINITE, "lb_set_positions: non-finite position");
     c->order_stale = true;
     c->stencil_ready = false;
+    if (on_device) {
+        int status = 0;
+        LB_CUDA(cudaMemcpyAsync(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "status read");
+        LB_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+        if (status) return fail(c, LB_ERR_NONFINITE, "lb_set_positions: non-finite position");
+    }
     return LB_OK;
 }
 

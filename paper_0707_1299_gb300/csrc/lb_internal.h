@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 
 #include "lb_device.cuh"
@@ -29,9 +30,8 @@ struct lb_ctx {
     void* vel;                // fluid velocity in the flagged tiles, 3 V elements of the
                               // arithmetic type (lattices with colloids only)
     bool field_ready;         // floc holds the forces at the current positions
-    unsigned* fix_list;       // flagged tiles of a field of fixed points (then a count)
-    int fix_count;
-    bool fix_ok;              // the list holds every flagged tile: collide field-free + fix-up
+    unsigned* fix_list;       // flagged tiles of a field of fixed points, then their count
+    bool fix_ok;              // few fixed points, listed: collide field-free + fix-up
 
     // monopoles after expansion (device, xyz interleaved)
     int npts, cap, n_mobile;
@@ -89,6 +89,7 @@ cudaError_t launch_gather(lb_ctx* c, int n, const double* qpos, double* vout);
 cudaError_t launch_interp(lb_ctx* c);
 cudaError_t launch_update(lb_ctx* c, const float* y);
 cudaError_t launch_stencil(lb_ctx* c);
+constexpr int SORT_MIN_POINTS = 2048;  // fewer points are taken in their own order
 cudaError_t launch_sort_points(lb_ctx* c);
 cudaError_t ensure_velocity_field(lb_ctx* c);
 cudaError_t list_fixed_tiles(lb_ctx* c);
@@ -112,6 +113,30 @@ size_t mlp_features_ws_ints(long long n, const int box[3]);
 cudaError_t mlp_features(long long n, const double* pos, const int box[3], float* feat, int* ws, cudaStream_t st);
 cudaError_t mlp_forward(const lb_mlp* net, long long n, const float* feat, float* out, cudaStream_t st);
 cudaError_t compute_inv_aL(const int grid[3], const double R[3], const double dir[3], double* inv_aL);
+
+// ------------------------------------------------- shared launch helpers
+constexpr int CS_WARPS = 4;  // tiles (warps) per block of the site kernels
+constexpr int CS_THREADS = CS_WARPS * 32;
+
+inline bool has_walls(const lb_ctx* c) { return c->geom.wall_lo >= 0 || c->geom.wall_hi >= 0; }
+inline dim3 site_block() { return dim3(TILE_X, CS_WARPS, 1); }
+// Capacity of the fixed-point tile list: 1/64 of all tiles, at least 1024.
+inline unsigned fixed_tile_cap(const lb_ctx* c) {
+    return (unsigned)std::max<long long>(1024, c->geom.ntiles / 64);
+}
+
+template <typename S>
+inline Pops<S> pops(void* base, long long V) {
+    Pops<S> p;
+    for (int i = 0; i < NQ; ++i) p.p[i] = (S*)base + (size_t)i * (size_t)V;
+    return p;
+}
+
+// Site kernels: block = 4 warps, one warp per 32-site x-row tile; grid =
+// (tiles per row, ceil(ny / 4), nz).  No division in the index math.
+inline dim3 site_grid(const Geom& g) {
+    return dim3((unsigned)g.ntx, (unsigned)((g.ny + CS_WARPS - 1) / CS_WARPS), (unsigned)g.nz);
+}
 
 size_t storage_bytes(int prec);
 size_t arith_bytes(int prec);

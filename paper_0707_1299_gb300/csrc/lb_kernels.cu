@@ -26,8 +26,6 @@
 
 namespace lbk {
 
-constexpr int CS_WARPS = 4;  // tiles (warps) per block of the site kernels
-constexpr int CS_THREADS = CS_WARPS * 32;
 
 size_t storage_bytes(int prec) {
     switch (prec) {
@@ -62,199 +60,6 @@ UForce<T> uniform_force(const lb_ctx* c) {  // instantiated for float and double
 
 template UForce<float> uniform_force<float>(const lb_ctx*);
 template UForce<double> uniform_force<double>(const lb_ctx*);
-
-template <typename S>
-static Pops<S> pops(void* base, long long V) {
-    Pops<S> p;
-    for (int i = 0; i < NQ; ++i) p.p[i] = (S*)base + (size_t)i * (size_t)V;
-    return p;
-}
-
-// Site kernels: block = 4 warps, one warp per 32-site x-row tile; grid =
-// (tiles per row, ceil(ny / 4), nz).  No division in the index math.
-static dim3 site_grid(const Geom& g) {
-    return dim3((unsigned)g.ntx, (unsigned)((g.ny + CS_WARPS - 1) / CS_WARPS), (unsigned)g.nz);
-}
-
-// Collision and store of one site from its pulled populations f: force =
-// uniform + (field ? localised : 0), in the stored units of the format;
-// with VOUT and a field, v = (j + F/2) / rho is written to vel as well.
-template <typename S, bool VOUT>
-__device__ __forceinline__ void finish_site(const typename Store<S>::T (&f)[NQ], const Pops<S>& dst,
-                                            const typename Store<S>::T* __restrict__ floc,
-                                            typename Store<S>::T* __restrict__ vel, unsigned V, unsigned site,
-                                            bool field, const Coef<typename Store<S>::T>& k,
-                                            const UForce<typename Store<S>::T>& fu, float scale, float inv_scale,
-                                            unsigned seed) {
-    using T = typename Store<S>::T;
-    constexpr bool SC = Store<S>::kScaled;
-    T Fx = fu.F[0], Fy = fu.F[1], Fz = fu.F[2];
-    if (field) {
-        const T s = SC ? (T)scale : T(1);
-        Fx += floc[site] * s;
-        Fy += floc[V + site] * s;
-        Fz += floc[2 * V + site] * s;
-    }
-    T o[NQ], v3[3];
-    collide19<T, Store<S>::kCompensate, SC, VOUT>(f, Fx, Fy, Fz, k, o, (T)inv_scale, v3);
-    unsigned rn = rng_seed(site, seed);
-#pragma unroll
-    for (int i = 0; i < NQ; ++i) Store<S>::st(dst.p[i], site, o[i], rng_next(rn));
-    if (VOUT && field) {
-        vel[site] = v3[0];
-        vel[V + site] = v3[1];
-        vel[2 * V + site] = v3[2];
-    }
-}
-
-// ------------------------------------------------------------ k_collide
-// NY consecutive y rows per thread (all loads of the NY sites issued
-// first).  The half format is handled in its scaled units throughout.
-// Occupancy bound (blocks of 128 threads per SM), swept on GB300 at 256^3:
-// the 4- and 2-byte formats are fastest at 12 (42 registers; 8-10 were
-// 2-10 % slower, 14 spills); FP64 at 8.
-// FMODE: FM_NONE a lattice without point forces (no flag or field access);
-// FM_FIELD the force field is read in flagged tiles; FM_VEL also writes the
-// fluid velocity v = (j + F/2) / rho there, for the colloid update.
-enum { FM_NONE = 0, FM_FIELD = 1, FM_VEL = 2 };
-template <typename S, bool WALLS, int NY, int FMODE>
-__global__ void __launch_bounds__(CS_THREADS, (NY == 1 ? (sizeof(S) == 8 ? 8 : 12) : 4))
-k_collide(const Pops<S> src, const Pops<S> dst, const typename Store<S>::T* __restrict__ floc,
-          const flag_t* __restrict__ flags, typename Store<S>::T* __restrict__ vel, Geom g,
-          Coef<typename Store<S>::T> k, UForce<typename Store<S>::T> fu, float scale, float inv_scale,
-          unsigned seed) {
-    using T = typename Store<S>::T;
-    constexpr bool FIELD = FMODE != FM_NONE, VOUT = FMODE == FM_VEL;
-    const int y0 = (blockIdx.y * CS_WARPS + threadIdx.y) * NY;
-    if (y0 >= g.ny) return;  // uniform per warp
-    const int z = blockIdx.z, lane = threadIdx.x;
-    const int x = blockIdx.x * TILE_X + lane;
-    const unsigned V = (unsigned)g.V;
-    unsigned fl[NY];
-#pragma unroll
-    for (int r = 0; r < NY; ++r) {
-        const unsigned tile = ((unsigned)z * (unsigned)g.ny + (unsigned)(y0 + r)) * (unsigned)g.ntx + blockIdx.x;
-        fl[r] = (FIELD && y0 + r < g.ny) ? __ldg(flags + tile) : 0u;
-    }
-
-    if (x < g.nx) {
-        if (WALLS && is_solid(g, z)) {
-#pragma unroll
-            for (int r = 0; r < NY; ++r) {
-                if (y0 + r >= g.ny) break;
-                const unsigned site = (unsigned)z * g.plane + (unsigned)(y0 + r) * (unsigned)g.nx + (unsigned)x;
-#pragma unroll
-                for (int i = 0; i < NQ; ++i) Store<S>::st(dst.p[i], site, T(0), 0u);
-            }
-        } else {
-            T f[NY][NQ];
-            Nbr n[NY];
-#pragma unroll
-            for (int r = 0; r < NY; ++r)  // every load of the NY sites first
-                if (y0 + r < g.ny) {
-                    n[r] = neighbours(g, x, y0 + r, z);
-                    pull19<S, WALLS>(src, n[r], f[r]);
-                }
-#pragma unroll
-            for (int r = 0; r < NY; ++r) {
-                if (y0 + r >= g.ny) break;
-                // the field loads come after the population loads, so both are in flight together
-                finish_site<S, VOUT>(f[r], dst, floc, vel, V, n[r].c + n[r].x, FIELD && fl[r], k, fu, scale, inv_scale,
-                                     seed);
-            }
-        }
-    }
-}
-
-// The collide for the 16-bit formats with nx even: two x-adjacent sites
-// per thread, one 32-bit word per population and site pair, and the two
-// sites' arithmetic on the packed FP32x2 datapath (F2), so a site costs
-// half the load, store and floating-point instructions of k_collide (the
-// instruction count, not the bytes, bounds these formats).  The rounding
-// bits are drawn per site as in k_collide; the arithmetic differs from it
-// only where k_collide's compiler contracts a product and a sum.
-// Grid: (ceil(nx / 64), ceil(ny / 4), nz).  Occupancy bound (blocks of 128
-// threads per SM), swept on GB300 at 256^3: 8 for half (64 registers), 10
-// for bfloat16 (51); 6 was slower for both.
-template <typename S, bool WALLS, int FMODE>
-__global__ void __launch_bounds__(CS_THREADS, (sizeof(S) == 2 && Store<S>::kScaled) ? 8 : 10)
-k_collide_pair(const Pops<S> src, const Pops<S> dst, const float* __restrict__ floc, const flag_t* __restrict__ flags,
-               float* __restrict__ vel, Geom g, Coef<float> k, UForce<float> fu, float scale, float inv_scale,
-               unsigned seed) {
-    using St = Store<S>;
-    constexpr bool SC = St::kScaled, FIELD = FMODE != FM_NONE, VOUT = FMODE == FM_VEL;
-    const int y = blockIdx.y * CS_WARPS + threadIdx.y;
-    if (y >= g.ny) return;  // uniform per warp
-    const int z = blockIdx.z, lane = threadIdx.x;
-    const unsigned nx = (unsigned)g.nx;
-    const unsigned x0 = (blockIdx.x * 32u + (unsigned)lane) * 2u;
-    const bool active = x0 < nx;
-    const unsigned row = (unsigned)z * g.plane + (unsigned)y * nx;
-    if (WALLS && is_solid(g, z)) {  // uniform per warp
-        if (active)
-#pragma unroll
-            for (int i = 0; i < NQ; ++i) *(unsigned*)(dst.p[i] + row + x0) = 0u;
-        return;
-    }
-    const unsigned fl =
-        (FIELD && active) ? __ldg(flags + ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.ntx + x0 / TILE_X) : 0u;
-    const Nbr n = neighbours(g, 0, y, z);
-    unsigned w[NQ];
-    pull19_pair<S, WALLS>(src, n, x0, nx, lane, active, w);
-    const unsigned V = (unsigned)g.V;
-    F2 f[NQ];
-#pragma unroll
-    for (int i = 0; i < NQ; ++i) f[i] = F2(St::unpack2(w[i]));
-    F2 Fx(fu.F[0]), Fy(fu.F[1]), Fz(fu.F[2]);
-    if (FIELD && fl) {  // after the population loads, so both are in flight together
-        const F2 sc(SC ? scale : 1.0f);
-        Fx = fma(F2(*(const float2*)(floc + row + x0)), sc, Fx);
-        Fy = fma(F2(*(const float2*)(floc + V + row + x0)), sc, Fy);
-        Fz = fma(F2(*(const float2*)(floc + 2 * V + row + x0)), sc, Fz);
-    }
-    Coef<F2> k2;
-    k2.tau_s = F2(k.tau_s);
-    k2.tau_b = F2(k.tau_b);
-    k2.om_s = F2(k.om_s);
-    k2.om_b = F2(k.om_b);
-    F2 o[NQ], v3[3];
-    collide19<F2, false, SC, VOUT>(f, Fx, Fy, Fz, k2, o, F2(inv_scale), v3);
-    unsigned r0 = rng_seed(row + x0, seed), r1 = rng_seed(row + x0 + 1, seed);
-    if (active) {
-#pragma unroll
-        for (int i = 0; i < NQ; ++i) {
-            const unsigned d0 = rng_next(r0), d1 = rng_next(r1);
-            *(unsigned*)(dst.p[i] + row + x0) = St::bits2(o[i].v.x, o[i].v.y, d0, d1);
-        }
-        if (VOUT && fl)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) *(float2*)(vel + a * V + row + x0) = v3[a].v;
-    }
-}
-
-// Fix-up for a few fixed points: the collide ran with the uniform force at
-// every site (FM_NONE); one warp per listed tile recomputes its sites with
-// the localised force added and overwrites them, with the same arithmetic
-// and the same rounding bits as the field-aware collide.  Solid sites carry
-// no force (the spread skips them), so they are left as they are.
-template <typename S, bool WALLS>
-__global__ void __launch_bounds__(CS_THREADS)
-k_fixup(const Pops<S> src, const Pops<S> dst, const typename Store<S>::T* __restrict__ floc,
-        const unsigned* __restrict__ list, int count, Geom g, Coef<typename Store<S>::T> k,
-        UForce<typename Store<S>::T> fu, float scale, float inv_scale, unsigned seed) {
-    using T = typename Store<S>::T;
-    const int w = blockIdx.x * CS_WARPS + threadIdx.y;
-    if (w >= count) return;
-    const unsigned tile = list[w];
-    const unsigned row = tile / (unsigned)g.ntx;
-    const int x = (int)(tile - row * (unsigned)g.ntx) * TILE_X + threadIdx.x;
-    const int y = (int)(row % (unsigned)g.ny), z = (int)(row / (unsigned)g.ny);
-    if (x >= g.nx || (WALLS && is_solid(g, z))) return;
-    const Nbr n = neighbours(g, x, y, z);
-    T f[NQ];
-    pull19<S, WALLS>(src, n, f);
-    finish_site<S, false>(f, dst, floc, nullptr, (unsigned)g.V, n.c + n.x, true, k, fu, scale, inv_scale, seed);
-}
 
 // Compact list of the flagged tiles (at most cap written; *count gets the
 // total).  One warp per 32 flags.
@@ -311,7 +116,7 @@ k_spread(const T* __restrict__ st, const double* __restrict__ force, const int* 
     const int q = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (q >= npts) return;  // uniform per warp
     const int lane = threadIdx.x & 31;
-    const int s = order[q];
+    const int s = order ? order[q] : q;
     const unsigned FULL = 0xffffffffu;
     const T r = lane < ST_W ? st[(size_t)s * ST_W + lane] : T(0);
     const T fl = lane < 3 ? (T)force[3 * s + lane] : T(0);
@@ -360,7 +165,7 @@ k_interp(const T* __restrict__ vel, Geom g, int n, const int* __restrict__ order
     const int q = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (q >= n) return;  // uniform per warp
     const int lane = threadIdx.x & 31;
-    const int s = order[q];
+    const int s = order ? order[q] : q;
     const unsigned FULL = 0xffffffffu;
     const T r = lane < ST_W ? st[(size_t)s * ST_W + lane] : T(0);
     const int bx = bits_int(__shfl_sync(FULL, r, 12)), by = bits_int(__shfl_sync(FULL, r, 13)),
@@ -861,13 +666,19 @@ size_t sort_ws_ints(const Geom& g, long long npts) {
 }
 
 // The flagged tiles of a field of fixed points, listed for the fix-up when
-// they are few (at most 1/64 of all tiles): reads the count back (waits).
+// they are few: a point flags at most 32 tiles (16 node rows, two x-tiles
+// each), so with npts * 32 within the list's capacity (1/64 of all tiles,
+// at least 1024) every flagged tile fits, and nothing is read back.
 cudaError_t list_fixed_tiles(lb_ctx* c) {
-    c->fix_ok = false;
-    const unsigned cap = (unsigned)std::max<long long>(1024, c->geom.ntiles / 64);
+    const unsigned cap = fixed_tile_cap(c);
+    c->fix_ok = (long long)c->npts * 32 <= (long long)cap;
+    if (!c->fix_ok) return cudaSuccess;
     if (!c->fix_list) {
         cudaError_t e = cudaMalloc(&c->fix_list, sizeof(unsigned) * (cap + 1));
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) {
+            c->fix_ok = false;
+            return e;
+        }
     }
     unsigned* count = c->fix_list + cap;
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned), c->stream);
@@ -875,13 +686,7 @@ cudaError_t list_fixed_tiles(lb_ctx* c) {
     k_list_tiles<<<(unsigned)((c->geom.ntiles + 255) / 256), 256, 0, c->stream>>>(c->flags, c->geom.ntiles, c->fix_list,
                                                                                  cap, count);
     c->launches++;
-    unsigned n = 0;
-    e = cudaMemcpyAsync(&n, count, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return e;
-    c->fix_count = (int)n;
-    c->fix_ok = n <= cap;
-    return cudaSuccess;
+    return cudaGetLastError();
 }
 
 cudaError_t ensure_velocity_field(lb_ctx* c) {
@@ -910,110 +715,20 @@ cudaError_t launch_sort_points(lb_ctx* c) {
 }
 
 // ------------------------------------------------------------ launchers
-static bool has_walls(const lb_ctx* c) { return c->geom.wall_lo >= 0 || c->geom.wall_hi >= 0; }
-static dim3 site_block() { return dim3(TILE_X, CS_WARPS, 1); }
 
-// The pair kernel exists for the 16-bit formats; for the others PairS maps
-// to a 16-bit type only to keep the dead branch of LB_COLLIDE compilable.
-template <typename S> struct PairSel { using type = __half; };
-template <> struct PairSel<__nv_bfloat16> { using type = __nv_bfloat16; };
-template <typename S> using PairS = typename PairSel<S>::type;
-template <typename T> static Coef<float> coef_f(const Coef<T>& k) {
-    Coef<float> r;
-    r.tau_s = (float)k.tau_s;
-    r.tau_b = (float)k.tau_b;
-    r.om_s = (float)k.om_s;
-    r.om_b = (float)k.om_b;
-    return r;
-}
-template <typename T> static UForce<float> uforce_f(const UForce<T>& u) {
-    UForce<float> r;
-    for (int a = 0; a < 3; ++a) r.F[a] = (float)u.F[a];
-    return r;
-}
-
-template <typename S>
-static cudaError_t collide_t(lb_ctx* c) {
-    using T = typename Store<S>::T;
-    Coef<T> k;
-    k.tau_s = (T)c->tau_s;
-    k.tau_b = (T)c->tau_b;
-    k.om_s = (T)(1.0 / (c->tau_s + 0.5));
-    k.om_b = (T)(1.0 / (c->tau_b + 0.5));
-    const Pops<S> src = pops<S>(c->f[c->cur], c->geom.V), dst = pops<S>(c->f[1 - c->cur], c->geom.V);
-    UForce<T> fu = uniform_force<T>(c);
-    if (Store<S>::kScaled)
-        for (int a = 0; a < 3; ++a) fu.F[a] = (T)((double)fu.F[a] * (double)c->scale);
-    // one site per thread for every format: two rows per thread (more loads
-    // in flight for the 2-byte formats) measured slower on GB300 (fewer
-    // resident warps at 80-92 registers)
-    constexpr int NY = 1;
-    const dim3 grid((unsigned)c->geom.ntx, (unsigned)((c->geom.ny + CS_WARPS * NY - 1) / (CS_WARPS * NY)),
-                    (unsigned)c->geom.nz);
-    const T* floc = (const T*)c->floc;
-    T* vel = (T*)c->vel;
-    // a few fixed points: field-free collide plus the fix-up of their tiles
-    const bool fixup = c->npts > 0 && c->n_mobile == 0 && c->fix_ok;
-    const int mode = (c->npts == 0 || fixup) ? FM_NONE : (c->n_mobile > 0 ? FM_VEL : FM_FIELD);
-    // the 16-bit formats take two sites a thread when the rows pair up
-    constexpr bool PAIRABLE = sizeof(S) == 2;
-    const bool pair = PAIRABLE && (c->geom.nx % 2) == 0;
-    const dim3 pgrid((unsigned)((c->geom.nx + 63) / 64), grid.y, grid.z);
-#define LB_COLLIDE(W, FM)                                                                                          \
-    do {                                                                                                           \
-        if (PAIRABLE && pair)                                                                                      \
-            k_collide_pair<PairS<S>, W, FM><<<pgrid, site_block(), 0, c->stream>>>(                                \
-                pops<PairS<S>>(c->f[c->cur], c->geom.V), pops<PairS<S>>(c->f[1 - c->cur], c->geom.V),              \
-                (const float*)floc, c->flags, (float*)vel, c->geom, coef_f(k), uforce_f(fu), c->scale, c->inv_scale, \
-                c->seed);                                                                                          \
-        else                                                                                                       \
-            k_collide<S, W, NY, FM><<<grid, site_block(), 0, c->stream>>>(src, dst, floc, c->flags, vel, c->geom,  \
-                                                                        k, fu, c->scale, c->inv_scale, c->seed);   \
-    } while (0)
-    if (has_walls(c)) {
-        if (mode == FM_VEL) LB_COLLIDE(true, FM_VEL);
-        else if (mode == FM_FIELD) LB_COLLIDE(true, FM_FIELD);
-        else LB_COLLIDE(true, FM_NONE);
-    } else {
-        if (mode == FM_VEL) LB_COLLIDE(false, FM_VEL);
-        else if (mode == FM_FIELD) LB_COLLIDE(false, FM_FIELD);
-        else LB_COLLIDE(false, FM_NONE);
-    }
-#undef LB_COLLIDE
-    c->launches++;
-    if (fixup && c->fix_count > 0) {
-        const unsigned blocks = (unsigned)((c->fix_count + CS_WARPS - 1) / CS_WARPS);
-        if (has_walls(c))
-            k_fixup<S, true><<<blocks, site_block(), 0, c->stream>>>(src, dst, floc, c->fix_list, c->fix_count, c->geom,
-                                                                     k, fu, c->scale, c->inv_scale, c->seed);
-        else
-            k_fixup<S, false><<<blocks, site_block(), 0, c->stream>>>(src, dst, floc, c->fix_list, c->fix_count,
-                                                                      c->geom, k, fu, c->scale, c->inv_scale, c->seed);
-        c->launches++;
-    }
-    c->seed = c->seed * 747796405u + 2891336453u;  // next step's rounding seed
-    return cudaGetLastError();
-}
-
-cudaError_t launch_collide(lb_ctx* c) {
-    switch (c->prec) {
-        case LB_F64: return collide_t<double>(c);
-        case LB_F32: return collide_t<float>(c);
-        case LB_F16S: return collide_t<__half>(c);
-        default: return collide_t<__nv_bfloat16>(c);
-    }
-}
+// The cell order of the points, or null (their own order) for a few.
+static const int* point_order(const lb_ctx* c) { return c->npts > SORT_MIN_POINTS ? c->order : nullptr; }
 
 template <typename T>
 static cudaError_t spread_t(lb_ctx* c) {
     const unsigned blocks = (unsigned)((c->npts + 7) / 8);  // 8 warps per block, one point each
     const T* st = (const T*)c->stencil;
     if (has_walls(c))
-        k_spread<T, true><<<blocks, 256, 0, c->stream>>>(st, c->force, c->order, c->npts, (T*)c->floc, c->flags,
-                                                          c->geom);
+        k_spread<T, true><<<blocks, 256, 0, c->stream>>>(st, c->force, point_order(c), c->npts, (T*)c->floc,
+                                                          c->flags, c->geom);
     else
-        k_spread<T, false><<<blocks, 256, 0, c->stream>>>(st, c->force, c->order, c->npts, (T*)c->floc, c->flags,
-                                                           c->geom);
+        k_spread<T, false><<<blocks, 256, 0, c->stream>>>(st, c->force, point_order(c), c->npts, (T*)c->floc,
+                                                           c->flags, c->geom);
     c->launches++;
     return cudaGetLastError();
 }
@@ -1055,9 +770,9 @@ static cudaError_t interp_t(lb_ctx* c) {
     const T* vel = (const T*)c->vel;
     const T* st = (const T*)c->stencil;
     if (has_walls(c))
-        k_interp<T, true><<<blocks, 256, 0, c->stream>>>(vel, c->geom, c->npts, c->order, st, c->pt_v);
+        k_interp<T, true><<<blocks, 256, 0, c->stream>>>(vel, c->geom, c->npts, point_order(c), st, c->pt_v);
     else
-        k_interp<T, false><<<blocks, 256, 0, c->stream>>>(vel, c->geom, c->npts, c->order, st, c->pt_v);
+        k_interp<T, false><<<blocks, 256, 0, c->stream>>>(vel, c->geom, c->npts, point_order(c), st, c->pt_v);
     c->launches++;
     return cudaGetLastError();
 }

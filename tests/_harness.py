@@ -38,6 +38,16 @@ def oracle_lattice(problem, fc=None):
     return o
 
 
+def disp_tol(prec, grid, steps, dmax):
+    """Tolerance of a colloid displacement error relative to the largest
+    displacement dmax: the format's bar, but not below what FP64 positions
+    can resolve -- each step rounds a position to its ulp (the two sides may
+    round differently: contracted or separate multiply-add), at most one
+    ulp of the box size per step."""
+    floor = float(np.spacing(float(max(grid)))) * steps / dmax
+    return max(TOL[prec], floor)
+
+
 def rel_err(a, ref):
     a = np.asarray(a, dtype=np.float64)
     ref = np.asarray(ref, dtype=np.float64)
