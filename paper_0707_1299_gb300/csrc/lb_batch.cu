@@ -171,24 +171,28 @@ __global__ void __launch_bounds__(256) kb_clear(const Entry* __restrict__ ent) {
                            (gridDim.x * blockDim.x) >> 5);
 }
 
-// Spreading, one warp per point (the stencil scheme of k_spread).
+// Spreading, one warp per point (the scheme of k_spread), from the stencil
+// rows st[gp] written by kb_stencil / kb_update.
 template <typename T>
 __global__ void __launch_bounds__(256)
-kb_spread(const Entry* __restrict__ ent, const long long* __restrict__ pbegin, int nrep, long long total_pts) {
+kb_spread(const Entry* __restrict__ ent, const long long* __restrict__ pbegin, const int* __restrict__ pent,
+          int nrep, long long total_pts,
+          const T* __restrict__ st) {
     const long long gp = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (gp >= total_pts) return;  // uniform per warp
     const int lane = threadIdx.x & 31;
-    const int e = find_entry(pbegin, nrep, gp);
+    const int e = pent[gp];
     const Entry& E = ent[e];
     const Geom& g = E.g;
     const int s = (int)(gp - pbegin[e]);
-    const double X = E.pos[3 * s], Y = E.pos[3 * s + 1], Z = E.pos[3 * s + 2];
-    const StencilLane<T> st = stencil_lane<T>(X, Y, Z, lane);
     const unsigned FULL = 0xffffffffu;
-    const int bx = __shfl_sync(FULL, st.base, 0), by = __shfl_sync(FULL, st.base, 4), bz = __shfl_sync(FULL, st.base, 8);
+    const T r = lane < ST_W ? st[gp * ST_W + lane] : T(0);
+    const T fl = lane < 3 ? (T)E.force[3 * s + lane] : T(0);
+    const int bx = bits_int(__shfl_sync(FULL, r, 12)), by = bits_int(__shfl_sync(FULL, r, 13)),
+              bz = bits_int(__shfl_sync(FULL, r, 14));
+    const T F0 = __shfl_sync(FULL, fl, 0), F1 = __shfl_sync(FULL, fl, 1), F2 = __shfl_sync(FULL, fl, 2);
     const int i = lane & 3, j = (lane >> 2) & 3;
-    const T wxy = __shfl_sync(FULL, st.phi, i) * __shfl_sync(FULL, st.phi, 4 + j);
-    const T F0 = (T)E.force[3 * s], F1 = (T)E.force[3 * s + 1], F2 = (T)E.force[3 * s + 2];
+    const T wxy = __shfl_sync(FULL, r, i) * __shfl_sync(FULL, r, 4 + j);
     const int x = wrap_node(bx + i, g.nx), y = wrap_node(by + j, g.ny);
     const bool marker = (i == 0) || ((x & (TILE_X - 1)) == 0);
     const unsigned V = (unsigned)g.V;
@@ -196,7 +200,7 @@ kb_spread(const Entry* __restrict__ ent, const long long* __restrict__ pbegin, i
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int k = (lane >> 4) + 2 * h;
-        const T wz = __shfl_sync(FULL, st.phi, 8 + k);
+        const T wz = __shfl_sync(FULL, r, 8 + k);
         const int z = wrap_node(bz + k, g.nz);
         if (is_solid(g, z)) continue;
         const T w = wxy * wz;
@@ -209,35 +213,50 @@ kb_spread(const Entry* __restrict__ ent, const long long* __restrict__ pbegin, i
     }
 }
 
+// Stencil rows of every point of the batch (thread per point).
+template <typename T>
+__global__ void kb_stencil(const Entry* __restrict__ ent, const long long* __restrict__ pbegin, const int* __restrict__ pent,
+          int nrep,
+                           long long total_pts, T* __restrict__ st) {
+    const long long gp = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gp >= total_pts) return;
+    const int e = pent[gp];
+    const Entry& E = ent[e];
+    const int s = (int)(gp - pbegin[e]);
+    write_stencil<T>(st + gp * ST_W, E.pos[3 * s], E.pos[3 * s + 1], E.pos[3 * s + 2]);
+}
+
 __global__ void kb_tick(unsigned* step_counter) { *step_counter += 1u; }
 
-// Interpolated velocity (from the velocity field the collide wrote) and
-// the Faxen update of every colloid, one warp each (the scheme of k_interp).
+// Interpolated velocity (from the velocity field the collide wrote) at
+// every colloid, one warp each (the scheme of k_interp): v[3 gp + a], FP64.
 template <typename T>
 __global__ void __launch_bounds__(256)
-kb_interp(const Entry* __restrict__ ent, const long long* __restrict__ pbegin, int nrep, long long total_pts) {
+kb_interp(const Entry* __restrict__ ent, const long long* __restrict__ pbegin, const int* __restrict__ pent,
+          int nrep, long long total_pts,
+          const T* __restrict__ st, double* __restrict__ vout) {
     const long long gp = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (gp >= total_pts) return;  // uniform per warp
-    const int e = find_entry(pbegin, nrep, gp);
+    const int e = pent[gp];
     const Entry& E = ent[e];
     const int s = (int)(gp - pbegin[e]);
     if (!E.mobile[s]) return;  // uniform per warp
     const Geom& g = E.g;
     const int lane = threadIdx.x & 31;
     const T* vel = (const T*)E.vel;
-    const double X = E.pos[3 * s], Y = E.pos[3 * s + 1], Z = E.pos[3 * s + 2];
-    const StencilLane<T> st = stencil_lane<T>(X, Y, Z, lane);
     const unsigned FULL = 0xffffffffu;
-    const int bx = __shfl_sync(FULL, st.base, 0), by = __shfl_sync(FULL, st.base, 4), bz = __shfl_sync(FULL, st.base, 8);
+    const T r = lane < ST_W ? st[gp * ST_W + lane] : T(0);
+    const int bx = bits_int(__shfl_sync(FULL, r, 12)), by = bits_int(__shfl_sync(FULL, r, 13)),
+              bz = bits_int(__shfl_sync(FULL, r, 14));
     const int i = lane & 3, j = (lane >> 2) & 3;
-    const T wxy = __shfl_sync(FULL, st.phi, i) * __shfl_sync(FULL, st.phi, 4 + j);
+    const T wxy = __shfl_sync(FULL, r, i) * __shfl_sync(FULL, r, 4 + j);
     const int x = wrap_node(bx + i, g.nx), y = wrap_node(by + j, g.ny);
     const unsigned V = (unsigned)g.V;
     T acc[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int k = (lane >> 4) + 2 * h;
-        const T wz = __shfl_sync(FULL, st.phi, 8 + k);
+        const T wz = __shfl_sync(FULL, r, 8 + k);
         const int z = wrap_node(bz + k, g.nz);
         if (is_solid(g, z)) continue;  // v = 0 on solid nodes
         const T w = wxy * wz;
@@ -249,19 +268,39 @@ kb_interp(const Entry* __restrict__ ent, const long long* __restrict__ pbegin, i
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
         for (int a = 0; a < 3; ++a) acc[a] += __shfl_xor_sync(FULL, acc[a], off);
-    if (lane >= 3) return;  // lanes 0-2 finish one axis each
-    const double v = (double)(lane == 0 ? acc[0] : (lane == 1 ? acc[1] : acc[2]));
-    const double c = (1.0 / E.radius[s] - E.inv_aL) * E.inv_6pi_eta;
-    const double P = lane == 0 ? X : (lane == 1 ? Y : Z);
-    const double L = (double)(lane == 0 ? g.nx : (lane == 1 ? g.ny : g.nz));
-    double r = P + v + E.force[3 * s + lane] * c;
-    if (r < 0.0) r += L;
-    else if (r >= L) r -= L;
-    if (!(r >= 0.0 && r < L)) {  // moved by a period or more
-        r = r - L * floor(r / L);
-        if (r >= L || r < 0.0) r = 0.0;
+    if (lane < 3) vout[3 * gp + lane] = (double)(lane == 0 ? acc[0] : (lane == 1 ? acc[1] : acc[2]));
+}
+
+// Colloid update of every mobile point of the batch (thread per point,
+// Sec. IV with the a_L subtraction, as k_update) and the stencil row of the
+// new position.
+template <typename T>
+__global__ void kb_update(const Entry* __restrict__ ent, const long long* __restrict__ pbegin, const int* __restrict__ pent,
+          int nrep,
+                          long long total_pts, const double* __restrict__ v, T* __restrict__ st) {
+    const long long gp = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gp >= total_pts) return;
+    const int e = pent[gp];
+    const Entry& E = ent[e];
+    const int s = (int)(gp - pbegin[e]);
+    double P[3] = {E.pos[3 * s], E.pos[3 * s + 1], E.pos[3 * s + 2]};
+    if (E.mobile[s]) {
+        const double c = (1.0 / E.radius[s] - E.inv_aL) * E.inv_6pi_eta;
+        const int nn[3] = {E.g.nx, E.g.ny, E.g.nz};
+        for (int a = 0; a < 3; ++a) {
+            const double L = (double)nn[a];
+            double r = P[a] + v[3 * gp + a] + E.force[3 * s + a] * c;
+            if (r < 0.0) r += L;
+            else if (r >= L) r -= L;
+            if (!(r >= 0.0 && r < L)) {  // moved by a period or more
+                r = r - L * floor(r / L);
+                if (r >= L || r < 0.0) r = 0.0;
+            }
+            P[a] = r;
+            E.pos[3 * s + a] = r;
+        }
     }
-    E.pos[3 * s + lane] = r;
+    write_stencil<T>(st + gp * ST_W, P[0], P[1], P[2]);
 }
 
 }  // namespace
@@ -280,6 +319,9 @@ struct lb_batch {
     long long total_groups, total_pts, n_mobile;
     int blocks;                // persistent grid of the collide kernel
     unsigned* d_step;          // step counter seeding the stochastic rounding
+    int* d_pent;               // member of every point of the batch
+    void* d_st;                // stencil rows of every point (ST_W elements of the arithmetic type)
+    double* d_v;               // interpolated velocity of every point (3 doubles)
     int parity;                // batch steps taken since creation, mod 2
     std::vector<int> cur0;     // each member's current buffer at creation
     std::vector<unsigned> version;  // each member's configuration version at creation
@@ -304,20 +346,46 @@ lb_status bfail(lb_batch* b, lb_status s, const std::string& m) {
                          std::string(where) + ": " + cudaGetErrorString(e_));                     \
     } while (0)
 
-// Launch the phases of one step (parity p) on the batch stream: spread,
-// collide (writing v at the colloids' stencil nodes), colloid update, tile
-// clearing, and the rounding-seed counter of the 16-bit formats.
+// Launch the phases of one step (parity p) on the batch stream: spread
+// (from the stencil rows), collide (writing v at the colloids' stencil
+// nodes), interpolation, colloid update (which writes the next stencil
+// rows), tile clearing, and the rounding-seed counter of the 16-bit formats.
 template <typename S>
 cudaError_t launch_step(lb_batch* b, int p, int blocks) {
     using T = typename Store<S>::T;
-    const unsigned pblocks = (unsigned)((b->total_pts + 7) / 8);
-    if (b->total_pts > 0) kb_spread<T><<<pblocks, 256, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->n, b->total_pts);
+    const unsigned wblocks = (unsigned)((b->total_pts + 7) / 8);      // warp per point
+    const unsigned tblocks = (unsigned)((b->total_pts + 127) / 128);  // thread per point
+    T* st = (T*)b->d_st;
+    if (b->total_pts > 0)
+        kb_spread<T><<<wblocks, 256, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->d_pent, b->n, b->total_pts, st);
     kb_collide<S><<<blocks, dim3(32, BW), 0, b->stream>>>(b->d_ent, b->d_gbegin, b->d_work, b->n, b->total_groups, p,
                                                           b->d_step);
-    if (b->n_mobile > 0) kb_interp<T><<<pblocks, 256, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->n, b->total_pts);
+    if (b->n_mobile > 0) {
+        kb_interp<T><<<wblocks, 256, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->d_pent, b->n, b->total_pts, st, b->d_v);
+        kb_update<T><<<tblocks, 128, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->d_pent, b->n, b->total_pts, b->d_v, st);
+    }
     if (b->total_pts > 0) kb_clear<T><<<dim3(8, b->n), 256, 0, b->stream>>>(b->d_ent);
     if (sizeof(S) == 2) kb_tick<<<1, 1, 0, b->stream>>>(b->d_step);
     return cudaGetLastError();
+}
+
+// Stencil rows of the members' current positions (before a batch step).
+template <typename S>
+cudaError_t launch_stencils(lb_batch* b) {
+    using T = typename Store<S>::T;
+    if (b->total_pts == 0) return cudaSuccess;
+    kb_stencil<T><<<(unsigned)((b->total_pts + 127) / 128), 128, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->d_pent, b->n,
+                                                                                b->total_pts, (T*)b->d_st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stencils_any(lb_batch* b) {
+    switch (b->prec) {
+        case LB_F64: return launch_stencils<double>(b);
+        case LB_F32: return launch_stencils<float>(b);
+        case LB_F16S: return launch_stencils<__half>(b);
+        default: return launch_stencils<__nv_bfloat16>(b);
+    }
 }
 
 cudaError_t launch_step_any(lb_batch* b, int p, int blocks) {
@@ -346,7 +414,7 @@ cudaError_t launch_collide_any(lb_batch* b, int blocks) {
 }
 
 int launches_per_step(const lb_batch* b) {
-    return 1 + (b->total_pts > 0 ? 2 : 0) + (b->n_mobile > 0 ? 1 : 0) + (b->prec >= LB_F16S ? 1 : 0);
+    return 1 + (b->total_pts > 0 ? 2 : 0) + (b->n_mobile > 0 ? 2 : 0) + (b->prec >= LB_F16S ? 1 : 0);
 }
 
 }  // namespace
@@ -430,6 +498,16 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
     if (e == cudaSuccess) e = cudaMalloc(&b->d_pbegin, sizeof(long long) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_work, sizeof(Work) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_step, sizeof(unsigned));
+    if (e == cudaSuccess && pts > 0)
+        e = cudaMalloc(&b->d_st, lbk::arith_bytes(b->prec) * ST_W * (size_t)pts);
+    if (e == cudaSuccess && pts > 0) e = cudaMalloc(&b->d_v, sizeof(double) * 3 * (size_t)pts);
+    if (e == cudaSuccess && pts > 0) {
+        std::vector<int> pent((size_t)pts);
+        for (int i = 0; i < n; ++i)
+            for (long long q = pbegin[i]; q < pbegin[i] + ctxs[i]->npts; ++q) pent[(size_t)q] = i;
+        e = cudaMalloc(&b->d_pent, sizeof(int) * (size_t)pts);
+        if (e == cudaSuccess) e = cudaMemcpy(b->d_pent, pent.data(), sizeof(int) * (size_t)pts, cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaMemset(b->d_step, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemcpy(b->d_ent, ent.data(), sizeof(Entry) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_gbegin, gbegin.data(), sizeof(long long) * n, cudaMemcpyHostToDevice);
@@ -452,6 +530,9 @@ void lb_batch_destroy(lb_batch* b) {
     cudaFree(b->d_pbegin);
     cudaFree(b->d_work);
     cudaFree(b->d_step);
+    cudaFree(b->d_st);
+    cudaFree(b->d_v);
+    cudaFree(b->d_pent);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->stream) cudaStreamDestroy(b->stream);
@@ -532,6 +613,9 @@ lb_status lb_batch_step(lb_batch* b, int nsteps) {
             c->field_ready = false;
         }
     }
+    // the positions may have been set since the last batch step
+    LB_BCUDA(launch_stencils_any(b), "stencil kernel");
+    b->launches += b->total_pts > 0 ? 1 : 0;
     if (!b->graph_ready && nsteps >= 2) {
         cudaGraph_t g;
         LB_BCUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");

@@ -335,6 +335,64 @@ def test_argument_validation():
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_degenerate_point_positions(prec):
+    # Points exactly on nodes (the outermost stencil weight is 0), at
+    # negative coordinates and at or beyond L (wrapped into [0, L)), a
+    # hair below L (its stencil wraps), and two colloids on the same spot:
+    # 40 steps against the oracle, field and trajectories.
+    lb = _lb()
+    n = (12, 10, 14)
+    pos = np.array([[3.0, 4.0, 5.0],          # on a node
+                    [-0.75, 9.5, 13.25],      # negative x
+                    [12.0, 2.25, 14.0],       # x = L and z = L: wrap to 0
+                    [11.999999999, 0.5, 6.5],  # a hair below L
+                    [7.3, 7.3, 7.3], [7.3, 7.3, 7.3]])  # coincident colloids
+    prob = W.Problem("degenerate", n, 0.6, 0.9, a_L=2.0, steps=40, points=[
+        W.PointSet(W.STOKESLET, pos[0:3], np.array([[1e-5, 2e-6, -3e-6], [0, 4e-6, 1e-6], [-2e-6, 0, 5e-6]]), None),
+        W.PointSet(W.COLLOID, pos[3:6], np.array([[0, 0, -2e-6], [1e-6, 0, -1e-6], [1e-6, 0, -1e-6]]),
+                   np.array([0.2, 0.15, 0.15]))])
+    g = gpu_lattice(prob, PREC_ID[prec])
+    p0, _ = g.particles()
+    p0 = p0.cpu().numpy()
+    assert np.all(p0 >= 0) and np.all(p0 < np.asarray(n))  # wrapped on entry
+    g.step(prob.steps)
+    _, u, _ = g.moments()
+    p1, _ = g.particles()
+    o = oracle_lattice(prob)
+    o.step(prob.steps)
+    ref = o.observe()
+    assert rel_err(u.cpu().numpy(), ref["u"]) < TOL[prec]
+    d_ref = periodic_diff(o.pos, p0, n)
+    d_gpu = periodic_diff(p1.cpu().numpy(), p0, n)
+    assert rel_err(d_gpu, d_ref) < disp_tol(prec, n, prob.steps, np.abs(d_ref).max())
+    g.close()
+
+
+def test_empty_and_zero_calls():
+    # No points, zero steps, zero queries, clearing twice, the lattice-size
+    # limit: nothing launches that should not, nothing fails that should not.
+    lb = _lb()
+    with pytest.raises(lb.LBError) as e:
+        lb.lb_create((65536, 65536, 1), 0.5, 0.5, lb.LB_F32)  # V = 2^32
+    assert e.value.status == lb.LB_ERR_ARG
+    g = lb.Lattice((6, 4, 2), 0.5, 0.5, lb.LB_F32)
+    n0 = g.kernel_launches()
+    g.step(0)
+    assert g.kernel_launches() == n0
+    g.add_point_forces(lb.LB_STOKESLET, np.zeros((0, 3)), np.zeros((0, 3)))
+    assert g.num_points() == 0
+    q = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+    assert g.velocity_at(q).shape == (0, 3)
+    g.clear_point_forces()
+    g.clear_point_forces()
+    g.step(3)  # a lattice without points: one collide launch a step
+    assert g.kernel_launches() == n0 + 3
+    rho, u, tot = g.moments()
+    assert abs(float(tot[0]) - 48.0) < 1e-9 and float(u.abs().max()) == 0.0
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_uniform_body_force_accumulates_exactly(prec):
     # A periodic box under a uniform body force accelerates uniformly:
     # rho u = (n + 1/2) g after n steps (Eq. macrovariables2), the case
