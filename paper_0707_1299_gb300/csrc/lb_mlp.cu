@@ -484,10 +484,11 @@ __global__ void kf_fill(const double* __restrict__ pos, long long n, const int* 
 }
 
 // Minimum-image difference, exactly as d - box * rint(d / box) (rint = 0
-// for |d| <= box / 4, where the division is skipped).
-__device__ __forceinline__ double min_image(double d, double box) {
-    return fabs(d) > 0.25 * box ? d - box * rint(d / box) : d;
+// for |d| <= box / 4, where the division is skipped); qbox = box / 4.
+__device__ __forceinline__ double min_image(double d, double box, double qbox) {
+    return fabs(d) > qbox ? d - box * rint(d / box) : d;
 }
+__device__ __forceinline__ double min_image(double d, double box) { return min_image(d, box, 0.25 * box); }
 
 // Squared distance summed in the order ((dx^2 + dy^2) + dz^2), each step
 // rounded once.
@@ -515,16 +516,21 @@ __device__ __forceinline__ void insert_exact(unsigned long long (&bk)[NNB], int 
 
 // Minimum-image difference along one axis, d = x_j - x_i, exactly as
 // min_image; the float difference df of the same pair (within 1 of d)
-// settles the common case |d| < box / 4, where no image shift applies.
-__device__ __forceinline__ double min_image_hint(double xj, double xi, float df, double box) {
+// settles the common case |d| < box / 4 (below qf = box / 4 - 1), where no
+// image shift applies.
+__device__ __forceinline__ double min_image_hint(double xj, double xi, float df, float qf, double box, double qbox) {
     const double d = xj - xi;
-    return fabsf(df) < 0.25f * (float)box - 1.0f ? d : min_image(d, box);
+    return fabsf(df) < qf ? d : min_image(d, box, qbox);
 }
 
 // The 27 cells around cell c0 (each visited once when an axis has fewer
-// than 3 cells), as a flat index for step t = 0 .. ncells - 1.
+// than 3 cells), as a flat index for step t = 0 .. count - 1, with the
+// periodic image shift of each: with 3 or more cells along an axis every
+// other point within R_CUT of a point lies in a neighbouring cell, at the
+// difference (x_j + shift) - x_i, shift = -box, 0 or +box by the cell's wrap.
 struct CellWalk {
     int c0[3], nc[3], lo[3], span[3], count;
+    bool shifts;  // every axis has 3 or more cells: shift() is the minimum image
     __device__ CellWalk(int ci, int3 n) {
         nc[0] = n.x;
         nc[1] = n.y;
@@ -533,18 +539,30 @@ struct CellWalk {
         c0[1] = (ci / n.x) % n.y;
         c0[2] = ci / (n.x * n.y);
         count = 1;
+        shifts = true;
         for (int a = 0; a < 3; ++a) {
             lo[a] = nc[a] >= 3 ? -1 : 0;
             span[a] = nc[a] >= 3 ? 3 : nc[a];
             count *= span[a];
+            shifts = shifts && nc[a] >= 3;
         }
     }
-    __device__ int cell(int t) const {
-        const int dx = t % span[0] + lo[0], dy = (t / span[0]) % span[1] + lo[1], dz = t / (span[0] * span[1]) + lo[2];
-        const int cx = nc[0] >= 3 ? wrap_node(c0[0] + dx, nc[0]) : dx;
-        const int cy = nc[1] >= 3 ? wrap_node(c0[1] + dy, nc[1]) : dy;
-        const int cz = nc[2] >= 3 ? wrap_node(c0[2] + dz, nc[2]) : dz;
-        return (cz * nc[1] + cy) * nc[0] + cx;
+    __device__ void step(int t, int& cell, float3& shift, const float box[3]) const {
+        const int d[3] = {t % span[0] + lo[0], (t / span[0]) % span[1] + lo[1], t / (span[0] * span[1]) + lo[2]};
+        int cc[3];
+        float sh[3];
+        for (int a = 0; a < 3; ++a) {
+            if (nc[a] >= 3) {
+                const int r = c0[a] + d[a];
+                cc[a] = r < 0 ? r + nc[a] : (r >= nc[a] ? r - nc[a] : r);
+                sh[a] = r < 0 ? -box[a] : (r >= nc[a] ? box[a] : 0.0f);
+            } else {
+                cc[a] = d[a];
+                sh[a] = 0.0f;
+            }
+        }
+        cell = (cc[2] * nc[1] + cc[1]) * nc[0] + cc[0];
+        shift = make_float3(sh[0], sh[1], sh[2]);
     }
 };
 
@@ -554,70 +572,75 @@ struct CellWalk {
 // warp's threads walk the same cells.
 //
 // Which 8, and in which order, is decided in FP64 exactly as the definition
-// states, but FP64 arithmetic is kept off the per-candidate loop:
-//   1. float pass: squared distances r2f from float positions, whose error
-//      is below `margin`; the KF = 16 smallest r2f <= R_CUT^2 + margin are
-//      kept (registers);
-//   2. window: with F8 the 8th smallest r2f kept, every candidate of the
-//      exact top 8 has r2f <= W = F8 + 2 margin (W = R_CUT^2 + margin when
-//      fewer than 8 were kept), so the FP64 distances of the kept entries
-//      with r2f <= W decide.  If all KF kept entries lie within W an entry
-//      may have been dropped: that thread repeats the search in FP64.
-constexpr int KF = 16;
+// states, with FP64 arithmetic and sorting kept off the per-candidate loop:
+// one float pass computes squared distances r2f from float positions (error
+// below `margin`), tracks the 8 smallest values r2f <= R_CUT^2 + margin
+// (values only) and lists in shared memory every candidate with r2f within
+// the current window F8 + 2 margin (F8 the current 8th smallest; the window
+// only shrinks, so the final window's candidates are all listed).  Every
+// candidate of the exact top 8 has r2f <= W = F8 + 2 margin (W = R_CUT^2 +
+// margin with fewer than 8); the FP64 distances of the listed candidates
+// within W decide.  A thread whose list overflows (more than KW entries)
+// searches again in FP64.
+constexpr int KW = 32;           // listed candidates a thread can hold
+constexpr int KNN_THREADS = 128;
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(KNN_THREADS)
 kf_knn(const double* __restrict__ pos, long long n, Geom g, int3 nc, const int* __restrict__ start,
        const int* __restrict__ sorted, const int* __restrict__ cell, const float4* __restrict__ spos, float margin,
        float* __restrict__ feat) {
+    __shared__ int wslot[KW][KNN_THREADS];    // [entry][thread]: no bank conflicts
+    __shared__ float wr2[KW][KNN_THREADS];
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
     const int i = sorted[q];
     const float4 me = spos[q];
     const double box[3] = {(double)g.nx, (double)g.ny, (double)g.nz};
+    const double qbox[3] = {0.25 * (double)g.nx, 0.25 * (double)g.ny, 0.25 * (double)g.nz};
     const float boxf[3] = {(float)g.nx, (float)g.ny, (float)g.nz};
     const float halff[3] = {0.5f * (float)g.nx, 0.5f * (float)g.ny, 0.5f * (float)g.nz};
+    const float qf[3] = {0.25f * (float)g.nx - 1.0f, 0.25f * (float)g.ny - 1.0f, 0.25f * (float)g.nz - 1.0f};
     const double P[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
     const double rc2 = (double)R_CUT * (double)R_CUT;
     const CellWalk walk(cell[i], nc);
+    const float lim = (float)rc2 + margin, twom = 2.0f * margin;
 
-    // 1. float pass
-    float fr[KF];
-    int fq[KF];  // slot in cell order (index = spos[slot].w)
+    float f8[NNB];
 #pragma unroll
-    for (int k = 0; k < KF; ++k) {
-        fr[k] = 3.0e38f;
-        fq[k] = -1;
-    }
-    int kept = 0;
-    float lim = (float)rc2 + margin;
+    for (int k = 0; k < NNB; ++k) f8[k] = 3.0e38f;
+    int nw = 0;
     for (int t = 0; t < walk.count; ++t) {
-        const int c = walk.cell(t);
+        int c;
+        float3 sh;
+        walk.step(t, c, sh, boxf);
         const int e = start[c + 1];
         for (int qq = start[c]; qq < e; ++qq) {
             const float4 o = spos[qq];
-            float df[3] = {o.x - me.x, o.y - me.y, o.z - me.z};
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-                df[a] = df[a] > halff[a] ? df[a] - boxf[a] : (df[a] < -halff[a] ? df[a] + boxf[a] : df[a]);
-            float cr = df[0] * df[0] + df[1] * df[1] + df[2] * df[2];
-            if (qq == q || !(cr <= lim)) continue;
-            int cq = qq;
-#pragma unroll
-            for (int k = 0; k < KF; ++k) {  // sorted insertion; the last entry drops out
-                const bool lt = cr < fr[k];
-                const float tr = fr[k];
-                const int tq = fq[k];
-                fr[k] = lt ? cr : tr;
-                fq[k] = lt ? cq : tq;
-                cr = lt ? tr : cr;
-                cq = lt ? tq : cq;
+            float dx = (o.x + sh.x) - me.x, dy = (o.y + sh.y) - me.y, dz = (o.z + sh.z) - me.z;
+            if (!walk.shifts) {  // fewer than 3 cells along an axis: minimum image per candidate
+                dx = dx > halff[0] ? dx - boxf[0] : (dx < -halff[0] ? dx + boxf[0] : dx);
+                dy = dy > halff[1] ? dy - boxf[1] : (dy < -halff[1] ? dy + boxf[1] : dy);
+                dz = dz > halff[2] ? dz - boxf[2] : (dz < -halff[2] ? dz + boxf[2] : dz);
             }
-            if (++kept >= KF) lim = fminf(lim, fr[KF - 1]);
+            float cr = dx * dx + dy * dy + dz * dz;
+            if (qq == q || !(cr <= fminf(lim, f8[NNB - 1] + twom))) continue;
+            if (nw < KW) {
+                wslot[nw][threadIdx.x] = qq;
+                wr2[nw][threadIdx.x] = cr;
+            }
+            ++nw;
+            if (cr < f8[NNB - 1]) {
+#pragma unroll
+                for (int k = 0; k < NNB; ++k) {
+                    const bool lt = cr < f8[k];
+                    const float tk = f8[k];
+                    f8[k] = lt ? cr : tk;
+                    cr = lt ? tk : cr;
+                }
+            }
         }
     }
-
-    // 2. exact decision over the window
-    const float W = kept >= NNB ? fr[NNB - 1] + 2.0f * margin : (float)rc2 + margin;
+    const float W = f8[NNB - 1] < 1.0e38f ? fminf(lim, f8[NNB - 1] + twom) : lim;
     const unsigned long long krc2 = (unsigned long long)__double_as_longlong(rc2);
     unsigned long long bk[NNB];
     int bj[NNB];
@@ -626,30 +649,31 @@ kf_knn(const double* __restrict__ pos, long long n, Geom g, int3 nc, const int* 
         bk[k] = ~0ull;
         bj[k] = 0x7fffffff;
     }
-    if (kept >= KF && fr[KF - 1] <= W) {  // window not held in full: search again in FP64
+    if (nw > KW) {  // list overflowed: search again in FP64
         for (int t = 0; t < walk.count; ++t) {
-            const int c = walk.cell(t);
+            int c;
+            float3 sh;
+            walk.step(t, c, sh, boxf);
             for (int qq = start[c]; qq < start[c + 1]; ++qq) {
                 const int jn = sorted[qq];
                 if (jn == i) continue;
                 double d[3];
-                for (int a = 0; a < 3; ++a) d[a] = min_image(pos[3 * (long long)jn + a] - P[a], box[a]);
+                for (int a = 0; a < 3; ++a) d[a] = min_image(pos[3 * (long long)jn + a] - P[a], box[a], qbox[a]);
                 const unsigned long long ck = (unsigned long long)__double_as_longlong(dist2(d));
                 if (ck <= krc2) insert_exact(bk, bj, ck, jn);
             }
         }
     } else {
-#pragma unroll
-        for (int k = 0; k < KF; ++k) {
-            if (fq[k] >= 0 && fr[k] <= W) {
-                const float4 o = spos[fq[k]];
-                const int jn = __float_as_int(o.w);
-                const float dfx[3] = {o.x - me.x, o.y - me.y, o.z - me.z};
-                double d[3];
-                for (int a = 0; a < 3; ++a) d[a] = min_image_hint(pos[3 * (long long)jn + a], P[a], dfx[a], box[a]);
-                const unsigned long long ck = (unsigned long long)__double_as_longlong(dist2(d));
-                if (ck <= krc2) insert_exact(bk, bj, ck, jn);
-            }
+        for (int k = 0; k < nw; ++k) {
+            if (!(wr2[k][threadIdx.x] <= W)) continue;
+            const float4 o = spos[wslot[k][threadIdx.x]];
+            const int jn = __float_as_int(o.w);
+            const float dfx[3] = {o.x - me.x, o.y - me.y, o.z - me.z};
+            double d[3];
+            for (int a = 0; a < 3; ++a)
+                d[a] = min_image_hint(pos[3 * (long long)jn + a], P[a], dfx[a], qf[a], box[a], qbox[a]);
+            const unsigned long long ck = (unsigned long long)__double_as_longlong(dist2(d));
+            if (ck <= krc2) insert_exact(bk, bj, ck, jn);
         }
     }
     // outputs: float(d / 4) = float(d) / 4 exactly
@@ -660,7 +684,8 @@ kf_knn(const double* __restrict__ pos, long long n, Geom g, int3 nc, const int* 
         if (bk[k] != ~0ull) {
             const int jn = bj[k];
             for (int a = 0; a < 3; ++a)
-                f[3 + 3 * k + a] = __double2float_rn(min_image(pos[3 * (long long)jn + a] - P[a], box[a])) * (1.0f / FEAT_LENGTH);
+                f[3 + 3 * k + a] =
+                    __double2float_rn(min_image(pos[3 * (long long)jn + a] - P[a], box[a], qbox[a])) * (1.0f / FEAT_LENGTH);
         } else {
             for (int a = 0; a < 3; ++a) f[3 + 3 * k + a] = 0.0f;
         }
@@ -761,7 +786,8 @@ cudaError_t mlp_features(long long n, const double* pos, const int box[3], float
     e = scan_exclusive(count, m, start, bsum, st);
     if (e != cudaSuccess) return e;
     kf_fill<<<blocks, 256, 0, st>>>(pos, n, cell, start, cursor, sorted, spos);
-    kf_knn<<<blocks, 256, 0, st>>>(pos, n, g, nc, start, sorted, cell, spos, margin, feat);
+    kf_knn<<<(unsigned)((n + KNN_THREADS - 1) / KNN_THREADS), KNN_THREADS, 0, st>>>(pos, n, g, nc, start, sorted, cell,
+                                                                                  spos, margin, feat);
     return cudaGetLastError();
 }
 
