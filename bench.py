@@ -268,7 +268,7 @@ def run_gpu(args, rank, world):
         others = per_precision(L, {p: (10 if p == "f64" else 100) for p in PREC_NAMES if p != prec})
     c512 = None
     if rank == 0 and world == 1 and not args.no_colloids512:
-        c512 = colloids_512()
+        c512 = colloids_512(L=args.colloids[0], n=args.colloids[1])
     batched = None
     if rank == 0 and world == 1 and not args.no_batched:
         batched = batched_replicas()
@@ -601,6 +601,8 @@ def main():
     ap.add_argument("--no-per-precision", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-colloids512", action="store_true")
+    ap.add_argument("--colloids", type=int, nargs=2, default=[512, 100000], metavar=("L", "N"),
+                    help="box side and colloid count of the sedimentation-box block")
     ap.add_argument("--no-learned", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
