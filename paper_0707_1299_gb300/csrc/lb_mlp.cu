@@ -488,7 +488,6 @@ __global__ void kf_fill(const double* __restrict__ pos, long long n, const int* 
 __device__ __forceinline__ double min_image(double d, double box, double qbox) {
     return fabs(d) > qbox ? d - box * rint(d / box) : d;
 }
-__device__ __forceinline__ double min_image(double d, double box) { return min_image(d, box, 0.25 * box); }
 
 // Squared distance summed in the order ((dx^2 + dy^2) + dz^2), each step
 // rounded once.
