@@ -14,9 +14,13 @@ distances: lower index first), each divided by FEAT_LENGTH (24 numbers);
 absent neighbours are zero vectors.
 
 `forward`/`backward` follow these definitions with plain numpy matrix
-products.  With `bf16=True` they round, as the CUDA kernels do, the
-weights, the input and the activations h1, h2 to bfloat16 (round to
-nearest even) before they enter a product; everything else stays FP64.
+products.  With `bf16_round=True` they round, as the CUDA kernels do, every
+operand of a product to bfloat16 (round to nearest even): the weights, the
+input and the activations h1, h2; in the backward pass dL/dy where it
+enters the layer-3 weight and bias gradients, and the pre-activation
+gradients gz2, gz1 where they enter the weight and bias gradients and
+gh1 = gz2 W2 (gh2 = (dL/dy) W3 takes the unrounded dL/dy).  Everything else
+stays FP64.
 """
 from __future__ import annotations
 
@@ -79,13 +83,14 @@ def backward(P, x, t, bf16_round=False):
     y, (xr, z1, h1, z2, h2) = forward(P, x, bf16_round)
     B = x.shape[0]
     gy = 2.0 * (y - t) / (B * y.shape[1])
-    G = {"W3": gy.T @ h2, "b3": gy.sum(0)}
+    gyr = r(gy)
+    G = {"W3": gyr.T @ h2, "b3": gyr.sum(0)}
     gh2 = gy @ r(P["W3"])
-    gz2 = gh2 * dsilu(z2)
+    gz2 = r(gh2 * dsilu(z2))
     G["W2"] = gz2.T @ h1
     G["b2"] = gz2.sum(0)
     gh1 = gz2 @ r(P["W2"])
-    gz1 = gh1 * dsilu(z1)
+    gz1 = r(gh1 * dsilu(z1))
     G["W1"] = gz1.T @ xr
     G["b1"] = gz1.sum(0)
     return G

@@ -1,13 +1,15 @@
 // lb_mlp.cu -- the learned correction of the interpolated colloid velocity:
 // neighbour features (cell list), and a 27 -> 64 -> 64 -> 3 SiLU perceptron
-// in bfloat16 with FP32 accumulation (forward, fused forward + backward,
-// Adam), all hand-written.
+// in bfloat16 with FP32 accumulation on the tensor cores (forward, fused
+// forward + backward), Adam, all hand-written.
 //
-// Rounding points (the training oracle mirrors them): the input x, the
-// weight matrices and the activations h1, h2 are rounded to bfloat16 (round
-// to nearest even) before they enter a product; pre-activations, biases,
-// accumulations and gradients are FP32; master weights and Adam moments are
-// FP32.
+// Rounding points (the training oracle mirrors them): every operand of a
+// product is bfloat16 (round to nearest even) -- the input x, the weight
+// matrices, the activations h1, h2, and in the backward pass dL/dy and the
+// pre-activation gradients gz2, gz1 where they enter the weight-gradient and
+// gh1 products; gh2 = (dL/dy) W3 takes the FP32 dL/dy.  Pre-activations,
+// biases, accumulations and gradients are FP32; master weights and Adam
+// moments are FP32.
 #include <math.h>
 #include <stdint.h>
 
@@ -26,9 +28,6 @@ using lbk::wrap_node;
 constexpr int D0 = 27, D1 = 64, D2 = 64, D3 = 3;
 constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + D1 * D0, OFF_W2 = OFF_B1 + D1, OFF_B2 = OFF_W2 + D2 * D1,
               OFF_W3 = OFF_B2 + D2, OFF_B3 = OFF_W3 + D3 * D2, NPARAM = OFF_B3 + D3;
-constexpr int TS = 64;        // samples per tile
-constexpr int NT = 256;       // threads per block
-constexpr int P2 = 65;        // padded row length of 64-wide smem arrays
 constexpr float FEAT_LENGTH = 4.0f;
 constexpr float R_CUT = 8.0f;
 constexpr int NNB = 8;
@@ -38,66 +37,6 @@ __device__ __forceinline__ float silu(float z) { return z / (1.0f + expf(-z)); }
 __device__ __forceinline__ float dsilu(float z) {
     const float s = 1.0f / (1.0f + expf(-z));
     return s * (1.0f + z * (1.0f - s));
-}
-
-// shared-memory layout (floats)
-struct Smem {
-    static constexpr int W1 = 0;                    // [64][27]
-    static constexpr int W2 = W1 + D1 * D0;         // [64][65]
-    static constexpr int W3 = W2 + D2 * P2;         // [3][64]
-    static constexpr int B = W3 + D3 * D2;          // b1 b2 b3
-    static constexpr int X = B + D1 + D2 + D3;      // [64][28]
-    static constexpr int Z1 = X + TS * 28;          // [64][65]
-    static constexpr int H1 = Z1 + TS * P2;
-    static constexpr int Z2 = H1 + TS * P2;
-    static constexpr int H2 = Z2 + TS * P2;
-    static constexpr int GY = H2 + TS * P2;         // [64][3]
-    static constexpr int GZ2 = GY + TS * D3;        // [64][65]
-    static constexpr int GZ1 = GZ2 + TS * P2;       // [64][65]
-    static constexpr int END = GZ1 + TS * P2;
-};
-
-__device__ void load_weights(const float* __restrict__ p, float* sm) {
-    for (int i = threadIdx.x; i < D1 * D0; i += NT) sm[Smem::W1 + i] = bf16r(p[OFF_W1 + i]);
-    for (int i = threadIdx.x; i < D2 * D1; i += NT) sm[Smem::W2 + (i / D1) * P2 + i % D1] = bf16r(p[OFF_W2 + i]);
-    for (int i = threadIdx.x; i < D3 * D2; i += NT) sm[Smem::W3 + i] = bf16r(p[OFF_W3 + i]);
-    for (int i = threadIdx.x; i < D1; i += NT) sm[Smem::B + i] = p[OFF_B1 + i];
-    for (int i = threadIdx.x; i < D2; i += NT) sm[Smem::B + D1 + i] = p[OFF_B2 + i];
-    for (int i = threadIdx.x; i < D3; i += NT) sm[Smem::B + D1 + D2 + i] = p[OFF_B3 + i];
-}
-
-// Forward pass of one tile of `ns` samples (rows >= ns are zero and unused).
-__device__ void tile_forward(const float* __restrict__ feat, long long s0, int ns, float* sm, float* __restrict__ y_out) {
-    for (int i = threadIdx.x; i < TS * 28; i += NT) {
-        const int s = i / 28, k = i % 28;
-        sm[Smem::X + i] = (s < ns && k < D0) ? bf16r(feat[(s0 + s) * D0 + k]) : 0.0f;
-    }
-    __syncthreads();
-    const int j = threadIdx.x & 63, sg = threadIdx.x >> 6;  // unit j, sample group sg (16 samples each)
-    for (int m = 0; m < TS / 4; ++m) {
-        const int s = sg + 4 * m;
-        float z = sm[Smem::B + j];
-        for (int k = 0; k < D0; ++k) z = fmaf(sm[Smem::X + s * 28 + k], sm[Smem::W1 + j * D0 + k], z);
-        sm[Smem::Z1 + s * P2 + j] = z;
-        sm[Smem::H1 + s * P2 + j] = bf16r(silu(z));
-    }
-    __syncthreads();
-    for (int m = 0; m < TS / 4; ++m) {
-        const int s = sg + 4 * m;
-        float z = sm[Smem::B + D1 + j];
-        for (int k = 0; k < D1; ++k) z = fmaf(sm[Smem::H1 + s * P2 + k], sm[Smem::W2 + j * P2 + k], z);
-        sm[Smem::Z2 + s * P2 + j] = z;
-        sm[Smem::H2 + s * P2 + j] = bf16r(silu(z));
-    }
-    __syncthreads();
-    if (threadIdx.x < TS * D3) {
-        const int s = threadIdx.x / D3, o = threadIdx.x % D3;
-        float yv = sm[Smem::B + D1 + D2 + o];
-        for (int k = 0; k < D2; ++k) yv = fmaf(sm[Smem::H2 + s * P2 + k], sm[Smem::W3 + o * D2 + k], yv);
-        if (y_out && s < ns) y_out[(s0 + s) * D3 + o] = yv;
-        sm[Smem::GY + threadIdx.x] = yv;  // the backward pass turns it into dL/dy
-    }
-    __syncthreads();
 }
 
 // ------------------------------------------------- tensor-core forward
@@ -148,11 +87,17 @@ constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(D1 >
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+// instruction descriptor for M = 128 and a given N (multiple of 16)
+__host__ __device__ constexpr uint32_t idesc_n(int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accumulate,
+                                    uint32_t idesc = IDESC) {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-        "l"(a), "l"(b), "r"(IDESC), "r"(accumulate));
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void commit(uint32_t mbar) {
@@ -196,11 +141,79 @@ __device__ __forceinline__ void load_row64(uint32_t taddr, float (&v)[64]) {
     for (int k = 0; k < 64; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+// 32 and 16 consecutive FP32 columns of this thread's accumulator row
+__device__ __forceinline__ void load_row32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+__device__ __forceinline__ void load_row16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// 64 consecutive FP32 columns of this thread's row into tensor memory
+__device__ __forceinline__ void store_row64(uint32_t taddr, const float (&v)[64]) {
+    uint32_t r[64];
+#pragma unroll
+    for (int k = 0; k < 64; ++k) r[k] = __float_as_uint(v[k]);
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x64.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,"
+        "%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63,%64};"
+        ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+          "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
+          "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]),
+          "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31]),
+          "r"(r[32]), "r"(r[33]), "r"(r[34]), "r"(r[35]), "r"(r[36]), "r"(r[37]), "r"(r[38]), "r"(r[39]),
+          "r"(r[40]), "r"(r[41]), "r"(r[42]), "r"(r[43]), "r"(r[44]), "r"(r[45]), "r"(r[46]), "r"(r[47]),
+          "r"(r[48]), "r"(r[49]), "r"(r[50]), "r"(r[51]), "r"(r[52]), "r"(r[53]), "r"(r[54]), "r"(r[55]),
+          "r"(r[56]), "r"(r[57]), "r"(r[58]), "r"(r[59]), "r"(r[60]), "r"(r[61]), "r"(r[62]), "r"(r[63])
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
     const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
     return a | (b << 16);
 }
+
+// Transposed write of 2-byte values into a K-major operand whose K runs
+// over the 128 samples of a tile: this thread (sample s) holds v[r] for
+// rows row0 + r; lane pairs (s, s^1) exchange by shuffle and each writes
+// the 32-bit words (samples 2j, 2j + 1) of every other row.
+template <int NROWS>
+__device__ __forceinline__ void write_transposed(unsigned char* base, int row0, int s, const float* v) {
+    const bool odd = (s & 1) != 0;
+#pragma unroll
+    for (int r = 0; r < NROWS; ++r) {
+        const float mine = v[r];
+        const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
+        if (((r & 1) != 0) == odd) {
+            const uint32_t w = odd ? pack_bf16(other, mine) : pack_bf16(mine, other);
+            *(uint32_t*)(base + kmajor_off(row0 + r, s & ~1, 128)) = w;
+        }
+    }
+}
+
 
 }  // namespace tc
 
@@ -338,104 +351,282 @@ __global__ void __launch_bounds__(tc::M) km_forward_tc(const float* __restrict__
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(NCOL) : "memory");
 }
 
-// Forward + backward of the mean squared error (1 / 3n) sum (y - t)^2 over
-// all n samples; gradients and the sum of squared errors are accumulated
-// into grad[NPARAM] and sse[0] (both cleared by the caller).
-__global__ void __launch_bounds__(NT) km_grad(const float* __restrict__ params, long long n,
-                                              const float* __restrict__ feat, const float* __restrict__ target,
-                                              float* __restrict__ grad, float* __restrict__ sse) {
-    extern __shared__ float sm[];
-    load_weights(params, sm);
+// ------------------------------------------------ tensor-core training
+// Gradient of the mean squared error (1 / 3n) sum (y - t)^2 on the tensor
+// cores.  A CTA of 128 threads takes tiles of 128 samples (thread r is
+// sample r); per tile, each step a tcgen05.mma (kind::f16, M = 128) with
+// its accumulator in tensor memory, committed to an mbarrier:
+//   z1 = x W1^T, z2 = h1 W2^T                          (forward, as km_forward_tc)
+//   gh1 = gz2 W2  (B = W2^T)                           (N = 64, K = 64)
+//   D3 += [h2^T; 1; 0] [gy^T; 0]^T                      (N = 16, K = 128 samples)
+//   DG += [gz2^T; gz1^T] [h1^T; x^T; 1; 0]^T            (N = 112, K = 128 samples)
+// so that, summed over the CTA's tiles, DG holds dW2 (rows 0-63, columns
+// 0-63), dW1 (rows 64-127, columns 64-90), db2 and db1 (column 96), and D3
+// holds dW3^T (rows 0-63, columns 0-2) and db3 (row 64); they are added to
+// the global gradient once per CTA.  The operands of these products are
+// bfloat16: x, h1, h2 (as in the forward) and gy, gz2, gz1 (rounded to
+// nearest even); gh2 = gy W3 and the SiLU derivatives are FP32 on the CUDA
+// cores.  Operands whose K runs over the samples are written transposed
+// into the K-major layout of the forward operands.
+namespace tc {
+struct G {  // shared memory (bytes)
+    static constexpr int B1 = 0;                  // W1   [64][32]   K-major over inputs
+    static constexpr int B2 = B1 + 64 * 32 * 2;   // W2   [64][64]   K-major over inputs
+    static constexpr int W2T = B2 + 64 * 64 * 2;  // W2^T [64][64]   K-major over outputs
+    static constexpr int A1 = W2T + 64 * 64 * 2;  // x    [128][32]
+    static constexpr int A2 = A1 + 128 * 32 * 2;  // h1   [128][64]
+    static constexpr int GZ = A2 + 128 * 64 * 2;  // gz2  [128][64]
+    static constexpr int AG = GZ + 128 * 64 * 2;  // [gz2^T; gz1^T]       [128][128 samples]
+    static constexpr int BG = AG + 128 * 128 * 2; // [h1^T; x^T; 1; 0]    [112][128 samples]
+    static constexpr int A3 = BG + 112 * 128 * 2; // [h2^T; 1; 0]         [128][128 samples]
+    static constexpr int B3 = A3 + 128 * 128 * 2; // [gy^T; 0]            [16][128 samples]
+    static constexpr int W3S = B3 + 16 * 128 * 2; // W3 float [3][64] (bfloat16-rounded)
+    static constexpr int BIAS = W3S + 3 * 64 * 4; // b1 b2 b3
+    static constexpr int MBAR = BIAS + 132 * 4;
+    static constexpr int TADDR = MBAR + 8;
+    static constexpr int USED = TADDR + 8;
+};
+constexpr int GSMEM = 200 * 1024;  // one CTA per SM: its 256 tensor-memory columns never wait
+static_assert(G::USED <= GSMEM, "training shared layout");
+constexpr int GCOLS = 256;
+constexpr int TZ = 0, TDG = 64, TD3 = 176, TZ1 = 192;  // tensor-memory columns
+constexpr int KS = 128;                                // samples: K of the weight-gradient products
+constexpr uint32_t SBO_S = (KS / 8) * 128;             // stride byte offset of those operands
+
+// Before a tensor-core phase: the operands written by the threads become
+// visible to the tensor cores, and every thread's tensor-memory reads are
+// ordered before the products.
+__device__ __forceinline__ void before_issue() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+}
+// After issuing and committing: the bounded wait, uniform across the CTA.
+__device__ __forceinline__ bool after_issue(uint32_t mbar, uint32_t& phase, long long polls) {
+    const bool ok = __syncthreads_and(wait_phase(mbar, phase, polls));
+    phase ^= 1u;
+    if (ok) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return ok;
+}
+}  // namespace tc
+
+__global__ void __launch_bounds__(tc::M, 1) km_grad_tc(const float* __restrict__ params, long long n,
+                                                       const float* __restrict__ feat,
+                                                       const float* __restrict__ target, float* __restrict__ grad,
+                                                       float* __restrict__ sse, int* __restrict__ status,
+                                                       long long polls) {
+    using namespace tc;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t mbar = smem_u32(smem + G::MBAR);
+    float* w3 = (float*)(smem + G::W3S);
+    float* bias = (float*)(smem + G::BIAS);
     const float gscale = 2.0f / (3.0f * (float)n);
-    // per-thread accumulators of the weight gradients it owns
-    float aW2[16], aW1[7], aW3 = 0.f, ab2 = 0.f, ab1 = 0.f, ab3 = 0.f, asse = 0.f;
-    for (int q = 0; q < 16; ++q) aW2[q] = 0.f;
-    for (int q = 0; q < 7; ++q) aW1[q] = 0.f;
-    const int j = threadIdx.x & 63, sg = threadIdx.x >> 6;
-    for (long long t = blockIdx.x; t * TS < n; t += gridDim.x) {
-        const long long s0 = t * TS;
-        const int ns = (int)(n - s0 < TS ? n - s0 : TS);
-        tile_forward(feat, s0, ns, sm, nullptr);
-        if (threadIdx.x < TS * D3) {  // dL/dy
-            const int s = threadIdx.x / D3, o = threadIdx.x % D3;
-            float g = 0.f;
-            if (s < ns) {
-                const float d = sm[Smem::GY + threadIdx.x] - target[(s0 + s) * D3 + o];
+
+    // weights (bfloat16) and the constant rows of the gradient operands
+    for (int i = tid; i < D1 * K1; i += M) {
+        const int r = i / K1, k = i % K1;
+        const float w = k < D0 ? params[OFF_W1 + r * D0 + k] : 0.0f;
+        *(__nv_bfloat16*)(smem + G::B1 + kmajor_off(r, k, K1)) = __float2bfloat16_rn(w);
+    }
+    for (int i = tid; i < D2 * D1; i += M) {
+        const int o = i / D1, k = i % D1;
+        const __nv_bfloat16 w = __float2bfloat16_rn(params[OFF_W2 + i]);
+        *(__nv_bfloat16*)(smem + G::B2 + kmajor_off(o, k, D1)) = w;   // [o][i]
+        *(__nv_bfloat16*)(smem + G::W2T + kmajor_off(k, o, D2)) = w;  // [i][o]
+    }
+    for (int i = tid; i < D3 * D2; i += M) w3[i] = bf16r(params[OFF_W3 + i]);
+    for (int i = tid; i < D1; i += M) bias[i] = params[OFF_B1 + i];
+    for (int i = tid; i < D2; i += M) bias[D1 + i] = params[OFF_B2 + i];
+    if (tid < D3) bias[D1 + D2 + tid] = params[OFF_B3 + tid];
+    {
+        const __nv_bfloat16 one = __float2bfloat16_rn(1.0f), zero = __float2bfloat16_rn(0.0f);
+        for (int r = 96; r < 112; ++r)  // BG: the ones row, then zeros
+            *(__nv_bfloat16*)(smem + G::BG + kmajor_off(r, tid, KS)) = r == 96 ? one : zero;
+        for (int r = 64; r < 128; ++r)  // A3: the ones row, then zeros
+            *(__nv_bfloat16*)(smem + G::A3 + kmajor_off(r, tid, KS)) = r == 64 ? one : zero;
+        for (int r = 3; r < 16; ++r) *(__nv_bfloat16*)(smem + G::B3 + kmajor_off(r, tid, KS)) = zero;
+    }
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(smem + G::TADDR)),
+                     "r"(GCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tbase = *(volatile uint32_t*)(smem + G::TADDR);
+    const uint32_t lanes = (uint32_t)(warp * 32) << 16;  // this warp's 32 lanes
+    const uint32_t a1 = smem_u32(smem + G::A1), a2 = smem_u32(smem + G::A2), gz = smem_u32(smem + G::GZ);
+    const uint32_t b1 = smem_u32(smem + G::B1), b2 = smem_u32(smem + G::B2), w2t = smem_u32(smem + G::W2T);
+    const uint32_t ag = smem_u32(smem + G::AG), bg = smem_u32(smem + G::BG);
+    const uint32_t a3 = smem_u32(smem + G::A3), b3 = smem_u32(smem + G::B3);
+    uint32_t phase = 0;
+    bool ok = true, first = true;
+    float asse = 0.0f;
+
+
+    for (long long t = blockIdx.x; t * M < n && ok; t += gridDim.x) {
+        const long long s = t * M + tid;
+        const bool live = s < n;
+        float z[64];
+        {  // x: bfloat16, zero-padded to 32; also x^T into the gradient operand
+            float x[K1];
+#pragma unroll
+            for (int k = 0; k < K1; ++k) x[k] = (live && k < D0) ? feat[s * D0 + k] : 0.0f;
+#pragma unroll
+            for (int kg = 0; kg < K1 / 8; ++kg) {
+                uint4 v;
+                v.x = pack_bf16(x[8 * kg + 0], x[8 * kg + 1]);
+                v.y = pack_bf16(x[8 * kg + 2], x[8 * kg + 3]);
+                v.z = pack_bf16(x[8 * kg + 4], x[8 * kg + 5]);
+                v.w = pack_bf16(x[8 * kg + 6], x[8 * kg + 7]);
+                *(uint4*)(smem + G::A1 + kmajor_off(tid, 8 * kg, K1)) = v;
+            }
+            write_transposed<K1>(smem + G::BG, 64, tid, x);
+        }
+        before_issue();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int ks = 0; ks < K1 / 16; ++ks)
+                mma(tbase + TZ, smem_desc(a1 + ks * 256, 128, (K1 / 8) * 128), smem_desc(b1 + ks * 256, 128, (K1 / 8) * 128),
+                    ks > 0);
+            commit(mbar);
+        }
+        ok = after_issue(mbar, phase, polls);
+        if (!ok) break;
+        load_row64(tbase + lanes + TZ, z);
+        store_row64(tbase + lanes + TZ1, z);  // z1, for the SiLU derivative of the backward pass
+        {
+            float h[64];
+#pragma unroll
+            for (int k = 0; k < 64; ++k) h[k] = silu(z[k] + bias[k]);
+#pragma unroll
+            for (int kg = 0; kg < D1 / 8; ++kg) {
+                uint4 v;
+                v.x = pack_bf16(h[8 * kg + 0], h[8 * kg + 1]);
+                v.y = pack_bf16(h[8 * kg + 2], h[8 * kg + 3]);
+                v.z = pack_bf16(h[8 * kg + 4], h[8 * kg + 5]);
+                v.w = pack_bf16(h[8 * kg + 6], h[8 * kg + 7]);
+                *(uint4*)(smem + G::A2 + kmajor_off(tid, 8 * kg, D1)) = v;
+            }
+            write_transposed<64>(smem + G::BG, 0, tid, h);
+        }
+        before_issue();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int ks = 0; ks < D1 / 16; ++ks)
+                mma(tbase + TZ, smem_desc(a2 + ks * 256, 128, (D1 / 8) * 128), smem_desc(b2 + ks * 256, 128, (D1 / 8) * 128),
+                    ks > 0);
+            commit(mbar);
+        }
+        ok = after_issue(mbar, phase, polls);
+        if (!ok) break;
+        load_row64(tbase + lanes + TZ, z);  // z2
+        {
+            float h[64], gy[D3];  // h holds h2, then gz2
+            float y0 = bias[D1 + D2], y1 = bias[D1 + D2 + 1], y2 = bias[D1 + D2 + 2];
+#pragma unroll
+            for (int k = 0; k < D2; ++k) {
+                h[k] = bf16r(silu(z[k] + bias[D1 + k]));
+                y0 = fmaf(h[k], w3[k], y0);
+                y1 = fmaf(h[k], w3[D2 + k], y1);
+                y2 = fmaf(h[k], w3[2 * D2 + k], y2);
+            }
+            write_transposed<64>(smem + G::A3, 0, tid, h);
+            const float yv[3] = {y0, y1, y2};
+#pragma unroll
+            for (int o = 0; o < D3; ++o) {
+                float d = 0.0f;
+                if (live) d = yv[o] - target[s * D3 + o];
                 asse = fmaf(d, d, asse);
-                g = gscale * d;
+                gy[o] = gscale * d;
             }
-            sm[Smem::GY + threadIdx.x] = g;
-        }
-        __syncthreads();
-        // layer 3: gW3[o][k] = sum_s gy[s][o] h2[s][k]; gb3
-        if (threadIdx.x < D3 * D2) {
-            const int o = threadIdx.x / D2, k = threadIdx.x % D2;
-            float a = 0.f;
-            for (int s = 0; s < TS; ++s) a = fmaf(sm[Smem::GY + s * D3 + o], sm[Smem::H2 + s * P2 + k], a);
-            aW3 += a;
-        }
-        if (threadIdx.x < D3) {
-            float a = 0.f;
-            for (int s = 0; s < TS; ++s) a += sm[Smem::GY + s * D3 + threadIdx.x];
-            ab3 += a;
-        }
-        // gz2[s][j] = (sum_o gy[s][o] W3[o][j]) dsilu(z2[s][j])
-        for (int m = 0; m < TS / 4; ++m) {
-            const int s = sg + 4 * m;
-            float g = 0.f;
-            for (int o = 0; o < D3; ++o) g = fmaf(sm[Smem::GY + s * D3 + o], sm[Smem::W3 + o * D2 + j], g);
-            sm[Smem::GZ2 + s * P2 + j] = g * dsilu(sm[Smem::Z2 + s * P2 + j]);
-        }
-        __syncthreads();
-        // layer 2: gW2[j][k] = sum_s gz2[s][j] h1[s][k]; thread owns k = j (its unit) for 16 rows
-        for (int q = 0; q < 16; ++q) {
-            const int row = sg + 4 * q;  // output unit
-            float a = 0.f;
-            for (int s = 0; s < TS; ++s) a = fmaf(sm[Smem::GZ2 + s * P2 + row], sm[Smem::H1 + s * P2 + j], a);
-            aW2[q] += a;
-        }
-        if (threadIdx.x < D2) {
-            float a = 0.f;
-            for (int s = 0; s < TS; ++s) a += sm[Smem::GZ2 + s * P2 + threadIdx.x];
-            ab2 += a;
-        }
-        // gz1[s][j] = (sum_i gz2[s][i] W2[i][j]) dsilu(z1[s][j])
-        for (int m = 0; m < TS / 4; ++m) {
-            const int s = sg + 4 * m;
-            float g = 0.f;
-            for (int i = 0; i < D2; ++i) g = fmaf(sm[Smem::GZ2 + s * P2 + i], sm[Smem::W2 + i * P2 + j], g);
-            sm[Smem::GZ1 + s * P2 + j] = g * dsilu(sm[Smem::Z1 + s * P2 + j]);
-        }
-        __syncthreads();
-        // layer 1: gW1[u][k] = sum_s gz1[s][u] x[s][k]; entries e = threadIdx.x + 256 q
-        for (int q = 0; q < 7; ++q) {
-            const int e = threadIdx.x + NT * q;
-            if (e < D1 * D0) {
-                const int u = e / D0, k = e % D0;
-                float a = 0.f;
-                for (int s = 0; s < TS; ++s) a = fmaf(sm[Smem::GZ1 + s * P2 + u], sm[Smem::X + s * 28 + k], a);
-                aW1[q] += a;
+            write_transposed<D3>(smem + G::B3, 0, tid, gy);
+#pragma unroll
+            for (int k = 0; k < D2; ++k) {
+                const float g = fmaf(gy[0], w3[k], fmaf(gy[1], w3[D2 + k], gy[2] * w3[2 * D2 + k]));
+                h[k] = g * dsilu(z[k] + bias[D1 + k]);
             }
+#pragma unroll
+            for (int kg = 0; kg < D2 / 8; ++kg) {
+                uint4 v;
+                v.x = pack_bf16(h[8 * kg + 0], h[8 * kg + 1]);
+                v.y = pack_bf16(h[8 * kg + 2], h[8 * kg + 3]);
+                v.z = pack_bf16(h[8 * kg + 4], h[8 * kg + 5]);
+                v.w = pack_bf16(h[8 * kg + 6], h[8 * kg + 7]);
+                *(uint4*)(smem + G::GZ + kmajor_off(tid, 8 * kg, D2)) = v;
+            }
+            write_transposed<64>(smem + G::AG, 0, tid, h);
         }
-        if (threadIdx.x < D1) {
-            float a = 0.f;
-            for (int s = 0; s < TS; ++s) a += sm[Smem::GZ1 + s * P2 + threadIdx.x];
-            ab1 += a;
+        const bool acc = !first;
+        before_issue();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int ks = 0; ks < D2 / 16; ++ks)  // gh1 = gz2 W2
+                mma(tbase + TZ, smem_desc(gz + ks * 256, 128, (D2 / 8) * 128), smem_desc(w2t + ks * 256, 128, (D2 / 8) * 128),
+                    ks > 0);
+            for (int ks = 0; ks < KS / 16; ++ks)  // D3 += [h2^T; 1] [gy^T]^T
+                mma(tbase + TD3, smem_desc(a3 + ks * 256, 128, SBO_S), smem_desc(b3 + ks * 256, 128, SBO_S),
+                    acc || ks > 0, idesc_n(16));
+            commit(mbar);
         }
+        ok = after_issue(mbar, phase, polls);
+        if (!ok) break;
+        {
+            float gh[64];
+            load_row64(tbase + lanes + TZ, gh);
+            load_row64(tbase + lanes + TZ1, z);  // z1
+#pragma unroll
+            for (int k = 0; k < D1; ++k) gh[k] *= dsilu(z[k] + bias[k]);
+            write_transposed<64>(smem + G::AG, 64, tid, gh);
+        }
+        before_issue();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int ks = 0; ks < KS / 16; ++ks)  // DG += [gz2^T; gz1^T] [h1^T; x^T; 1]^T
+                mma(tbase + TDG, smem_desc(ag + ks * 256, 128, SBO_S), smem_desc(bg + ks * 256, 128, SBO_S),
+                    acc || ks > 0, idesc_n(112));
+            commit(mbar);
+        }
+        ok = after_issue(mbar, phase, polls);
+        first = false;
+        // every thread's tensor-memory reads are complete before the next tile's products
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
     }
-    for (int q = 0; q < 16; ++q) atomicAdd(&grad[OFF_W2 + (sg + 4 * q) * D1 + j], aW2[q]);
-    for (int q = 0; q < 7; ++q) {
-        const int e = threadIdx.x + NT * q;
-        if (e < D1 * D0) atomicAdd(&grad[OFF_W1 + e], aW1[q]);
+    if (!ok) {
+        if (tid == 0) atomicExch(status, 1);
+        wait_phase(mbar, phase ^ 1u, WAIT_POLLS);  // bounded: let the tensor-core work in flight finish
+    } else if (!first) {  // this CTA's gradient sums into the global gradient
+        float v[64];
+        load_row64(tbase + lanes + TDG, v);
+        float u[32];
+        load_row32(tbase + lanes + TDG + 64, u);
+        float w[16];
+        load_row16(tbase + lanes + TDG + 96, w);
+        float d3[16];
+        load_row16(tbase + lanes + TD3, d3);
+        if (tid < 64) {
+            for (int c = 0; c < D1; ++c) atomicAdd(&grad[OFF_W2 + tid * D1 + c], v[c]);
+            atomicAdd(&grad[OFF_B2 + tid], w[0]);
+            for (int k = 0; k < D3; ++k) atomicAdd(&grad[OFF_W3 + k * D2 + tid], d3[k]);
+        } else {
+            const int o = tid - 64;
+            for (int c = 0; c < D0; ++c) atomicAdd(&grad[OFF_W1 + o * D0 + c], u[c]);
+            atomicAdd(&grad[OFF_B1 + o], w[0]);
+            if (tid == 64)
+                for (int k = 0; k < D3; ++k) atomicAdd(&grad[OFF_B3 + k], d3[k]);
+        }
     }
-    if (threadIdx.x < D3 * D2) atomicAdd(&grad[OFF_W3 + threadIdx.x], aW3);
-    if (threadIdx.x < D3) atomicAdd(&grad[OFF_B3 + threadIdx.x], ab3);
-    if (threadIdx.x < D2) atomicAdd(&grad[OFF_B2 + threadIdx.x], ab2);
-    if (threadIdx.x < D1) atomicAdd(&grad[OFF_B1 + threadIdx.x], ab1);
     for (int off = 16; off > 0; off >>= 1) asse += __shfl_xor_sync(0xffffffffu, asse, off);
-    if ((threadIdx.x & 31) == 0) atomicAdd(sse, asse);
+    if ((tid & 31) == 0) atomicAdd(sse, asse);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(GCOLS) : "memory");
 }
 
 __global__ void km_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
@@ -701,7 +892,6 @@ struct lb_mlp {
     long long t;              // Adam steps taken
     int *ws;                  // feature workspace (cell lists), grown on demand
     size_t ws_ints;
-    int smem_grad, blocks;
     std::string err;
 };
 
@@ -732,10 +922,6 @@ lb_status check_status(lb_mlp* net) {
     return LB_OK;
 }
 
-int grid_for(long long n) {
-    const long long tiles = (n + TS - 1) / TS;
-    return (int)(tiles < 152LL * 2 ? (tiles > 0 ? tiles : 1) : 152LL * 2);
-}
 
 }  // namespace
 
@@ -809,7 +995,6 @@ lb_status lb_mlp_create(lb_mlp** out, const float* init, void* stream) {
     lb_mlp* net = new (std::nothrow) lb_mlp();
     if (!net) return LB_ERR_OOM;
     net->stream = (cudaStream_t)stream;
-    net->smem_grad = Smem::END * (int)sizeof(float);
     net->wait_polls = tc::WAIT_POLLS;
     cudaError_t e = cudaMalloc(&net->p, sizeof(float) * (4 * NPARAM + 1));
     if (e == cudaSuccess) {
@@ -820,7 +1005,8 @@ lb_status lb_mlp_create(lb_mlp** out, const float* init, void* stream) {
         e = cudaMemsetAsync(net->p, 0, sizeof(float) * (4 * NPARAM + 1), net->stream);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(net->p, init, sizeof(float) * NPARAM, cudaMemcpyDefault, net->stream);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(km_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, net->smem_grad);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(km_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::GSMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(km_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM);
     if (e == cudaSuccess) e = cudaMalloc(&net->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(net->status, 0, sizeof(int), net->stream);
@@ -893,7 +1079,10 @@ lb_status lb_mlp_forward(lb_mlp* net, long long n, const float* feat, float* out
 static lb_status run_grad(lb_mlp* net, long long n, const float* feat, const float* target) {
     LB_MCUDA(cudaMemsetAsync(net->g, 0, sizeof(float) * NPARAM, net->stream), "memset");
     LB_MCUDA(cudaMemsetAsync(net->sse, 0, sizeof(float), net->stream), "memset");
-    km_grad<<<grid_for(n), NT, net->smem_grad, net->stream>>>(net->p, n, feat, target, net->g, net->sse);
+    const long long tiles = (n + tc::M - 1) / tc::M;
+    const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(tiles, 152LL));
+    km_grad_tc<<<grid, tc::M, tc::GSMEM, net->stream>>>(net->p, n, feat, target, net->g, net->sse, net->status,
+                                                       net->wait_polls);
     LB_MCUDA(cudaGetLastError(), "gradient kernel");
     return LB_OK;
 }
