@@ -146,6 +146,38 @@ def build_lattices(prec_id, L):
     return lats
 
 
+# ------------------------------------------------------------ ranks
+# One process per GPU, each stepping its own replica of the workload (the
+# lattices of different ranks share nothing): the job's time is its slowest
+# rank's, and the job's throughput is all ranks' site updates over it.
+def _reduce_device():
+    import torch
+    import torch.distributed as dist
+    return torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    """The largest x over the ranks (x itself with one rank)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=_reduce_device())
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(sites_per_rank, steps, seconds, world):
+    """Whole-job throughput: every rank's site updates over the job's time."""
+    return world * sites_per_rank * steps / seconds / 1e6
+
+
 def run_gpu(args, rank, world):
     import torch
     from paper_0707_1299_gb300 import build, lb
@@ -183,16 +215,11 @@ def run_gpu(args, rank, world):
         one_step()
     torch.cuda.synchronize()
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
     launches0 = sum(g.kernel_launches() for _, g in lats)
     ev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in lats]
           for _ in range(args.steps)]
     clocks = ClockSampler(dev)
-    barrier()
+    barrier(world)
     torch.cuda.synchronize()
     clocks.start()
     t0 = torch.cuda.Event(enable_timing=True)
@@ -202,15 +229,10 @@ def run_gpu(args, rank, world):
         one_step(ev[s])
     t1.record(stream)
     torch.cuda.synchronize()
-    barrier()
+    barrier(world)
     clk = clocks.stop()
-    ms = t0.elapsed_time(t1)
+    ms = max_over_ranks(t0.elapsed_time(t1), world)
     launches = sum(g.kernel_launches() for _, g in lats) - launches0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     # lb_step(1) of the channel lattice (no points) launches exactly one
     # kernel, k_collide: its events time that kernel alone.  The point
     # lattices' lb_step(1) also clears their force tiles (their points were
@@ -219,7 +241,7 @@ def run_gpu(args, rank, world):
                for k in range(len(lats))]
     coll_ms = per_lat[0]
     step_ms = ms / args.steps
-    mlups = world * 4 * V * args.steps / (ms * 1e-3) / 1e6
+    mlups = job_mlups(4 * V, args.steps, ms * 1e-3, world)
 
     # end to end through the C ABI with host buffers: per step copy the
     # point positions (the step's input) in from pinned host memory, step,
@@ -231,7 +253,7 @@ def run_gpu(args, rank, world):
     e2e_steps = max(3, args.steps // 4)
     h2d = sum(hq.numel() * 8 for hq, hp in zip(host_q, has_pts) if hp)
     d2h = sum(hv.numel() * 8 for hv in host_v)
-    barrier()
+    barrier(world)
     torch.cuda.synchronize()
     te = time.perf_counter()
     for _ in range(e2e_steps):
@@ -241,13 +263,8 @@ def run_gpu(args, rank, world):
             g.step(1)
             lb.lb_velocity_at(g.ctx, host_q[k].shape[0], host_q[k].numpy(), host_v[k].numpy())
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - te
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_mlups = world * 4 * V * e2e_steps / e2e_s / 1e6
+    e2e_s = max_over_ranks(time.perf_counter() - te, world)
+    e2e_mlups = job_mlups(4 * V, e2e_steps, e2e_s, world)
 
     # stated error: the channel lattice against the exactly equivalent
     # 1 x 1 x L oracle column after the same number of steps (rank 0)
