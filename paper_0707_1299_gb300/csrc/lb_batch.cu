@@ -116,7 +116,7 @@ kb_collide(const Entry* __restrict__ ent, const long long* __restrict__ gbegin, 
         const int x = tx * TILE_X + lane;
         if (y >= g.ny) continue;  // uniform per warp
         const unsigned tile = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.ntx + (unsigned)tx;
-        const unsigned fl = __ldg(E.flags + tile);
+        const unsigned fl = group_flag(__ldg((const unsigned*)E.flags + tile), (unsigned)lane);
         const unsigned V = (unsigned)g.V;
         const int b = parity ^ E.cur0;
         if (x < g.nx) {
@@ -194,7 +194,7 @@ kb_spread(const Entry* __restrict__ ent, const long long* __restrict__ pbegin, c
     const int i = lane & 3, j = (lane >> 2) & 3;
     const T wxy = __shfl_sync(FULL, r, i) * __shfl_sync(FULL, r, 4 + j);
     const int x = wrap_node(bx + i, g.nx), y = wrap_node(by + j, g.ny);
-    const bool marker = (i == 0) || ((x & (TILE_X - 1)) == 0);
+    const bool marker = (i == 0) || ((x & (GROUP_X - 1)) == 0);
     const unsigned V = (unsigned)g.V;
     T* floc = (T*)E.floc;
 #pragma unroll
@@ -209,7 +209,7 @@ kb_spread(const Entry* __restrict__ ent, const long long* __restrict__ pbegin, c
         atomicAdd(floc + site, F0 * w);
         atomicAdd(floc + V + site, F1 * w);
         atomicAdd(floc + 2 * V + site, F2 * w);
-        if (marker) E.flags[row * (unsigned)g.ntx + (unsigned)(x / TILE_X)] = 1;
+        if (marker) E.flags[row * (unsigned)g.ntx * (TILE_X / GROUP_X) + (unsigned)(x / GROUP_X)] = 1;
     }
 }
 

@@ -74,7 +74,7 @@ k_collide(const Pops<S> src, const Pops<S> dst, const typename Store<S>::T* __re
 #pragma unroll
     for (int r = 0; r < NY; ++r) {
         const unsigned tile = ((unsigned)z * (unsigned)g.ny + (unsigned)(y0 + r)) * (unsigned)g.ntx + blockIdx.x;
-        fl[r] = (FIELD && y0 + r < g.ny) ? __ldg(flags + tile) : 0u;
+        fl[r] = (FIELD && y0 + r < g.ny) ? group_flag(__ldg((const unsigned*)flags + tile), lane) : 0u;
     }
 
     if (x < g.nx) {
@@ -136,8 +136,10 @@ k_collide_pair(const Pops<S> src, const Pops<S> dst, const float* __restrict__ f
             for (int i = 0; i < NQ; ++i) *(unsigned*)(dst.p[i] + row + x0) = 0u;
         return;
     }
-    const unsigned fl =
-        (FIELD && active) ? __ldg(flags + ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.ntx + x0 / TILE_X) : 0u;
+    const unsigned fl = (FIELD && active) ? group_flag(__ldg((const unsigned*)flags + ((unsigned)z * (unsigned)g.ny + (unsigned)y) *
+                                                                                  (unsigned)g.ntx + x0 / TILE_X),
+                                                       x0 % TILE_X)
+                                          : 0u;
     const Nbr n = neighbours(g, 0, y, z);
     unsigned w[NQ];
     pull19_pair<S, WALLS>(src, n, x0, nx, lane, active, w);

@@ -66,7 +66,7 @@ template UForce<double> uniform_force<double>(const lb_ctx*);
 __global__ void k_list_tiles(const flag_t* __restrict__ flags, long long ntiles, unsigned* __restrict__ list,
                              unsigned cap, unsigned* __restrict__ count) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool mine = t < ntiles && flags[t] != 0;
+    const bool mine = t < ntiles && ((const unsigned*)flags)[t] != 0u;
     const unsigned m = __ballot_sync(0xffffffffu, mine);
     const int lane = threadIdx.x & 31;
     unsigned base = 0;
@@ -126,7 +126,7 @@ k_spread(const T* __restrict__ st, const double* __restrict__ force, const int* 
     const int i = lane & 3, j = (lane >> 2) & 3;
     const T wxy = __shfl_sync(FULL, r, i) * __shfl_sync(FULL, r, 4 + j);
     const int x = wrap_node(bx + i, g.nx), y = wrap_node(by + j, g.ny);
-    const bool marker = (i == 0) || ((x & (TILE_X - 1)) == 0);
+    const bool marker = (i == 0) || ((x & (GROUP_X - 1)) == 0);
     const unsigned V = (unsigned)g.V;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -140,7 +140,7 @@ k_spread(const T* __restrict__ st, const double* __restrict__ force, const int* 
         atomicAdd(floc + site, F0 * w);
         atomicAdd(floc + V + site, F1 * w);
         atomicAdd(floc + 2 * V + site, F2 * w);
-        if (marker) flags[row * (unsigned)g.ntx + (unsigned)(x / TILE_X)] = 1;
+        if (marker) flags[row * (unsigned)g.ntx * (TILE_X / GROUP_X) + (unsigned)(x / GROUP_X)] = 1;
     }
 }
 
@@ -905,7 +905,7 @@ cudaError_t launch_convert_in(lb_ctx* c, const double* df) {
 
 cudaError_t launch_clear_field(lb_ctx* c) {
     cudaError_t e = cudaMemsetAsync(c->floc, 0, arith_bytes(c->prec) * 3 * (size_t)c->geom.V, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, sizeof(flag_t) * (size_t)c->geom.ntiles, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, sizeof(unsigned) * (size_t)c->geom.ntiles, c->stream);
     return e;
 }
 
