@@ -110,14 +110,19 @@ k_collide(const Pops<S> src, const Pops<S> dst, const typename Store<S>::T* __re
 // per thread, one 32-bit word per population and site pair, and the two
 // sites' arithmetic on the packed FP32x2 datapath (F2), so a site costs
 // half the load, store and floating-point instructions of k_collide (the
-// instruction count, not the bytes, bounds these formats).  The rounding
-// bits are drawn per site as in k_collide; the arithmetic differs from it
-// only where k_collide's compiler contracts a product and a sum.
+// instruction count, not the bytes, bounds these formats).  Each word is
+// rounded by one stochastic-rounding conversion of the pair, from one
+// random draw of a stream seeded by the pair's first site; the arithmetic
+// differs from k_collide's in its reciprocal of rho and in folding F into
+// j before the odd parts (see collide19).
 // Grid: (ceil(nx / 64), ceil(ny / 4), nz).  Occupancy bound (blocks of 128
-// threads per SM), swept on GB300 at 256^3: 8 for half (64 registers), 10
-// for bfloat16 (51); 6 was slower for both.
+// threads per SM) and store order, swept on GB300 at 256^3 (the four
+// lattices of the channel workload): half 8 blocks (64 registers) with the
+// stores after the arithmetic; bfloat16 9 blocks (56 registers) with each
+// store issued as its population is known.  The other combinations, and 6,
+// 7 or 10 blocks, were 1-6 % slower.
 template <typename S, bool WALLS, int FMODE>
-__global__ void __launch_bounds__(CS_THREADS, (sizeof(S) == 2 && Store<S>::kScaled) ? 8 : 10)
+__global__ void __launch_bounds__(CS_THREADS, Store<S>::kScaled ? 8 : 9)
 k_collide_pair(const Pops<S> src, const Pops<S> dst, const float* __restrict__ floc, const flag_t* __restrict__ flags,
                float* __restrict__ vel, Geom g, Coef<float> k, UForce<float> fu, float scale, float inv_scale,
                unsigned seed) {
@@ -159,19 +164,25 @@ k_collide_pair(const Pops<S> src, const Pops<S> dst, const float* __restrict__ f
     k2.tau_b = F2(k.tau_b);
     k2.om_s = F2(k.om_s);
     k2.om_b = F2(k.om_b);
-    F2 o[NQ], v3[3];
-    collide19<F2, false, SC, VOUT>(f, Fx, Fy, Fz, k2, o, F2(inv_scale), v3);
-    unsigned r0 = rng_seed(row + x0, seed), r1 = rng_seed(row + x0 + 1, seed);
-    if (active) {
+    F2 v3[3];
+    unsigned rs = rng_seed(row + x0, seed);
+    if constexpr (SC) {  // half: all populations first, then the stores
+        F2 o[NQ];
+        collide19<F2, false, SC, VOUT>(f, Fx, Fy, Fz, k2, o, F2(inv_scale), v3);
+        if (active)
 #pragma unroll
-        for (int i = 0; i < NQ; ++i) {
-            const unsigned d0 = rng_next(r0), d1 = rng_next(r1);
-            *(unsigned*)(dst.p[i] + row + x0) = St::bits2(o[i].v.x, o[i].v.y, d0, d1);
-        }
-        if (VOUT && fl)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) *(float2*)(vel + a * V + row + x0) = v3[a].v;
+            for (int i = 0; i < NQ; ++i)
+                *(unsigned*)(dst.p[i] + row + x0) = St::bits2_rs(o[i].v.x, o[i].v.y, rng_next2(rs));
+    } else {  // bfloat16: each population is rounded and stored as soon as it is computed
+        const auto emit = [&](int i, F2 v) {
+            const unsigned word = St::bits2_rs(v.v.x, v.v.y, rng_next2(rs));
+            if (active) *(unsigned*)(dst.p[i] + row + x0) = word;
+        };
+        collide19<F2, false, SC, VOUT>(f, Fx, Fy, Fz, k2, emit, F2(inv_scale), v3);
     }
+    if (VOUT && fl && active)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) *(float2*)(vel + a * V + row + x0) = v3[a].v;
 }
 
 // Fix-up for a few fixed points: the collide ran with the uniform force at

@@ -12,6 +12,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <type_traits>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -143,6 +144,15 @@ template <> struct Store<__half> {
         asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
         return r;
     }
+    // stochastic rounding of two values into one word by the conversion's
+    // own stochastic-rounding mode (sm_100a and later): random bits 12:0 of
+    // rb dither lo, bits 28:16 hi; beyond the half range the result is
+    // infinite (and caught by the finiteness checks)
+    static __device__ __forceinline__ unsigned bits2_rs(float lo, float hi, unsigned rb) {
+        unsigned r;
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(r) : "f"(hi), "f"(lo), "r"(rb));
+        return r;
+    }
 };
 template <> struct Store<__nv_bfloat16> {
     using T = float;
@@ -169,6 +179,12 @@ template <> struct Store<__nv_bfloat16> {
         const unsigned a = __float_as_uint(lo) + (rlo >> 16), b = __float_as_uint(hi) + (rhi >> 16);
         return __byte_perm(a, b, 0x7632);  // the upper halves: (a >> 16) | (b & 0xffff0000)
     }
+    // as Store<__half>::bits2_rs: random bits 15:0 dither lo, 31:16 hi
+    static __device__ __forceinline__ unsigned bits2_rs(float lo, float hi, unsigned rb) {
+        unsigned r;
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(r) : "f"(hi), "f"(lo), "r"(rb));
+        return r;
+    }
 };
 
 // Counter-based random bits for stochastic rounding: a hash of the site and
@@ -185,6 +201,13 @@ __device__ __forceinline__ unsigned rng_seed(unsigned site, unsigned step_seed) 
 __device__ __forceinline__ unsigned rng_next(unsigned& x) {
     x = x * 1664525u + 1013904223u;
     return x;
+}
+// One draw for the two 16-bit halves of a stochastically rounded word: the
+// high half of the state is its well-mixed part, so it goes to both halves
+// (folded into the low one, whose own low bits have short periods).
+__device__ __forceinline__ unsigned rng_next2(unsigned& x) {
+    const unsigned r = rng_next(x);
+    return r ^ (r >> 16);
 }
 
 // ------------------------------------------------------------ pull stream
@@ -529,19 +552,34 @@ template <> struct Wts<F2> : Wts<float> {};
 // With VOUT the fluid velocity v = (j + F/2) / rho of Eq. (macrovariables2)
 // is also returned in v3, in physical units (the same expression, rounding
 // for rounding, as macro19).
-template <typename T, bool COMP, bool SCALED = false, bool VOUT = false>
-__device__ __forceinline__ void collide19(const T f[NQ], T Fx, T Fy, T Fz, const Coef<T>& k, T out[NQ],
+// `out` is an array of NQ, or (packed path) a callable out(i, value) that
+// consumes each population as soon as it is known, so that the stores of
+// the first ones are issued before the last are computed.
+template <typename O, typename T>
+__device__ __forceinline__ void put(O& out, int i, T v) {
+    if constexpr (std::is_pointer<O>::value)
+        out[i] = v;
+    else
+        out(i, v);
+}
+template <typename T, bool COMP, bool SCALED = false, bool VOUT = false, typename O>
+__device__ __forceinline__ void collide19(const T f[NQ], T Fx, T Fy, T Fz, const Coef<T>& k, O out,
                                           T is = T(1), T* v3 = nullptr) {
     using W = Wts<T>;
+    constexpr bool PACKED = std::is_same<T, F2>::value;
     const Moments<T> m = moments19<T, COMP>(f);
     const T third = T(1) / T(3);
     const T rho = T(1) + (SCALED ? m.drho * is : m.drho);
-    const T irho = T(1) / rho;
+    T irho;
+    if constexpr (PACKED)  // the 16-bit formats: an approximate reciprocal, 2 ulp of float
+        irho = F2(make_float2(__fdividef(1.0f, rho.v.x), __fdividef(1.0f, rho.v.y)));
+    else
+        irho = T(1) / rho;
     if (VOUT) {
         const T iv = SCALED ? is * irho : irho;
-        v3[0] = (m.jx + (m.jx_lo + T(0.5) * Fx)) * iv;
-        v3[1] = (m.jy + (m.jy_lo + T(0.5) * Fy)) * iv;
-        v3[2] = (m.jz + (m.jz_lo + T(0.5) * Fz)) * iv;
+        v3[0] = (m.jx + (COMP ? m.jx_lo + T(0.5) * Fx : T(0.5) * Fx)) * iv;
+        v3[1] = (m.jy + (COMP ? m.jy_lo + T(0.5) * Fy : T(0.5) * Fy)) * iv;
+        v3[2] = (m.jz + (COMP ? m.jz_lo + T(0.5) * Fz : T(0.5) * Fz)) * iv;
     }
     const T vx = (m.jx + T(0.5) * Fx) * irho;
     const T vy = (m.jy + T(0.5) * Fy) * irho;
@@ -565,42 +603,71 @@ __device__ __forceinline__ void collide19(const T f[NQ], T Fx, T Fy, T Fz, const
     const T byz = m.pyz - k.om_s * (xyz - k.tau_s * yyz);
 
     const T base = m.drho - T(1.5) * (bxx + byy + bzz);
-    out[0] = W::w0 * base;
+    put(out, 0, W::w0 * base);
     // axis populations: w1 (base + 4.5 B_aa) + a1 (+-F_a) + a1 (+-j_a)
     const T hx = W::w1 * (base + T(4.5) * bxx), hy = W::w1 * (base + T(4.5) * byy),
             hz = W::w1 * (base + T(4.5) * bzz);
     // force density plus the low part of j: both are far smaller than j
-    const T Gx = Fx + m.jx_lo, Gy = Fy + m.jy_lo, Gz = Fz + m.jz_lo;
-    const T fx = W::a1 * Gx, fy = W::a1 * Gy, fz = W::a1 * Gz;
-    out[1] = fma(W::a1, m.jx, hx + fx);
-    out[2] = fma(-W::a1, m.jx, hx - fx);
-    out[3] = fma(W::a1, m.jy, hy + fy);
-    out[4] = fma(-W::a1, m.jy, hy - fy);
-    out[5] = fma(W::a1, m.jz, hz + fz);
-    out[6] = fma(-W::a1, m.jz, hz - fz);
-    // face diagonals (s1, s2) in plane (a, b):
-    //   w2 (base + 4.5 (B_aa + B_bb) + 9 s1 s2 B_ab) + b1 (s1 F_a + s2 F_b) + b1 (s1 j_a + s2 j_b)
+    const T Gx = COMP ? Fx + m.jx_lo : Fx, Gy = COMP ? Fy + m.jy_lo : Fy, Gz = COMP ? Fz + m.jz_lo : Fz;
+    if constexpr (PACKED) {
+        // The 16-bit formats round their storage at 2^-11 (half) or 2^-8
+        // (bfloat16) relative, far above the rounding of A = j + F in
+        // float, so the force is folded into j first and each population
+        // pair (c, -c) shares its odd part: out = even +- w A.c / c_s^2.
+        const T Ax = m.jx + Gx, Ay = m.jy + Gy, Az = m.jz + Gz;
+        const T ox = W::a1 * Ax, oy = W::a1 * Ay, oz = W::a1 * Az;
+        put(out, 1, hx + ox);
+        put(out, 2, hx - ox);
+        put(out, 3, hy + oy);
+        put(out, 4, hy - oy);
+        put(out, 5, hz + oz);
+        put(out, 6, hz - oz);
+        // face diagonals in plane (a, b), populations n..n+3 with
+        // c = (+,+), (-,-), (+,-), (-,+)
+        const auto plane = [&](int n, T baa_bb, T bab, T Aa, T Ab) {
+            const T p = base + T(4.5) * baa_bb, q = T(9) * bab;
+            const T gp = W::w2 * (p + q), gm = W::w2 * (p - q);
+            const T op = W::b1 * (Aa + Ab), om = W::b1 * (Aa - Ab);
+            put(out, n, gp + op);
+            put(out, n + 1, gp - op);
+            put(out, n + 2, gm + om);
+            put(out, n + 3, gm - om);
+        };
+        plane(7, bxx + byy, bxy, Ax, Ay);
+        plane(11, bxx + bzz, bxz, Ax, Az);
+        plane(15, byy + bzz, byz, Ay, Az);
+        return;
+    }
     const T pxy_ = base + T(4.5) * (bxx + byy), pxz_ = base + T(4.5) * (bxx + bzz), pyz_ = base + T(4.5) * (byy + bzz);
     const T qxy = T(9) * bxy, qxz = T(9) * bxz, qyz = T(9) * byz;
     const T gpxy = W::w2 * (pxy_ + qxy), gmxy = W::w2 * (pxy_ - qxy);
     const T gpxz = W::w2 * (pxz_ + qxz), gmxz = W::w2 * (pxz_ - qxz);
     const T gpyz = W::w2 * (pyz_ + qyz), gmyz = W::w2 * (pyz_ - qyz);
+    const T fx = W::a1 * Gx, fy = W::a1 * Gy, fz = W::a1 * Gz;
+    put(out, 1, fma(W::a1, m.jx, hx + fx));
+    put(out, 2, fma(-W::a1, m.jx, hx - fx));
+    put(out, 3, fma(W::a1, m.jy, hy + fy));
+    put(out, 4, fma(-W::a1, m.jy, hy - fy));
+    put(out, 5, fma(W::a1, m.jz, hz + fz));
+    put(out, 6, fma(-W::a1, m.jz, hz - fz));
+    // face diagonals (s1, s2) in plane (a, b):
+    //   w2 (base + 4.5 (B_aa + B_bb) + 9 s1 s2 B_ab) + b1 (s1 F_a + s2 F_b) + b1 (s1 j_a + s2 j_b)
     const T Fpxy = W::b1 * (Gx + Gy), Fmxy = W::b1 * (Gx - Gy);
     const T Fpxz = W::b1 * (Gx + Gz), Fmxz = W::b1 * (Gx - Gz);
     const T Fpyz = W::b1 * (Gy + Gz), Fmyz = W::b1 * (Gy - Gz);
     const T b = W::b1;
-    out[7] = fma(b, m.jx, fma(b, m.jy, gpxy + Fpxy));
-    out[8] = fma(-b, m.jx, fma(-b, m.jy, gpxy - Fpxy));
-    out[9] = fma(b, m.jx, fma(-b, m.jy, gmxy + Fmxy));
-    out[10] = fma(-b, m.jx, fma(b, m.jy, gmxy - Fmxy));
-    out[11] = fma(b, m.jx, fma(b, m.jz, gpxz + Fpxz));
-    out[12] = fma(-b, m.jx, fma(-b, m.jz, gpxz - Fpxz));
-    out[13] = fma(b, m.jx, fma(-b, m.jz, gmxz + Fmxz));
-    out[14] = fma(-b, m.jx, fma(b, m.jz, gmxz - Fmxz));
-    out[15] = fma(b, m.jy, fma(b, m.jz, gpyz + Fpyz));
-    out[16] = fma(-b, m.jy, fma(-b, m.jz, gpyz - Fpyz));
-    out[17] = fma(b, m.jy, fma(-b, m.jz, gmyz + Fmyz));
-    out[18] = fma(-b, m.jy, fma(b, m.jz, gmyz - Fmyz));
+    put(out, 7, fma(b, m.jx, fma(b, m.jy, gpxy + Fpxy)));
+    put(out, 8, fma(-b, m.jx, fma(-b, m.jy, gpxy - Fpxy)));
+    put(out, 9, fma(b, m.jx, fma(-b, m.jy, gmxy + Fmxy)));
+    put(out, 10, fma(-b, m.jx, fma(b, m.jy, gmxy - Fmxy)));
+    put(out, 11, fma(b, m.jx, fma(b, m.jz, gpxz + Fpxz)));
+    put(out, 12, fma(-b, m.jx, fma(-b, m.jz, gpxz - Fpxz)));
+    put(out, 13, fma(b, m.jx, fma(-b, m.jz, gmxz + Fmxz)));
+    put(out, 14, fma(-b, m.jx, fma(b, m.jz, gmxz - Fmxz)));
+    put(out, 15, fma(b, m.jy, fma(b, m.jz, gpyz + Fpyz)));
+    put(out, 16, fma(-b, m.jy, fma(-b, m.jz, gpyz - Fpyz)));
+    put(out, 17, fma(b, m.jy, fma(-b, m.jz, gmyz + Fmyz)));
+    put(out, 18, fma(-b, m.jy, fma(b, m.jz, gmyz - Fmyz)));
 }
 
 // drho = rho - 1 and v = (j + F/2) / rho, Eq. (macrovariables2).
