@@ -22,6 +22,7 @@ namespace {
 using namespace lbk;
 
 constexpr int BW = 4;  // warps (tiles) per work item of the collide kernel
+constexpr int SORT_EVERY = 64;  // steps between renewals of the batch's cell order
 
 // One replica as the batched kernels see it.
 struct Entry {
@@ -42,6 +43,8 @@ struct Entry {
     float ufs_f[3];            // uniform force in the stored units (scaled for half), float
     double inv_6pi_eta, inv_aL;
     float scale, inv_scale;
+    int bin0;                  // first cell-order bin of the replica
+    int nb[3];                 // its 8^3 bricks along x, y, z
 };
 
 struct Work {
@@ -116,6 +119,8 @@ kb_collide(const Entry* __restrict__ ent, const long long* __restrict__ gbegin, 
         const int x = tx * TILE_X + lane;
         if (y >= g.ny) continue;  // uniform per warp
         const unsigned tile = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.ntx + (unsigned)tx;
+        // the flags and the field are read through the read-only path and
+        // reset below by the one warp (thread) that read them, as in k_collide
         const unsigned fl = group_flag(__ldg((const unsigned*)E.flags + tile), (unsigned)lane);
         const unsigned V = (unsigned)g.V;
         const int b = parity ^ E.cur0;
@@ -128,7 +133,7 @@ kb_collide(const Entry* __restrict__ ent, const long long* __restrict__ gbegin, 
             }
             const Nbr n = neighbours(g, x, y, z);
             const unsigned site = n.c + n.x;
-            const T* floc = (const T*)E.floc;
+            T* floc = (T*)E.floc;
             if (is_solid(g, z)) {
 #pragma unroll
                 for (int i = 0; i < NQ; ++i) Store<S>::st(dst.p[i], site, T(0), 0u);
@@ -138,9 +143,9 @@ kb_collide(const Entry* __restrict__ ent, const long long* __restrict__ gbegin, 
                 T Fx = EP<T>::uf(E, 0), Fy = EP<T>::uf(E, 1), Fz = EP<T>::uf(E, 2);
                 if (fl) {
                     const T s = SC ? (T)E.scale : T(1);
-                    Fx += floc[site] * s;
-                    Fy += floc[V + site] * s;
-                    Fz += floc[2 * V + site] * s;
+                    Fx += __ldg(floc + site) * s;
+                    Fy += __ldg(floc + V + site) * s;
+                    Fz += __ldg(floc + 2 * V + site) * s;
                 }
                 Coef<T> k;
                 k.tau_s = EP<T>::coef(E, 0);
@@ -157,29 +162,30 @@ kb_collide(const Entry* __restrict__ ent, const long long* __restrict__ gbegin, 
                     vel[V + site] = v3[1];
                     vel[2 * V + site] = v3[2];
                 }
+                if (fl) {  // the field is spread anew every step: zero what was consumed
+                    floc[site] = T(0);
+                    floc[V + site] = T(0);
+                    floc[2 * V + site] = T(0);
+                }
             }
         }
+        // the first lane of each flagged group resets its flag (this warp
+        // alone read the tile's flag word, in one warp-wide load)
+        if (fl && (lane % GROUP_X) == 0) E.flags[tile * (TILE_X / GROUP_X) + (unsigned)lane / GROUP_X] = 0;
     }
 }
 
-// Clear every member's consumed force tiles: grid (blocks per member,
-// members), each member's flags scanned by its blocks' warps.
-template <typename T>
-__global__ void __launch_bounds__(256) kb_clear(const Entry* __restrict__ ent) {
-    const Entry& E = ent[blockIdx.y];
-    clear_flagged_tiles<T>(E.g, (T*)E.floc, E.flags, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
-                           (gridDim.x * blockDim.x) >> 5);
-}
 
 // Spreading, one warp per point (the scheme of k_spread), from the stencil
-// rows st[gp] written by kb_stencil / kb_update.
+// rows st[gp] written by kb_stencil / kb_update; warps take the points in
+// the batch's cell order (kb_brick_*).
 template <typename T>
 __global__ void __launch_bounds__(256)
 kb_spread(const Entry* __restrict__ ent, const long long* __restrict__ pbegin, const int* __restrict__ pent,
-          int nrep, long long total_pts,
-          const T* __restrict__ st) {
-    const long long gp = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (gp >= total_pts) return;  // uniform per warp
+          const int* __restrict__ order, long long total_pts, const T* __restrict__ st) {
+    const long long slot = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (slot >= total_pts) return;  // uniform per warp
+    const long long gp = order[slot];
     const int lane = threadIdx.x & 31;
     const int e = pent[gp];
     const Entry& E = ent[e];
@@ -228,15 +234,46 @@ __global__ void kb_stencil(const Entry* __restrict__ ent, const long long* __res
 
 __global__ void kb_tick(unsigned* step_counter) { *step_counter += 1u; }
 
+// Cell order of the batch's points, so that neighbouring warps of the
+// spread and the interpolation work on nearby stencils of one replica: a
+// counting sort on key = the replica's first bin + the 8^3 brick of the
+// point within the replica.  Each replica's points stay in its own range
+// of slots.  Only the order of the work depends on it, never a result
+// (beyond the order of the spread's atomic additions).
+constexpr int BATCH_BRICK = 8;
+__global__ void kb_brick_count(const Entry* __restrict__ ent, const long long* __restrict__ pbegin,
+                               const int* __restrict__ pent, long long total_pts, int* __restrict__ count,
+                               int* __restrict__ key) {
+    const long long gp = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gp >= total_pts) return;
+    const int e = pent[gp];
+    const Entry& E = ent[e];
+    const int s = (int)(gp - pbegin[e]);
+    int b[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) b[a] = min(max((int)E.pos[3 * s + a] / BATCH_BRICK, 0), E.nb[a] - 1);
+    const int k = E.bin0 + (b[2] * E.nb[1] + b[1]) * E.nb[0] + b[0];
+    key[gp] = k;
+    atomicAdd(&count[k], 1);
+}
+
+__global__ void kb_brick_fill(long long total_pts, const int* __restrict__ key, const int* __restrict__ start,
+                              int* __restrict__ cursor, int* __restrict__ order) {
+    const long long gp = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gp >= total_pts) return;
+    const int k = key[gp];
+    order[start[k] + atomicAdd(&cursor[k], 1)] = (int)gp;
+}
+
 // Interpolated velocity (from the velocity field the collide wrote) at
 // every colloid, one warp each (the scheme of k_interp): v[3 gp + a], FP64.
 template <typename T>
 __global__ void __launch_bounds__(256)
 kb_interp(const Entry* __restrict__ ent, const long long* __restrict__ pbegin, const int* __restrict__ pent,
-          int nrep, long long total_pts,
-          const T* __restrict__ st, double* __restrict__ vout) {
-    const long long gp = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (gp >= total_pts) return;  // uniform per warp
+          const int* __restrict__ order, long long total_pts, const T* __restrict__ st, double* __restrict__ vout) {
+    const long long slot = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (slot >= total_pts) return;  // uniform per warp
+    const long long gp = order[slot];
     const int e = pent[gp];
     const Entry& E = ent[e];
     const int s = (int)(gp - pbegin[e]);
@@ -320,6 +357,10 @@ struct lb_batch {
     int blocks;                // persistent grid of the collide kernel
     unsigned* d_step;          // step counter seeding the stochastic rounding
     int* d_pent;               // member of every point of the batch
+    int* d_order;              // the points in cell order (slot -> point)
+    int* d_sort;               // counting-sort workspace: count, cursor, start, scan sums, keys
+    long long total_bins;      // cell-order bins of all members
+    int steps_since_sort;
     void* d_st;                // stencil rows of every point (ST_W elements of the arithmetic type)
     double* d_v;               // interpolated velocity of every point (3 doubles)
     int parity;                // batch steps taken since creation, mod 2
@@ -348,8 +389,9 @@ lb_status bfail(lb_batch* b, lb_status s, const std::string& m) {
 
 // Launch the phases of one step (parity p) on the batch stream: spread
 // (from the stencil rows), collide (writing v at the colloids' stencil
-// nodes), interpolation, colloid update (which writes the next stencil
-// rows), tile clearing, and the rounding-seed counter of the 16-bit formats.
+// nodes and zeroing the consumed field), interpolation, colloid update
+// (which writes the next stencil rows), and the rounding-seed counter of
+// the 16-bit formats.
 template <typename S>
 cudaError_t launch_step(lb_batch* b, int p, int blocks) {
     using T = typename Store<S>::T;
@@ -357,15 +399,37 @@ cudaError_t launch_step(lb_batch* b, int p, int blocks) {
     const unsigned tblocks = (unsigned)((b->total_pts + 127) / 128);  // thread per point
     T* st = (T*)b->d_st;
     if (b->total_pts > 0)
-        kb_spread<T><<<wblocks, 256, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->d_pent, b->n, b->total_pts, st);
+        kb_spread<T><<<wblocks, 256, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->d_pent, b->d_order, b->total_pts, st);
     kb_collide<S><<<blocks, dim3(32, BW), 0, b->stream>>>(b->d_ent, b->d_gbegin, b->d_work, b->n, b->total_groups, p,
                                                           b->d_step);
     if (b->n_mobile > 0) {
-        kb_interp<T><<<wblocks, 256, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->d_pent, b->n, b->total_pts, st, b->d_v);
+        kb_interp<T><<<wblocks, 256, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->d_pent, b->d_order, b->total_pts, st,
+                                                     b->d_v);
         kb_update<T><<<tblocks, 128, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->d_pent, b->n, b->total_pts, b->d_v, st);
     }
-    if (b->total_pts > 0) kb_clear<T><<<dim3(8, b->n), 256, 0, b->stream>>>(b->d_ent);
     if (sizeof(S) == 2) kb_tick<<<1, 1, 0, b->stream>>>(b->d_step);
+    return cudaGetLastError();
+}
+
+// The batch's cell order (5 kernel launches): counts per bin, their
+// exclusive scan, and the fill of the order.
+cudaError_t launch_sort(lb_batch* b) {
+    if (b->total_pts == 0) return cudaSuccess;
+    const long long nb = b->total_bins;
+    int* count = b->d_sort;
+    int* cursor = count + nb;
+    int* start = cursor + nb;
+    int* bsum = start + nb + 1;
+    int* key = bsum + scan_ws_ints(nb);
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * 2 * (size_t)nb, b->stream);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)((b->total_pts + 255) / 256);
+    kb_brick_count<<<blocks, 256, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->d_pent, b->total_pts, count, key);
+    e = scan_exclusive(count, nb, start, bsum, b->stream);
+    if (e != cudaSuccess) return e;
+    kb_brick_fill<<<blocks, 256, 0, b->stream>>>(b->total_pts, key, start, cursor, b->d_order);
+    b->launches += 5;
+    b->steps_since_sort = 0;
     return cudaGetLastError();
 }
 
@@ -414,7 +478,7 @@ cudaError_t launch_collide_any(lb_batch* b, int blocks) {
 }
 
 int launches_per_step(const lb_batch* b) {
-    return 1 + (b->total_pts > 0 ? 2 : 0) + (b->n_mobile > 0 ? 2 : 0) + (b->prec >= LB_F16S ? 1 : 0);
+    return 1 + (b->total_pts > 0 ? 1 : 0) + (b->n_mobile > 0 ? 2 : 0) + (b->prec >= LB_F16S ? 1 : 0);
 }
 
 }  // namespace
@@ -436,7 +500,7 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
     std::vector<Entry> ent(n);
     std::vector<long long> gbegin(n), pbegin(n);
     std::vector<Work> work(n);
-    long long groups = 0, pts = 0, mob = 0;
+    long long groups = 0, pts = 0, mob = 0, bins = 0;
     for (int i = 0; i < n; ++i) {
         lb_ctx* c = ctxs[i];
         Entry& E = ent[i];
@@ -476,6 +540,12 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
         E.inv_aL = isinf(c->a_L) ? 0.0 : 1.0 / c->a_L;
         E.scale = c->scale;
         E.inv_scale = c->inv_scale;
+        for (int a = 0; a < 3; ++a) {
+            const int len = a == 0 ? c->geom.nx : (a == 1 ? c->geom.ny : c->geom.nz);
+            E.nb[a] = (len + BATCH_BRICK - 1) / BATCH_BRICK;
+        }
+        E.bin0 = (int)bins;
+        bins += (long long)E.nb[0] * E.nb[1] * E.nb[2];
         work[i].groups_x = c->geom.ntx;
         work[i].groups_y = (c->geom.ny + BW - 1) / BW;
         work[i].group_begin = groups;
@@ -489,6 +559,8 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
     b->total_groups = groups;
     b->total_pts = pts;
     b->n_mobile = mob;
+    b->total_bins = bins;
+    b->steps_since_sort = SORT_EVERY;  // the first step sorts
     b->blocks = (int)std::min<long long>(std::max<long long>(groups, 1), 0x7fffffffLL);  // untuned: one per item
     cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
@@ -501,6 +573,9 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
     if (e == cudaSuccess && pts > 0)
         e = cudaMalloc(&b->d_st, lbk::arith_bytes(b->prec) * ST_W * (size_t)pts);
     if (e == cudaSuccess && pts > 0) e = cudaMalloc(&b->d_v, sizeof(double) * 3 * (size_t)pts);
+    if (e == cudaSuccess && pts > 0) e = cudaMalloc(&b->d_order, sizeof(int) * (size_t)pts);
+    if (e == cudaSuccess && pts > 0)
+        e = cudaMalloc(&b->d_sort, sizeof(int) * ((size_t)(3 * bins + 1) + scan_ws_ints(bins) + (size_t)pts));
     if (e == cudaSuccess && pts > 0) {
         std::vector<int> pent((size_t)pts);
         for (int i = 0; i < n; ++i)
@@ -533,6 +608,8 @@ void lb_batch_destroy(lb_batch* b) {
     cudaFree(b->d_st);
     cudaFree(b->d_v);
     cudaFree(b->d_pent);
+    cudaFree(b->d_order);
+    cudaFree(b->d_sort);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->stream) cudaStreamDestroy(b->stream);
@@ -631,15 +708,19 @@ lb_status lb_batch_step(lb_batch* b, int nsteps) {
     }
     // The graph holds two steps starting at parity 0: a batch at odd parity
     // takes one plain step first.
+    // The cell order is renewed every SORT_EVERY steps (outside the graph).
     int done = 0;
     while (done < nsteps) {
+        if (b->steps_since_sort >= SORT_EVERY) LB_BCUDA(launch_sort(b), "cell order kernels");
         if (b->graph_ready && b->parity == 0 && nsteps - done >= 2) {
             LB_BCUDA(cudaGraphLaunch(b->graph2, b->stream), "graph launch");
             done += 2;
+            b->steps_since_sort += 2;
         } else {
             LB_BCUDA(launch_step_any(b, b->parity, b->blocks), "batched step");
             b->parity ^= 1;
             done += 1;
+            b->steps_since_sort += 1;
         }
     }
     b->launches += (long long)nsteps * launches_per_step(b);

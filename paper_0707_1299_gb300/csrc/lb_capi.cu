@@ -490,8 +490,9 @@ lb_status lb_step(lb_ctx* c, int nsteps) {
     // stream with F^n, writing v^n = (j + F^n/2) / rho at the stencil nodes;
     // interpolate v^n at R^n and move the colloids (plus the learned
     // correction when a network is attached), which also prepares the
-    // stencil rows of R^{n+1}; clear the consumed force tiles.  Fixed points
-    // keep their field from step to step.
+    // stencil rows of R^{n+1}.  With mobile colloids the collide zeroes the
+    // force it consumed; fixed points alone keep their field from step to
+    // step.
     for (int s = 0; s < nsteps; ++s) {
         lb_status st = ensure_field(c);
         if (st != LB_OK) return st;
@@ -506,8 +507,7 @@ lb_status lb_step(lb_ctx* c, int nsteps) {
         if (c->n_mobile > 0) {
             LB_CUDA(lbk::launch_interp(c), "interpolation kernel");
             LB_CUDA(lbk::launch_update(c, corrected ? c->corr_y : nullptr), "colloid update kernel");
-            LB_CUDA(lbk::launch_clear_tiles(c), "tile clearing kernel");
-            c->field_ready = false;
+            c->field_ready = false;  // the collide zeroed the consumed field and flags
             if (++c->steps_since_sort >= SORT_INTERVAL) c->order_stale = true;
         }
     }

@@ -18,10 +18,12 @@ namespace lbk {
 
 // Collision and store of one site from its pulled populations f: force =
 // uniform + (field ? localised : 0), in the stored units of the format;
-// with VOUT and a field, v = (j + F/2) / rho is written to vel as well.
+// with VOUT and a field, v = (j + F/2) / rho is written to vel as well and
+// the consumed force is zeroed (VOUT is the mode of mobile colloids, whose
+// field is spread anew every step).
 template <typename S, bool VOUT>
 __device__ __forceinline__ void finish_site(const typename Store<S>::T (&f)[NQ], const Pops<S>& dst,
-                                            const typename Store<S>::T* __restrict__ floc,
+                                            typename Store<S>::T* floc,
                                             typename Store<S>::T* __restrict__ vel, unsigned V, unsigned site,
                                             bool field, const Coef<typename Store<S>::T>& k,
                                             const UForce<typename Store<S>::T>& fu, float scale, float inv_scale,
@@ -29,11 +31,11 @@ __device__ __forceinline__ void finish_site(const typename Store<S>::T (&f)[NQ],
     using T = typename Store<S>::T;
     constexpr bool SC = Store<S>::kScaled;
     T Fx = fu.F[0], Fy = fu.F[1], Fz = fu.F[2];
-    if (field) {
+    if (field) {  // read-only path: see reset_group_flag
         const T s = SC ? (T)scale : T(1);
-        Fx += floc[site] * s;
-        Fy += floc[V + site] * s;
-        Fz += floc[2 * V + site] * s;
+        Fx += __ldg(floc + site) * s;
+        Fy += __ldg(floc + V + site) * s;
+        Fz += __ldg(floc + 2 * V + site) * s;
     }
     T o[NQ], v3[3];
     collide19<T, Store<S>::kCompensate, SC, VOUT>(f, Fx, Fy, Fz, k, o, (T)inv_scale, v3);
@@ -44,7 +46,22 @@ __device__ __forceinline__ void finish_site(const typename Store<S>::T (&f)[NQ],
         vel[site] = v3[0];
         vel[V + site] = v3[1];
         vel[2 * V + site] = v3[2];
+        floc[site] = T(0);
+        floc[V + site] = T(0);
+        floc[2 * V + site] = T(0);
     }
+}
+
+// With VOUT, the first lane of each flagged 8-site group resets the group's
+// flag once the group's sites are done.  The flag word and the field are
+// read through the read-only (non-coherent) path although this kernel
+// writes them afterwards: each flag word is read by one warp-wide load of
+// the one warp that owns its tile, and each field value by the one thread
+// of its site, always before that warp or thread overwrites it; nothing
+// else reads them in the launch.  (Coherent loads of the two measured 9 %
+// slower on the FP32 colloid step at 512^3 on GB300.)
+__device__ __forceinline__ void reset_group_flag(flag_t* flags, unsigned tile, unsigned x_in_tile, unsigned fl) {
+    if (fl && x_in_tile % GROUP_X == 0) flags[tile * (TILE_X / GROUP_X) + x_in_tile / GROUP_X] = 0;
 }
 
 // ------------------------------------------------------------ k_collide
@@ -54,13 +71,14 @@ __device__ __forceinline__ void finish_site(const typename Store<S>::T (&f)[NQ],
 // the 4- and 2-byte formats are fastest at 12 (42 registers; 8-10 were
 // 2-10 % slower, 14 spills); FP64 at 8.
 // FMODE: FM_NONE a lattice without point forces (no flag or field access);
-// FM_FIELD the force field is read in flagged tiles; FM_VEL also writes the
-// fluid velocity v = (j + F/2) / rho there, for the colloid update.
+// FM_FIELD the force field is read in flagged groups; FM_VEL also writes the
+// fluid velocity v = (j + F/2) / rho there, for the colloid update, and
+// zeroes the consumed field and flags (so no clearing pass follows).
 enum { FM_NONE = 0, FM_FIELD = 1, FM_VEL = 2 };
 template <typename S, bool WALLS, int NY, int FMODE>
 __global__ void __launch_bounds__(CS_THREADS, (NY == 1 ? (sizeof(S) == 8 ? 8 : 12) : 4))
-k_collide(const Pops<S> src, const Pops<S> dst, const typename Store<S>::T* __restrict__ floc,
-          const flag_t* __restrict__ flags, typename Store<S>::T* __restrict__ vel, Geom g,
+k_collide(const Pops<S> src, const Pops<S> dst, typename Store<S>::T* __restrict__ floc,
+          flag_t* __restrict__ flags, typename Store<S>::T* __restrict__ vel, Geom g,
           Coef<typename Store<S>::T> k, UForce<typename Store<S>::T> fu, float scale, float inv_scale,
           unsigned seed) {
     using T = typename Store<S>::T;
@@ -104,6 +122,12 @@ k_collide(const Pops<S> src, const Pops<S> dst, const typename Store<S>::T* __re
             }
         }
     }
+    if (VOUT)
+#pragma unroll
+        for (int r = 0; r < NY; ++r)
+            if (y0 + r < g.ny)
+                reset_group_flag(flags, ((unsigned)z * (unsigned)g.ny + (unsigned)(y0 + r)) * (unsigned)g.ntx + blockIdx.x,
+                                 (unsigned)lane, fl[r]);
 }
 
 // The collide for the 16-bit formats with nx even: two x-adjacent sites
@@ -123,7 +147,7 @@ k_collide(const Pops<S> src, const Pops<S> dst, const typename Store<S>::T* __re
 // 7 or 10 blocks, were 1-6 % slower.
 template <typename S, bool WALLS, int FMODE>
 __global__ void __launch_bounds__(CS_THREADS, Store<S>::kScaled ? 8 : 9)
-k_collide_pair(const Pops<S> src, const Pops<S> dst, const float* __restrict__ floc, const flag_t* __restrict__ flags,
+k_collide_pair(const Pops<S> src, const Pops<S> dst, float* __restrict__ floc, flag_t* __restrict__ flags,
                float* __restrict__ vel, Geom g, Coef<float> k, UForce<float> fu, float scale, float inv_scale,
                unsigned seed) {
     using St = Store<S>;
@@ -141,10 +165,8 @@ k_collide_pair(const Pops<S> src, const Pops<S> dst, const float* __restrict__ f
             for (int i = 0; i < NQ; ++i) *(unsigned*)(dst.p[i] + row + x0) = 0u;
         return;
     }
-    const unsigned fl = (FIELD && active) ? group_flag(__ldg((const unsigned*)flags + ((unsigned)z * (unsigned)g.ny + (unsigned)y) *
-                                                                                  (unsigned)g.ntx + x0 / TILE_X),
-                                                       x0 % TILE_X)
-                                          : 0u;
+    const unsigned tile = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.ntx + x0 / TILE_X;
+    const unsigned fl = (FIELD && active) ? group_flag(__ldg((const unsigned*)flags + tile), x0 % TILE_X) : 0u;
     const Nbr n = neighbours(g, 0, y, z);
     unsigned w[NQ];
     pull19_pair<S, WALLS>(src, n, x0, nx, lane, active, w);
@@ -155,9 +177,9 @@ k_collide_pair(const Pops<S> src, const Pops<S> dst, const float* __restrict__ f
     F2 Fx(fu.F[0]), Fy(fu.F[1]), Fz(fu.F[2]);
     if (FIELD && fl) {  // after the population loads, so both are in flight together
         const F2 sc(SC ? scale : 1.0f);
-        Fx = fma(F2(*(const float2*)(floc + row + x0)), sc, Fx);
-        Fy = fma(F2(*(const float2*)(floc + V + row + x0)), sc, Fy);
-        Fz = fma(F2(*(const float2*)(floc + 2 * V + row + x0)), sc, Fz);
+        Fx = fma(F2(__ldg((const float2*)(floc + row + x0))), sc, Fx);
+        Fy = fma(F2(__ldg((const float2*)(floc + V + row + x0))), sc, Fy);
+        Fz = fma(F2(__ldg((const float2*)(floc + 2 * V + row + x0))), sc, Fz);
     }
     Coef<F2> k2;
     k2.tau_s = F2(k.tau_s);
@@ -180,9 +202,14 @@ k_collide_pair(const Pops<S> src, const Pops<S> dst, const float* __restrict__ f
         };
         collide19<F2, false, SC, VOUT>(f, Fx, Fy, Fz, k2, emit, F2(inv_scale), v3);
     }
-    if (VOUT && fl && active)
+    if (VOUT && fl && active) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) *(float2*)(vel + a * V + row + x0) = v3[a].v;
+        for (int a = 0; a < 3; ++a) {
+            *(float2*)(vel + a * V + row + x0) = v3[a].v;
+            *(float2*)(floc + a * V + row + x0) = make_float2(0.0f, 0.0f);  // the consumed force
+        }
+    }
+    if (VOUT) reset_group_flag(flags, tile, x0 % TILE_X, fl);
 }
 
 // Fix-up for a few fixed points: the collide ran with the uniform force at
@@ -192,7 +219,7 @@ k_collide_pair(const Pops<S> src, const Pops<S> dst, const float* __restrict__ f
 // no force (the spread skips them), so they are left as they are.
 template <typename S, bool WALLS>
 __global__ void __launch_bounds__(CS_THREADS)
-k_fixup(const Pops<S> src, const Pops<S> dst, const typename Store<S>::T* __restrict__ floc,
+k_fixup(const Pops<S> src, const Pops<S> dst, typename Store<S>::T* __restrict__ floc,
         const unsigned* __restrict__ list, const unsigned* __restrict__ count, Geom g, Coef<typename Store<S>::T> k,
         UForce<typename Store<S>::T> fu, float scale, float inv_scale, unsigned seed) {
     using T = typename Store<S>::T;
@@ -246,7 +273,7 @@ static cudaError_t collide_t(lb_ctx* c) {
     constexpr int NY = 1;
     const dim3 grid((unsigned)c->geom.ntx, (unsigned)((c->geom.ny + CS_WARPS * NY - 1) / (CS_WARPS * NY)),
                     (unsigned)c->geom.nz);
-    const T* floc = (const T*)c->floc;
+    T* floc = (T*)c->floc;
     T* vel = (T*)c->vel;
     // a few fixed points: field-free collide plus the fix-up of their tiles
     const bool fixup = c->npts > 0 && c->n_mobile == 0 && c->fix_ok;
@@ -260,7 +287,7 @@ static cudaError_t collide_t(lb_ctx* c) {
         if (PAIRABLE && pair)                                                                                      \
             k_collide_pair<PairS<S>, W, FM><<<pgrid, site_block(), 0, c->stream>>>(                                \
                 pops<PairS<S>>(c->f[c->cur], c->geom.V), pops<PairS<S>>(c->f[1 - c->cur], c->geom.V),              \
-                (const float*)floc, c->flags, (float*)vel, c->geom, coef_f(k), uforce_f(fu), c->scale, c->inv_scale, \
+                (float*)floc, c->flags, (float*)vel, c->geom, coef_f(k), uforce_f(fu), c->scale, c->inv_scale, \
                 c->seed);                                                                                          \
         else                                                                                                       \
             k_collide<S, W, NY, FM><<<grid, site_block(), 0, c->stream>>>(src, dst, floc, c->flags, vel, c->geom,  \

@@ -41,49 +41,16 @@ __device__ __forceinline__ bool is_solid(const Geom& g, int z) {
 // Force flags.  Spreading sets the byte flag of every 8-site x-group it adds
 // force to (a plain store: any number of writers store the same value); the
 // four groups of a 32-site x-row tile form one 32-bit word, read once per
-// warp, byte lane / 8 for lane.  The collide kernel reads the field (and
-// writes the velocity) only in flagged groups; after the collide a clearing
-// pass zeroes the flagged groups and their flags.
+// warp, byte lane / 8 for lane.  The collide kernel reads the field only in
+// flagged groups; where the field is spread anew every step (mobile
+// colloids, batches) it also writes the velocity there and then zeroes the
+// consumed field and the flags.
 using flag_t = unsigned char;
 constexpr int GROUP_X = 8;  // sites of an x-group
 
 // This lane's group flag in a tile's flag word (x the lane's site offset in the tile).
 __device__ __forceinline__ unsigned group_flag(unsigned word, unsigned x_in_tile) {
     return (word >> (8u * (x_in_tile / GROUP_X))) & 0xFFu;
-}
-
-// Zero the field and the flags of every flagged group: each warp takes
-// groups of 32 tiles (one flag word per lane), then clears the flagged
-// groups of each flagged tile one tile after the other, one site per lane.
-// Runs after the collide kernel has consumed the field, so no load of it is
-// in flight.
-template <typename T>
-__device__ __forceinline__ void clear_flagged_tiles(const Geom& g, T* __restrict__ floc, flag_t* __restrict__ flags,
-                                                    unsigned warp0, unsigned nwarps) {
-    const unsigned lane = threadIdx.x & 31u;
-    const unsigned V = (unsigned)g.V, ntiles = (unsigned)g.ntiles, ntx = (unsigned)g.ntx;
-    const unsigned ngroups = (ntiles + 31u) >> 5;
-    unsigned* words = (unsigned*)flags;
-    for (unsigned grp = warp0; grp < ngroups; grp += nwarps) {
-        const unsigned t = (grp << 5) + lane;
-        const unsigned w = t < ntiles ? words[t] : 0u;
-        unsigned m = __ballot_sync(0xffffffffu, w != 0u);
-        if (w) words[t] = 0u;
-        while (m) {
-            const unsigned b = (unsigned)(__ffs(m) - 1);
-            m &= m - 1u;
-            const unsigned wt = __shfl_sync(0xffffffffu, w, b);
-            const unsigned tile = (grp << 5) + b;
-            const unsigned row = tile / ntx;               // z * ny + y
-            const unsigned x = (tile - row * ntx) * TILE_X + lane;
-            if (x < (unsigned)g.nx && group_flag(wt, lane)) {
-                const unsigned site = row * (unsigned)g.nx + x;
-                floc[site] = T(0);
-                floc[V + site] = T(0);
-                floc[2 * V + site] = T(0);
-            }
-        }
-    }
 }
 
 // ----------------------------------------------------------- storage types

@@ -105,7 +105,6 @@ cudaError_t launch_set_positions(lb_ctx* c, const double* pos);
 cudaError_t launch_convert_out(lb_ctx* c, double* df);
 cudaError_t launch_convert_in(lb_ctx* c, const double* df);
 cudaError_t launch_clear_field(lb_ctx* c);
-cudaError_t launch_clear_tiles(lb_ctx* c);
 template <typename T>
 UForce<T> uniform_force(const lb_ctx* c);
 constexpr int MLP_FEATURE_LAUNCHES = 6;  // kernels of one mlp_features call

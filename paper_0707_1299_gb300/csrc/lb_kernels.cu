@@ -1,12 +1,10 @@
 // lb_kernels.cu -- sm_103a kernels of the forced D3Q19 MRT lattice
 // Boltzmann method with singular point forces, and their launchers.
 //
-//   k_collide   fused pull-stream + moment-space collision with the
-//               second-order forcing term (Sec. II, Eq. fiexp); one thread
-//               per site, one warp per 32-site x-row tile; reads the
-//               localised force only in tiles flagged by k_spread and, for
-//               lattices with colloids, writes the fluid velocity there.
-//   k_clear_tiles  zeroes the flagged tiles once the collide has read them.
+//   (the collide kernels are in lb_collide.cu: they read the localised
+//   force only in the 8-site groups flagged by k_spread and, for lattices
+//   with colloids, write the fluid velocity there and zero the consumed
+//   force and flags)
 //   k_spread    regularised point forces onto the lattice (Sec. III,
 //               Eq. deltadef): one warp per point in cell order, the 12
 //               one-dimensional weights evaluated once and shuffled,
@@ -78,13 +76,6 @@ __global__ void k_list_tiles(const flag_t* __restrict__ flags, long long ntiles,
     }
 }
 
-// Clear the consumed force tiles (k_clear_tiles runs after k_collide): the
-// collide kernel only reads the field, so it never stores to a line whose
-// load may still be in flight.
-template <typename T>
-__global__ void __launch_bounds__(256) k_clear_tiles(Geom g, T* __restrict__ floc, flag_t* __restrict__ flags) {
-    clear_flagged_tiles<T>(g, floc, flags, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5);
-}
 
 // Position wrapped into [0, n).
 __device__ __forceinline__ double wrap_pos(double r, int n) {
@@ -909,18 +900,6 @@ cudaError_t launch_clear_field(lb_ctx* c) {
     return e;
 }
 
-cudaError_t launch_clear_tiles(lb_ctx* c) {
-    // one warp per group of 32 tiles, grid-strided, at most 4 blocks of 256
-    // threads per SM: the flags (one byte per tile) are read once
-    const long long warps = (c->geom.ntiles + 31) / 32;
-    const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>(152 * 4, (warps + 7) / 8));
-    if (c->prec == LB_F64)
-        k_clear_tiles<double><<<blocks, 256, 0, c->stream>>>(c->geom, (double*)c->floc, c->flags);
-    else
-        k_clear_tiles<float><<<blocks, 256, 0, c->stream>>>(c->geom, (float*)c->floc, c->flags);
-    c->launches++;
-    return cudaGetLastError();
-}
 
 cudaError_t compute_inv_aL(const int grid[3], const double R[3], const double dir[3], double* inv_aL) {
     const int blocks = 152 * 4;
