@@ -23,6 +23,7 @@ using namespace lbk;
 
 constexpr int BW = 4;  // warps (tiles) per work item of the collide kernel
 constexpr int SORT_EVERY = 64;  // steps between renewals of the batch's cell order
+constexpr int FLAT_MIN_BLOCKS = 8;  // occupancy bound of the flat collide (blocks of 128 threads per SM)
 
 // One replica as the batched kernels see it.
 struct Entry {
@@ -45,6 +46,7 @@ struct Entry {
     float scale, inv_scale;
     int bin0;                  // first cell-order bin of the replica
     int nb[3];                 // its 8^3 bricks along x, y, z
+    float inv_nx, inv_ny;      // 1/nx, 1/ny for the flat collide's site coordinates
 };
 
 struct Work {
@@ -73,6 +75,94 @@ template <> struct EP<double> {
     static __device__ __forceinline__ double coef(const Entry& E, int i) { return E.coef[i]; }
     static __device__ __forceinline__ double uf(const Entry& E, int a) { return E.uf[a]; }
 };
+
+// pull19 of one site from a single population buffer: population i of
+// element j is base[i * V + j] (32-bit indices: 19 V < 2^32 for the members
+// the batch takes), so no per-population pointers are held.  A solid source
+// plane selects the opposite population of the site itself.
+template <typename S>
+__device__ __forceinline__ void pull19_base(const S* __restrict__ base, unsigned V, const Nbr& n,
+                                            typename Store<S>::T f[NQ]) {
+    using St = Store<S>;
+    const unsigned own = n.c + n.x;
+    const unsigned ym = n.c + n.dym, yp = n.c + n.dyp, zm = n.c + n.dzm, zp = n.c + n.dzp;
+    const bool bm = n.solid_zm, bp = n.solid_zp;
+    f[0] = St::ld(base, own);
+    f[1] = St::ld(base, V + n.c + n.xm);
+    f[2] = St::ld(base, 2 * V + n.c + n.xp);
+    f[3] = St::ld(base, 3 * V + ym + n.x);
+    f[4] = St::ld(base, 4 * V + yp + n.x);
+    f[7] = St::ld(base, 7 * V + ym + n.xm);
+    f[8] = St::ld(base, 8 * V + yp + n.xp);
+    f[9] = St::ld(base, 9 * V + yp + n.xm);
+    f[10] = St::ld(base, 10 * V + ym + n.xp);
+    f[5] = St::ld(base, bm ? 6 * V + own : 5 * V + zm + n.x);
+    f[11] = St::ld(base, bm ? 12 * V + own : 11 * V + zm + n.xm);
+    f[14] = St::ld(base, bm ? 13 * V + own : 14 * V + zm + n.xp);
+    f[15] = St::ld(base, bm ? 16 * V + own : 15 * V + zm + n.dym + n.x);
+    f[18] = St::ld(base, bm ? 17 * V + own : 18 * V + zm + n.dyp + n.x);
+    f[6] = St::ld(base, bp ? 5 * V + own : 6 * V + zp + n.x);
+    f[12] = St::ld(base, bp ? 11 * V + own : 12 * V + zp + n.xp);
+    f[13] = St::ld(base, bp ? 14 * V + own : 13 * V + zp + n.xm);
+    f[16] = St::ld(base, bp ? 15 * V + own : 16 * V + zp + n.dyp + n.x);
+    f[17] = St::ld(base, bp ? 18 * V + own : 17 * V + zp + n.dym + n.x);
+}
+
+// One site (x, y, z) of member e: pull (bounce-back at its solid planes),
+// collide with the member's uniform force plus its localised force where
+// the site's 8-site group is flagged (fl), store with the member's rounding
+// stream; in flagged groups also the velocity for the member's colloids,
+// and the consumed force is zeroed (the batch spreads it anew every step).
+// The field is read through the read-only path: only this thread reads
+// this site's force in the launch, and only after the read does it write.
+template <typename S>
+__device__ __forceinline__ void batch_site(const Entry& E, int e, int x, int y, int z, unsigned fl, int parity,
+                                           unsigned seed) {
+    using T = typename Store<S>::T;
+    constexpr bool SC = Store<S>::kScaled;
+    const Geom& g = E.g;
+    const unsigned V = (unsigned)g.V;
+    const int b = parity ^ E.cur0;
+    const S* src = (const S*)E.pop[b];
+    S* dst = (S*)E.pop[b ^ 1];
+    const Nbr n = neighbours(g, x, y, z);
+    const unsigned site = n.c + n.x;
+    T* floc = (T*)E.floc;
+    if (is_solid(g, z)) {
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) Store<S>::st(dst, (unsigned)i * V + site, T(0), 0u);
+        return;
+    }
+    T f[NQ], o[NQ], v3[3];
+    pull19_base<S>(src, V, n, f);  // populations first: in flight with the force loads below
+    T Fx = EP<T>::uf(E, 0), Fy = EP<T>::uf(E, 1), Fz = EP<T>::uf(E, 2);
+    if (fl) {
+        const T s = SC ? (T)E.scale : T(1);
+        Fx += __ldg(floc + site) * s;
+        Fy += __ldg(floc + V + site) * s;
+        Fz += __ldg(floc + 2 * V + site) * s;
+    }
+    Coef<T> k;
+    k.tau_s = EP<T>::coef(E, 0);
+    k.tau_b = EP<T>::coef(E, 1);
+    k.om_s = EP<T>::coef(E, 2);
+    k.om_b = EP<T>::coef(E, 3);
+    collide19<T, Store<S>::kCompensate, SC, true>(f, Fx, Fy, Fz, k, o, (T)E.inv_scale, v3);
+    unsigned rn = rng_seed(site ^ (unsigned)(e * 0x27d4eb2d), seed);
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) Store<S>::st(dst, (unsigned)i * V + site, o[i], rng_next(rn));
+    if (fl && E.vel) {  // v at the stencil nodes of the replica's colloids
+        T* vel = (T*)E.vel;
+        vel[site] = v3[0];
+        vel[V + site] = v3[1];
+        vel[2 * V + site] = v3[2];
+    }
+    if (fl) {
+        floc[site] = T(0);
+        floc[V + site] = T(0);
+        floc[2 * V + site] = T(0);
+    }
+}
 
 template <typename S>
 __global__ void __launch_bounds__(BW * 32, 8)
@@ -122,59 +212,55 @@ kb_collide(const Entry* __restrict__ ent, const long long* __restrict__ gbegin, 
         // the flags and the field are read through the read-only path and
         // reset below by the one warp (thread) that read them, as in k_collide
         const unsigned fl = group_flag(__ldg((const unsigned*)E.flags + tile), (unsigned)lane);
-        const unsigned V = (unsigned)g.V;
-        const int b = parity ^ E.cur0;
-        if (x < g.nx) {
-            Pops<S> src, dst;
-#pragma unroll
-            for (int i = 0; i < NQ; ++i) {
-                src.p[i] = (S*)E.pop[b] + (size_t)i * V;
-                dst.p[i] = (S*)E.pop[b ^ 1] + (size_t)i * V;
-            }
-            const Nbr n = neighbours(g, x, y, z);
-            const unsigned site = n.c + n.x;
-            T* floc = (T*)E.floc;
-            if (is_solid(g, z)) {
-#pragma unroll
-                for (int i = 0; i < NQ; ++i) Store<S>::st(dst.p[i], site, T(0), 0u);
-            } else {
-                T f[NQ], o[NQ], v3[3];
-                pull19<S, true>(src, n, f);  // populations first: in flight with the force loads below
-                T Fx = EP<T>::uf(E, 0), Fy = EP<T>::uf(E, 1), Fz = EP<T>::uf(E, 2);
-                if (fl) {
-                    const T s = SC ? (T)E.scale : T(1);
-                    Fx += __ldg(floc + site) * s;
-                    Fy += __ldg(floc + V + site) * s;
-                    Fz += __ldg(floc + 2 * V + site) * s;
-                }
-                Coef<T> k;
-                k.tau_s = EP<T>::coef(E, 0);
-                k.tau_b = EP<T>::coef(E, 1);
-                k.om_s = EP<T>::coef(E, 2);
-                k.om_b = EP<T>::coef(E, 3);
-                collide19<T, Store<S>::kCompensate, SC, true>(f, Fx, Fy, Fz, k, o, (T)E.inv_scale, v3);
-                unsigned rn = rng_seed(site ^ (unsigned)(e * 0x27d4eb2d), seed);
-#pragma unroll
-                for (int i = 0; i < NQ; ++i) Store<S>::st(dst.p[i], site, o[i], rng_next(rn));
-                if (fl && E.vel) {  // v at the stencil nodes of the replica's colloids
-                    T* vel = (T*)E.vel;
-                    vel[site] = v3[0];
-                    vel[V + site] = v3[1];
-                    vel[2 * V + site] = v3[2];
-                }
-                if (fl) {  // the field is spread anew every step: zero what was consumed
-                    floc[site] = T(0);
-                    floc[V + site] = T(0);
-                    floc[2 * V + site] = T(0);
-                }
-            }
-        }
+        if (x < g.nx) batch_site<S>(E, e, x, y, z, fl, parity, seed);
         // the first lane of each flagged group resets its flag (this warp
         // alone read the tile's flag word, in one warp-wide load)
         if (fl && (lane % GROUP_X) == 0) E.flags[tile * (TILE_X / GROUP_X) + (unsigned)lane / GROUP_X] = 0;
     }
 }
 
+
+// The collide over flat 32-site windows of each member's site index (x
+// fastest), so that no lane idles where nx is not a multiple of 32.  Valid
+// when every member has nx a multiple of 8, so that an 8-site force group
+// never straddles two windows (each group's flag byte is then read and
+// reset by one warp; other warps that read the same flag word use only
+// their own groups' bytes), and fewer than 2^24 sites, so that the float
+// division of a site index below is off by at most one before its
+// correction.  Each warp walks a contiguous chunk of windows.
+__device__ __forceinline__ unsigned div_small(unsigned a, unsigned d, float inv_d) {
+    unsigned q = __float2uint_rz(__uint2float_rn(a) * inv_d);
+    const int r = (int)(a - q * d);
+    if (r < 0) --q;
+    else if (r >= (int)d) ++q;
+    return q;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(128, FLAT_MIN_BLOCKS)
+kb_collide_flat(const Entry* __restrict__ ent, const long long* __restrict__ wbegin, int nrep, long long total_windows,
+                int parity, const unsigned* __restrict__ step_counter) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned seed = Store<S>::kScaled || sizeof(S) == 2 ? rng_seed(*step_counter, 0xB5297A4Du) : 0u;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (long long w = wid; w < total_windows; w += nwarps) {
+        const int e = find_entry(wbegin, nrep, w);
+        const long long lo = wbegin[e];
+        const Entry& E = ent[e];
+        const Geom& g = E.g;
+        const unsigned s = (unsigned)(w - lo) * 32u + lane;
+        if (s >= (unsigned)g.V) continue;  // the ragged last window of a member
+        const unsigned zy = div_small(s, (unsigned)g.nx, E.inv_nx);
+        const unsigned x = s - zy * (unsigned)g.nx;
+        const unsigned z = div_small(zy, (unsigned)g.ny, E.inv_ny);
+        const unsigned y = zy - z * (unsigned)g.ny;
+        const unsigned tile = zy * (unsigned)g.ntx + x / TILE_X;
+        const unsigned fl = group_flag(__ldg((const unsigned*)E.flags + tile), x % TILE_X);
+        batch_site<S>(E, e, (int)x, (int)y, (int)z, fl, parity, seed);
+        if (fl && x % GROUP_X == 0) E.flags[tile * (TILE_X / GROUP_X) + (x % TILE_X) / GROUP_X] = 0;
+    }
+}
 
 // Spreading, one warp per point (the scheme of k_spread), from the stencil
 // rows st[gp] written by kb_stencil / kb_update; warps take the points in
@@ -361,6 +447,9 @@ struct lb_batch {
     int* d_sort;               // counting-sort workspace: count, cursor, start, scan sums, keys
     long long total_bins;      // cell-order bins of all members
     int steps_since_sort;
+    bool flat;                 // the flat collide applies (every nx % 8 == 0, V < 2^24)
+    long long* d_wbegin;       // first 32-site window of every member (flat collide)
+    long long total_windows;
     void* d_st;                // stencil rows of every point (ST_W elements of the arithmetic type)
     double* d_v;               // interpolated velocity of every point (3 doubles)
     int parity;                // batch steps taken since creation, mod 2
@@ -400,8 +489,11 @@ cudaError_t launch_step(lb_batch* b, int p, int blocks) {
     T* st = (T*)b->d_st;
     if (b->total_pts > 0)
         kb_spread<T><<<wblocks, 256, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->d_pent, b->d_order, b->total_pts, st);
-    kb_collide<S><<<blocks, dim3(32, BW), 0, b->stream>>>(b->d_ent, b->d_gbegin, b->d_work, b->n, b->total_groups, p,
-                                                          b->d_step);
+    if (b->flat)
+        kb_collide_flat<S><<<blocks, 128, 0, b->stream>>>(b->d_ent, b->d_wbegin, b->n, b->total_windows, p, b->d_step);
+    else
+        kb_collide<S><<<blocks, dim3(32, BW), 0, b->stream>>>(b->d_ent, b->d_gbegin, b->d_work, b->n, b->total_groups,
+                                                              p, b->d_step);
     if (b->n_mobile > 0) {
         kb_interp<T><<<wblocks, 256, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->d_pent, b->d_order, b->total_pts, st,
                                                      b->d_v);
@@ -463,8 +555,12 @@ cudaError_t launch_step_any(lb_batch* b, int p, int blocks) {
 
 template <typename S>
 cudaError_t launch_collide_only(lb_batch* b, int blocks) {
-    kb_collide<S><<<blocks, dim3(32, BW), 0, b->stream>>>(b->d_ent, b->d_gbegin, b->d_work, b->n, b->total_groups,
-                                                          b->parity, b->d_step);
+    if (b->flat)
+        kb_collide_flat<S><<<blocks, 128, 0, b->stream>>>(b->d_ent, b->d_wbegin, b->n, b->total_windows, b->parity,
+                                                          b->d_step);
+    else
+        kb_collide<S><<<blocks, dim3(32, BW), 0, b->stream>>>(b->d_ent, b->d_gbegin, b->d_work, b->n, b->total_groups,
+                                                              b->parity, b->d_step);
     return cudaGetLastError();
 }
 
@@ -500,7 +596,9 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
     std::vector<Entry> ent(n);
     std::vector<long long> gbegin(n), pbegin(n);
     std::vector<Work> work(n);
-    long long groups = 0, pts = 0, mob = 0, bins = 0;
+    long long groups = 0, pts = 0, mob = 0, bins = 0, windows = 0;
+    std::vector<long long> wbegin(n);
+    bool flat = true;
     for (int i = 0; i < n; ++i) {
         lb_ctx* c = ctxs[i];
         Entry& E = ent[i];
@@ -546,6 +644,11 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
         }
         E.bin0 = (int)bins;
         bins += (long long)E.nb[0] * E.nb[1] * E.nb[2];
+        E.inv_nx = 1.0f / (float)c->geom.nx;
+        E.inv_ny = 1.0f / (float)c->geom.ny;
+        flat = flat && c->geom.nx % GROUP_X == 0 && c->geom.V < (1LL << 24);
+        wbegin[i] = windows;
+        windows += (c->geom.V + 31) / 32;
         work[i].groups_x = c->geom.ntx;
         work[i].groups_y = (c->geom.ny + BW - 1) / BW;
         work[i].group_begin = groups;
@@ -561,7 +664,10 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
     b->n_mobile = mob;
     b->total_bins = bins;
     b->steps_since_sort = SORT_EVERY;  // the first step sorts
-    b->blocks = (int)std::min<long long>(std::max<long long>(groups, 1), 0x7fffffffLL);  // untuned: one per item
+    b->flat = flat;
+    b->total_windows = windows;
+    // untuned: the flat collide 8 blocks per SM, the tiled one a block per item
+    b->blocks = flat ? 152 * 8 : (int)std::min<long long>(std::max<long long>(groups, 1), 0x7fffffffLL);
     cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
@@ -569,6 +675,7 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
     if (e == cudaSuccess) e = cudaMalloc(&b->d_gbegin, sizeof(long long) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_pbegin, sizeof(long long) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_work, sizeof(Work) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_wbegin, sizeof(long long) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_step, sizeof(unsigned));
     if (e == cudaSuccess && pts > 0)
         e = cudaMalloc(&b->d_st, lbk::arith_bytes(b->prec) * ST_W * (size_t)pts);
@@ -588,6 +695,7 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
     if (e == cudaSuccess) e = cudaMemcpy(b->d_gbegin, gbegin.data(), sizeof(long long) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_pbegin, pbegin.data(), sizeof(long long) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_work, work.data(), sizeof(Work) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_wbegin, wbegin.data(), sizeof(long long) * n, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         lb_batch_destroy(b);
         return e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA;
@@ -604,6 +712,7 @@ void lb_batch_destroy(lb_batch* b) {
     cudaFree(b->d_gbegin);
     cudaFree(b->d_pbegin);
     cudaFree(b->d_work);
+    cudaFree(b->d_wbegin);
     cudaFree(b->d_step);
     cudaFree(b->d_st);
     cudaFree(b->d_v);
@@ -636,11 +745,16 @@ lb_status lb_batch_tune(lb_batch* b, int* blocks_out) {
     LB_BCUDA(cudaEventCreate(&t0), "event");
     LB_BCUDA(cudaEventCreate(&t1), "event");
     // candidates: persistent grids of 2-16 blocks per SM (contiguous chunks of
-    // work items per block), and one block per work item (no persistence)
-    const long long per_sm[] = {2, 4, 8, 16, 0};
-    for (long long k : per_sm) {
-        const long long want = k ? 152LL * k : std::min<long long>(b->total_groups, 0x7fffffffLL);
-        const int blocks = (int)std::min<long long>(want, std::max<long long>(1, b->total_groups));
+    // work per block or warp), and for the tiled collide one block per work
+    // item (no persistence)
+    const long long per_sm_tiled[] = {2, 4, 8, 16, 0};
+    const long long per_sm_flat[] = {4, 6, 8, 12, 16};
+    const long long* per_sm = b->flat ? per_sm_flat : per_sm_tiled;
+    const long long items = b->flat ? (b->total_windows + 3) / 4 : b->total_groups;
+    for (int ci = 0; ci < 5; ++ci) {
+        const long long k = per_sm[ci];
+        const long long want = k ? 152LL * k : std::min<long long>(items, 0x7fffffffLL);
+        const int blocks = (int)std::min<long long>(want, std::max<long long>(1, items));
         LB_BCUDA(launch_collide_any(b, blocks), "tune launch");  // warm
         LB_BCUDA(cudaEventRecord(t0, b->stream), "event");
         for (int r = 0; r < 3; ++r) LB_BCUDA(launch_collide_any(b, blocks), "tune launch");

@@ -28,9 +28,15 @@ def _lb():
     return lb
 
 
-def _uneven_members():
+# Member sets: "uneven" takes the tiled collide (an nx that is not a multiple
+# of 8); "x8" (every nx a multiple of 8) the flat 32-site-window collide.
+GRIDS = {"uneven": [(12, 12, 12), (20, 16, 8), (9, 13, 11), (33, 5, 7), (16, 16, 16)],
+         "x8": [(16, 12, 12), (24, 16, 8), (8, 13, 11), (40, 5, 7), (16, 9, 10)]}
+
+
+def _uneven_members(kind="uneven"):
     r = W.rng(77)
-    grids = [(12, 12, 12), (20, 16, 8), (9, 13, 11), (33, 5, 7), (16, 16, 16)]
+    grids = GRIDS[kind]
     probs = []
     for k, n in enumerate(grids):
         m = [3, 0, 5, 2, 8][k]
@@ -47,14 +53,16 @@ def _uneven_members():
     return probs
 
 
-@pytest.mark.parametrize("steps", [31, 30])
-def test_batch_matches_oracle_fp64(steps):
+@pytest.mark.parametrize("kind,steps", [("uneven", 31), ("uneven", 30), ("x8", 31)])
+def test_batch_matches_oracle_fp64(kind, steps):
     # Each member of the batch advances exactly as the method does on its
     # own lattice: velocity field and colloid positions against the oracle.
     lb = _lb()
-    probs = _uneven_members()
+    probs = _uneven_members(kind)
     gs = [gpu_lattice(p, lb.LB_F64) for p in probs]
     batch = lb.lb_batch_create([g.ctx for g in gs])
+    if kind == "x8":  # the flat collide's untuned grid: 8 blocks per SM
+        assert lb.lb_batch_info(batch)["blocks"] == 152 * 8
     lb.lb_batch_step(batch, steps)
     for p, g in zip(probs, gs):
         _, u, _ = g.moments()
