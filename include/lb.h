@@ -209,7 +209,11 @@ lb_status lb_colloid_velocity(lb_ctx *ctx, int n, const double *pos, const doubl
  * master weights), trained on pairs of runs of the method at two lattice
  * resolutions.  Input of a colloid: its fractional lattice offset and the
  * minimum-image vectors to its 8 nearest others within 8 lattice units
- * (nearest first, in units of 4 lattice spacings, zero where absent).
+ * (nearest first, equal distances by lower index, in units of 4 lattice
+ * spacings, zero where absent).  The vectors and the distances that select
+ * and order them are float32, each operation rounded once: positions
+ * rounded to float, d = x_j - x_i, then d -+ box beyond +-box/2, squared
+ * distance (dx^2 + dy^2) + dz^2, kept up to 64.
  * Parameters: one float vector, W1[64][27] b1[64] W2[64][64] b2[64]
  * W3[3][64] b3[3] (lb_mlp_num_params() floats).  n-sized arrays are device
  * pointers; parameter vectors host or device.  Work runs on the stream

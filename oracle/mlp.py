@@ -11,7 +11,12 @@ input x of a colloid s is its fractional lattice offset R_s - floor(R_s)
 (3 numbers) followed by the minimum-image vectors R_j - R_s to its 8
 nearest other colloids within R_CUT lattice units, nearest first (equal
 distances: lower index first), each divided by FEAT_LENGTH (24 numbers);
-absent neighbours are zero vectors.
+absent neighbours are zero vectors.  The neighbour vectors, and the
+distances that select and order the neighbours, are float32 (the
+network's input precision), each operation rounded once: positions
+rounded to float32, d = p_j - p_s, then d - box where d > box/2 and
+d + box where d < -box/2, r2 = (dx dx + dy dy) + dz dz, kept where
+r2 <= R_CUT^2.
 
 `forward`/`backward` follow these definitions with plain numpy matrix
 products.  With `bf16_round=True` they round, as the CUDA kernels do, every
@@ -97,22 +102,27 @@ def backward(P, x, t, bf16_round=False):
 
 
 def features(pos, box):
-    """Inputs of every colloid by brute force over all pairs (minimum image)."""
+    """Inputs of every colloid by brute force over all pairs (minimum image,
+    float32 neighbour arithmetic as the module docstring states)."""
     pos = np.asarray(pos, dtype=np.float64)
-    box = np.asarray(box, dtype=np.float64)
+    p = pos.astype(np.float32)
+    bf = np.asarray(box, dtype=np.float32)
+    half = bf * np.float32(0.5)
+    rc2 = np.float32(R_CUT * R_CUT)
     n = len(pos)
     out = np.zeros((n, DIMS[0]))
     out[:, :3] = pos - np.floor(pos)
     for s in range(n):
-        d = pos - pos[s]
-        d -= box * np.round(d / box)
-        r2 = (d * d).sum(1)
-        r2[s] = np.inf
-        r2[r2 > R_CUT * R_CUT] = np.inf
-        order = np.argsort(r2, kind="stable")[:N_NEIGH]
-        order = [j for j in order if np.isfinite(r2[j])]
+        d = p - p[s]
+        d = np.where(d > half, d - bf, np.where(d < -half, d + bf, d))
+        r2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+        assert r2.dtype == np.float32
+        ok = r2 <= rc2
+        ok[s] = False
+        cand = np.nonzero(ok)[0]
+        order = cand[np.argsort(r2[cand], kind="stable")][:N_NEIGH]
         for k, j in enumerate(order):
-            out[s, 3 + 3 * k: 6 + 3 * k] = d[j] / FEAT_LENGTH
+            out[s, 3 + 3 * k: 6 + 3 * k] = d[j] / np.float32(FEAT_LENGTH)
     return out
 
 

@@ -642,243 +642,144 @@ __global__ void km_adam(float* __restrict__ p, const float* __restrict__ g, floa
 }
 
 // --------------------------------------------------------- features
-// Cell list with cells of at least R_CUT (nc = floor(box / R_CUT) per
-// axis), so that the 27 cells around a point's cell hold every other point
-// within R_CUT.
-__device__ __forceinline__ int cell_of(double X, double box, int nc) {
-    int c = (int)(X / box * nc);
+// Cell list with cells wider than R_CUT by 1/64 (nc = floor(box / (R_CUT +
+// 1/64)) per axis, at least 1), so that the 27 cells around a point's cell
+// hold every other point whose float32 separation is within R_CUT: the
+// float rounding of a position or of the cell arithmetic (below 1e-3 for
+// boxes under 2^16) stays far inside the 1/64.
+constexpr float CELL_W = R_CUT + 1.0f / 64.0f;
+
+__device__ __forceinline__ int cell_of(float X, float inv_w, int nc) {
+    const int c = (int)(X * inv_w);
     return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
 }
 
-__global__ void kf_count(const double* __restrict__ pos, long long n, Geom g, int3 nc, int* __restrict__ count,
-                         int* __restrict__ cell) {
+// Each point's cell, and its float32 position (round to nearest) with its
+// index in w: the neighbour search reads only these.
+__global__ void kf_count(const double* __restrict__ pos, long long n, float3 inv_w, int3 nc, int* __restrict__ count,
+                         int* __restrict__ cell, float4* __restrict__ fpos) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int cx = cell_of(pos[3 * i], g.nx, nc.x), cy = cell_of(pos[3 * i + 1], g.ny, nc.y),
-              cz = cell_of(pos[3 * i + 2], g.nz, nc.z);
-    const int c = (cz * nc.y + cy) * nc.x + cx;
+    const float x = (float)pos[3 * i], y = (float)pos[3 * i + 1], z = (float)pos[3 * i + 2];
+    const int c = (cell_of(z, inv_w.z, nc.z) * nc.y + cell_of(y, inv_w.y, nc.y)) * nc.x + cell_of(x, inv_w.x, nc.x);
     cell[i] = c;
+    fpos[i] = make_float4(x, y, z, __int_as_float((int)i));
     atomicAdd(&count[c], 1);
 }
 
-// Points in cell order: their indices, and their positions rounded to float
-// with the index in w (the candidate filter of kf_knn reads these).
-__global__ void kf_fill(const double* __restrict__ pos, long long n, const int* __restrict__ cell,
-                        const int* __restrict__ start, int* __restrict__ cursor, int* __restrict__ sorted,
-                        float4* __restrict__ spos) {
+// The points in cell order (float4 records as kf_count made them).
+__global__ void kf_fill(long long n, const int* __restrict__ cell, const float4* __restrict__ fpos,
+                        const int* __restrict__ start, int* __restrict__ cursor, float4* __restrict__ spos) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int c = cell[i];
-    const int slot = start[c] + atomicAdd(&cursor[c], 1);
-    sorted[slot] = (int)i;
-    spos[slot] = make_float4((float)pos[3 * i], (float)pos[3 * i + 1], (float)pos[3 * i + 2], __int_as_float((int)i));
+    spos[start[c] + atomicAdd(&cursor[c], 1)] = fpos[i];
 }
 
-// Minimum-image difference, exactly as d - box * rint(d / box) (rint = 0
-// for |d| <= box / 4, where the division is skipped); qbox = box / 4.
-__device__ __forceinline__ double min_image(double d, double box, double qbox) {
-    return fabs(d) > qbox ? d - box * rint(d / box) : d;
+// Minimum-image float32 difference along one axis, each operation rounded
+// once: d = xj - xi, then d - box above box/2, d + box below -box/2.
+__device__ __forceinline__ float min_image_f(float xj, float xi, float box, float half) {
+    const float d = __fsub_rn(xj, xi);
+    return d > half ? __fsub_rn(d, box) : (d < -half ? __fadd_rn(d, box) : d);
 }
 
-// Squared distance summed in the order ((dx^2 + dy^2) + dz^2), each step
-// rounded once.
-__device__ __forceinline__ double dist2(const double d[3]) {
-    return __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
-}
+// 27 features per point: the fractional offset, then the 8 nearest others
+// within R_CUT (minimum image), nearest first, equal distances by lower
+// index.  The distances that select and order them are float32, each
+// operation rounded once (the definition the oracle states), so one pass
+// over the candidates decides exactly: the key of a candidate is the bit
+// pattern of its squared distance (non-negative floats order as their bit
+// patterns) above its index, kept in an 8-entry insertion list.  One thread
+// per point, the points taken in cell order so that a warp's threads walk
+// the same cells.
+constexpr int KNN_THREADS = 128;
 
-// Exact top-8 insertion of candidate (ck, cj): ck is the bit pattern of a
-// non-negative FP64 squared distance (ordered as the distances are, so the
-// comparisons run on the integer pipe), equal distances by lower index; the
-// last entry drops out.
-__device__ __forceinline__ void insert_exact(unsigned long long (&bk)[NNB], int (&bj)[NNB], unsigned long long ck,
-                                             int cj) {
-#pragma unroll
-    for (int k = 0; k < NNB; ++k) {
-        const bool lt = ck < bk[k] || (ck == bk[k] && cj < bj[k]);
-        const unsigned long long tk = bk[k];
-        const int tj = bj[k];
-        bk[k] = lt ? ck : tk;
-        bj[k] = lt ? cj : tj;
-        ck = lt ? tk : ck;
-        cj = lt ? tj : cj;
-    }
-}
-
-// Minimum-image difference along one axis, d = x_j - x_i, exactly as
-// min_image; the float difference df of the same pair (within 1 of d)
-// settles the common case |d| < box / 4 (below qf = box / 4 - 1), where no
-// image shift applies.
-__device__ __forceinline__ double min_image_hint(double xj, double xi, float df, float qf, double box, double qbox) {
-    const double d = xj - xi;
-    return fabsf(df) < qf ? d : min_image(d, box, qbox);
-}
-
-// The 27 cells around cell c0 (each visited once when an axis has fewer
-// than 3 cells), as a flat index for step t = 0 .. count - 1, with the
-// periodic image shift of each: with 3 or more cells along an axis every
-// other point within R_CUT of a point lies in a neighbouring cell, at the
-// difference (x_j + shift) - x_i, shift = -box, 0 or +box by the cell's wrap.
-struct CellWalk {
-    int c0[3], nc[3], lo[3], span[3], count;
-    bool shifts;  // every axis has 3 or more cells: shift() is the minimum image
-    __device__ CellWalk(int ci, int3 n) {
-        nc[0] = n.x;
-        nc[1] = n.y;
-        nc[2] = n.z;
-        c0[0] = ci % n.x;
-        c0[1] = (ci / n.x) % n.y;
-        c0[2] = ci / (n.x * n.y);
-        count = 1;
-        shifts = true;
-        for (int a = 0; a < 3; ++a) {
-            lo[a] = nc[a] >= 3 ? -1 : 0;
-            span[a] = nc[a] >= 3 ? 3 : nc[a];
-            count *= span[a];
-            shifts = shifts && nc[a] >= 3;
-        }
-    }
-    __device__ void step(int t, int& cell, float3& shift, const float box[3]) const {
-        const int d[3] = {t % span[0] + lo[0], (t / span[0]) % span[1] + lo[1], t / (span[0] * span[1]) + lo[2]};
-        int cc[3];
-        float sh[3];
-        for (int a = 0; a < 3; ++a) {
-            if (nc[a] >= 3) {
-                const int r = c0[a] + d[a];
-                cc[a] = r < 0 ? r + nc[a] : (r >= nc[a] ? r - nc[a] : r);
-                sh[a] = r < 0 ? -box[a] : (r >= nc[a] ? box[a] : 0.0f);
-            } else {
-                cc[a] = d[a];
-                sh[a] = 0.0f;
-            }
-        }
-        cell = (cc[2] * nc[1] + cc[1]) * nc[0] + cc[0];
-        shift = make_float3(sh[0], sh[1], sh[2]);
+// Offsets -1, 0, 1 of a cell coordinate along an axis with n cells, wrapped
+// (every cell once when n < 3): the k-th of count() of them.
+struct AxisWalk {
+    int c, n;
+    __device__ AxisWalk(int c_, int n_) : c(c_), n(n_) {}
+    __device__ int count() const { return n >= 3 ? 3 : n; }
+    __device__ int at(int k) const {
+        if (n < 3) return k;
+        const int r = c + k - 1;
+        return r < 0 ? r + n : (r >= n ? r - n : r);
     }
 };
 
-// 27 features per point: fractional offset, then the 8 nearest others
-// within R_CUT (minimum image), nearest first, equal distances by lower
-// index.  One thread per point, the points taken in cell order so that a
-// warp's threads walk the same cells.
-//
-// Which 8, and in which order, is decided in FP64 exactly as the definition
-// states, with FP64 arithmetic and sorting kept off the per-candidate loop:
-// one float pass computes squared distances r2f from float positions (error
-// below `margin`), tracks the 8 smallest values r2f <= R_CUT^2 + margin
-// (values only) and lists in shared memory every candidate with r2f within
-// the current window F8 + 2 margin (F8 the current 8th smallest; the window
-// only shrinks, so the final window's candidates are all listed).  Every
-// candidate of the exact top 8 has r2f <= W = F8 + 2 margin (W = R_CUT^2 +
-// margin with fewer than 8); the FP64 distances of the listed candidates
-// within W decide.  A thread whose list overflows (more than KW entries)
-// searches again in FP64.
-constexpr int KW = 32;           // listed candidates a thread can hold
-constexpr int KNN_THREADS = 128;
-
 __global__ void __launch_bounds__(KNN_THREADS)
 kf_knn(const double* __restrict__ pos, long long n, Geom g, int3 nc, const int* __restrict__ start,
-       const int* __restrict__ sorted, const int* __restrict__ cell, const float4* __restrict__ spos, float margin,
-       float* __restrict__ feat) {
-    __shared__ int wslot[KW][KNN_THREADS];    // [entry][thread]: no bank conflicts
-    __shared__ float wr2[KW][KNN_THREADS];
+       const int* __restrict__ cell, const float4* __restrict__ spos, float* __restrict__ feat) {
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
-    const int i = sorted[q];
     const float4 me = spos[q];
-    const double box[3] = {(double)g.nx, (double)g.ny, (double)g.nz};
-    const double qbox[3] = {0.25 * (double)g.nx, 0.25 * (double)g.ny, 0.25 * (double)g.nz};
-    const float boxf[3] = {(float)g.nx, (float)g.ny, (float)g.nz};
-    const float halff[3] = {0.5f * (float)g.nx, 0.5f * (float)g.ny, 0.5f * (float)g.nz};
-    const float qf[3] = {0.25f * (float)g.nx - 1.0f, 0.25f * (float)g.ny - 1.0f, 0.25f * (float)g.nz - 1.0f};
-    const double P[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
-    const double rc2 = (double)R_CUT * (double)R_CUT;
-    const CellWalk walk(cell[i], nc);
-    const float lim = (float)rc2 + margin, twom = 2.0f * margin;
-
-    float f8[NNB];
-#pragma unroll
-    for (int k = 0; k < NNB; ++k) f8[k] = 3.0e38f;
-    int nw = 0;
-    for (int t = 0; t < walk.count; ++t) {
-        int c;
-        float3 sh;
-        walk.step(t, c, sh, boxf);
-        const int e = start[c + 1];
-        for (int qq = start[c]; qq < e; ++qq) {
-            const float4 o = spos[qq];
-            float dx = (o.x + sh.x) - me.x, dy = (o.y + sh.y) - me.y, dz = (o.z + sh.z) - me.z;
-            if (!walk.shifts) {  // fewer than 3 cells along an axis: minimum image per candidate
-                dx = dx > halff[0] ? dx - boxf[0] : (dx < -halff[0] ? dx + boxf[0] : dx);
-                dy = dy > halff[1] ? dy - boxf[1] : (dy < -halff[1] ? dy + boxf[1] : dy);
-                dz = dz > halff[2] ? dz - boxf[2] : (dz < -halff[2] ? dz + boxf[2] : dz);
-            }
-            float cr = dx * dx + dy * dy + dz * dz;
-            if (qq == q || !(cr <= fminf(lim, f8[NNB - 1] + twom))) continue;
-            if (nw < KW) {
-                wslot[nw][threadIdx.x] = qq;
-                wr2[nw][threadIdx.x] = cr;
-            }
-            ++nw;
-            if (cr < f8[NNB - 1]) {
-#pragma unroll
-                for (int k = 0; k < NNB; ++k) {
-                    const bool lt = cr < f8[k];
-                    const float tk = f8[k];
-                    f8[k] = lt ? cr : tk;
-                    cr = lt ? tk : cr;
-                }
-            }
-        }
-    }
-    const float W = f8[NNB - 1] < 1.0e38f ? fminf(lim, f8[NNB - 1] + twom) : lim;
-    const unsigned long long krc2 = (unsigned long long)__double_as_longlong(rc2);
-    unsigned long long bk[NNB];
-    int bj[NNB];
+    const int i = __float_as_int(me.w);
+    const float box[3] = {(float)g.nx, (float)g.ny, (float)g.nz};
+    const float half[3] = {0.5f * box[0], 0.5f * box[1], 0.5f * box[2]};
+    const float rc2 = R_CUT * R_CUT;
+    unsigned long long bk[NNB];  // (r2 bits << 32) | index, ascending
+    int bs[NNB];                 // slot of each in cell order
 #pragma unroll
     for (int k = 0; k < NNB; ++k) {
         bk[k] = ~0ull;
-        bj[k] = 0x7fffffff;
+        bs[k] = -1;
     }
-    if (nw > KW) {  // list overflowed: search again in FP64
-        for (int t = 0; t < walk.count; ++t) {
-            int c;
-            float3 sh;
-            walk.step(t, c, sh, boxf);
-            for (int qq = start[c]; qq < start[c + 1]; ++qq) {
-                const int jn = sorted[qq];
-                if (jn == i) continue;
-                double d[3];
-                for (int a = 0; a < 3; ++a) d[a] = min_image(pos[3 * (long long)jn + a] - P[a], box[a], qbox[a]);
-                const unsigned long long ck = (unsigned long long)__double_as_longlong(dist2(d));
-                if (ck <= krc2) insert_exact(bk, bj, ck, jn);
-            }
+    const auto consider = [&](int qq) {
+        const float4 o = __ldg(spos + qq);
+        const float dx = min_image_f(o.x, me.x, box[0], half[0]);
+        const float dy = min_image_f(o.y, me.y, box[1], half[1]);
+        const float dz = min_image_f(o.z, me.z, box[2], half[2]);
+        const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+        unsigned long long ck = ((unsigned long long)__float_as_uint(r2) << 32) | (unsigned)__float_as_int(o.w);
+        if (!(r2 <= rc2) || qq == q || ck >= bk[NNB - 1]) return;
+        int cs = qq;
+#pragma unroll
+        for (int k = 0; k < NNB; ++k) {
+            const bool lt = ck < bk[k];
+            const unsigned long long tk = bk[k];
+            const int ts = bs[k];
+            bk[k] = lt ? ck : tk;
+            bs[k] = lt ? cs : ts;
+            ck = lt ? tk : ck;
+            cs = lt ? ts : cs;
         }
+    };
+    // the cells around the point's cell, row by row: along x the (up to) 3
+    // cells of a row are contiguous in cell order unless the row wraps
+    const int c0 = cell[i];
+    const int cx = c0 % nc.x, cyz = c0 / nc.x;
+    const AxisWalk wy(cyz % nc.y, nc.y), wz(cyz / nc.y, nc.z);
+    int xa, xb, xc, xd;  // x cells [xa, xb) and [xc, xd) of every row
+    if (nc.x < 3) {
+        xa = 0, xb = nc.x, xc = xd = 0;
+    } else if (cx == 0) {
+        xa = 0, xb = 2, xc = nc.x - 1, xd = nc.x;
+    } else if (cx == nc.x - 1) {
+        xa = cx - 1, xb = nc.x, xc = 0, xd = 1;
     } else {
-        for (int k = 0; k < nw; ++k) {
-            if (!(wr2[k][threadIdx.x] <= W)) continue;
-            const float4 o = spos[wslot[k][threadIdx.x]];
-            const int jn = __float_as_int(o.w);
-            const float dfx[3] = {o.x - me.x, o.y - me.y, o.z - me.z};
-            double d[3];
-            for (int a = 0; a < 3; ++a)
-                d[a] = min_image_hint(pos[3 * (long long)jn + a], P[a], dfx[a], qf[a], box[a], qbox[a]);
-            const unsigned long long ck = (unsigned long long)__double_as_longlong(dist2(d));
-            if (ck <= krc2) insert_exact(bk, bj, ck, jn);
+        xa = cx - 1, xb = cx + 2, xc = xd = 0;
+    }
+    for (int kz = 0; kz < wz.count(); ++kz) {
+        const int rz = wz.at(kz) * nc.y;
+        for (int ky = 0; ky < wy.count(); ++ky) {
+            const int row = (rz + wy.at(ky)) * nc.x;
+            for (int qq = start[row + xa], e = start[row + xb]; qq < e; ++qq) consider(qq);
+            for (int qq = start[row + xc], e = start[row + xd]; qq < e; ++qq) consider(qq);
         }
     }
-    // outputs: float(d / 4) = float(d) / 4 exactly
     float* f = feat + (long long)i * D0;
-    for (int a = 0; a < 3; ++a) f[a] = (float)(P[a] - floor(P[a]));
+    for (int a = 0; a < 3; ++a) f[a] = (float)(pos[3 * (long long)i + a] - floor(pos[3 * (long long)i + a]));
+    // the vectors: the same float32 differences, exactly scaled by 1/4
 #pragma unroll
     for (int k = 0; k < NNB; ++k) {
-        if (bk[k] != ~0ull) {
-            const int jn = bj[k];
-            for (int a = 0; a < 3; ++a)
-                f[3 + 3 * k + a] =
-                    __double2float_rn(min_image(pos[3 * (long long)jn + a] - P[a], box[a], qbox[a])) * (1.0f / FEAT_LENGTH);
-        } else {
-            for (int a = 0; a < 3; ++a) f[3 + 3 * k + a] = 0.0f;
+        float d[3] = {0.0f, 0.0f, 0.0f};
+        if (bs[k] >= 0) {
+            const float4 o = spos[bs[k]];
+            d[0] = min_image_f(o.x, me.x, box[0], half[0]);
+            d[1] = min_image_f(o.y, me.y, box[1], half[1]);
+            d[2] = min_image_f(o.z, me.z, box[2], half[2]);
         }
+        for (int a = 0; a < 3; ++a) f[3 + 3 * k + a] = d[a] * (1.0f / FEAT_LENGTH);
     }
 }
 
@@ -929,31 +830,31 @@ namespace lbk {
 
 static int3 feature_cells(const int box[3]) {
     int3 nc;
-    nc.x = box[0] / (int)R_CUT > 0 ? box[0] / (int)R_CUT : 1;
-    nc.y = box[1] / (int)R_CUT > 0 ? box[1] / (int)R_CUT : 1;
-    nc.z = box[2] / (int)R_CUT > 0 ? box[2] / (int)R_CUT : 1;
+    nc.x = std::max(1, (int)((float)box[0] / CELL_W));
+    nc.y = std::max(1, (int)((float)box[1] / CELL_W));
+    nc.z = std::max(1, (int)((float)box[2] / CELL_W));
     return nc;
 }
 
-// Workspace in ints: the float4 positions in cell order (4 n, first, so
-// 16-byte aligned), count, cursor, start (m + 1), cell and sorted index per
-// point, the scan's tile sums.
+// Workspace in ints: the float4 records in point order and in cell order
+// (4 n each, first, so 16-byte aligned), count, cursor, start (m + 1), the
+// cell of every point, the scan's tile sums.
 size_t mlp_features_ws_ints(long long n, const int box[3]) {
     const int3 nc = feature_cells(box);
     const long long m = (long long)nc.x * nc.y * nc.z;
-    return (size_t)(4 * n + 3 * m + 1 + 2 * n) + scan_ws_ints(m);
+    return (size_t)(8 * n + 3 * m + 1 + n) + scan_ws_ints(m);
 }
 
 cudaError_t mlp_features(long long n, const double* pos, const int box[3], float* feat, int* ws, cudaStream_t st) {
     const int3 nc = feature_cells(box);
     const long long m = (long long)nc.x * nc.y * nc.z;
-    float4* spos = (float4*)ws;
-    int* count = ws + 4 * n;
+    float4* fpos = (float4*)ws;
+    float4* spos = fpos + n;
+    int* count = ws + 8 * n;
     int* cursor = count + m;
     int* start = cursor + m;
     int* cell = start + m + 1;
-    int* sorted = cell + n;
-    int* bsum = sorted + n;
+    int* bsum = cell + n;
     Geom g{};
     g.nx = box[0];
     g.ny = box[1];
@@ -961,18 +862,14 @@ cudaError_t mlp_features(long long n, const double* pos, const int box[3], float
     if (n == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * 2 * m, st);
     if (e != cudaSuccess) return e;
-    // float error of a coordinate difference <= box 2^-22 + |d| 2^-23; the
-    // margin bounds the error of |d|^2 near the cutoff with a factor 4 to spare
-    const double bmax = (double)std::max(box[0], std::max(box[1], box[2]));
-    const double ea = bmax * 0x1p-20 + 0x1p-18;
-    const float margin = (float)(2.0 * ea * 1.7320508075688772 * (R_CUT + 1.0) + 3.0 * ea * ea + 1e-5);
+    const float3 inv_w = make_float3((float)nc.x / (float)box[0], (float)nc.y / (float)box[1], (float)nc.z / (float)box[2]);
     const unsigned blocks = (unsigned)((n + 255) / 256);
-    kf_count<<<blocks, 256, 0, st>>>(pos, n, g, nc, count, cell);
+    kf_count<<<blocks, 256, 0, st>>>(pos, n, inv_w, nc, count, cell, fpos);
     e = scan_exclusive(count, m, start, bsum, st);
     if (e != cudaSuccess) return e;
-    kf_fill<<<blocks, 256, 0, st>>>(pos, n, cell, start, cursor, sorted, spos);
-    kf_knn<<<(unsigned)((n + KNN_THREADS - 1) / KNN_THREADS), KNN_THREADS, 0, st>>>(pos, n, g, nc, start, sorted, cell,
-                                                                                  spos, margin, feat);
+    kf_fill<<<blocks, 256, 0, st>>>(n, cell, fpos, start, cursor, spos);
+    kf_knn<<<(unsigned)((n + KNN_THREADS - 1) / KNN_THREADS), KNN_THREADS, 0, st>>>(pos, n, g, nc, start, cell, spos,
+                                                                                  feat);
     return cudaGetLastError();
 }
 

@@ -46,6 +46,21 @@ def test_bf16_rounding():
     assert np.array_equal(mlp.bf16(r), r)
 
 
+def test_features_decide_in_float32():
+    # The selection distances are float32: a neighbour 2 + 1e-9 away (index
+    # 1) and one 2 away (index 2) tie in float32, so the lower index comes
+    # first although it is the farther one in exact arithmetic; the vectors
+    # are the float32 differences (12 + 1e-9 rounds to 12).
+    box = (40, 40, 40)
+    pos = np.array([[10.0, 10.0, 10.0], [12.0 + 1e-9, 10.0, 10.0], [8.0, 10.0, 10.0]])
+    f = mlp.features(pos, box)
+    nb = f[0, 3:9].reshape(2, 3) * mlp.FEAT_LENGTH
+    assert np.array_equal(nb, [[2.0, 0.0, 0.0], [-2.0, 0.0, 0.0]])
+    # a separation that float32 rounds to exactly R_CUT is kept
+    pos = np.array([[1.0, 1.0, 1.0], [9.0 + 1e-8, 1.0, 1.0]])
+    assert mlp.features(pos, box)[0, 3] * mlp.FEAT_LENGTH == 8.0
+
+
 def test_features_known_geometry():
     # a colloid at the centre of a cube of 8 others: its 8 neighbours are the
     # corners, distance sqrt(3); the far colloid is never among them
