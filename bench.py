@@ -288,10 +288,10 @@ def run_gpu(args, rank, world):
         c512 = colloids_512(L=args.colloids[0], n=args.colloids[1])
     batched = None
     if rank == 0 and world == 1 and not args.no_batched:
-        batched = batched_replicas()
+        batched = batched_replicas(replicas=args.replicas)
     learned = None
     if rank == 0 and world == 1 and not args.no_learned:
-        learned = learned_correction()
+        learned = learned_correction(train=not args.no_training)
     out = {
         "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True,
@@ -430,14 +430,14 @@ def colloids_512(L=512, n=100000, steps=100, timed=40):
     return out
 
 
-def batched_replicas(steps=50, seq_steps=10):
+def batched_replicas(steps=50, seq_steps=10, replicas=64):
     """64 independent sedimentation boxes of uneven sizes (48^3-128^3, 100-2000
     colloids each, FP32) advanced by one batch (a launch per phase over all
     boxes, graph-replayed steps, tuned persistent grid) against the same boxes
     stepped one after another with lb_step."""
     import torch
     from paper_0707_1299_gb300 import lb, workloads as W
-    probs = W.replicas()
+    probs = W.replicas(n=replicas)
     lats = []
     for p in probs:
         g = lb.Lattice(p.grid, p.tau_s, p.tau_b, lb.LB_F32)
@@ -484,7 +484,7 @@ def batched_replicas(steps=50, seq_steps=10):
                                    "steps": seq_steps}}
 
 
-def learned_correction(train_pairs=32, test_pairs=4, L_pair=64, T_pair=1000, steps=20):
+def learned_correction(train_pairs=32, test_pairs=4, L_pair=64, T_pair=1000, steps=20, train=True):
     """The learned correction of the colloid velocity: trained on ~1e5
     samples of 1x/2x run pairs of the method (64^3 / 128^3 boxes at the
     number density of the workload below), judged on held-out pairs; then
@@ -492,22 +492,25 @@ def learned_correction(train_pairs=32, test_pairs=4, L_pair=64, T_pair=1000, ste
     stepped with the plain update and with the corrected one."""
     import torch
     from paper_0707_1299_gb300 import lb, learned, workloads as W
-    t0 = time.perf_counter()
-    data = [learned.pair_samples(L=L_pair, seed=s, T=T_pair) for s in range(train_pairs + test_pairs)]
-    torch.cuda.synchronize()
-    t_gen = time.perf_counter() - t0
-    ftr = torch.cat([d[0] for d in data[:train_pairs]]).contiguous()
-    ltr = torch.cat([d[1] for d in data[:train_pairs]]).contiguous()
-    fte = torch.cat([d[0] for d in data[train_pairs:]]).contiguous()
-    lte = torch.cat([d[1] for d in data[train_pairs:]]).contiguous()
-    warm, _ = learned.train(ftr, ltr, steps=5, batch=4096, lr=2e-3)  # first use of torch's sampling kernels
-    lb.lb_mlp_destroy(warm)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    net, hist = learned.train(ftr, ltr, steps=4000, batch=4096, lr=2e-3)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    ev = learned.evaluate(net, fte, lte)
+    if train:
+        t0 = time.perf_counter()
+        data = [learned.pair_samples(L=L_pair, seed=s, T=T_pair) for s in range(train_pairs + test_pairs)]
+        torch.cuda.synchronize()
+        t_gen = time.perf_counter() - t0
+        ftr = torch.cat([d[0] for d in data[:train_pairs]]).contiguous()
+        ltr = torch.cat([d[1] for d in data[:train_pairs]]).contiguous()
+        fte = torch.cat([d[0] for d in data[train_pairs:]]).contiguous()
+        lte = torch.cat([d[1] for d in data[train_pairs:]]).contiguous()
+        warm, _ = learned.train(ftr, ltr, steps=5, batch=4096, lr=2e-3)  # first use of torch's sampling kernels
+        lb.lb_mlp_destroy(warm)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        net, hist = learned.train(ftr, ltr, steps=4000, batch=4096, lr=2e-3)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        ev = learned.evaluate(net, fte, lte)
+    else:  # the seeded initial network: the corrected step costs the same
+        net = lb.lb_mlp_create(learned.initial_params(0))
     prob = W.colloids(L=256, n=200000, seed=5, force=1e-6)
     g = lb.Lattice(prob.grid, prob.tau_s, prob.tau_b, lb.LB_F32)
     g.set_colloid_aL(lb.lb_compute_aL(prob.grid, [128.5] * 3, [0, 0, 1]))
@@ -531,6 +534,10 @@ def learned_correction(train_pairs=32, test_pairs=4, L_pair=64, T_pair=1000, ste
     g.close()
     lb.lb_mlp_destroy(net)
     torch.cuda.empty_cache()
+    if not train:
+        return {"workload": "256^3 FP32, 2e5 colloids (seed 5), force 1e-6, a = 0.117", "unit": "MLUPS",
+                "plain": out["plain"], "corrected": out["corrected"], "training": None,
+                "note": "untrained seeded network (--no-training): step costs only"}
     return {"workload": "256^3 FP32, 2e5 colloids (seed 5), force 1e-6, a = 0.117", "unit": "MLUPS",
             "plain": out["plain"], "corrected": out["corrected"],
             "training": {"samples": int(ftr.shape[0]), "pairs": f"{train_pairs} x ({L_pair}^3 T={T_pair}, "
@@ -621,6 +628,10 @@ def main():
     ap.add_argument("--colloids", type=int, nargs=2, default=[512, 100000], metavar=("L", "N"),
                     help="box side and colloid count of the sedimentation-box block")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--replicas", type=int, default=64, help="members of the batched-replicas block (first N)")
+    ap.add_argument("--no-training", action="store_true",
+                    help="learned block: time the plain and corrected steps with the seeded initial "
+                         "network, without generating pairs or training (for profiling)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 

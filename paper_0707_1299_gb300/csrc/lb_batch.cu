@@ -80,13 +80,13 @@ template <> struct EP<double> {
 // element j is base[i * V + j] (32-bit indices: 19 V < 2^32 for the members
 // the batch takes), so no per-population pointers are held.  A solid source
 // plane selects the opposite population of the site itself.
-template <typename S>
+template <typename S, bool WALLS>
 __device__ __forceinline__ void pull19_base(const S* __restrict__ base, unsigned V, const Nbr& n,
                                             typename Store<S>::T f[NQ]) {
     using St = Store<S>;
     const unsigned own = n.c + n.x;
     const unsigned ym = n.c + n.dym, yp = n.c + n.dyp, zm = n.c + n.dzm, zp = n.c + n.dzp;
-    const bool bm = n.solid_zm, bp = n.solid_zp;
+    const bool bm = WALLS && n.solid_zm, bp = WALLS && n.solid_zp;
     f[0] = St::ld(base, own);
     f[1] = St::ld(base, V + n.c + n.xm);
     f[2] = St::ld(base, 2 * V + n.c + n.xp);
@@ -115,7 +115,7 @@ __device__ __forceinline__ void pull19_base(const S* __restrict__ base, unsigned
 // and the consumed force is zeroed (the batch spreads it anew every step).
 // The field is read through the read-only path: only this thread reads
 // this site's force in the launch, and only after the read does it write.
-template <typename S>
+template <typename S, bool WALLS>
 __device__ __forceinline__ void batch_site(const Entry& E, int e, int x, int y, int z, unsigned fl, int parity,
                                            unsigned seed) {
     using T = typename Store<S>::T;
@@ -128,13 +128,13 @@ __device__ __forceinline__ void batch_site(const Entry& E, int e, int x, int y, 
     const Nbr n = neighbours(g, x, y, z);
     const unsigned site = n.c + n.x;
     T* floc = (T*)E.floc;
-    if (is_solid(g, z)) {
+    if (WALLS && is_solid(g, z)) {
 #pragma unroll
         for (int i = 0; i < NQ; ++i) Store<S>::st(dst, (unsigned)i * V + site, T(0), 0u);
         return;
     }
     T f[NQ], o[NQ], v3[3];
-    pull19_base<S>(src, V, n, f);  // populations first: in flight with the force loads below
+    pull19_base<S, WALLS>(src, V, n, f);  // populations first: in flight with the force loads below
     T Fx = EP<T>::uf(E, 0), Fy = EP<T>::uf(E, 1), Fz = EP<T>::uf(E, 2);
     if (fl) {
         const T s = SC ? (T)E.scale : T(1);
@@ -212,7 +212,7 @@ kb_collide(const Entry* __restrict__ ent, const long long* __restrict__ gbegin, 
         // the flags and the field are read through the read-only path and
         // reset below by the one warp (thread) that read them, as in k_collide
         const unsigned fl = group_flag(__ldg((const unsigned*)E.flags + tile), (unsigned)lane);
-        if (x < g.nx) batch_site<S>(E, e, x, y, z, fl, parity, seed);
+        if (x < g.nx) batch_site<S, true>(E, e, x, y, z, fl, parity, seed);
         // the first lane of each flagged group resets its flag (this warp
         // alone read the tile's flag word, in one warp-wide load)
         if (fl && (lane % GROUP_X) == 0) E.flags[tile * (TILE_X / GROUP_X) + (unsigned)lane / GROUP_X] = 0;
@@ -236,17 +236,24 @@ __device__ __forceinline__ unsigned div_small(unsigned a, unsigned d, float inv_
     return q;
 }
 
-template <typename S>
+template <typename S, bool WALLS>
 __global__ void __launch_bounds__(128, FLAT_MIN_BLOCKS)
 kb_collide_flat(const Entry* __restrict__ ent, const long long* __restrict__ wbegin, int nrep, long long total_windows,
                 int parity, const unsigned* __restrict__ step_counter) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned seed = Store<S>::kScaled || sizeof(S) == 2 ? rng_seed(*step_counter, 0xB5297A4Du) : 0u;
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    for (long long w = wid; w < total_windows; w += nwarps) {
-        const int e = find_entry(wbegin, nrep, w);
-        const long long lo = wbegin[e];
+    long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= total_windows) return;
+    // the member of window w, tracked forward as w grows
+    int e = find_entry(wbegin, nrep, w);
+    long long lo = wbegin[e], hi = e + 1 < nrep ? wbegin[e + 1] : total_windows;
+    for (; w < total_windows; w += nwarps) {
+        while (w >= hi) {  // uniform per warp
+            ++e;
+            lo = hi;
+            hi = e + 1 < nrep ? wbegin[e + 1] : total_windows;
+        }
         const Entry& E = ent[e];
         const Geom& g = E.g;
         const unsigned s = (unsigned)(w - lo) * 32u + lane;
@@ -257,7 +264,7 @@ kb_collide_flat(const Entry* __restrict__ ent, const long long* __restrict__ wbe
         const unsigned y = zy - z * (unsigned)g.ny;
         const unsigned tile = zy * (unsigned)g.ntx + x / TILE_X;
         const unsigned fl = group_flag(__ldg((const unsigned*)E.flags + tile), x % TILE_X);
-        batch_site<S>(E, e, (int)x, (int)y, (int)z, fl, parity, seed);
+        batch_site<S, WALLS>(E, e, (int)x, (int)y, (int)z, fl, parity, seed);
         if (fl && x % GROUP_X == 0) E.flags[tile * (TILE_X / GROUP_X) + (x % TILE_X) / GROUP_X] = 0;
     }
 }
@@ -448,6 +455,7 @@ struct lb_batch {
     long long total_bins;      // cell-order bins of all members
     int steps_since_sort;
     bool flat;                 // the flat collide applies (every nx % 8 == 0, V < 2^24)
+    bool walls;                // some member has solid planes
     long long* d_wbegin;       // first 32-site window of every member (flat collide)
     long long total_windows;
     void* d_st;                // stencil rows of every point (ST_W elements of the arithmetic type)
@@ -489,8 +497,12 @@ cudaError_t launch_step(lb_batch* b, int p, int blocks) {
     T* st = (T*)b->d_st;
     if (b->total_pts > 0)
         kb_spread<T><<<wblocks, 256, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->d_pent, b->d_order, b->total_pts, st);
-    if (b->flat)
-        kb_collide_flat<S><<<blocks, 128, 0, b->stream>>>(b->d_ent, b->d_wbegin, b->n, b->total_windows, p, b->d_step);
+    if (b->flat && b->walls)
+        kb_collide_flat<S, true><<<blocks, 128, 0, b->stream>>>(b->d_ent, b->d_wbegin, b->n, b->total_windows, p,
+                                                                b->d_step);
+    else if (b->flat)
+        kb_collide_flat<S, false><<<blocks, 128, 0, b->stream>>>(b->d_ent, b->d_wbegin, b->n, b->total_windows, p,
+                                                                 b->d_step);
     else
         kb_collide<S><<<blocks, dim3(32, BW), 0, b->stream>>>(b->d_ent, b->d_gbegin, b->d_work, b->n, b->total_groups,
                                                               p, b->d_step);
@@ -555,9 +567,12 @@ cudaError_t launch_step_any(lb_batch* b, int p, int blocks) {
 
 template <typename S>
 cudaError_t launch_collide_only(lb_batch* b, int blocks) {
-    if (b->flat)
-        kb_collide_flat<S><<<blocks, 128, 0, b->stream>>>(b->d_ent, b->d_wbegin, b->n, b->total_windows, b->parity,
-                                                          b->d_step);
+    if (b->flat && b->walls)
+        kb_collide_flat<S, true><<<blocks, 128, 0, b->stream>>>(b->d_ent, b->d_wbegin, b->n, b->total_windows,
+                                                                b->parity, b->d_step);
+    else if (b->flat)
+        kb_collide_flat<S, false><<<blocks, 128, 0, b->stream>>>(b->d_ent, b->d_wbegin, b->n, b->total_windows,
+                                                                 b->parity, b->d_step);
     else
         kb_collide<S><<<blocks, dim3(32, BW), 0, b->stream>>>(b->d_ent, b->d_gbegin, b->d_work, b->n, b->total_groups,
                                                               b->parity, b->d_step);
@@ -598,7 +613,7 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
     std::vector<Work> work(n);
     long long groups = 0, pts = 0, mob = 0, bins = 0, windows = 0;
     std::vector<long long> wbegin(n);
-    bool flat = true;
+    bool flat = true, walls = false;
     for (int i = 0; i < n; ++i) {
         lb_ctx* c = ctxs[i];
         Entry& E = ent[i];
@@ -647,6 +662,7 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
         E.inv_nx = 1.0f / (float)c->geom.nx;
         E.inv_ny = 1.0f / (float)c->geom.ny;
         flat = flat && c->geom.nx % GROUP_X == 0 && c->geom.V < (1LL << 24);
+        walls = walls || has_walls(c);
         wbegin[i] = windows;
         windows += (c->geom.V + 31) / 32;
         work[i].groups_x = c->geom.ntx;
@@ -665,6 +681,7 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
     b->total_bins = bins;
     b->steps_since_sort = SORT_EVERY;  // the first step sorts
     b->flat = flat;
+    b->walls = walls;
     b->total_windows = windows;
     // untuned: the flat collide 8 blocks per SM, the tiled one a block per item
     b->blocks = flat ? 152 * 8 : (int)std::min<long long>(std::max<long long>(groups, 1), 0x7fffffffLL);
