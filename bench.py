@@ -68,6 +68,31 @@ def committed_traffic(prec):
         return None
 
 
+def committed_fp64_mix():
+    """FP64 instructions and flops per site of k_collide<double> from the
+    committed ncu instruction-mix summary (None once the sources changed)."""
+    path = os.path.join(PROFILE_DIR, "k_collide_f64_160.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_sha") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["fp64_inst_per_site"]), float(vals["fp64_flop_per_site"])
+    except (KeyError, ValueError):
+        return None
+
+
+# FP64 peak from the nominal 1.25 TFLOP/s of GB300: 152 SMs x 2.07 GHz x 2
+# FP64 lanes per SM and clock x 2 flops per fused multiply-add.
+FP64_LANES_PER_SM_CLK = 2
+SM_COUNT, SM_MAX_HZ = 152, 2.07e9
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -369,6 +394,20 @@ def per_precision(L, steps_for):
                      "hbm_achieved_gbs": round(achieved, 1), "hbm_frac": round(achieved / peak, 4),
                      "bound": "alu (FP64 pipe)" if prec == "f64" else "hbm / issue",
                      "max_rel_velocity_vs_oracle": err, "error_steps": warm + steps}
+        if prec == "f64":
+            mix = committed_fp64_mix()
+            peak_inst = SM_COUNT * SM_MAX_HZ * FP64_LANES_PER_SM_CLK
+            if mix is not None:
+                inst, flop = mix
+                rate = inst * V / (coll * 1e-3)
+                out[prec]["alu"] = {"unit": "FP64 thread-instructions/s", "achieved": round(rate / 1e9, 1),
+                                    "peak": round(peak_inst / 1e9, 1), "frac": round(rate / peak_inst, 4),
+                                    "scale": "1e9", "inst_per_site": inst, "flop_per_site": flop,
+                                    "tflops": round(flop * V / (coll * 1e-3) / 1e12, 3),
+                                    "peak_tflops_nominal": round(2 * peak_inst / 1e12, 3),
+                                    "source": "profiles/k_collide_f64_160.txt"}
+            else:
+                out[prec]["alu"] = None
         for _, g in lats:
             g.close()
         torch.cuda.empty_cache()

@@ -439,15 +439,29 @@ template <> struct MomentumSum<float, true> {
 
 template <typename T, bool COMP>
 __device__ __forceinline__ Moments<T> moments19(const T f[NQ]) {
+    // pair sums (c, -c); then, in FP64 (bound by its arithmetic pipe), the
+    // diagonal pairs summed per plane and the diagonal second moments and
+    // rho from them (22 additions); in float and the packed pair (bound by
+    // bytes and issue, where the other order measured 0.6-2 % faster on
+    // GB300 at 256^3) each sum written out (30 additions)
     Moments<T> m;
     const T a12 = f[1] + f[2], a34 = f[3] + f[4], a56 = f[5] + f[6];
     const T d78 = f[7] + f[8], d910 = f[9] + f[10], d1112 = f[11] + f[12], d1314 = f[13] + f[14];
     const T d1516 = f[15] + f[16], d1718 = f[17] + f[18];
-    m.drho = f[0] + a12 + a34 + a56 + d78 + d910 + d1112 + d1314 + d1516 + d1718;
-    MomentumSum<T, COMP>::eval(f, m);
-    m.pxx = a12 + d78 + d910 + d1112 + d1314;
-    m.pyy = a34 + d78 + d910 + d1516 + d1718;
-    m.pzz = a56 + d1112 + d1314 + d1516 + d1718;
+    if constexpr (!std::is_same<T, double>::value) {
+        m.drho = f[0] + a12 + a34 + a56 + d78 + d910 + d1112 + d1314 + d1516 + d1718;
+        MomentumSum<T, COMP>::eval(f, m);
+        m.pxx = a12 + d78 + d910 + d1112 + d1314;
+        m.pyy = a34 + d78 + d910 + d1516 + d1718;
+        m.pzz = a56 + d1112 + d1314 + d1516 + d1718;
+    } else {
+        const T sxy = d78 + d910, sxz = d1112 + d1314, syz = d1516 + d1718;
+        MomentumSum<T, COMP>::eval(f, m);
+        m.pxx = (a12 + sxy) + sxz;
+        m.pyy = (a34 + sxy) + syz;
+        m.pzz = (a56 + sxz) + syz;
+        m.drho = ((f[0] + m.pxx) + (a34 + a56)) + syz;
+    }
     m.pxy = d78 - d910;
     m.pxz = d1112 - d1314;
     m.pyz = d1516 - d1718;
@@ -534,14 +548,27 @@ __device__ __forceinline__ void collide19(const T f[NQ], T Fx, T Fy, T Fz, const
                                           T is = T(1), T* v3 = nullptr) {
     using W = Wts<T>;
     constexpr bool PACKED = std::is_same<T, F2>::value;
+    // FP64 keeps 53 bits against the tolerance's 40, so it takes the same
+    // folded reconstruction as the 16-bit formats (fewer FP64 operations,
+    // each an issue of the SM's FP64 unit); FP32 keeps the ordering that
+    // rounds the momentum term once.
+    constexpr bool FOLD = PACKED || std::is_same<T, double>::value;
     const Moments<T> m = moments19<T, COMP>(f);
     const T third = T(1) / T(3);
     const T rho = T(1) + (SCALED ? m.drho * is : m.drho);
     T irho;
-    if constexpr (PACKED)  // the 16-bit formats: an approximate reciprocal, 2 ulp of float
+    if constexpr (PACKED) {  // the 16-bit formats: an approximate reciprocal, 2 ulp of float
         irho = F2(make_float2(__fdividef(1.0f, rho.v.x), __fdividef(1.0f, rho.v.y)));
-    else
+    } else if constexpr (std::is_same<T, double>::value) {
+        // Newton-Raphson from the float reciprocal (relative error e ->
+        // e^2 per step: 2^-23 -> 2^-46 -> below 2^-53), four FP64
+        // operations in place of a division
+        double r = (double)__frcp_rn((float)rho);
+        r = r * fma(-rho, r, 2.0);
+        irho = r * fma(-rho, r, 2.0);
+    } else {
         irho = T(1) / rho;
+    }
     if (VOUT) {
         const T iv = SCALED ? is * irho : irho;
         v3[0] = (m.jx + (COMP ? m.jx_lo + T(0.5) * Fx : T(0.5) * Fx)) * iv;
@@ -576,11 +603,12 @@ __device__ __forceinline__ void collide19(const T f[NQ], T Fx, T Fy, T Fz, const
             hz = W::w1 * (base + T(4.5) * bzz);
     // force density plus the low part of j: both are far smaller than j
     const T Gx = COMP ? Fx + m.jx_lo : Fx, Gy = COMP ? Fy + m.jy_lo : Fy, Gz = COMP ? Fz + m.jz_lo : Fz;
-    if constexpr (PACKED) {
+    if constexpr (FOLD) {
         // The 16-bit formats round their storage at 2^-11 (half) or 2^-8
         // (bfloat16) relative, far above the rounding of A = j + F in
-        // float, so the force is folded into j first and each population
-        // pair (c, -c) shares its odd part: out = even +- w A.c / c_s^2.
+        // float, and FP64 far below its tolerance, so the force is folded
+        // into j first and each population pair (c, -c) shares its odd
+        // part: out = even +- w A.c / c_s^2.
         const T Ax = m.jx + Gx, Ay = m.jy + Gy, Az = m.jz + Gz;
         const T ox = W::a1 * Ax, oy = W::a1 * Ay, oz = W::a1 * Az;
         put(out, 1, hx + ox);
