@@ -140,6 +140,18 @@ lb_status lb_num_points(const lb_ctx *ctx, int *n_out);
  * or device, in the order they were created); forces are kept. */
 lb_status lb_set_positions(lb_ctx *ctx, const double *pos);
 
+/* Host memory without waiting (default off).  With on != 0, a call that
+ * copies results into host memory (lb_velocity_at, lb_colloid_velocity,
+ * lb_moments, lb_particles, lb_get_populations) enqueues the copy on the
+ * context's stream and returns without waiting for it; host inputs are
+ * read by copies enqueued likewise.  The caller leaves every host buffer
+ * it passed untouched until lb_synchronize returns.  Host buffers should be
+ * page-locked (cudaHostAlloc, cudaHostRegister) for the copies to run
+ * asynchronously.  Calls that read a device status on the host
+ * (lb_add_point_forces, lb_set_positions with device positions, lb_save,
+ * ...) still wait. */
+lb_status lb_set_host_async(lb_ctx *ctx, int on);
+
 /* Advance nsteps >= 0 time steps.  Each step: spread the point forces at
  * their current positions, interpolate the velocity at each colloid and
  * move it (forward Euler, dt = 1), then collide and stream every site. */

@@ -102,7 +102,7 @@ lb_status finish(lb_ctx* c, Arg* args, int nargs, bool any_host) {
             LB_CUDA(cudaMemcpyAsync(const_cast<void*>(args[i].user), args[i].dev, args[i].bytes, cudaMemcpyDeviceToHost,
                                     c->stream),
                     "device-to-host copy");
-    if (any_host) LB_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+    if (any_host && !c->host_async) LB_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
     return LB_OK;
 }
 
@@ -407,6 +407,12 @@ lb_status lb_clear_point_forces(lb_ctx* c) {
 lb_status lb_num_points(const lb_ctx* c, int* n_out) {
     if (!c || !n_out) return LB_ERR_ARG;
     *n_out = c->npts;
+    return LB_OK;
+}
+
+lb_status lb_set_host_async(lb_ctx* c, int on) {
+    if (!c) return LB_ERR_ARG;
+    c->host_async = on != 0;
     return LB_OK;
 }
 

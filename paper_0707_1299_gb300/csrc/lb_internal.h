@@ -26,9 +26,11 @@ struct lb_ctx {
     void* f[2];               // population buffers (19 V elements of the storage type)
     int cur;                  // index of the buffer holding the current state
     void* floc;               // localised force field, 3 V elements of the arithmetic type
-    lbk::flag_t* flags;       // one byte per 32-site x-row tile: the tile holds spread force
-    void* vel;                // fluid velocity in the flagged tiles, 3 V elements of the
+    lbk::flag_t* flags;       // one byte per 8-site x-group (four per 32-site tile): the group
+                              // holds spread force
+    void* vel;                // fluid velocity in the flagged groups, 3 V elements of the
                               // arithmetic type (lattices with colloids only)
+    bool host_async;          // host-memory copies are not waited for (lb_set_host_async)
     bool field_ready;         // floc holds the forces at the current positions
     unsigned* fix_list;       // flagged tiles of a field of fixed points, then their count
     bool fix_ok;              // few fixed points, listed: collide field-free + fix-up

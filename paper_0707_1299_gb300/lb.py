@@ -33,7 +33,7 @@ EXPORTS = ["lb_create", "lb_destroy", "lb_last_error", "lb_set_body_force", "lb_
            "lb_colloid_velocity", "lb_mlp_num_params", "lb_mlp_create", "lb_mlp_destroy", "lb_mlp_last_error",
            "lb_mlp_get_params", "lb_mlp_set_params", "lb_mlp_features", "lb_mlp_forward", "lb_mlp_grad",
            "lb_mlp_train_step", "lb_set_colloid_correction", "lb_save", "lb_load",
-           "lb_mlp_set_wait_limit"]
+           "lb_mlp_set_wait_limit", "lb_set_host_async"]
 
 _lib = None
 
@@ -67,6 +67,7 @@ def load():
         "lb_num_points": ([vp, ip], ctypes.c_int),
         "lb_set_positions": ([vp, dp], ctypes.c_int),
         "lb_step": ([vp, ctypes.c_int], ctypes.c_int),
+        "lb_set_host_async": ([vp, ctypes.c_int], ctypes.c_int),
         "lb_velocity_at": ([vp, ctypes.c_int, dp, dp], ctypes.c_int),
         "lb_moments": ([vp, dp, dp, dp], ctypes.c_int),
         "lb_particles": ([vp, dp, dp], ctypes.c_int),
@@ -190,6 +191,10 @@ def lb_set_positions(ctx, pos):
 
 def lb_step(ctx, nsteps):
     _check(ctx, load().lb_step(ctx, int(nsteps)))
+
+
+def lb_set_host_async(ctx, on):
+    _check(ctx, load().lb_set_host_async(ctx, int(bool(on))))
 
 
 def lb_velocity_at(ctx, n, pos, v_out):

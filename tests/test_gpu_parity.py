@@ -313,6 +313,39 @@ def test_populations_roundtrip_and_host_pointers():
         g.close()
 
 
+def test_host_async_calls_match_waiting_calls():
+    # Host-async mode: positions in and velocities out through page-locked
+    # host buffers, one lb_synchronize per step; the results equal those of the
+    # waiting calls on a twin lattice, bit for bit.
+    lb = _lb()
+    grid = (24, 20, 16)
+    r = np.random.default_rng(8)
+    pos = r.uniform(0, 1, (6, 3)) * np.asarray(grid, float)
+    F = r.normal(0, 1e-5, (6, 3))
+    q = r.uniform(0, 1, (9, 3)) * np.asarray(grid, float)
+    a, b = (lb.Lattice(grid, 0.6, 0.7, lb.LB_F32) for _ in range(2))
+    for g in (a, b):
+        g.add_point_forces(lb.LB_STOKESLET, pos, F)
+    lb.lb_set_host_async(a.ctx, 1)
+    hp = torch.empty((6, 3), dtype=torch.float64).pin_memory()
+    hq = torch.as_tensor(q).pin_memory()
+    hv = torch.empty((9, 3), dtype=torch.float64).pin_memory()
+    for s in range(4):
+        p = pos + 0.25 * s
+        hp.copy_(torch.as_tensor(p))
+        lb.lb_set_positions(a.ctx, hp.numpy())
+        a.step(1)
+        lb.lb_velocity_at(a.ctx, 9, hq.numpy(), hv.numpy())
+        lb.lb_synchronize(a.ctx)
+        lb.lb_set_positions(b.ctx, np.ascontiguousarray(p))
+        b.step(1)
+        vb = np.empty((9, 3))
+        lb.lb_velocity_at(b.ctx, 9, np.ascontiguousarray(q), vb)
+        assert np.array_equal(hv.numpy(), vb)
+    a.close()
+    b.close()
+
+
 def test_argument_validation():
     lb = _lb()
     with pytest.raises(lb.LBError):
