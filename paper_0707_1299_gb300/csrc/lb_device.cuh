@@ -92,24 +92,11 @@ template <> struct Store<__half> {
     static __device__ __forceinline__ void st(__half* p, unsigned i, float v, unsigned rnd) {
         p[i] = __ushort_as_half(bits(v, rnd));
     }
-    // element h (0: low, 1: high half) of a 32-bit word holding two values
-    static __device__ __forceinline__ float unpack(unsigned w, int h) {
-        return __half2float(__ushort_as_half((unsigned short)(h ? w >> 16 : w & 0xFFFFu)));
-    }
     // both elements of a word
     static __device__ __forceinline__ float2 unpack2(unsigned w) {
         __half2 h;
         memcpy(&h, &w, sizeof(w));
         return __half22float2(h);
-    }
-    // stochastic rounding of two values into one word (lo: low half), one
-    // round-toward-zero conversion for the pair
-    static __device__ __forceinline__ unsigned bits2(float lo, float hi, unsigned rlo, unsigned rhi) {
-        const float a = __uint_as_float(__float_as_uint(lo) + (rlo >> 19));
-        const float b = __uint_as_float(__float_as_uint(hi) + (rhi >> 19));
-        unsigned r;
-        asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
-        return r;
     }
     // stochastic rounding of two values into one word by the conversion's
     // own stochastic-rounding mode (sm_100a and later): random bits 12:0 of
@@ -136,15 +123,8 @@ template <> struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ void st(__nv_bfloat16* p, unsigned i, float v, unsigned rnd) {
         p[i] = __ushort_as_bfloat16(bits(v, rnd));
     }
-    static __device__ __forceinline__ float unpack(unsigned w, int h) {
-        return __uint_as_float(h ? (w & 0xFFFF0000u) : (w << 16));
-    }
     static __device__ __forceinline__ float2 unpack2(unsigned w) {
         return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u));
-    }
-    static __device__ __forceinline__ unsigned bits2(float lo, float hi, unsigned rlo, unsigned rhi) {
-        const unsigned a = __float_as_uint(lo) + (rlo >> 16), b = __float_as_uint(hi) + (rhi >> 16);
-        return __byte_perm(a, b, 0x7632);  // the upper halves: (a >> 16) | (b & 0xffff0000)
     }
     // as Store<__half>::bits2_rs: random bits 15:0 dither lo, 31:16 hi
     static __device__ __forceinline__ unsigned bits2_rs(float lo, float hi, unsigned rb) {
