@@ -313,6 +313,39 @@ def test_populations_roundtrip_and_host_pointers():
         g.close()
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_moved_fixed_points_rebuild_their_field(prec):
+    # Fixed Stokeslets moved with lb_set_positions between steps (each move
+    # after a velocity query has spread the field, so the kept field must be
+    # cleared where it was flagged and spread anew), in a box with walls:
+    # field, query velocities and totals against the oracle, which spreads
+    # from its positions every step.
+    lb = _lb()
+    r = np.random.default_rng(12)
+    grid = (24, 18, 14)
+    pos0 = r.uniform(0, 1, (5, 3)) * np.asarray(grid, float)
+    F = r.normal(0, 1e-5, (5, 3))
+    prob = W.Problem("moved", grid, 0.55, 0.8, g=(1e-6, 0, 0), walls=(0, 13),
+                     points=[W.PointSet(W.STOKESLET, pos0, F, None)])
+    g = gpu_lattice(prob, {"f64": lb.LB_F64, "f32": lb.LB_F32}[prec])
+    o = oracle_lattice(prob)
+    q = r.uniform(0, 1, (7, 3)) * np.asarray(grid, float)
+    v = np.empty((7, 3))
+    for s in range(6):
+        lb.lb_velocity_at(g.ctx, 7, np.ascontiguousarray(q), v)  # spreads the field
+        new = np.mod(pos0 + np.array([0.37, -0.61, 0.29]) * (s + 1), np.asarray(grid, float))
+        lb.lb_set_positions(g.ctx, np.ascontiguousarray(new))
+        o.pos = new.astype(o.pos.dtype)
+        g.step(3)
+        o.step(3)
+    ref = o.observe(q)
+    _, u, _ = g.moments()
+    assert rel_err(u.cpu().numpy(), ref["u"]) < TOL[prec]
+    lb.lb_velocity_at(g.ctx, 7, np.ascontiguousarray(q), v)
+    assert rel_err(v, ref["qv"]) < TOL[prec]
+    g.close()
+
+
 def test_host_async_calls_match_waiting_calls():
     # Host-async mode: positions in and velocities out through page-locked
     # host buffers, one lb_synchronize per step; the results equal those of the
