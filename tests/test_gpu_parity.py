@@ -233,6 +233,31 @@ def test_colloids_reduced(prec):
     g.close()
 
 
+def test_colloids_1000_steps():
+    # The tolerances are stated after 1000 steps: the colloid recipe at the
+    # 1e5-in-512^3 number density in a 64^3 box (195 colloids), 1000 steps,
+    # FP64 and FP32 against one oracle run: velocity field and colloid
+    # displacements.
+    L = 64
+    n = int(round(1e5 * (L / 512) ** 3))
+    aL = oracle.aL_along((L, L, L), [L / 2] * 3, [0, 0, 1])
+    prob = W.colloids(L=L, n=n, seed=31, steps=1000, a_L=aL)
+    o = oracle_lattice(prob)
+    p0 = o.pos.copy()
+    o.step(prob.steps)
+    ref = o.observe()
+    d_ref = periodic_diff(o.pos, p0, prob.grid)
+    for prec in ("f64", "f32"):
+        g = gpu_lattice(prob, PREC_ID[prec])
+        g.step(prob.steps)
+        _, u, _ = g.moments()
+        p1, _ = g.particles()
+        assert rel_err(u.cpu().numpy(), ref["u"]) < TOL[prec], prec
+        d_gpu = periodic_diff(p1.cpu().numpy(), p0, prob.grid)
+        assert rel_err(d_gpu, d_ref) < disp_tol(prec, prob.grid, prob.steps, np.abs(d_ref).max()), prec
+        g.close()
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_colloids_cell_ordered(prec):
     # More than 2048 points take the cell-ordered path (sorted by 8^3
