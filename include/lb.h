@@ -294,10 +294,14 @@ lb_status lb_batch_create(lb_batch **out, int n, lb_ctx *const *ctxs, void *stre
 void lb_batch_destroy(lb_batch *batch);
 const char *lb_batch_last_error(const lb_batch *batch);
 
-/* Time the collide kernel of this batch for several grid sizes (persistent
- * grids of 2 to 16 blocks of 128 threads per SM, and one block per work
- * item), keep the fastest, report its block count in *blocks (may be NULL).  Leaves every member's state unchanged (it clears
- * a spread force field, which the next step spreads again). */
+/* Autotune the grid of the collide phase: time whole batch steps (every
+ * phase) for several grid sizes (persistent grids of 2 to 16 blocks of 128
+ * threads per SM, and for the tiled collide one block per work item), keep
+ * the fastest, report its block count in *blocks (may be NULL).  Leaves
+ * every member's state unchanged: the trial steps write only the spare
+ * population buffers, and the positions (and the stochastic-rounding
+ * counter) they move are put back; a force field spread by a query is
+ * cleared (the next step spreads again).  Waits for the batch's stream. */
 lb_status lb_batch_tune(lb_batch *batch, int *blocks);
 
 /* Advance every member nsteps >= 0 time steps (Sec. II-IV, as lb_step). */

@@ -746,9 +746,14 @@ const char* lb_batch_last_error(const lb_batch* b) { return b ? b->err.c_str() :
 
 lb_status lb_batch_tune(lb_batch* b, int* blocks_out) {
     if (!b) return LB_ERR_ARG;
-    // Side-effect free: the member fields are cleared first, so the collide
-    // kernel reads and writes no force tiles; it writes the spare buffer of
-    // every replica and leaves the state (current buffer) untouched.
+    // Whole trial steps are timed (spread, collide + stream, interpolation,
+    // update), since the collide's best grid depends on the phases around
+    // it.  A trial does not advance the batch: the parity is not flipped,
+    // so every trial reads the same current population buffers and writes
+    // the spare ones; the collide zeroes the force it consumed; the
+    // positions and the rounding counter the trials move are saved first
+    // and put back after the last trial.  A spread field of a query is
+    // cleared first (the next step spreads again).
     for (lb_ctx* c : b->ctx) {
         if (c->field_ready) {
             LB_BCUDA(lbk::launch_clear_field(c), "clear force field");
@@ -756,11 +761,38 @@ lb_status lb_batch_tune(lb_batch* b, int* blocks_out) {
         }
         LB_BCUDA(cudaStreamSynchronize(c->stream), "member stream");
     }
+    double* saved_pos = nullptr;
+    unsigned* saved_step = nullptr;
+    LB_BCUDA(cudaMalloc(&saved_step, sizeof(unsigned)), "tuner scratch");
+    if (b->total_pts > 0) {
+        cudaError_t e = cudaMalloc(&saved_pos, sizeof(double) * 3 * (size_t)b->total_pts);
+        if (e != cudaSuccess) {
+            cudaFree(saved_step);
+            return bfail(b, LB_ERR_OOM, "tuner scratch");
+        }
+    }
+    const auto copy_positions = [&](bool save) -> cudaError_t {
+        size_t off = 0;
+        for (lb_ctx* c : b->ctx) {
+            if (c->npts == 0) continue;
+            const size_t bytes = sizeof(double) * 3 * (size_t)c->npts;
+            cudaError_t e = save ? cudaMemcpyAsync(saved_pos + off, c->pos, bytes, cudaMemcpyDeviceToDevice, b->stream)
+                                 : cudaMemcpyAsync(c->pos, saved_pos + off, bytes, cudaMemcpyDeviceToDevice, b->stream);
+            if (e != cudaSuccess) return e;
+            off += 3 * (size_t)c->npts;
+        }
+        return save ? cudaMemcpyAsync(saved_step, b->d_step, sizeof(unsigned), cudaMemcpyDeviceToDevice, b->stream)
+                    : cudaMemcpyAsync(b->d_step, saved_step, sizeof(unsigned), cudaMemcpyDeviceToDevice, b->stream);
+    };
+    cudaError_t err = copy_positions(true);
+    // the stencil rows and the cell order of the current positions
+    if (err == cudaSuccess) err = launch_stencils_any(b);
+    if (err == cudaSuccess && b->total_pts > 0) err = launch_sort(b);
     int best = b->blocks;
     float best_ms = 1e30f;
-    cudaEvent_t t0, t1;
-    LB_BCUDA(cudaEventCreate(&t0), "event");
-    LB_BCUDA(cudaEventCreate(&t1), "event");
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (err == cudaSuccess) err = cudaEventCreate(&t0);
+    if (err == cudaSuccess) err = cudaEventCreate(&t1);
     // candidates: persistent grids of 2-16 blocks per SM (contiguous chunks of
     // work per block or warp), and for the tiled collide one block per work
     // item (no persistence)
@@ -768,25 +800,31 @@ lb_status lb_batch_tune(lb_batch* b, int* blocks_out) {
     const long long per_sm_flat[] = {4, 6, 8, 12, 16};
     const long long* per_sm = b->flat ? per_sm_flat : per_sm_tiled;
     const long long items = b->flat ? (b->total_windows + 3) / 4 : b->total_groups;
-    for (int ci = 0; ci < 5; ++ci) {
+    for (int ci = 0; ci < 5 && err == cudaSuccess; ++ci) {
         const long long k = per_sm[ci];
         const long long want = k ? 152LL * k : std::min<long long>(items, 0x7fffffffLL);
         const int blocks = (int)std::min<long long>(want, std::max<long long>(1, items));
-        LB_BCUDA(launch_collide_any(b, blocks), "tune launch");  // warm
-        LB_BCUDA(cudaEventRecord(t0, b->stream), "event");
-        for (int r = 0; r < 3; ++r) LB_BCUDA(launch_collide_any(b, blocks), "tune launch");
-        LB_BCUDA(cudaEventRecord(t1, b->stream), "event");
-        LB_BCUDA(cudaEventSynchronize(t1), "event");
+        err = launch_step_any(b, b->parity, blocks);  // warm
+        if (err == cudaSuccess) err = cudaEventRecord(t0, b->stream);
+        for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = launch_step_any(b, b->parity, blocks);
+        if (err == cudaSuccess) err = cudaEventRecord(t1, b->stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(t1);
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, t0, t1);
-        if (ms < best_ms) {
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, t0, t1);
+        if (err == cudaSuccess && ms < best_ms) {
             best_ms = ms;
             best = blocks;
         }
-        b->launches += 4;
+        b->launches += 4LL * launches_per_step(b);
     }
-    cudaEventDestroy(t0);
-    cudaEventDestroy(t1);
+    if (err == cudaSuccess) err = copy_positions(false);
+    if (err == cudaSuccess) err = launch_stencils_any(b);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(b->stream);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    cudaFree(saved_pos);
+    cudaFree(saved_step);
+    if (err != cudaSuccess) return bfail(b, LB_ERR_CUDA, std::string("lb_batch_tune: ") + cudaGetErrorString(err));
     if (best != b->blocks && b->graph_ready) {
         cudaGraphExecDestroy(b->graph2);
         b->graph_ready = false;
