@@ -260,8 +260,8 @@ def run_gpu(args, rank, world):
     launches = sum(g.kernel_launches() for _, g in lats) - launches0
     # lb_step(1) of the channel lattice (no points) launches exactly one
     # kernel, k_collide: its events time that kernel alone.  The point
-    # lattices' lb_step(1) also clears their force tiles (their points were
-    # spread by the preceding lb_velocity_at), reported beside it.
+    # lattices' lb_step(1) runs the field-free collide and the fix-up of
+    # the few tiles their fixed points flag, reported beside it.
     per_lat = [float(np.mean([ev[s][k][0].elapsed_time(ev[s][k][1]) for s in range(args.steps)]))
                for k in range(len(lats))]
     coll_ms = per_lat[0]

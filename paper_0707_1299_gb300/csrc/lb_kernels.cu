@@ -146,8 +146,8 @@ __global__ void k_stencil(int n, const double* __restrict__ pos, T* __restrict__
 // ------------------------------------------------------------- k_interp
 // Velocity at every point, v(R) = sum over the 64 stencil nodes of phi phi
 // phi v (Sec. IV), from the velocity field the collide kernel wrote in the
-// flagged tiles (every fluid stencil node of a point lies in one: the
-// spread flagged it).  One warp per point, in cell order; lane l takes
+// flagged 8-site groups (every fluid stencil node of a point lies in one:
+// the spread flagged it).  One warp per point, in cell order; lane l takes
 // nodes l and l + 32; lanes 0-2 write v[3 s + a] (FP64).
 template <typename T, bool WALLS>
 __global__ void __launch_bounds__(256)
