@@ -275,10 +275,12 @@ lb_status lb_set_colloid_correction(lb_ctx *ctx, lb_mlp *net);
  * Batches: independent lattices (replicas of uneven sizes, e.g. many small
  * sedimentation boxes) advanced together.  Each phase of a time step
  * (spreading, colloid update, collide + stream) is one launch over all
- * members -- the collide + stream phase walks one work list of 4 x 32-site
- * tiles over every member, in a grid shape picked by lb_batch_tune -- and
- * two steps are replayed
- * from a CUDA graph.  The method per member is exactly that of lb_step.
+ * members -- the collide + stream phase walks the 32-site windows of every
+ * member's flat site index (every nx a multiple of 8, fewer than 2^24
+ * sites a member) or else a work list of 4 x 32-site tiles, in a grid
+ * picked by lb_batch_tune -- and two steps are replayed from a CUDA graph.
+ * The colloids are taken in cell order, renewed every 64 steps.  The
+ * method per member is exactly that of lb_step.
  * --------------------------------------------------------------------- */
 typedef struct lb_batch lb_batch;
 
