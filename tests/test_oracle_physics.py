@@ -116,6 +116,45 @@ def test_stokeslet_fourier_modes_c1():
             assert np.abs(sim - th).max() < tol * np.abs(th).max()
 
 
+@pytest.mark.parametrize("kind", ["stresslet", "rotlet"])
+def test_multipole_fourier_modes(kind):
+    # The same unsteady Stokes response (Eq. oseen) for the force pairs and
+    # quartets of Sec. III: the velocity's solenoidal low Fourier modes
+    # against (1 - e^{-eta k^2 T}) P F(k) / (eta k^2), F(k) the exact
+    # lattice transform of the spread multipole (32^3, 600 steps).  Modes
+    # the multipole hardly drives (below a tenth of the largest) are left out.
+    L, tau, T = 32, 0.5, 600
+    eta = tau / 3
+    R = np.array([16.3, 15.7, 16.45])
+    k_id = {"stresslet": oracle.STRESSLET, "rotlet": oracle.ROTLET}[kind]
+    Fv = np.array([2e-5, -1e-5, 6e-5])
+    lb = oracle.OracleLB((L, L, L), tau, tau)
+    lb.add_points(k_id, R, Fv, [2.0])
+    lb.step(T)
+    u = lb.observe()["u"]
+    uk = np.fft.fftn(u, axes=(1, 2, 3))
+    P_, f_, _, _ = oracle.expand_points(k_id, R, Fv, [2.0])
+    Fk = np.fft.fftn(oracle.force_field((L, L, L), P_, f_), axes=(1, 2, 3))
+    modes = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1), (0, 1, 1), (1, 1, 1), (2, 1, 0),
+             (0, 2, 1), (1, 0, 2)]
+    ths, sims = [], []
+    for n in modes:
+        kv = 2 * np.pi * np.array(n) / L
+        k2 = kv @ kv
+        P = np.eye(3) - np.outer(kv, kv) / k2
+        idx = (slice(None), n[2] % L, n[1] % L, n[0] % L)
+        ths.append((1 - np.exp(-eta * k2 * T)) / (eta * k2) * (P @ Fk[idx]))
+        sims.append(P @ uk[idx])
+    big = max(np.abs(t).max() for t in ths)
+    tested = 0
+    for th, sim in zip(ths, sims):
+        if np.abs(th).max() < 0.1 * big:
+            continue
+        assert np.abs(sim - th).max() < 0.02 * np.abs(th).max()
+        tested += 1
+    assert tested >= 5
+
+
 def test_conservation_mass_momentum():
     # Eq. (conservation): total mass is constant; the momentum of the
     # physical distribution grows by the net force each step,
