@@ -16,6 +16,7 @@
 
 #include "../../include/lb.h"
 #include "lb_internal.h"
+#include "lb_points.cuh"
 
 namespace {
 
@@ -322,7 +323,7 @@ __global__ void kb_stencil(const Entry* __restrict__ ent, const long long* __res
     const int e = pent[gp];
     const Entry& E = ent[e];
     const int s = (int)(gp - pbegin[e]);
-    write_stencil<T>(st + gp * ST_W, E.pos[3 * s], E.pos[3 * s + 1], E.pos[3 * s + 2]);
+    stencil_row<T>(st + gp * ST_W, E.pos[3 * s], E.pos[3 * s + 1], E.pos[3 * s + 2]);
 }
 
 __global__ void kb_tick(unsigned* step_counter) { *step_counter += 1u; }
@@ -415,7 +416,7 @@ __global__ void kb_update(const Entry* __restrict__ ent, const long long* __rest
     const int s = (int)(gp - pbegin[e]);
     double P[3] = {E.pos[3 * s], E.pos[3 * s + 1], E.pos[3 * s + 2]};
     if (E.mobile[s]) {
-        const double c = (1.0 / E.radius[s] - E.inv_aL) * E.inv_6pi_eta;
+        const double c = (recip_fp64(E.radius[s]) - E.inv_aL) * E.inv_6pi_eta;
         const int nn[3] = {E.g.nx, E.g.ny, E.g.nz};
         for (int a = 0; a < 3; ++a) {
             const double L = (double)nn[a];
@@ -430,7 +431,7 @@ __global__ void kb_update(const Entry* __restrict__ ent, const long long* __rest
             E.pos[3 * s + a] = r;
         }
     }
-    write_stencil<T>(st + gp * ST_W, P[0], P[1], P[2]);
+    stencil_row<T>(st + gp * ST_W, P[0], P[1], P[2]);
 }
 
 }  // namespace

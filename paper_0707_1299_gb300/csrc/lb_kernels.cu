@@ -21,6 +21,7 @@
 
 #include "../../include/lb.h"
 #include "lb_internal.h"
+#include "lb_points.cuh"
 
 namespace lbk {
 
@@ -140,7 +141,7 @@ template <typename T>
 __global__ void k_stencil(int n, const double* __restrict__ pos, T* __restrict__ st) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
-    write_stencil<T>(st + (size_t)t * ST_W, pos[3 * t], pos[3 * t + 1], pos[3 * t + 2]);
+    stencil_row<T>(st + (size_t)t * ST_W, pos[3 * t], pos[3 * t + 1], pos[3 * t + 2]);
 }
 
 // ------------------------------------------------------------- k_interp
@@ -199,10 +200,11 @@ __global__ void k_update(int n, double* __restrict__ pos, const double* __restri
     double P[3] = {pos[3 * t], pos[3 * t + 1], pos[3 * t + 2]};
     if (mobile[t]) {
         const int nn[3] = {g.nx, g.ny, g.nz};
-        const double c = (1.0 / a[t] - inv_aL) * inv_6pi_eta;
+        const double ia = recip_fp64(a[t]);
+        const double c = (ia - inv_aL) * inv_6pi_eta;
         if (y) {
             const double f0 = F[3 * t], f1 = F[3 * t + 1], f2 = F[3 * t + 2];
-            const double v0 = sqrt(f0 * f0 + f1 * f1 + f2 * f2) * inv_6pi_eta / a[t];
+            const double v0 = sqrt(f0 * f0 + f1 * f1 + f2 * f2) * inv_6pi_eta * ia;
             for (int k = 0; k < 3; ++k)
                 P[k] = wrap_step(P[k] + v[3 * t + k] + F[3 * t + k] * c + (double)y[3 * t + k] * v0, nn[k]);
         } else {
@@ -210,7 +212,7 @@ __global__ void k_update(int n, double* __restrict__ pos, const double* __restri
         }
         for (int k = 0; k < 3; ++k) pos[3 * t + k] = P[k];
     }
-    write_stencil<T>(st + (size_t)t * ST_W, P[0], P[1], P[2]);
+    stencil_row<T>(st + (size_t)t * ST_W, P[0], P[1], P[2]);
 }
 
 // ------------------------------------------------------------- k_gather
