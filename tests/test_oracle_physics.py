@@ -49,6 +49,34 @@ def _startup_series(z, t, g, nu, H, M=4001):
     return u
 
 
+@pytest.mark.parametrize("tau_b", [0.5, 2.0])
+def test_sound_damping_bulk_rate(tau_b):
+    # Reading A5: the trace of the stress relaxes at 1/(tau_b + 1/2), a bulk
+    # viscosity zeta = (2/3) rho c_s^2 tau_b beside eta = rho c_s^2 tau_s.
+    # A standing sound wave (density cos(kx), at rest) then decays at the
+    # linearised Navier-Stokes rate Gamma = (k^2 / 2 rho)(4 eta / 3 + zeta)
+    # = k^2 c_s^2 (2 tau_s + tau_b) / 3 (64 sites, to 1 %; relaxing the
+    # trace at the shear rate instead would miss tau_b = 2 by 40 %).
+    from scipy.signal import hilbert
+    L, tau_s = 64, 0.5
+    lb = oracle.OracleLB((L, 1, 1), tau_s, tau_b)
+    c, w = oracle.lattice()
+    x = np.arange(L)
+    k = 2 * np.pi / L
+    for i in range(19):
+        lb.df[i, 0, 0, :] = w[i] * 1e-5 * np.cos(k * x)
+    T = int(6 * L / np.sqrt(1 / 3))
+    amp = np.empty(T)
+    for t in range(T):
+        amp[t] = 2 * np.mean((lb.observe()["rho"][0, 0, :] - 1) * np.cos(k * x))
+        lb.step(1)
+    env = np.abs(hilbert(amp))
+    t = np.arange(T)
+    sel = slice(T // 5, 4 * T // 5)
+    gamma = -np.polyfit(t[sel], np.log(env[sel]), 1)[0]
+    assert abs(gamma / (k * k / 9 * (2 * tau_s + tau_b)) - 1) < 0.01
+
+
 def test_poiseuille_steady_curvature_and_slip():
     # Body-force channel between halfway bounce-back walls: at steady state
     # the second difference of u in the bulk is exactly -g/nu, and the
