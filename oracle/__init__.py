@@ -154,15 +154,29 @@ class OracleLB:
         p.a_L = self.a_L
         return p
 
-    def step(self, nsteps: int = 1):
+    def step(self, nsteps: int = 1, net=None):
+        """Advance nsteps.  With `net` (parameters of the correction network,
+        the dict of ``mlp.unflatten``) every step first evaluates the
+        network on the features of the positions at the start of the step
+        (``mlp.features``, ``mlp.forward`` with bfloat16 operands) and moves
+        each colloid by its Sec. IV velocity plus y |F| / (6 pi eta a)."""
         lib, _, pre = _lib.load(self.precision)
         p = self._params()
-        rc = getattr(lib, pre + "run")(
-            p, _lib.ptr(self.df, self.precision), len(self.mobile),
-            _lib.ptr(self.pos, self.precision), _lib.ptr(self.f, self.precision),
-            _lib.ptr(self.mobile), _lib.ptr(self.radius, self.precision), int(nsteps))
-        if rc != 0:
-            raise MemoryError("oracle run failed to allocate")
+        run = getattr(lib, pre + "run")
+        args = lambda y, k: (p, _lib.ptr(self.df, self.precision), len(self.mobile),
+                             _lib.ptr(self.pos, self.precision), _lib.ptr(self.f, self.precision),
+                             _lib.ptr(self.mobile), _lib.ptr(self.radius, self.precision),
+                             _lib.ptr(y, self.precision), int(k))
+        if net is None:
+            if run(*args(None, nsteps)) != 0:
+                raise MemoryError("oracle run failed to allocate")
+            return
+        from . import mlp
+        for _ in range(int(nsteps)):
+            y, _ = mlp.forward(net, mlp.features(np.asarray(self.pos, dtype=np.float64), self.n), bf16_round=True)
+            y = np.ascontiguousarray(y, dtype=self.R)
+            if run(*args(y, 1)) != 0:
+                raise MemoryError("oracle run failed to allocate")
 
     def observe(self, qpos=None, fields=True):
         """rho (nz,ny,nx), u (3,nz,ny,nx), velocities at qpos (m,3) and

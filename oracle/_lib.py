@@ -79,7 +79,7 @@ def load(kind: str = "double"):
         fn("force_field").argtypes = [P(Params), ctypes.c_int, P(R), P(R), P(R)]
         fn("force_field").restype = None
         fn("run").argtypes = [P(Params), P(R), ctypes.c_int, P(R), P(R), P(ctypes.c_int),
-                              P(R), ctypes.c_int]
+                              P(R), P(R), ctypes.c_int]
         fn("run").restype = ctypes.c_int
         fn("observe").argtypes = [P(Params), P(R), ctypes.c_int, P(R), P(R), P(R), P(R),
                                   ctypes.c_int, P(R), P(R), P(R)]

@@ -335,11 +335,17 @@ static void interp(const orc_params *p, const real *u, const real *R, real *out)
 /* Advance `nsteps` time steps.  df (19*V, SoA df[i*V + site]) holds the
  * post-collision state df* on entry and on exit.  Points: pos/f are 3*npts
  * (xyz interleaved); points with mobile[s] != 0 are colloids of radius
- * radius[s] and move; the others are fixed.  Returns 0, or -1 on allocation
- * failure. */
+ * radius[s] and move; the others are fixed.
+ * ycorr (3*npts, or NULL): the learned correction of the colloid velocity
+ * in units of v0 = |f_s| / (6 pi eta a_s); a colloid then moves by its
+ * Sec. IV velocity plus ycorr_s v0.  The correction is a function of the
+ * positions at the start of the step, so with ycorr the call advances one
+ * step (nsteps must be 1).  Not part of the paper.
+ * Returns 0, -1 on allocation failure, -2 for ycorr with nsteps != 1. */
 int SYM(run)(const orc_params *p, real *df, int npts, real *pos, const real *f,
-             const int *mobile, const real *radius, int nsteps)
+             const int *mobile, const real *radius, const real *ycorr, int nsteps)
 {
+    if (ycorr && nsteps != 1) return -2;
     long V = (long)p->n[0] * p->n[1] * p->n[2];
     real *fs = malloc(sizeof(real) * NQ * V);
     real *F = malloc(sizeof(real) * 3 * V);
@@ -361,8 +367,16 @@ int SYM(run)(const orc_params *p, real *df, int npts, real *pos, const real *f,
             real vR[3];
             interp(p, u, &pos[3 * s], vR);
             real c = (1 / radius[s] - 1 / p->a_L) / (6 * pi * eta);
-            for (int a = 0; a < 3; ++a)
-                pos[3 * s + a] = wrapr(pos[3 * s + a] + vR[a] + f[3 * s + a] * c, p->n[a]);
+            real v0 = 0; /* velocity unit of the learned correction */
+            if (ycorr) {
+                real fn = R_SQRT(f[3 * s] * f[3 * s] + f[3 * s + 1] * f[3 * s + 1] + f[3 * s + 2] * f[3 * s + 2]);
+                v0 = fn / (6 * pi * eta * radius[s]);
+            }
+            for (int a = 0; a < 3; ++a) {
+                real X = pos[3 * s + a] + vR[a] + f[3 * s + a] * c;
+                if (ycorr) X += ycorr[3 * s + a] * v0;
+                pos[3 * s + a] = wrapr(X, p->n[a]);
+            }
         }
 #pragma omp parallel for schedule(static)       /* 5 */
         for (int z = 0; z < p->n[2]; ++z)
