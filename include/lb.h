@@ -181,6 +181,21 @@ lb_status lb_set_populations(lb_ctx *ctx, const double *df);
  * count kept on the host; copies and memsets are not counted). */
 lb_status lb_kernel_launches(const lb_ctx *ctx, long long *count);
 
+/* Phase timing of lb_step, for measurement (not part of the paper).  With
+ * on != 0 every lb_step records a pair of CUDA events on the context's
+ * stream around each phase of each step; lb_phase_times waits for the
+ * stream and returns, per phase, the summed elapsed time in milliseconds
+ * (ms, 5 doubles, host) and the number of timed occurrences (counts, 5
+ * long longs, host, may be NULL) since the last call, then recycles the
+ * events.  Phases: 0 spreading (with the stencil rows and the periodic
+ * cell-order sort when they run), 1 collide + stream, 2 interpolation,
+ * 3 colloid update, 4 learned correction (features and forward).  The
+ * events are host-side objects: no device memory is allocated.  Turning
+ * timing off waits for the stream and discards unread pairs.  LB_ERR_STATE
+ * if a step failed between the two events of a pair. */
+lb_status lb_set_phase_timing(lb_ctx *ctx, int on);
+lb_status lb_phase_times(lb_ctx *ctx, double ms[5], long long counts[5]);
+
 /* Checkpoint of the whole state of a context: lattice parameters, the
  * expanded point list (positions, forces, radii, mobility), the populations
  * of the current step in the storage format (raw bytes: the restored state
@@ -336,11 +351,17 @@ lb_status lb_batch_info(const lb_batch *batch, long long *sites, long long *poin
  *             not wait for them.
  * Scratch: a library-wide static device array of 1024 x 4 doubles
  * (32 KiB) that every GPU using the library keeps until the process
- * exits.  The first call on a device looks its address up (with that
- * device current) and should come before any stream capture.  All calls
- * share the array; calls whose kernels overlap on the GPU race on it.
+ * exits.  Its device address is looked up (with the device current) by
+ * every call whose stream is not capturing, so a device reset or a new
+ * context never leaves a stale address; a call on a capturing stream
+ * reuses the address found by the last such lookup on that device, so the
+ * first call on a device should come before any stream capture (else
+ * LB_ERR_STATE).  All calls share the array; calls whose kernels overlap
+ * on the GPU race on it.
  * Errors: LB_ERR_ARG (NULL pointer, bad precision, grid or plane, or a
- * lattice beyond the limit above), LB_ERR_NONFINITE (F), LB_ERR_CUDA.
+ * lattice beyond the limit above), LB_ERR_NONFINITE (F), LB_ERR_STATE,
+ * LB_ERR_CUDA.  The pointers are trusted: df must hold 19 V elements of
+ * the storage type and totals 4 doubles, both in device memory.
  * Does not call cudaMalloc, cudaFree or any allocating routine, and does
  * not touch lb_last_error. */
 lb_status lb_totals_noalloc(const void *df, int precision, const int grid[3], int z_lo, int z_hi,

@@ -212,6 +212,45 @@ lb_status ensure_vel(lb_ctx* c) {
     return LB_OK;
 }
 
+// Phase timing: an event recorded on the context's stream before and after
+// the launches of one phase of a step.
+enum { PH_SPREAD = 0, PH_COLLIDE, PH_INTERP, PH_UPDATE, PH_CORRECTION, PH_COUNT };
+
+lb_status phase_event(lb_ctx* c, cudaEvent_t* ev) {
+    if (!c->ev_free.empty()) {
+        *ev = c->ev_free.back();
+        c->ev_free.pop_back();
+    } else {
+        LB_CUDA(cudaEventCreate(ev), "timing event");
+    }
+    LB_CUDA(cudaEventRecord(*ev, c->stream), "timing event record");
+    return LB_OK;
+}
+
+lb_status phase_begin(lb_ctx* c, int phase) {
+    if (!c->phase_timing) return LB_OK;
+    cudaEvent_t e;
+    lb_status s = phase_event(c, &e);
+    if (s != LB_OK) return s;
+    c->mark_phase.push_back(phase);
+    c->mark_ev.push_back(e);
+    return LB_OK;
+}
+
+lb_status phase_end(lb_ctx* c) {
+    if (!c->phase_timing) return LB_OK;
+    cudaEvent_t e;
+    lb_status s = phase_event(c, &e);
+    if (s == LB_OK) c->mark_ev.push_back(e);
+    return s;
+}
+
+void drop_phase_events(lb_ctx* c) {
+    for (cudaEvent_t e : c->mark_ev) c->ev_free.push_back(e);
+    c->mark_ev.clear();
+    c->mark_phase.clear();
+}
+
 }  // namespace
 
 extern "C" {
@@ -309,6 +348,8 @@ void lb_destroy(lb_ctx* c) {
     cudaFree(c->corr_feat);
     cudaFree(c->corr_y);
     cudaFree(c->corr_ws);
+    drop_phase_events(c);
+    for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
     delete c;
 }
 
@@ -499,24 +540,40 @@ lb_status lb_step(lb_ctx* c, int nsteps) {
     // stencil rows of R^{n+1}.  With mobile colloids the collide zeroes the
     // force it consumed; fixed points alone keep their field from step to
     // step.
+#define LB_PHASE(call)                       \
+    do {                                     \
+        lb_status ps_ = (call);              \
+        if (ps_ != LB_OK) return ps_;        \
+    } while (0)
     for (int s = 0; s < nsteps; ++s) {
+        LB_PHASE(phase_begin(c, PH_SPREAD));
         lb_status st = ensure_field(c);
         if (st != LB_OK) return st;
+        LB_PHASE(phase_end(c));
         const bool corrected = c->n_mobile > 0 && c->corr;
         if (corrected) {  // the network's inputs depend on R^n only
+            LB_PHASE(phase_begin(c, PH_CORRECTION));
             LB_CUDA(lbk::mlp_features(c->npts, c->pos, box, c->corr_feat, c->corr_ws, c->stream), "feature kernels");
             LB_CUDA(lbk::mlp_forward(c->corr, c->npts, c->corr_feat, c->corr_y, c->stream), "forward kernel");
             c->launches += lbk::MLP_FEATURE_LAUNCHES + 1;
+            LB_PHASE(phase_end(c));
         }
+        LB_PHASE(phase_begin(c, PH_COLLIDE));
         LB_CUDA(lbk::launch_collide(c), "collide-stream kernel");
+        LB_PHASE(phase_end(c));
         c->cur ^= 1;
         if (c->n_mobile > 0) {
+            LB_PHASE(phase_begin(c, PH_INTERP));
             LB_CUDA(lbk::launch_interp(c), "interpolation kernel");
+            LB_PHASE(phase_end(c));
+            LB_PHASE(phase_begin(c, PH_UPDATE));
             LB_CUDA(lbk::launch_update(c, corrected ? c->corr_y : nullptr), "colloid update kernel");
+            LB_PHASE(phase_end(c));
             c->field_ready = false;  // the collide zeroed the consumed field and flags
             if (++c->steps_since_sort >= SORT_INTERVAL) c->order_stale = true;
         }
     }
+#undef LB_PHASE
     return LB_OK;
 }
 
@@ -726,9 +783,20 @@ lb_status lb_load(lb_ctx* c, const char* path) {
         return fail(c, LB_ERR_ARG, "lb_load: not a checkpoint file");
     }
     if (h.grid[0] != c->geom.nx || h.grid[1] != c->geom.ny || h.grid[2] != c->geom.nz || h.prec != c->prec ||
-        h.pop_bytes != pop_bytes || h.npts < 0 || h.n_mobile < 0 || h.n_mobile > h.npts) {
+        h.pop_bytes != pop_bytes) {
         fclose(f);
         return fail(c, LB_ERR_ARG, "lb_load: checkpoint of another grid or precision");
+    }
+    // A file written by another build or tool can carry an intact digest
+    // and still hold values that the kernels would index with: the header
+    // and (below) the point block get the checks the setters apply.
+    if (h.npts < 0 || (long long)h.npts >= (1LL << 31) / 64 || h.n_mobile < 0 || h.n_mobile > h.npts ||
+        h.wall_lo < -1 || h.wall_lo >= c->geom.nz || h.wall_hi < -1 || h.wall_hi >= c->geom.nz ||
+        !(h.tau_s > 0) || !(h.tau_b > 0) || !isfinite(h.tau_s) || !isfinite(h.tau_b) || !(h.a_L > 0) ||
+        isnan(h.a_L) || !isfinite(h.g[0]) || !isfinite(h.g[1]) || !isfinite(h.g[2]) ||
+        (h.counter != 0 && h.counter != 1) || h.scale != c->scale || h.inv_scale != c->inv_scale) {
+        fclose(f);
+        return fail(c, LB_ERR_ARG, "lb_load: checkpoint header out of range");
     }
     const size_t n = (size_t)h.npts;
     std::string pts;
@@ -740,7 +808,31 @@ lb_status lb_load(lb_ctx* c, const char* path) {
                     fread(&digest, sizeof(digest), 1, f) == 1 && digest == hash.h;
     fclose(f);
     if (!ok) return fail(c, LB_ERR_ARG, "lb_load: truncated or corrupt checkpoint");
-    // the file is complete and intact: replace the state
+    {  // positions finite and inside [0, n), forces finite, radius > 0 and mobile flag 1 for colloids only
+        const double* P = (const double*)pts.data();
+        const double* Fp = P + 3 * n;
+        const double* Rd = P + 6 * n;
+        int* Mb = (int*)(P + 7 * n);
+        const int nn[3] = {c->geom.nx, c->geom.ny, c->geom.nz};
+        int mobile = 0;
+        for (size_t k = 0; k < n; ++k) {
+            int mb;
+            memcpy(&mb, Mb + k, sizeof(int));
+            double rad;
+            memcpy(&rad, Rd + k, sizeof(double));
+            bool good = (mb == 0 || mb == 1) && isfinite(rad) && (mb ? rad > 0 : rad >= 0);
+            for (int a = 0; a < 3 && good; ++a) {
+                double x, F;
+                memcpy(&x, P + 3 * k + a, sizeof(double));
+                memcpy(&F, Fp + 3 * k + a, sizeof(double));
+                good = isfinite(x) && x >= 0.0 && x < (double)nn[a] && isfinite(F);
+            }
+            if (!good) return fail(c, LB_ERR_ARG, "lb_load: checkpoint point block out of range");
+            mobile += mb;
+        }
+        if (mobile != h.n_mobile) return fail(c, LB_ERR_ARG, "lb_load: checkpoint mobile count mismatch");
+    }
+    // the file is complete, intact and in range: replace the state
     lb_status s = invalidate_field(c);
     if (s == LB_OK) s = grow_points(c, std::max(h.npts, 1));
     if (s != LB_OK) return s;
@@ -778,6 +870,42 @@ lb_status lb_load(lb_ctx* c, const char* path) {
     LB_CUDA(cudaMemcpyAsync(c->fsum_host, c->fsum, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream),
             "force sum read");
     LB_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+    return LB_OK;
+}
+
+lb_status lb_set_phase_timing(lb_ctx* c, int on) {
+    if (!c) return LB_ERR_ARG;
+    c->phase_timing = on != 0;
+    if (!c->phase_timing) {
+        LB_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+        drop_phase_events(c);
+    }
+    return LB_OK;
+}
+
+lb_status lb_phase_times(lb_ctx* c, double ms[5], long long counts[5]) {
+    if (!c || !ms) return LB_ERR_ARG;
+    LB_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+    for (int p = 0; p < PH_COUNT; ++p) {
+        ms[p] = 0.0;
+        if (counts) counts[p] = 0;
+    }
+    const size_t n = c->mark_phase.size();
+    if (c->mark_ev.size() != 2 * n) {  // a step failed between a begin and its end
+        drop_phase_events(c);
+        return fail(c, LB_ERR_STATE, "lb_phase_times: unpaired timing events (a step failed)");
+    }
+    for (size_t k = 0; k < n; ++k) {
+        float t = 0.0f;
+        cudaError_t e = cudaEventElapsedTime(&t, c->mark_ev[2 * k], c->mark_ev[2 * k + 1]);
+        if (e != cudaSuccess) {
+            drop_phase_events(c);
+            return cuda_fail(c, e, "timing event read");
+        }
+        ms[c->mark_phase[k]] += (double)t;
+        if (counts) counts[c->mark_phase[k]]++;
+    }
+    drop_phase_events(c);
     return LB_OK;
 }
 

@@ -541,8 +541,8 @@ __device__ __forceinline__ void collide19(const T f[NQ], T Fx, T Fy, T Fz, const
         irho = F2(make_float2(__fdividef(1.0f, rho.v.x), __fdividef(1.0f, rho.v.y)));
     } else if constexpr (std::is_same<T, double>::value) {
         // Newton-Raphson from the float reciprocal (relative error e ->
-        // e^2 per step: 2^-23 -> 2^-46 -> below 2^-53), four FP64
-        // operations in place of a division
+        // e^2 per step: 2^-23 -> 2^-46 -> about one unit in the last
+        // place), four FP64 operations in place of a division
         double r = (double)__frcp_rn((float)rho);
         r = r * fma(-rho, r, 2.0);
         irho = r * fma(-rho, r, 2.0);

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <string>
+#include <vector>
 
 #include "lb_device.cuh"
 
@@ -68,6 +69,13 @@ struct lb_ctx {
     float* corr_y;            // network output (3 npts)
     int* corr_ws;             // feature workspace
     size_t corr_cap, corr_ws_ints;
+
+    // phase timing (lb_set_phase_timing): an event pair around each phase of
+    // every lb_step, summed by lb_phase_times
+    bool phase_timing;
+    std::vector<cudaEvent_t> ev_free;   // recorded and read back, ready for reuse
+    std::vector<int> mark_phase;        // phase of each recorded pair
+    std::vector<cudaEvent_t> mark_ev;   // start, end of each recorded pair
 
     long long launches;       // kernels launched so far
     unsigned seed;            // seed of the stochastic rounding of the 16-bit formats

@@ -12,9 +12,14 @@
 //
 // Scratch: the per-block partial sums live in the file-scope array below,
 // which every GPU that loads this library keeps until the process exits.
-// Its address is looked up with cudaGetSymbolAddress once per device, by
-// the first call made on that device (with the device current); that first
-// call should therefore come before any stream capture on that device.
+// Host code cannot use the array's name as a device address; the address
+// is looked up with cudaGetSymbolAddress (with the device current).  Every
+// call that is not being captured into a CUDA graph looks it up again, so a
+// device reset or a new primary context (which may load the module at
+// another address) never leaves a stale pointer behind; a call made while
+// its stream is capturing takes the address the last uncaptured call on
+// that device found, so the first call on a device must come before any
+// stream capture there.
 // All calls share the array and it keeps the previous call's contents: each
 // block overwrites its own slot before the final reduction reads it, so
 // nothing needs clearing, but two calls whose work overlaps on the GPU
@@ -136,10 +141,15 @@ extern "C" lb_status lb_totals_noalloc(const void* df, int precision, const int 
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return LB_ERR_CUDA;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return LB_ERR_CUDA;
+    }
     double* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!g_scratch_ptr[dev]) {
+        if (cap == cudaStreamCaptureStatusNone) {  // refresh: the module may have moved since the last call
             void* p = nullptr;
             if (cudaGetSymbolAddress(&p, g_totals_scratch) != cudaSuccess || !p) {
                 cudaGetLastError();
@@ -149,6 +159,7 @@ extern "C" lb_status lb_totals_noalloc(const void* df, int precision, const int 
         }
         scratch = g_scratch_ptr[dev];
     }
+    if (!scratch) return LB_ERR_STATE;  // captured before any uncaptured call on this device
 
     lbk::Geom g;
     g.nx = grid[0];

@@ -34,7 +34,8 @@ __device__ __forceinline__ void stencil_row(T* __restrict__ row, double X, doubl
 }
 
 // 1 / x by two Newton-Raphson steps from the float reciprocal (relative
-// error 2^-23 -> 2^-46 -> the FP64 rounding), four FP64 operations in place
+// error 2^-23 -> 2^-46 -> within about one unit in the last place of the
+// FP64 1/x, not always its correct rounding), four FP64 operations in place
 // of a division; x outside the float range takes the division.
 __device__ __forceinline__ double recip_fp64(double x) {
     const double ax = fabs(x);

@@ -33,7 +33,7 @@ EXPORTS = ["lb_create", "lb_destroy", "lb_last_error", "lb_set_body_force", "lb_
            "lb_colloid_velocity", "lb_mlp_num_params", "lb_mlp_create", "lb_mlp_destroy", "lb_mlp_last_error",
            "lb_mlp_get_params", "lb_mlp_set_params", "lb_mlp_features", "lb_mlp_forward", "lb_mlp_grad",
            "lb_mlp_train_step", "lb_set_colloid_correction", "lb_save", "lb_load",
-           "lb_mlp_set_wait_limit", "lb_set_host_async"]
+           "lb_mlp_set_wait_limit", "lb_set_host_async", "lb_set_phase_timing", "lb_phase_times"]
 
 _lib = None
 
@@ -74,6 +74,8 @@ def load():
         "lb_get_populations": ([vp, dp], ctypes.c_int),
         "lb_set_populations": ([vp, dp], ctypes.c_int),
         "lb_kernel_launches": ([vp, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
+        "lb_set_phase_timing": ([vp, ctypes.c_int], ctypes.c_int),
+        "lb_phase_times": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
         "lb_synchronize": ([vp], ctypes.c_int),
         "lb_save": ([vp, ctypes.c_char_p], ctypes.c_int),
         "lb_load": ([vp, ctypes.c_char_p], ctypes.c_int),
@@ -223,6 +225,21 @@ def lb_kernel_launches(ctx):
     return n.value
 
 
+PHASES = ("spread", "collide", "interp", "update", "correction")
+
+
+def lb_set_phase_timing(ctx, on):
+    _check(ctx, load().lb_set_phase_timing(ctx, int(bool(on))))
+
+
+def lb_phase_times(ctx):
+    """{phase: (total ms, occurrences)} since the last call (waits for the stream)."""
+    ms = (ctypes.c_double * 5)()
+    cnt = (ctypes.c_longlong * 5)()
+    _check(ctx, load().lb_phase_times(ctx, ms, cnt))
+    return {name: (ms[k], cnt[k]) for k, name in enumerate(PHASES)}
+
+
 def lb_synchronize(ctx):
     _check(ctx, load().lb_synchronize(ctx))
 
@@ -246,17 +263,43 @@ def lb_compute_aL(grid, R, direction=None):
 
 def lb_totals_noalloc(df, precision, grid, z_lo, z_hi, F, totals, stream=None):
     """Totals of a caller-owned device population array without any device
-    allocation (see include/lb.h).  df: device tensor or address in the
-    storage format of `precision`; totals: device float64 tensor of 4."""
-    g = (ctypes.c_int * 3)(*[int(v) for v in grid])
-    f = None if F is None else np.ascontiguousarray(F, dtype=np.float64)
+    allocation (see include/lb.h).  df: contiguous CUDA tensor of the
+    storage type of `precision` (float64, float32, float16 holding df * 2^20,
+    bfloat16) with at least 19 * nx * ny * nz elements; totals: contiguous
+    CUDA float64 tensor of at least 4 elements; F: None or 3 numbers.  The
+    C call trusts its pointers, so they are checked here: a host array or a
+    short buffer would make its kernels read or write out of bounds."""
+    import torch
+    storage = {LB_F64: torch.float64, LB_F32: torch.float32, LB_F16S: torch.float16, LB_BF16S: torch.bfloat16}
+    if int(precision) not in storage:
+        raise ValueError(f"lb_totals_noalloc: unknown precision {precision}")
+    dims = [int(v) for v in grid]
+    if len(dims) != 3 or min(dims) < 1:
+        raise ValueError("lb_totals_noalloc: grid must be three sizes >= 1")
+    V = dims[0] * dims[1] * dims[2]
+    if not isinstance(df, torch.Tensor) or not df.is_cuda or not df.is_contiguous():
+        raise TypeError("lb_totals_noalloc: df must be a contiguous CUDA tensor")
+    if df.dtype != storage[int(precision)]:
+        raise TypeError(f"lb_totals_noalloc: df is {df.dtype}, the format stores {storage[int(precision)]}")
+    if df.numel() < NQ * V:
+        raise ValueError(f"lb_totals_noalloc: df holds {df.numel()} elements, the grid needs {NQ * V}")
+    if (not isinstance(totals, torch.Tensor) or not totals.is_cuda or totals.dtype != torch.float64
+            or not totals.is_contiguous() or totals.numel() < 4):
+        raise TypeError("lb_totals_noalloc: totals must be a contiguous CUDA float64 tensor of >= 4 elements")
+    if totals.device != df.device:
+        raise ValueError("lb_totals_noalloc: df and totals are on different devices")
+    f = None
+    if F is not None:
+        f = np.ascontiguousarray(F, dtype=np.float64).ravel()
+        if f.shape != (3,):
+            raise ValueError("lb_totals_noalloc: F must hold exactly 3 numbers")
+    g = (ctypes.c_int * 3)(*dims)
     if stream is None:
-        import torch
-        stream = torch.cuda.current_stream().cuda_stream
-    addr = df if isinstance(df, int) else df.data_ptr()
-    status = load().lb_totals_noalloc(addr, int(precision), g, int(z_lo), int(z_hi),
-                                      None if f is None else f.ctypes.data, _ptr(totals),
-                                      ctypes.c_void_p(stream))
+        stream = torch.cuda.current_stream(df.device).cuda_stream
+    with torch.cuda.device(df.device):  # the C call works on the current device
+        status = load().lb_totals_noalloc(df.data_ptr(), int(precision), g, int(z_lo), int(z_hi),
+                                          None if f is None else f.ctypes.data, totals.data_ptr(),
+                                          ctypes.c_void_p(stream))
     if status != LB_OK:
         raise LBError(status, "lb_totals_noalloc failed")
 

@@ -89,3 +89,53 @@ def test_bad_checkpoints_are_refused(tmp_path):
     after = _state(g)
     assert np.array_equal(before[1], after[1]) and np.array_equal(before[0], after[0])
     g.close()
+
+
+def _fnv1a(data):
+    h = 1469598103934665603
+    for b in data:
+        h = ((h ^ b) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def _reseal(body):
+    """A checkpoint body with a valid digest appended (the file another tool
+    could write)."""
+    return bytes(body) + int(_fnv1a(body)).to_bytes(8, "little")
+
+
+def test_intact_but_out_of_range_checkpoints_are_refused(tmp_path):
+    """A file whose digest is valid but whose header or point block holds
+    values the kernels would index with (a position outside the box, a wall
+    plane outside the lattice) is refused, and the context is unchanged."""
+    import struct
+    from paper_0707_1299_gb300 import lb
+    g = lb.Lattice((16, 16, 16), 0.5, 0.5, lb.LB_F32)
+    g.add_point_forces(lb.LB_STOKESLET, [[8.2, 8.3, 8.4]], [[0.0, 0.0, 1e-5]])
+    g.step(3)
+    path = str(tmp_path / "a.ckpt")
+    g.save(path)
+    before = _state(g)
+    body = bytearray(open(path, "rb").read()[:-8])
+    assert _reseal(body) == open(path, "rb").read()  # the digest is FNV-1a over the body
+    hdr = 112  # magic, grid, prec, tau_s, tau_b, g, a_L, counter, walls, seed, scales, counts, pop_bytes
+    cases = {}
+    far = bytearray(body)
+    far[hdr:hdr + 8] = struct.pack("<d", 1.0e6)  # x of the first point
+    cases["position"] = far
+    nan = bytearray(body)
+    nan[hdr + 24:hdr + 32] = struct.pack("<d", float("nan"))  # F_x of the first point
+    cases["force"] = nan
+    wall = bytearray(body)
+    wall[76:80] = struct.pack("<i", 99)  # wall_lo beyond nz
+    cases["wall"] = wall
+    for name, b in cases.items():
+        bad = str(tmp_path / f"{name}.ckpt")
+        open(bad, "wb").write(_reseal(b))
+        with pytest.raises(lb.LBError) as e:
+            g.load(bad)
+        assert e.value.status == lb.LB_ERR_ARG, name
+    after = _state(g)
+    assert np.array_equal(before[1], after[1]) and np.array_equal(before[0], after[0])
+    g.load(path)  # the genuine file still loads
+    g.close()

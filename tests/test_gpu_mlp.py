@@ -248,3 +248,63 @@ def test_corrected_step_moves_colloids_by_network_output():
     assert np.abs(periodic_diff(R2.cpu().numpy(), expect, prob.grid)).max() < 1e-12
     g.close()
     lb.lb_mlp_destroy(net)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_corrected_step_matches_oracle(prec):
+    # Reading L4 end to end: lb_step with a network attached against the
+    # oracle stepping the same colloids with its own features and its own
+    # bfloat16-operand forward (oracle.OracleLB.step(net=...)), 120 steps,
+    # trajectories compared.  The method's bar holds for the fluid part of
+    # the update; the network's own output is FP32-accumulated on the GPU
+    # (FP64 in the oracle, bfloat16 operands on both sides), so for the FP64
+    # lattice its share of the displacement -- measured on the oracle as
+    # corrected minus plain run -- is held to 1e-5 of itself (FP32 sums and
+    # an operand that a near-boundary pre-activation rounds the other way).
+    lb = _lb()
+    import oracle
+    from paper_0707_1299_gb300 import learned, workloads as W
+    from _harness import TOL, disp_tol
+    pid = {"f64": lb.LB_F64, "f32": lb.LB_F32}[prec]
+    steps = 120
+    prob = W.colloids(L=32, n=90, seed=12, force=1e-5, a_L=1.6)  # ~3 others within the cutoff
+    params = learned.initial_params(11)
+    params[-(3 * 64 + 3):] *= 0.1  # y ~ 0.1: the correction moves colloids by ~10 % of v0
+    params = params.astype(np.float32)
+    net = lb.lb_mlp_create(params)
+    P = mlp.unflatten(params.astype(np.float64))
+    g = lb.Lattice(prob.grid, prob.tau_s, prob.tau_b, pid)
+    g.set_colloid_aL(1.6)
+    ps = prob.points[0]
+    g.add_point_forces(ps.kind, ps.pos, ps.F, ps.param)
+    lb.lb_set_colloid_correction(g.ctx, net)
+    p0, _ = g.particles()
+    p0 = p0.cpu().numpy()
+    g.step(steps)
+    p1, _ = g.particles()
+    _, u, _ = g.moments()
+    torch.cuda.synchronize()
+    corr = oracle.OracleLB(prob.grid, prob.tau_s, prob.tau_b, a_L=1.6)
+    plain = oracle.OracleLB(prob.grid, prob.tau_s, prob.tau_b, a_L=1.6)
+    for o in (corr, plain):
+        o.add_points(ps.kind, ps.pos, ps.F, ps.param)
+    corr.step(steps, net=P)
+    plain.step(steps)
+    d_gpu = periodic_diff(p1.cpu().numpy(), p0, prob.grid)
+    d_ref = periodic_diff(corr.pos, p0, prob.grid)
+    d_net = periodic_diff(corr.pos, plain.pos, prob.grid)  # the network's share
+    dmax = np.abs(d_ref).max()
+    assert np.abs(d_net).max() > 0.05 * dmax  # the correction matters
+    err = np.abs(d_gpu - d_ref).max()
+    bar = disp_tol(prec, prob.grid, steps, dmax) * dmax
+    allow = bar + (1e-5 * np.abs(d_net).max() if prec == "f64" else 0.0)
+    assert err <= allow, (err / dmax, allow / dmax)
+    # the fluid is driven by the colloids: a position that differs by err
+    # (lattice units) moves the spread force by ~err of its own size, so the
+    # field may differ relatively by about err beyond the format's bar
+    ref_u = corr.observe()["u"]
+    err_u = np.abs(u.cpu().numpy() - ref_u).max() / np.abs(ref_u).max()
+    assert err_u <= TOL[prec] + 10 * err, (err_u, err)
+    lb.lb_set_colloid_correction(g.ctx, None)
+    g.close()
+    lb.lb_mlp_destroy(net)
