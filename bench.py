@@ -1,13 +1,16 @@
 """Benchmark: D3Q19 forced-MRT lattice Boltzmann MLUPS and HBM roofline
 fraction on one GB300 (or N independent replicas under torchrun).
 
-Workload (one "step"): one time step of each of the four 256^3 FP32
-lattices of the wall-bounded channel / multipole recipe -- the body-force
-channel with solid planes z = 0, 255, a Stokeslet, a stresslet and a
-rotlet at seeded positions (see paper_0707_1299_gb300.workloads).  Every
-lattice step spreads its point forces (Peskin kernel), then runs the fused
-collide + pull-stream kernel over all 256^3 sites.  The velocity at the
-force points is interpolated back every step (gather kernel).
+Headline workload (one "step"): one time step of the 512^3 periodic
+sedimentation box with 1e5 point colloids (seeded uniform positions,
+force (0, 0, -1e-6) each, radius 0.117, uniform counter-force, a_L of
+Appendix A), FP32 storage: the colloids' forces are spread with Peskin's
+kernel, the fused collide + pull-stream kernel runs over all 512^3 sites
+(writing the fluid velocity at the colloids' stencil nodes), the velocity
+is interpolated back and every colloid moves (Sec. II-IV).  The blocks
+beside it: the same box in the other storage formats with errors per field
+against the FP64 run, the four-lattice 256^3 channel / multipole step, the
+32^3 Stokeslet in FP64, the batched replicas and the learned correction.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f32]
     python bench.py --impl reference ...   (the CPU oracle on a bounded sample)
@@ -32,27 +35,51 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "D3Q19 forced-MRT MLUPS & HBM-roofline fraction per precision at stated error"
-WORKLOAD = ("channel_256: four 256^3 D3Q19 MRT lattices per step (body-force channel g=1e-6 between "
-            "solid planes z=0,255; Stokeslet F=1e-5; stresslet dipole 1e-4; rotlet torque 1e-4; "
-            "seeded off-lattice positions), tau_s=tau_b=1/2")
+L_HEAD, N_HEAD = 512, 100000  # the sedimentation box of the headline
 PREC_NAMES = {"f64": 0, "f32": 1, "f16s": 2, "bf16s": 3}
 BYTES = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2}
+ARITH = {"f64": 8, "f32": 4, "f16s": 4, "bf16s": 4}
 PROFILE_DIR = os.path.join(ROOT, "profiles")
+# Algorithmic bytes per colloid and step beyond the lattice's 2*19*s per
+# site: its 64 stencil nodes x 3 force components, in the arithmetic type a:
+# the spread reads and writes them (2), the collide reads the force and
+# writes the velocity (2), the interpolation reads the velocity (1).
+COLLIDE_NODE_PASSES, STEP_NODE_PASSES = 2, 5
+
+
+def workload_name(L, n):
+    return (f"colloids_{L}: {L}^3 periodic D3Q19 MRT (tau_s = tau_b = 1/2), {n} point colloids at seeded "
+            f"uniform positions (seed 3), force (0,0,-1e-6) each, radius 0.117, uniform counter-force, "
+            f"a_L of Appendix A")
+
+
+def default_colloids(L):
+    """The headline's number density (1e5 in 512^3) at side L."""
+    return max(1, int(round(N_HEAD * (L / L_HEAD) ** 3)))
+
+
+def collide_bytes(prec, V, n):
+    return 2 * 19 * BYTES[prec] * V + COLLIDE_NODE_PASSES * 64 * 3 * ARITH[prec] * n
+
+
+def step_bytes(prec, V, n):
+    return 2 * 19 * BYTES[prec] * V + STEP_NODE_PASSES * 64 * 3 * ARITH[prec] * n
 
 
 def kernel_source_hash():
-    """Hash of the CUDA sources; the committed ncu traffic figure is only
-    quoted while the kernels are unchanged since it was taken."""
+    """Hash of the CUDA sources the collide kernels are built from; a
+    committed ncu figure is only quoted while they are unchanged."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_0707_1299_gb300", "csrc")
-    for f in ("lb_device.cuh", "lb_collide.cu"):  # what k_collide is built from
+    for f in ("lb_device.cuh", "lb_collide.cu"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def committed_traffic(prec):
-    """dram bytes per k_collide launch from the committed ncu summary."""
-    path = os.path.join(PROFILE_DIR, f"k_collide_{prec}_channel_256.txt")
+def committed_profile(name):
+    """key: value fields of profiles/<name>.txt, or None when the file is
+    missing or was taken from other kernel sources."""
+    path = os.path.join(PROFILE_DIR, name + ".txt")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -62,8 +89,14 @@ def committed_traffic(prec):
             vals[k.strip()] = v.strip()
     if vals.get("source_sha") != kernel_source_hash():
         return None
+    return vals
+
+
+def committed_traffic(name):
+    """DRAM bytes per full-size launch from a committed ncu summary."""
+    vals = committed_profile(name)
     try:
-        return float(vals["dram_bytes_per_launch_full_size"])
+        return float(vals["dram_bytes_per_launch_full_size"]) if vals else None
     except (KeyError, ValueError):
         return None
 
@@ -71,18 +104,9 @@ def committed_traffic(prec):
 def committed_fp64_mix():
     """FP64 instructions and flops per site of k_collide<double> from the
     committed ncu instruction-mix summary (None once the sources changed)."""
-    path = os.path.join(PROFILE_DIR, "k_collide_f64_160.txt")
-    if not os.path.exists(path):
-        return None
-    vals = {}
-    for line in open(path):
-        if ":" in line and not line.startswith("#"):
-            k, v = line.split(":", 1)
-            vals[k.strip()] = v.strip()
-    if vals.get("source_sha") != kernel_source_hash():
-        return None
+    vals = committed_profile("k_collide_f64_160")
     try:
-        return float(vals["fp64_inst_per_site"]), float(vals["fp64_flop_per_site"])
+        return (float(vals["fp64_inst_per_site"]), float(vals["fp64_flop_per_site"])) if vals else None
     except (KeyError, ValueError):
         return None
 
@@ -91,6 +115,17 @@ def committed_fp64_mix():
 # FP64 lanes per SM and clock x 2 flops per fused multiply-add.
 FP64_LANES_PER_SM_CLK = 2
 SM_COUNT, SM_MAX_HZ = 152, 2.07e9
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.TimeoutExpired):
+        pass
+    return None
 
 
 def measured_peaks():
@@ -158,21 +193,9 @@ class ClockSampler:
 # --------------------------------------------------------------- GPU arm
 def build_lattices(prec_id, L):
     from paper_0707_1299_gb300 import lb, workloads as W
-    lats = []
-    for prob in W.channel_256(L=L):
-        g = lb.Lattice(prob.grid, prob.tau_s, prob.tau_b, prec_id)
-        g.set_body_force(prob.g)
-        if prob.walls is not None:
-            g.set_walls_z(*prob.walls)
-        g.set_counterforce(prob.counter)
-        for ps in prob.points:
-            g.add_point_forces(ps.kind, ps.pos, ps.F, ps.param)
-        lats.append((prob, g))
-    return lats
 
 
 # ------------------------------------------------------------ ranks
-# One process per GPU, each stepping its own replica of the workload (the
 # lattices of different ranks share nothing): the job's time is its slowest
 # rank's, and the job's throughput is all ranks' site updates over it.
 def _reduce_device():
@@ -203,6 +226,37 @@ def job_mlups(sites_per_rank, steps, seconds, world):
     return world * sites_per_rank * steps / seconds / 1e6
 
 
+# --------------------------------------------------------------- GPU arm
+def colloid_lattice(prec, L, n):
+    from paper_0707_1299_gb300 import lb, workloads as W
+    prob = W.colloids(L=L, n=n, seed=3, force=1e-6)
+    aL = lb.lb_compute_aL(prob.grid, [L / 2 + 0.5] * 3, [0, 0, 1])
+    g = lb.Lattice(prob.grid, prob.tau_s, prob.tau_b, PREC_NAMES[prec])
+    g.set_colloid_aL(aL)
+    ps = prob.points[0]
+    g.add_point_forces(ps.kind, ps.pos, ps.F, ps.param)
+    return g, aL
+
+
+def field_snapshot(g, p0, L):
+    """rho, u and the colloid displacements of a lattice (device, FP64)."""
+    import torch
+    rho, u, tot = g.moments()
+    p1, _ = g.particles()
+    disp = p1 - p0
+    disp -= L * torch.round(disp / L)
+    return {"rho": rho, "u": u, "disp": disp, "totals": tot}
+
+
+def field_errors(s, ref):
+    """Errors per field against the FP64 run (reading A20: max error over
+    max reference magnitude; density as the deviation from rest)."""
+    def rel(a, b):
+        return float((a - b).abs().max() / b.abs().max())
+    return {"velocity": rel(s["u"], ref["u"]), "density": rel(s["rho"] - 1.0, ref["rho"] - 1.0),
+            "displacement": rel(s["disp"], ref["disp"])}
+
+
 def run_gpu(args, rank, world):
     import torch
     from paper_0707_1299_gb300 import build, lb
@@ -213,36 +267,17 @@ def run_gpu(args, rank, world):
     torch.cuda.set_device(dev)
     prec = args.precision
     L = args.size
-    lats = build_lattices(PREC_NAMES[prec], L)
+    n = args.colloids if args.colloids else default_colloids(L)
     V = L ** 3
     stream = torch.cuda.current_stream()
-
-    # query points: the force points of each lattice, or the channel centre,
-    # where the velocity is interpolated back every step
-    qpos = []
-    for prob, g in lats:
-        p, _ = g.particles()
-        if p.shape[0] == 0:
-            p = torch.tensor([[L / 2, L / 2, L / 2]], dtype=torch.float64, device=p.device)
-        qpos.append(p)
-    vbuf = [torch.empty_like(q) for q in qpos]
-
-    def one_step(events=None):
-        for k, (prob, g) in enumerate(lats):
-            if events is not None:
-                events[k][0].record(stream)
-            g.step(1)
-            if events is not None:
-                events[k][1].record(stream)
-            lb.lb_velocity_at(g.ctx, qpos[k].shape[0], qpos[k], vbuf[k])
+    g, aL = colloid_lattice(prec, L, n)
+    p0, _ = g.particles()
 
     for _ in range(args.warmup):
-        one_step()
+        g.step(1)
     torch.cuda.synchronize()
-
-    launches0 = sum(g.kernel_launches() for _, g in lats)
-    ev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in lats]
-          for _ in range(args.steps)]
+    lb.lb_set_phase_timing(g.ctx, 1)
+    launches0 = g.kernel_launches()
     clocks = ClockSampler(dev)
     barrier(world)
     torch.cuda.synchronize()
@@ -250,107 +285,197 @@ def run_gpu(args, rank, world):
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
-    for s in range(args.steps):
-        one_step(ev[s])
+    for _ in range(args.steps):
+        g.step(1)
     t1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
     ms = max_over_ranks(t0.elapsed_time(t1), world)
-    launches = sum(g.kernel_launches() for _, g in lats) - launches0
-    # lb_step(1) of the channel lattice (no points) launches exactly one
-    # kernel, k_collide: its events time that kernel alone.  The point
-    # lattices' lb_step(1) runs the field-free collide and the fix-up of
-    # the few tiles their fixed points flag, reported beside it.
-    per_lat = [float(np.mean([ev[s][k][0].elapsed_time(ev[s][k][1]) for s in range(args.steps)]))
-               for k in range(len(lats))]
-    coll_ms = per_lat[0]
+    launches = g.kernel_launches() - launches0
+    phases = lb.lb_phase_times(g.ctx)
+    lb.lb_set_phase_timing(g.ctx, 0)
     step_ms = ms / args.steps
-    mlups = job_mlups(4 * V, args.steps, ms * 1e-3, world)
+    mlups = job_mlups(V, args.steps, ms * 1e-3, world)
+    phase_ms = {k: round(t / c, 5) for k, (t, c) in phases.items() if c}
+    coll_ms = phases["collide"][0] / phases["collide"][1]
 
-    # end to end through the C ABI with host buffers: per step copy the
-    # point positions (the step's input) in from pinned host memory, step,
-    # and read the interpolated velocities (the step's result) back into
-    # pinned host memory
-    has_pts = [g.num_points() > 0 for _, g in lats]
-    host_q = [q.cpu().pin_memory() for q in qpos]
-    host_v = [torch.empty(q.shape, dtype=torch.float64).pin_memory() for q in qpos]
-    e2e_steps = max(3, args.steps // 4)
-    h2d = sum(hq.numel() * 8 for hq, hp in zip(host_q, has_pts) if hp)
-    d2h = sum(hv.numel() * 8 for hv in host_v)
-    # host-async calls: the four lattices' copies and steps are enqueued
-    # back to back, and each step ends with lb_synchronize, after which the step's
-    # velocities are in host memory
-    for _, g in lats:
-        lb.lb_set_host_async(g.ctx, 1)
+    # end to end through the C ABI with host buffers: every step the colloid
+    # positions (the step's input) go in from page-locked host memory, the
+    # step runs, and the new positions (its result) come back into host
+    # memory; the positions read back feed the next step, so the trajectory
+    # is the device-only one
+    host_pos = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    hp = host_pos.numpy()
+    lb.lb_set_host_async(g.ctx, 1)
+    lb.lb_particles(g.ctx, hp, None)
+    lb.lb_synchronize(g.ctx)
+    e2e_steps = args.e2e_steps
     barrier(world)
     torch.cuda.synchronize()
     te = time.perf_counter()
     for _ in range(e2e_steps):
-        for k, (prob, g) in enumerate(lats):
-            if has_pts[k]:
-                lb.lb_set_positions(g.ctx, host_q[k].numpy())
-            g.step(1)
-            lb.lb_velocity_at(g.ctx, host_q[k].shape[0], host_q[k].numpy(), host_v[k].numpy())
-        for _, g in lats:
-            lb.lb_synchronize(g.ctx)
+        lb.lb_set_positions(g.ctx, hp)
+        g.step(1)
+        lb.lb_particles(g.ctx, hp, None)
+        lb.lb_synchronize(g.ctx)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - te, world)
-    e2e_mlups = job_mlups(4 * V, e2e_steps, e2e_s, world)
-
-    # stated error: the channel lattice against the exactly equivalent
-    # 1 x 1 x L oracle column after the same number of steps (rank 0)
-    err = None
-    nsteps_done = args.warmup + args.steps + e2e_steps
-    if rank == 0 and not args.no_check:
-        err = channel_error(lats[0][0], lats[0][1], L, nsteps_done)
+    lb.lb_set_host_async(g.ctx, 0)
+    e2e_mlups = job_mlups(V, e2e_steps, e2e_s, world)
+    steps_done = args.warmup + args.steps + e2e_steps
 
     peak, peak_kind = measured_peaks()
-    b_alg = 2 * 19 * BYTES[prec] * V
-    achieved = b_alg / (coll_ms * 1e-3) / 1e9
-    traffic = committed_traffic(prec)
-    for _, g in lats:
-        g.close()
-    torch.cuda.empty_cache()
-    others = None
-    if rank == 0 and world == 1 and not args.no_per_precision:
-        others = per_precision(L, {p: (10 if p == "f64" else 100) for p in PREC_NAMES if p != prec})
-    c512 = None
-    if rank == 0 and world == 1 and not args.no_colloids512:
-        c512 = colloids_512(L=args.colloids[0], n=args.colloids[1])
-    batched = None
-    if rank == 0 and world == 1 and not args.no_batched:
-        batched = batched_replicas(replicas=args.replicas)
-    learned = None
-    if rank == 0 and world == 1 and not args.no_learned:
-        learned = learned_correction(train=not args.no_training)
+    b_coll = collide_bytes(prec, V, n)
+    b_step = step_bytes(prec, V, n)
+    achieved = b_coll / (coll_ms * 1e-3) / 1e9
+    traffic = committed_traffic(f"k_collide_{prec}_vel_{L}_{n}")
     out = {
         "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
-        "config": {"workload": WORKLOAD, "lattice": [L, L, L], "lattices_per_step": 4,
-                   "sites_per_step": 4 * V, "precision": prec,
+        "config": {"workload": workload_name(L, n), "lattice": [L, L, L], "colloids": n, "precision": prec,
+                   "a_L": round(aL, 6), "sites_per_step": V,
                    "l2": "inputs larger than L2 (each population buffer %.2f GB)" % (19 * BYTES[prec] * V / 1e9),
                    "parallelism": f"replicas{world}"},
-        "error": {"max_rel_velocity_vs_oracle": err, "steps": nsteps_done,
-                  "case": "channel lattice vs exactly equivalent 1x1xL FP64 oracle column"},
-        "roofline": {"bound": "hbm", "kernel": f"k_collide<{prec}> (channel lattice: 256^3, walls, one launch per lb_step)",
-                     "lb_step_ms_per_lattice": {p.name: round(t, 5) for (p, _), t in zip(lats, per_lat)},
+        "roofline": {"bound": "hbm",
+                     "kernel": f"k_collide<{prec}, periodic, FM_VEL> ({L}^3, {n} colloids; one launch per step)",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                     "bytes_per_site": 2 * 19 * BYTES[prec], "launch_ms": round(coll_ms, 5),
-                     "traffic": traffic},
-        "e2e": {"value": round(e2e_mlups, 1), "unit": "MLUPS", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "steps": e2e_steps,
-                "mode": "C ABI with page-locked host buffers, host-async calls, lb_synchronize once per step"},
+                     "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+                     "launch_ms": round(coll_ms, 5), "launches_timed": phases["collide"][1],
+                     "bytes_per_launch": b_coll,
+                     "bytes_rule": f"2*19*{BYTES[prec]} B per site + {COLLIDE_NODE_PASSES}*64*3*{ARITH[prec]} B per "
+                                   "colloid (force read, velocity written at its stencil nodes)"},
+        "step_roofline": {"bytes_per_step": b_step, "achieved": round(b_step / (step_ms * 1e-3) / 1e9, 1),
+                          "frac": round(b_step / (step_ms * 1e-3) / 1e9 / peak, 4), "phase_ms": phase_ms,
+                          "bytes_rule": f"2*19*{BYTES[prec]} B per site + {STEP_NODE_PASSES}*64*3*{ARITH[prec]} B "
+                                        "per colloid (spread read+write, collide read+write, interpolation read)"},
+        "e2e": {"value": round(e2e_mlups, 1), "unit": "MLUPS", "h2d_bytes_per_step": 24 * n,
+                "d2h_bytes_per_step": 24 * n, "steps": e2e_steps,
+                "mode": "C ABI, page-locked host buffers, host-async calls: lb_set_positions(host) + lb_step(1) + "
+                        "lb_particles(host) + lb_synchronize every step"},
         "gpu_launches": launches,
         "clocks": clk,
-        "per_precision": others,
-        "colloids_512": c512,
-        "batched": batched,
-        "learned": learned,
     }
+    if rank != 0 or world != 1 or args.no_per_precision:
+        g.close()
+        torch.cuda.empty_cache()
+        return out
+
+    # errors per field against the FP64 run of the same box and step count
+    # (the FP64 CUDA path is held to the oracle at 1e-12 by the parity
+    # tests, at this size too), and the other storage formats beside it
+    mine = field_snapshot(g, p0, L)
+    g.close()
+    torch.cuda.empty_cache()
+    out["per_precision"] = per_precision_colloids(L, n, steps_done, prec, mine, out)
     return out
+
+
+def per_precision_colloids(L, n, steps, head_prec, head_snap, head, timed=40):
+    """The headline box in every storage format for the same number of
+    steps, the last `timed` device-timed; errors per field against the FP64
+    run.  The FP64 run goes first and is kept as the reference."""
+    import torch
+    peak, _ = measured_peaks()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    V = L ** 3
+    res = {"steps": steps, "timed_steps": timed, "reference": "FP64 run of the same box and steps"}
+    ref = head_snap if head_prec == "f64" else None
+    if ref is not None:
+        head["error"] = None  # the headline is the FP64 run
+    for prec in ("f64", "f16s", "bf16s", "f32"):
+        if prec == head_prec:
+            continue
+        g, _ = colloid_lattice(prec, L, n)
+        p0, _ = g.particles()
+        g.step(steps - timed)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        g.step(timed)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / timed
+        snap = field_snapshot(g, p0, L)
+        row = {"value": round(V / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS", "ms_per_step": round(ms, 4),
+               "hbm_frac_of_step": round(step_bytes(prec, V, n) / (ms * 1e-3) / 1e9 / peak, 4)}
+        if prec == "f64":
+            ref = snap
+            t = snap["totals"].cpu().numpy()
+            row["totals"] = {"mass_minus_V": float(t[0] - V), "momentum": [float(x) for x in t[1:]]}
+            row["bound"] = "alu (FP64 pipe)"
+            head["error"] = dict(field_errors(head_snap, ref), steps=steps,
+                                 reference="FP64 run (CUDA, oracle-checked) of the same box")
+            del head_snap
+        else:
+            row["error_vs_f64"] = field_errors(snap, ref)
+        del snap
+        res[prec] = row
+        g.close()
+        torch.cuda.empty_cache()
+    del ref
+    torch.cuda.empty_cache()
+    return res
+
+
+def channel_block(steps=200, warm=5, L=256):
+    """The four 256^3 lattices of the wall-bounded channel / multipole
+    workload (body-force channel between solid planes, a Stokeslet, a
+    stresslet and a rotlet; FP32), one step each per step, device-timed;
+    the channel lattice's lb_step launches exactly one kernel, k_collide,
+    whose events give its roofline; its error against the exactly
+    equivalent 1 x 1 x L FP64 oracle column."""
+    import torch
+    from paper_0707_1299_gb300 import lb, workloads as W
+    lats = []
+    for prob in W.channel_256(L=L):
+        g = lb.Lattice(prob.grid, prob.tau_s, prob.tau_b, lb.LB_F32)
+        g.set_body_force(prob.g)
+        if prob.walls is not None:
+            g.set_walls_z(*prob.walls)
+        g.set_counterforce(prob.counter)
+        for ps in prob.points:
+            g.add_point_forces(ps.kind, ps.pos, ps.F, ps.param)
+        lats.append((prob, g))
+    stream = torch.cuda.current_stream()
+    for _ in range(warm):
+        for _, g in lats:
+            g.step(1)
+    torch.cuda.synchronize()
+    ev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in lats]
+          for _ in range(steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for s in range(steps):
+        for k, (_, g) in enumerate(lats):
+            ev[s][k][0].record(stream)
+            g.step(1)
+            ev[s][k][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    per_lat = [float(np.mean([ev[s][k][0].elapsed_time(ev[s][k][1]) for s in range(steps)]))
+               for k in range(len(lats))]
+    V = L ** 3
+    peak, _ = measured_peaks()
+    achieved = 152 * V / (per_lat[0] * 1e-3) / 1e9
+    err = channel_error(lats[0][0], lats[0][1], L, warm + steps)
+    for _, g in lats:
+        g.close()
+    torch.cuda.empty_cache()
+    return {"workload": "channel_256: four 256^3 FP32 lattices (channel g=1e-6 between planes z=0,255; "
+                        "Stokeslet 1e-5; stresslet dipole 1e-4; rotlet torque 1e-4), tau_s = tau_b = 1/2",
+            "value": round(4 * V * steps / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS", "steps": steps,
+            "ms_per_step": round(ms / steps, 4),
+            "lb_step_ms_per_lattice": {p.name: round(t, 5) for (p, _), t in zip(lats, per_lat)},
+            "roofline": {"kernel": "k_collide<float, walls, FM_NONE> (channel lattice)", "launch_ms": round(per_lat[0], 5),
+                         "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "bytes_per_site": 152, "traffic": committed_traffic("k_collide_f32_channel_256")},
+            "error": {"max_rel_velocity_vs_oracle": err, "steps": warm + steps,
+                      "case": "channel lattice vs exactly equivalent 1x1xL FP64 oracle column"}}
 
 
 def channel_error(prob, g, L, nsteps):
@@ -364,117 +489,37 @@ def channel_error(prob, g, L, nsteps):
     return float(np.abs(uu - ref[:, None, None]).max() / np.abs(ref).max())
 
 
-def per_precision(L, steps_for):
-    """The same four-lattice step in the other storage formats: device-timed
-    (CUDA events around the collide launches, as for the headline line),
-    with the channel lattice's error against the FP64 oracle column."""
+def stokeslet_block(steps=1000):
+    """The 32^3 Stokeslet in FP64 (1000 steps), device-timed in one call,
+    against the oracle's 1000 steps."""
     import torch
-    from paper_0707_1299_gb300 import lb
-    peak, peak_kind = measured_peaks()
-    stream = torch.cuda.current_stream()
-    out = {}
-    for prec, steps in steps_for.items():
-        lats = build_lattices(PREC_NAMES[prec], L)
-        warm = 3
-        for _ in range(warm):
-            for _, g in lats:
-                g.step(1)
-        torch.cuda.synchronize()
-        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps * len(lats))]
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        for s in range(steps):
-            for k, (_, g) in enumerate(lats):
-                e = ev[s * len(lats) + k]
-                e[0].record(stream)
-                g.step(1)
-                e[1].record(stream)
-        t1.record(stream)
-        torch.cuda.synchronize()
-        ms = t0.elapsed_time(t1)
-        coll = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
-        V = L ** 3
-        achieved = 2 * 19 * BYTES[prec] * V / (coll * 1e-3) / 1e9
-        err = channel_error(lats[0][0], lats[0][1], L, warm + steps)
-        out[prec] = {"value": round(4 * V * steps / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS", "steps": steps,
-                     "collide_ms": round(coll, 5), "bytes_per_site": 2 * 19 * BYTES[prec],
-                     "hbm_achieved_gbs": round(achieved, 1), "hbm_frac": round(achieved / peak, 4),
-                     "bound": "alu (FP64 pipe)" if prec == "f64" else "hbm / issue",
-                     "max_rel_velocity_vs_oracle": err, "error_steps": warm + steps}
-        if prec == "f64":
-            mix = committed_fp64_mix()
-            peak_inst = SM_COUNT * SM_MAX_HZ * FP64_LANES_PER_SM_CLK
-            if mix is not None:
-                inst, flop = mix
-                rate = inst * V / (coll * 1e-3)
-                out[prec]["alu"] = {"unit": "FP64 thread-instructions/s", "achieved": round(rate / 1e9, 1),
-                                    "peak": round(peak_inst / 1e9, 1), "frac": round(rate / peak_inst, 4),
-                                    "scale": "1e9", "inst_per_site": inst, "flop_per_site": flop,
-                                    "tflops": round(flop * V / (coll * 1e-3) / 1e12, 3),
-                                    "peak_tflops_nominal": round(2 * peak_inst / 1e12, 3),
-                                    "source": "profiles/k_collide_f64_160.txt"}
-            else:
-                out[prec]["alu"] = None
-        for _, g in lats:
-            g.close()
-        torch.cuda.empty_cache()
-    return out
-
-
-def colloids_512(L=512, n=100000, steps=100, timed=40):
-    """The 512^3 sedimentation box: 1e5 colloids (seed 3) with force 1e-6
-    and radius 0.117, counter-force, a_L along z; every storage format
-    stepped `steps` times, the last `timed` device-timed with CUDA events.
-    Velocity field and colloid displacements are compared with the FP64
-    run of the same configuration (the FP64 CUDA path is checked against
-    the oracle on this recipe at 40^3 by the parity tests); FP64 mass and
-    momentum totals are reported beside it."""
-    import torch
+    import oracle
     from paper_0707_1299_gb300 import lb, workloads as W
-    peak, _ = measured_peaks()
-    prob = W.colloids(L=L, n=n, seed=3, force=1e-6)
-    aL = lb.lb_compute_aL(prob.grid, [L / 2 + 0.5] * 3, [0, 0, 1])
+    prob = W.stokeslet_32()
+    g = lb.Lattice(prob.grid, prob.tau_s, prob.tau_b, lb.LB_F64)
+    ps = prob.points[0]
+    g.add_point_forces(ps.kind, ps.pos, ps.F, ps.param)
+    g.step(3)
+    torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    V = L ** 3
-    ref = None
-    out = {"workload": f"{L}^3 periodic, {n} colloids (seed 3), force 1e-6, a = 0.117, counter-force, a_L = {aL:.4g}",
-           "steps": steps, "timed_steps": timed}
-    for prec in ("f64", "f32", "f16s", "bf16s"):
-        g = lb.Lattice(prob.grid, prob.tau_s, prob.tau_b, PREC_NAMES[prec])
-        g.set_colloid_aL(aL)
-        ps = prob.points[0]
-        g.add_point_forces(ps.kind, ps.pos, ps.F, ps.param)
-        p0, _ = g.particles()
-        g.step(steps - timed)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        g.step(timed)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / timed
-        _, u, tot = g.moments()
-        p1, _ = g.particles()
-        disp = p1 - p0
-        disp -= L * torch.round(disp / L)
-        row = {"value": round(V / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS", "ms_per_step": round(ms, 4),
-               "hbm_frac_of_step": round(2 * 19 * BYTES[prec] * V / (ms * 1e-3) / 1e9 / peak, 4)}
-        if ref is None:
-            ref = (u, disp)
-            t = tot.cpu().numpy()
-            row["totals"] = {"mass_minus_V": float(t[0] - V), "momentum": [float(x) for x in t[1:]]}
-        else:
-            row["max_rel_velocity_vs_f64"] = float((u - ref[0]).abs().max() / ref[0].abs().max())
-            row["max_rel_displacement_vs_f64"] = float((disp - ref[1]).abs().max() / ref[1].abs().max())
-            del u
-        out[prec] = row
-        g.close()
-        torch.cuda.empty_cache()
-    del ref
-    torch.cuda.empty_cache()
-    return out
+    e0.record(stream)
+    g.step(steps - 3)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / (steps - 3)
+    _, u, _ = g.moments()
+    o = oracle.OracleLB(prob.grid, prob.tau_s, prob.tau_b)
+    o.add_points(ps.kind, ps.pos, ps.F, ps.param)
+    o.step(steps)
+    ref = o.observe()["u"]
+    err = float(np.abs(u.cpu().numpy() - ref).max() / np.abs(ref).max())
+    g.close()
+    return {"workload": "stokeslet_32: 32^3 FP64, Stokeslet (0,0,1e-5) at (16.3,15.7,16.45), counter-force",
+            "value": round(32 ** 3 / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS", "ms_per_step": round(ms, 5),
+            "steps": steps, "max_rel_velocity_vs_oracle": err,
+            "note": "10 MB per step: launch- and latency-bound, not a bandwidth case"}
 
 
 def batched_replicas(steps=50, seq_steps=10, replicas=64):
@@ -598,82 +643,108 @@ def learned_correction(train_pairs=32, test_pairs=4, L_pair=64, T_pair=1000, ste
 
 
 # ---------------------------------------------------------- oracle (CPU)
-def oracle_sample_step(lats):
-    for o in lats:
-        o.step(1)
 
 
-def oracle_lattices(L, nxy):
+# ---------------------------------------------------------- oracle (CPU)
+CPU_SAMPLE_L = 128  # the headline box cropped to 128^3 at the same colloid density
+
+
+def oracle_colloids(L, n):
     import oracle
     from paper_0707_1299_gb300 import workloads as W
-    out = []
-    for prob in W.channel_256(L=L, nx=nxy, ny=nxy):
-        o = oracle.OracleLB(prob.grid, prob.tau_s, prob.tau_b, g=prob.g, walls=prob.walls, counter=prob.counter)
-        for ps in prob.points:
-            o.add_points(ps.kind, ps.pos, ps.F, ps.param)
-        out.append(o)
-    return out
+    prob = W.colloids(L=L, n=n, seed=3, force=1e-6)
+    aL = oracle.aL_along(prob.grid, [L / 2 + 0.5] * 3, [0, 0, 1])
+    o = oracle.OracleLB(prob.grid, prob.tau_s, prob.tau_b, a_L=aL)
+    ps = prob.points[0]
+    o.add_points(ps.kind, ps.pos, ps.F, ps.param)
+    return o
 
 
-def cpu_baseline(L, budget_s=12.0, nxy=64):
-    """The oracle on a bounded sample: the same four lattices cropped to
-    nxy x nxy x L (the recipe's points stay inside), stepped until about
-    budget_s seconds of CPU work."""
+def cpu_sample(L, budget_s, max_steps=400):
+    """MLUPS of the oracle stepping the headline recipe cropped to L^3 (same
+    number density, seed 3), for about budget_s seconds."""
     import oracle
-    lats = oracle_lattices(L, nxy)
-    oracle_sample_step(lats)  # first-touch of the oracle's buffers
-    sites = sum(o.V for o in lats)
+    n = default_colloids(L)
+    o = oracle_colloids(L, n)
+    o.step(1)  # first touch of the oracle's buffers
     t = time.perf_counter()
-    n = 0
-    while time.perf_counter() - t < budget_s and n < 50:
-        oracle_sample_step(lats)
-        n += 1
+    k = 0
+    while time.perf_counter() - t < budget_s and k < max_steps:
+        o.step(1)
+        k += 1
     dt = time.perf_counter() - t
-    return {"value": round(sites * n / dt / 1e6, 3), "unit": "MLUPS", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": f"four lattices {nxy}x{nxy}x{L} (channel recipe cropped in x,y), {n} steps, FP64, "
-                      f"{sites * n / 1e6:.1f} M site updates in {dt:.1f} s"}
+    return {"value": round(o.V * k / dt / 1e6, 3), "unit": "MLUPS", "cores": oracle.num_threads(),
+            "sample": f"{L}^3 with {n} colloids (the {L_HEAD}^3 / {N_HEAD} recipe cropped at its number density), "
+                      f"FP64, {k} steps, {o.V * k / 1e6:.1f} M site updates in {dt:.1f} s"}
+
+
+def cpu_baseline(budget_s=12.0):
+    """The oracle as it stands on all host cores (OpenMP) on the cropped
+    headline box, and on one core (a child process with OMP_NUM_THREADS=1)
+    on a 64^3 crop."""
+    import oracle
+    oracle.build()
+    res = cpu_sample(CPU_SAMPLE_L, budget_s)
+    res["kind"] = "oracle"
+    res["cpu_model"] = cpu_model()
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.cpu_sample(64, 6.0)))" % ROOT)
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        one = json.loads(r.stdout.strip().splitlines()[-1])
+        res["one_core"] = one
+    except (subprocess.TimeoutExpired, ValueError, IndexError):
+        res["one_core"] = None
+    return res
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the oracle as it stands, on the host cores, one
+    step of the headline recipe cropped to 128^3 (same number density) per
+    step (the paper publishes no code to run instead)."""
     import oracle
     oracle.build()
-    nxy = 64
-    lats = oracle_lattices(args.size, nxy)
+    L = min(args.size, CPU_SAMPLE_L)
+    n = default_colloids(L)
+    o = oracle_colloids(L, n)
     for _ in range(args.warmup):
-        oracle_sample_step(lats)
-    sites = sum(o.V for o in lats)
+        o.step(1)
     t = time.perf_counter()
     for _ in range(args.steps):
-        oracle_sample_step(lats)
+        o.step(1)
     dt = time.perf_counter() - t
-    v = sites * args.steps / dt / 1e6
-    sample = f"four lattices {nxy}x{nxy}x{args.size} (channel recipe cropped in x,y) per step, FP64"
+    v = o.V * args.steps / dt / 1e6
+    sample = (f"{L}^3 with {n} colloids per step (the {L_HEAD}^3 / {N_HEAD} recipe cropped at its number density), "
+              f"FP64")
     return {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "MLUPS", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / max(args.steps, 1) * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": sample, "parallelism": "host cores"},
+            "config": {"workload": workload_name(args.size, args.colloids or default_colloids(args.size)),
+                       "sample": sample, "parallelism": "host cores"},
             "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": oracle.num_threads(),
-                             "kind": "oracle", "sample": sample},
+                             "kind": "oracle", "sample": sample, "cpu_model": cpu_model()},
             "e2e": {"value": round(v, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="f32", choices=list(PREC_NAMES))
-    ap.add_argument("--size", type=int, default=256)
-    ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--size", type=int, default=L_HEAD, help="side of the headline sedimentation box")
+    ap.add_argument("--colloids", type=int, default=None,
+                    help="colloids of the headline box (default: 1e5 x (size/512)^3)")
+    ap.add_argument("--e2e-steps", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-precision", action="store_true")
+    ap.add_argument("--no-channel", action="store_true")
+    ap.add_argument("--channel-size", type=int, default=256)
+    ap.add_argument("--no-stokeslet", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--no-colloids512", action="store_true")
-    ap.add_argument("--colloids", type=int, nargs=2, default=[512, 100000], metavar=("L", "N"),
-                    help="box side and colloid count of the sedimentation-box block")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--replicas", type=int, default=64, help="members of the batched-replicas block (first N)")
     ap.add_argument("--no-training", action="store_true",
@@ -694,10 +765,12 @@ def main():
         dist.init_process_group("nccl")
     out = run_gpu(args, rank, world)
     if rank == 0:
-        if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(args.size)
-        else:
-            out["cpu_baseline"] = None
+        extra = world == 1
+        out["channel_256"] = channel_block(L=args.channel_size) if extra and not args.no_channel else None
+        out["stokeslet_32"] = stokeslet_block() if extra and not args.no_stokeslet else None
+        out["batched"] = batched_replicas(replicas=args.replicas) if extra and not args.no_batched else None
+        out["learned"] = learned_correction(train=not args.no_training) if extra and not args.no_learned else None
+        out["cpu_baseline"] = cpu_baseline() if extra and not args.no_cpu_baseline else None
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -40,12 +40,28 @@ def test_quoted_figures_follow_the_source_hash(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "PROFILE_DIR", str(tmp_path))
     (tmp_path / "k_collide_f32_channel_256.txt").write_text(text)
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: sha)
-    assert bench.committed_traffic("f32") == float(_field(src, "dram_bytes_per_launch_full_size"))
+    assert bench.committed_traffic("k_collide_f32_channel_256") == float(_field(src, "dram_bytes_per_launch_full_size"))
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
-    assert bench.committed_traffic("f32") is None
+    assert bench.committed_traffic("k_collide_f32_channel_256") is None
 
 
 def test_fp64_peak_from_unit_counts():
     # 152 SMs x 2.07 GHz x 2 FP64 lanes x 2 flops = the nominal 1.25 TFLOP/s
     peak = bench.SM_COUNT * bench.SM_MAX_HZ * bench.FP64_LANES_PER_SM_CLK * 2
     assert abs(peak / 1.25e12 - 1) < 0.01
+
+
+def test_algorithmic_bytes_of_the_headline():
+    # 512^3 FP32 with 1e5 colloids: 152 B a site, plus 64 nodes x 3 components
+    # x 4 B per colloid twice for the collide (force in, velocity out) and
+    # five times for the whole step (spread read + write, collide, interpolation)
+    V, n = 512 ** 3, 100000
+    assert bench.collide_bytes("f32", V, n) == 152 * V + 2 * 768 * n
+    assert bench.step_bytes("f32", V, n) == 152 * V + 5 * 768 * n
+    assert bench.step_bytes("bf16s", V, n) == 76 * V + 5 * 768 * n
+    assert bench.default_colloids(512) == 100000 and bench.default_colloids(128) == 1562
+
+
+def test_cpu_sample_runs_the_cropped_recipe():
+    r = bench.cpu_sample(16, 0.2, max_steps=3)
+    assert r["value"] > 0 and r["cores"] >= 1 and "16^3" in r["sample"]
