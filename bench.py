@@ -524,9 +524,9 @@ def stokeslet_block(steps=1000):
 
 def batched_replicas(steps=50, seq_steps=10, replicas=64):
     """64 independent sedimentation boxes of uneven sizes (48^3-128^3, 100-2000
-    colloids each, FP32) advanced by one batch (a launch per phase over all
-    boxes, graph-replayed steps, tuned persistent grid) against the same boxes
-    stepped one after another with lb_step."""
+    colloids each, FP32) advanced by one batch (one persistent cooperative
+    launch per step over all boxes, graph-replayed, tuned grid) against the
+    same boxes stepped one after another with lb_step."""
     import torch
     from paper_0707_1299_gb300 import lb, workloads as W
     probs = W.replicas(n=replicas)
@@ -550,6 +550,7 @@ def batched_replicas(steps=50, seq_steps=10, replicas=64):
     lb.lb_batch_step(batch, steps)
     t1.record(stream)
     torch.cuda.synchronize()
+    lb.lb_batch_synchronize(batch)  # raises if a barrier wait ran out
     ms_b = t0.elapsed_time(t1) / steps
     launches = lb.lb_batch_info(batch)["launches"] - l0
     lb.lb_batch_destroy(batch)
@@ -571,7 +572,7 @@ def batched_replicas(steps=50, seq_steps=10, replicas=64):
     return {"replicas": len(probs), "sites_per_step": sites, "colloids": npts, "precision": "f32",
             "value": round(sites / (ms_b * 1e-3) / 1e6, 1), "unit": "MLUPS", "ms_per_step": round(ms_b, 4),
             "hbm_frac_of_step": round(152 * sites / (ms_b * 1e-3) / 1e9 / peak, 4),
-            "launches_per_step": launches / steps, "collide_blocks": blocks, "steps": steps,
+            "launches_per_step": launches / steps, "persistent_blocks": blocks, "steps": steps,
             "sequential_lb_step": {"value": round(sites / (ms_s * 1e-3) / 1e6, 1), "ms_per_step": round(ms_s, 4),
                                    "steps": seq_steps}}
 

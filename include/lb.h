@@ -153,8 +153,10 @@ lb_status lb_set_positions(lb_ctx *ctx, const double *pos);
 lb_status lb_set_host_async(lb_ctx *ctx, int on);
 
 /* Advance nsteps >= 0 time steps.  Each step: spread the point forces at
- * their current positions, interpolate the velocity at each colloid and
- * move it (forward Euler, dt = 1), then collide and stream every site. */
+ * their current positions (unless the previous step already did), collide
+ * and stream every site, then interpolate the velocity at each colloid,
+ * move it (forward Euler, dt = 1) and spread the forces at the new
+ * positions for the next step.  Sec. II-IV. */
 lb_status lb_step(lb_ctx *ctx, int nsteps);
 
 /* Velocity v = (sum fbar c + F/2) / rho (Eq. macrovariables2) interpolated
@@ -187,9 +189,10 @@ lb_status lb_kernel_launches(const lb_ctx *ctx, long long *count);
  * stream and returns, per phase, the summed elapsed time in milliseconds
  * (ms, 5 doubles, host) and the number of timed occurrences (counts, 5
  * long longs, host, may be NULL) since the last call, then recycles the
- * events.  Phases: 0 spreading (with the stencil rows and the periodic
- * cell-order sort when they run), 1 collide + stream, 2 interpolation,
- * 3 colloid update, 4 learned correction (features and forward).  The
+ * events.  Phases: 0 spreading at the current positions (the first step,
+ * or after the points changed), 1 collide + stream, 2 point phase
+ * (interpolation, colloid update, spreading at the new positions), 3 the
+ * periodic cell-order sort, 4 learned correction (features and forward).  The
  * events are host-side objects: no device memory is allocated.  Turning
  * timing off waits for the stream and discards unread pairs.  LB_ERR_STATE
  * if a step failed between the two events of a pair. */
@@ -288,14 +291,17 @@ lb_status lb_set_colloid_correction(lb_ctx *ctx, lb_mlp *net);
 
 /* ------------------------------------------------------------------------
  * Batches: independent lattices (replicas of uneven sizes, e.g. many small
- * sedimentation boxes) advanced together.  Each phase of a time step
- * (spreading, colloid update, collide + stream) is one launch over all
- * members -- the collide + stream phase walks the 32-site windows of every
- * member's flat site index (every nx a multiple of 8, fewer than 2^24
- * sites a member) or else a work list of 4 x 32-site tiles, in a grid
- * picked by lb_batch_tune -- and two steps are replayed from a CUDA graph.
- * The colloids are taken in cell order, renewed every 64 steps.  The
- * method per member is exactly that of lb_step.
+ * sedimentation boxes) advanced together, one persistent cooperative kernel
+ * launch per time step over all members.  Inside the launch, phases are
+ * separated by grid-wide barriers whose waits are bounded: every 64 steps
+ * the cell order of all colloids (a counting sort); on the first step of a
+ * call whose force fields are not spread, the spread; the collide + stream
+ * of every site of every member (the 32-site windows of each member's flat
+ * site index when every nx is a multiple of 8 and every member has fewer
+ * than 2^24 sites, else 4 x 32-site tiles); then the point phase --
+ * interpolation, colloid update and the spread of the forces at the new
+ * positions for the next step.  Two steps are replayed from a CUDA graph.
+ * The method per member is exactly that of lb_step.
  * --------------------------------------------------------------------- */
 typedef struct lb_batch lb_batch;
 
@@ -311,21 +317,35 @@ lb_status lb_batch_create(lb_batch **out, int n, lb_ctx *const *ctxs, void *stre
 void lb_batch_destroy(lb_batch *batch);
 const char *lb_batch_last_error(const lb_batch *batch);
 
-/* Autotune the grid of the collide phase: time whole batch steps (every
- * phase) for several grid sizes (persistent grids of 2 to 16 blocks of 128
- * threads per SM, and for the tiled collide one block per work item), keep
- * the fastest, report its block count in *blocks (may be NULL).  Leaves
- * every member's state unchanged: the trial steps write only the spare
- * population buffers, and the positions (and the stochastic-rounding
- * counter) they move are put back; a force field spread by a query is
- * cleared (the next step spreads again).  Waits for the batch's stream. */
+/* Autotune the grid of the persistent kernel: time whole batch steps for
+ * grids of 2, 4, 6 and 8 blocks of 128 threads per SM (as many as can be
+ * resident together), keep the fastest, report its block count in *blocks
+ * (may be NULL).  Leaves every member's state unchanged: the trial steps
+ * write only the spare population buffers, and the positions and counters
+ * they move are put back; the force fields they spread are cleared (the
+ * next step spreads again).  Waits for the batch's stream; LB_ERR_TIMEOUT
+ * if a barrier wait ran out during the trials. */
 lb_status lb_batch_tune(lb_batch *batch, int *blocks);
 
-/* Advance every member nsteps >= 0 time steps (Sec. II-IV, as lb_step). */
+/* Advance every member nsteps >= 0 time steps (Sec. II-IV, as lb_step).
+ * Returns without waiting.  Afterwards each member's force field holds
+ * the forces at its new positions (queries on a member use it as is). */
 lb_status lb_batch_step(lb_batch *batch, int nsteps);
 
-/* Sites and points over all members, the collide grid size and the number
- * of kernels launched by the batch so far (any pointer may be NULL). */
+/* Wait for the batch's stream; LB_ERR_TIMEOUT if a grid-barrier wait of
+ * the steps issued since the last call ran out (those steps are then
+ * incomplete and the members' state is undefined; the barrier is reset so
+ * that the batch can be used again). */
+lb_status lb_batch_synchronize(lb_batch *batch);
+
+/* Bound of every grid-barrier wait of the batch kernel, in polls of the
+ * barrier's generation word with a short sleep between polls (default
+ * 2^22, about a second).  0 makes every wait give up at once, which drives
+ * the timeout path.  Waits for the batch's stream; LB_ERR_ARG for polls < 0. */
+lb_status lb_batch_set_wait_limit(lb_batch *batch, long long polls);
+
+/* Sites and points over all members, the persistent grid size and the
+ * number of kernels launched by the batch so far (any pointer may be NULL). */
 lb_status lb_batch_info(const lb_batch *batch, long long *sites, long long *points, int *blocks,
                         long long *launches);
 

@@ -1,9 +1,17 @@
 // lb_batch.cu -- many independent lattices (replicas of uneven sizes)
-// advanced together: every phase of a time step is one launch over all
-// replicas, the collide+stream phase a persistent kernel that walks a work
-// list of 4-tile groups spanning every replica, and a CUDA graph replays the
-// step so a short lattice costs no launch overhead.  The launch shape of
-// the persistent kernel is picked by timing candidates on the batch itself.
+// advanced together, one persistent cooperative launch per time step over
+// all replicas.  Inside the launch, phases separated by grid-wide barriers:
+//   (every 64 steps) the cell order of all points -- a counting sort;
+//   (first step of a call, when the force fields are not spread) stencil
+//     rows of the current positions and the spread;
+//   collide + stream of every site of every replica (writing the fluid
+//     velocity at the colloids' stencil nodes, zeroing the consumed force);
+//   the point phase: interpolation, colloid update and the spread of the
+//     forces at the new positions for the next step.
+// Every barrier wait is bounded; a wait that runs out sets an error flag and
+// the kernel returns (lb_batch_synchronize reports LB_ERR_TIMEOUT).  Two
+// steps (the two buffer parities) are replayed from a CUDA graph.  The grid
+// (blocks per SM) is picked by timing candidates on the batch itself.
 //
 // The method per replica is exactly that of lb_step (same device helpers:
 // Sec. II collision, Sec. III spreading, Sec. IV colloid update).
@@ -22,11 +30,23 @@ namespace {
 
 using namespace lbk;
 
-constexpr int BW = 4;  // warps (tiles) per work item of the collide kernel
-constexpr int SORT_EVERY = 64;  // steps between renewals of the batch's cell order
-constexpr int FLAT_MIN_BLOCKS = 8;  // occupancy bound of the flat collide (blocks of 128 threads per SM)
+constexpr int BW = 4;               // warps (tiles) per work item of the tiled collide
+constexpr int BT = BW * 32;         // threads per block of the persistent kernel
+constexpr int SORT_EVERY = 64;      // steps between renewals of the batch's cell order
+constexpr int MIN_BLOCKS = 8;       // occupancy bound of the persistent kernel (blocks of 128 threads per SM)
+constexpr long long DEFAULT_WAIT = 1LL << 22;  // polls of a barrier wait (~1 s) before it gives up
 
-// One replica as the batched kernels see it.
+// Barrier and step state of a batch, in device memory.
+struct BatchCtl {
+    unsigned count;      // blocks arrived at the current barrier
+    unsigned gen;        // barrier generation
+    int err;             // 1: a barrier wait ran out
+    int init;            // 1: spread the forces at the current positions before the collide
+    unsigned since_sort; // steps since the cell order was renewed
+    unsigned step;       // step counter seeding the stochastic rounding of the 16-bit formats
+    long long limit;     // polls of a barrier wait
+};
+
 struct Entry {
     void* pop[2];              // population buffers: index = parity ^ cur0
     void* floc;
@@ -165,62 +185,6 @@ __device__ __forceinline__ void batch_site(const Entry& E, int e, int x, int y, 
     }
 }
 
-template <typename S>
-__global__ void __launch_bounds__(BW * 32, 8)
-kb_collide(const Entry* __restrict__ ent, const long long* __restrict__ gbegin, const Work* __restrict__ wk, int nrep,
-           long long total_groups, int parity, const unsigned* __restrict__ step_counter) {
-    using T = typename Store<S>::T;
-    constexpr bool SC = Store<S>::kScaled;
-    const int lane = threadIdx.x, warp = threadIdx.y;
-    // rounding seed of this step (the 16-bit formats): read from device
-    // memory so that graph replays draw new bits every step
-    const unsigned seed = Store<S>::kScaled || sizeof(S) == 2 ? rng_seed(*step_counter, 0xB5297A4Du) : 0u;
-    // each block takes a contiguous chunk of work items and walks it with
-    // incremental coordinates: one search per block, none per item
-    const long long chunk = (total_groups + gridDim.x - 1) / gridDim.x;
-    const long long w0 = (long long)blockIdx.x * chunk;
-    const long long w1 = w0 + chunk < total_groups ? w0 + chunk : total_groups;
-    if (w0 >= w1) return;
-    int e = find_entry(gbegin, nrep, w0);
-    int tx, yg, zz;
-    {
-        const long long local = w0 - wk[e].group_begin;
-        tx = (int)(local % wk[e].groups_x);
-        const long long r = local / wk[e].groups_x;
-        yg = (int)(r % wk[e].groups_y);
-        zz = (int)(r / wk[e].groups_y);
-    }
-    for (long long w = w0; w < w1; ++w) {
-        if (w > w0) {  // advance (tx, yg, z, entry)
-            if (++tx == wk[e].groups_x) {
-                tx = 0;
-                if (++yg == wk[e].groups_y) {
-                    yg = 0;
-                    if (++zz == ent[e].g.nz) {
-                        zz = 0;
-                        ++e;
-                    }
-                }
-            }
-        }
-        const Entry& E = ent[e];
-        const Geom& g = E.g;
-        const int y = yg * BW + warp;
-        const int z = zz;
-        const int x = tx * TILE_X + lane;
-        if (y >= g.ny) continue;  // uniform per warp
-        const unsigned tile = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.ntx + (unsigned)tx;
-        // the flags and the field are read through the read-only path and
-        // reset below by the one warp (thread) that read them, as in k_collide
-        const unsigned fl = group_flag(__ldg((const unsigned*)E.flags + tile), (unsigned)lane);
-        if (x < g.nx) batch_site<S, true>(E, e, x, y, z, fl, parity, seed);
-        // the first lane of each flagged group resets its flag (this warp
-        // alone read the tile's flag word, in one warp-wide load)
-        if (fl && (lane % GROUP_X) == 0) E.flags[tile * (TILE_X / GROUP_X) + (unsigned)lane / GROUP_X] = 0;
-    }
-}
-
-
 // The collide over flat 32-site windows of each member's site index (x
 // fastest), so that no lane idles where nx is not a multiple of 32.  Valid
 // when every member has nx a multiple of 8, so that an 8-site force group
@@ -237,25 +201,215 @@ __device__ __forceinline__ unsigned div_small(unsigned a, unsigned d, float inv_
     return q;
 }
 
+
+
+// ------------------------------------------------------ grid barrier
+// All blocks of the (cooperative, co-resident) grid meet here.  Thread 0 of
+// each block arrives with a fenced atomic; the last to arrive resets the
+// count and opens the next generation.  The others poll the generation at
+// most ctl->limit times (with a short sleep between polls); a wait that runs
+// out sets the error flag and the block leaves the kernel.  Returns false
+// (in every thread of the block) after a timeout.
+__device__ __forceinline__ bool grid_sync(BatchCtl* ctl, long long limit) {
+    __syncthreads();
+    int ok = 1;
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = &ctl->gen;
+        const unsigned g0 = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&ctl->count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&ctl->count, 0u);
+            __threadfence();
+            atomicAdd(&ctl->gen, 1u);
+        } else {
+            long long polls = 0;
+            while (*vgen == g0) {
+                if (polls++ >= limit) {
+                    ok = 0;
+                    atomicOr(&ctl->err, 1);
+                    break;
+                }
+                __nanosleep(128);
+            }
+        }
+        __threadfence();
+    }
+    return __syncthreads_and(ok) != 0;
+}
+
+// Everything the persistent kernel reads.
+struct StepArgs {
+    const Entry* ent;
+    int nrep;
+    // collide work: flat windows or tiled groups
+    const long long* wbegin;
+    long long total_windows;
+    const long long* gbegin;
+    const Work* work;
+    long long total_groups;
+    // points
+    const long long* pbegin;
+    const int* pent;
+    int* order;
+    long long total_pts, n_mobile;
+    void* st;               // stencil rows (ST_W elements of the arithmetic type per point)
+    // cell order
+    int* sort_ws;           // count[nb], cursor[nb], start[nb + 1], key[total_pts]
+    long long total_bins;
+    BatchCtl* ctl;
+};
+
+// The point view of point gp of the batch.
+template <typename T>
+struct BatchPoints {
+    const Entry* ent;
+    const long long* pbegin;
+    const int* pent;
+    __device__ __forceinline__ PointView<T> view(long long gp) const {
+        const int e = pent[gp];
+        const Entry& E = ent[e];
+        PointView<T> P;
+        P.g = E.g;
+        P.floc = (T*)E.floc;
+        P.flags = E.flags;
+        P.vel = (const T*)E.vel;
+        P.pos = E.pos;
+        P.force = E.force;
+        P.radius = E.radius;
+        P.mobile = E.mobile;
+        P.inv_aL = E.inv_aL;
+        P.inv_6pi_eta = E.inv_6pi_eta;
+        P.s = (int)(gp - pbegin[e]);
+        return P;
+    }
+    __device__ __forceinline__ const float* y(long long) const { return nullptr; }
+};
+
+// Cell order of the batch's points (a counting sort on key = the member's
+// first bin + the 8^3 brick of the point within the member), so that
+// neighbouring warps of the point phase work on nearby stencils of one
+// replica.  Only the order of the work depends on it, never a result
+// (beyond the order of the spread's atomic additions).  Four barriers.
+constexpr int BATCH_BRICK = 8;
+__device__ bool sort_points(const StepArgs& a, long long limit) {
+    const long long nb = a.total_bins;
+    int* count = a.sort_ws;
+    int* cursor = count + nb;
+    int* start = cursor + nb;
+    int* key = start + nb + 1;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    for (long long i = tid; i < 2 * nb; i += nthreads) count[i] = 0;  // count and cursor
+    if (!grid_sync(a.ctl, limit)) return false;
+    for (long long gp = tid; gp < a.total_pts; gp += nthreads) {
+        const int e = a.pent[gp];
+        const Entry& E = a.ent[e];
+        const int s = (int)(gp - a.pbegin[e]);
+        int b[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) b[d] = min(max((int)E.pos[3 * s + d] / BATCH_BRICK, 0), E.nb[d] - 1);
+        const int k = E.bin0 + (b[2] * E.nb[1] + b[1]) * E.nb[0] + b[0];
+        key[gp] = k;
+        atomicAdd(&count[k], 1);
+    }
+    if (!grid_sync(a.ctl, limit)) return false;
+    if (blockIdx.x == 0) {  // exclusive scan of the counts by one block: a chunk a thread
+        __shared__ int part[BT + 1];
+        const long long chunk = (nb + BT - 1) / BT;
+        const long long c0 = threadIdx.x * chunk, c1 = min(c0 + chunk, nb);
+        int sum = 0;
+        for (long long i = c0; i < c1; ++i) sum += count[i];
+        part[threadIdx.x] = sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int run = 0;
+            for (int t = 0; t < BT; ++t) {
+                const int v = part[t];
+                part[t] = run;
+                run += v;
+            }
+            part[BT] = run;
+        }
+        __syncthreads();
+        int run = part[threadIdx.x];
+        for (long long i = c0; i < c1; ++i) {
+            start[i] = run;
+            run += count[i];
+        }
+        if (threadIdx.x == 0) start[nb] = part[BT];
+    }
+    if (!grid_sync(a.ctl, limit)) return false;
+    for (long long gp = tid; gp < a.total_pts; gp += nthreads) {
+        const int k = key[gp];
+        a.order[start[k] + atomicAdd(&cursor[k], 1)] = (int)gp;
+    }
+    return grid_sync(a.ctl, limit);
+}
+
+// The collide over a block's contiguous chunk of 4-tile work items (any
+// member geometry); warp w of the block takes row y = 4 yg + w of an item.
+template <typename S>
+__device__ __forceinline__ void collide_tiled(const StepArgs& a, int parity, unsigned seed) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long chunk = (a.total_groups + gridDim.x - 1) / gridDim.x;
+    const long long w0 = (long long)blockIdx.x * chunk;
+    const long long w1 = w0 + chunk < a.total_groups ? w0 + chunk : a.total_groups;
+    if (w0 >= w1) return;
+    int e = find_entry(a.gbegin, a.nrep, w0);
+    int tx, yg, zz;
+    {
+        const long long local = w0 - a.work[e].group_begin;
+        tx = (int)(local % a.work[e].groups_x);
+        const long long r = local / a.work[e].groups_x;
+        yg = (int)(r % a.work[e].groups_y);
+        zz = (int)(r / a.work[e].groups_y);
+    }
+    for (long long w = w0; w < w1; ++w) {
+        if (w > w0) {  // advance (tx, yg, z, entry)
+            if (++tx == a.work[e].groups_x) {
+                tx = 0;
+                if (++yg == a.work[e].groups_y) {
+                    yg = 0;
+                    if (++zz == a.ent[e].g.nz) {
+                        zz = 0;
+                        ++e;
+                    }
+                }
+            }
+        }
+        const Entry& E = a.ent[e];
+        const Geom& g = E.g;
+        const int y = yg * BW + warp;
+        const int z = zz;
+        const int x = tx * TILE_X + lane;
+        if (y >= g.ny) continue;  // uniform per warp
+        const unsigned tile = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.ntx + (unsigned)tx;
+        // the flags and the field are read through the read-only path and
+        // reset below by the one warp (thread) that read them, as in k_collide
+        const unsigned fl = group_flag(__ldg((const unsigned*)E.flags + tile), (unsigned)lane);
+        if (x < g.nx) batch_site<S, true>(E, e, x, y, z, fl, parity, seed);
+        if (fl && (lane % GROUP_X) == 0) E.flags[tile * (TILE_X / GROUP_X) + (unsigned)lane / GROUP_X] = 0;
+    }
+}
+
+// The collide over flat 32-site windows of each member's site index (see
+// div_small), each warp a contiguous chunk of windows.
 template <typename S, bool WALLS>
-__global__ void __launch_bounds__(128, FLAT_MIN_BLOCKS)
-kb_collide_flat(const Entry* __restrict__ ent, const long long* __restrict__ wbegin, int nrep, long long total_windows,
-                int parity, const unsigned* __restrict__ step_counter) {
+__device__ __forceinline__ void collide_flat(const StepArgs& a, int parity, unsigned seed) {
     const unsigned lane = threadIdx.x & 31u;
-    const unsigned seed = Store<S>::kScaled || sizeof(S) == 2 ? rng_seed(*step_counter, 0xB5297A4Du) : 0u;
-    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (w >= total_windows) return;
-    // the member of window w, tracked forward as w grows
-    int e = find_entry(wbegin, nrep, w);
-    long long lo = wbegin[e], hi = e + 1 < nrep ? wbegin[e + 1] : total_windows;
-    for (; w < total_windows; w += nwarps) {
+    const long long nwarps = (long long)gridDim.x * (BT / 32);
+    long long w = (long long)blockIdx.x * (BT / 32) + (threadIdx.x >> 5);
+    if (w >= a.total_windows) return;
+    int e = find_entry(a.wbegin, a.nrep, w);
+    long long lo = a.wbegin[e], hi = e + 1 < a.nrep ? a.wbegin[e + 1] : a.total_windows;
+    for (; w < a.total_windows; w += nwarps) {
         while (w >= hi) {  // uniform per warp
             ++e;
             lo = hi;
-            hi = e + 1 < nrep ? wbegin[e + 1] : total_windows;
+            hi = e + 1 < a.nrep ? a.wbegin[e + 1] : a.total_windows;
         }
-        const Entry& E = ent[e];
+        const Entry& E = a.ent[e];
         const Geom& g = E.g;
         const unsigned s = (unsigned)(w - lo) * 32u + lane;
         if (s >= (unsigned)g.V) continue;  // the ragged last window of a member
@@ -270,168 +424,42 @@ kb_collide_flat(const Entry* __restrict__ ent, const long long* __restrict__ wbe
     }
 }
 
-// Spreading, one warp per point (the scheme of k_spread), from the stencil
-// rows st[gp] written by kb_stencil / kb_update; warps take the points in
-// the batch's cell order (kb_brick_*).
-template <typename T>
-__global__ void __launch_bounds__(256)
-kb_spread(const Entry* __restrict__ ent, const long long* __restrict__ pbegin, const int* __restrict__ pent,
-          const int* __restrict__ order, long long total_pts, const T* __restrict__ st) {
-    const long long slot = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (slot >= total_pts) return;  // uniform per warp
-    const long long gp = order[slot];
-    const int lane = threadIdx.x & 31;
-    const int e = pent[gp];
-    const Entry& E = ent[e];
-    const Geom& g = E.g;
-    const int s = (int)(gp - pbegin[e]);
-    const unsigned FULL = 0xffffffffu;
-    const T r = lane < ST_W ? st[gp * ST_W + lane] : T(0);
-    const T fl = lane < 3 ? (T)E.force[3 * s + lane] : T(0);
-    const int bx = bits_int(__shfl_sync(FULL, r, 12)), by = bits_int(__shfl_sync(FULL, r, 13)),
-              bz = bits_int(__shfl_sync(FULL, r, 14));
-    const T F0 = __shfl_sync(FULL, fl, 0), F1 = __shfl_sync(FULL, fl, 1), F2 = __shfl_sync(FULL, fl, 2);
-    const int i = lane & 3, j = (lane >> 2) & 3;
-    const T wxy = __shfl_sync(FULL, r, i) * __shfl_sync(FULL, r, 4 + j);
-    const int x = wrap_node(bx + i, g.nx), y = wrap_node(by + j, g.ny);
-    const bool marker = (i == 0) || ((x & (GROUP_X - 1)) == 0);
-    const unsigned V = (unsigned)g.V;
-    T* floc = (T*)E.floc;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int k = (lane >> 4) + 2 * h;
-        const T wz = __shfl_sync(FULL, r, 8 + k);
-        const int z = wrap_node(bz + k, g.nz);
-        if (is_solid(g, z)) continue;
-        const T w = wxy * wz;
-        const unsigned row = (unsigned)z * (unsigned)g.ny + (unsigned)y;
-        const unsigned site = row * (unsigned)g.nx + (unsigned)x;
-        atomicAdd(floc + site, F0 * w);
-        atomicAdd(floc + V + site, F1 * w);
-        atomicAdd(floc + 2 * V + site, F2 * w);
-        if (marker) E.flags[row * (unsigned)g.ntx * (TILE_X / GROUP_X) + (unsigned)(x / GROUP_X)] = 1;
+// One time step of every member (buffer parity `parity`).  The state flags
+// (init, since_sort, step, limit) are read by every block before its first
+// barrier and rewritten by block 0 after its last, so all blocks of a
+// launch see the same values.
+template <typename S, bool FLAT, bool WALLS>
+__global__ void __launch_bounds__(BT, MIN_BLOCKS) kb_step(const StepArgs a, int parity) {
+    using T = typename Store<S>::T;
+    BatchCtl* ctl = a.ctl;
+    const volatile BatchCtl* vc = ctl;
+    const long long limit = vc->limit;
+    const bool init = vc->init != 0 && a.total_pts > 0;
+    const unsigned since = vc->since_sort;
+    const bool sort_due = since >= (unsigned)SORT_EVERY && a.total_pts > 0;
+    const unsigned step = vc->step;
+    const unsigned seed = sizeof(S) == 2 ? rng_seed(step, 0xB5297A4Du) : 0u;
+    constexpr int NPB = 4 * (BT / 32);  // points of a block's point-phase item
+    const long long items = (a.total_pts + NPB - 1) / NPB;
+    __shared__ double vsh[NPB][3];
+    const BatchPoints<T> src{a.ent, a.pbegin, a.pent};
+    T* st = (T*)a.st;
+    if (sort_due && !sort_points(a, limit)) return;
+    if (init) {  // stencil rows and spread at the current positions
+        for (long long q = blockIdx.x; q < items; q += gridDim.x)
+            point_block<T, WALLS, false, BT / 32>(src, q * NPB, a.total_pts, a.order, st, vsh);
+        if (!grid_sync(ctl, limit)) return;
     }
-}
-
-// Stencil rows of every point of the batch (thread per point).
-template <typename T>
-__global__ void kb_stencil(const Entry* __restrict__ ent, const long long* __restrict__ pbegin, const int* __restrict__ pent,
-          int nrep,
-                           long long total_pts, T* __restrict__ st) {
-    const long long gp = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gp >= total_pts) return;
-    const int e = pent[gp];
-    const Entry& E = ent[e];
-    const int s = (int)(gp - pbegin[e]);
-    stencil_row<T>(st + gp * ST_W, E.pos[3 * s], E.pos[3 * s + 1], E.pos[3 * s + 2]);
-}
-
-__global__ void kb_tick(unsigned* step_counter) { *step_counter += 1u; }
-
-// Cell order of the batch's points, so that neighbouring warps of the
-// spread and the interpolation work on nearby stencils of one replica: a
-// counting sort on key = the replica's first bin + the 8^3 brick of the
-// point within the replica.  Each replica's points stay in its own range
-// of slots.  Only the order of the work depends on it, never a result
-// (beyond the order of the spread's atomic additions).
-constexpr int BATCH_BRICK = 8;
-__global__ void kb_brick_count(const Entry* __restrict__ ent, const long long* __restrict__ pbegin,
-                               const int* __restrict__ pent, long long total_pts, int* __restrict__ count,
-                               int* __restrict__ key) {
-    const long long gp = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gp >= total_pts) return;
-    const int e = pent[gp];
-    const Entry& E = ent[e];
-    const int s = (int)(gp - pbegin[e]);
-    int b[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) b[a] = min(max((int)E.pos[3 * s + a] / BATCH_BRICK, 0), E.nb[a] - 1);
-    const int k = E.bin0 + (b[2] * E.nb[1] + b[1]) * E.nb[0] + b[0];
-    key[gp] = k;
-    atomicAdd(&count[k], 1);
-}
-
-__global__ void kb_brick_fill(long long total_pts, const int* __restrict__ key, const int* __restrict__ start,
-                              int* __restrict__ cursor, int* __restrict__ order) {
-    const long long gp = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gp >= total_pts) return;
-    const int k = key[gp];
-    order[start[k] + atomicAdd(&cursor[k], 1)] = (int)gp;
-}
-
-// Interpolated velocity (from the velocity field the collide wrote) at
-// every colloid, one warp each (the scheme of k_interp): v[3 gp + a], FP64.
-template <typename T>
-__global__ void __launch_bounds__(256)
-kb_interp(const Entry* __restrict__ ent, const long long* __restrict__ pbegin, const int* __restrict__ pent,
-          const int* __restrict__ order, long long total_pts, const T* __restrict__ st, double* __restrict__ vout) {
-    const long long slot = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (slot >= total_pts) return;  // uniform per warp
-    const long long gp = order[slot];
-    const int e = pent[gp];
-    const Entry& E = ent[e];
-    const int s = (int)(gp - pbegin[e]);
-    if (!E.mobile[s]) return;  // uniform per warp
-    const Geom& g = E.g;
-    const int lane = threadIdx.x & 31;
-    const T* vel = (const T*)E.vel;
-    const unsigned FULL = 0xffffffffu;
-    const T r = lane < ST_W ? st[gp * ST_W + lane] : T(0);
-    const int bx = bits_int(__shfl_sync(FULL, r, 12)), by = bits_int(__shfl_sync(FULL, r, 13)),
-              bz = bits_int(__shfl_sync(FULL, r, 14));
-    const int i = lane & 3, j = (lane >> 2) & 3;
-    const T wxy = __shfl_sync(FULL, r, i) * __shfl_sync(FULL, r, 4 + j);
-    const int x = wrap_node(bx + i, g.nx), y = wrap_node(by + j, g.ny);
-    const unsigned V = (unsigned)g.V;
-    T acc[3] = {T(0), T(0), T(0)};
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int k = (lane >> 4) + 2 * h;
-        const T wz = __shfl_sync(FULL, r, 8 + k);
-        const int z = wrap_node(bz + k, g.nz);
-        if (is_solid(g, z)) continue;  // v = 0 on solid nodes
-        const T w = wxy * wz;
-        const unsigned site = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.nx + (unsigned)x;
-        acc[0] += w * vel[site];
-        acc[1] += w * vel[V + site];
-        acc[2] += w * vel[2 * V + site];
+    if (FLAT) collide_flat<S, WALLS>(a, parity, seed);
+    else collide_tiled<S>(a, parity, seed);
+    if (!grid_sync(ctl, limit)) return;
+    for (long long q = blockIdx.x; q < items; q += gridDim.x)
+        point_block<T, WALLS, true, BT / 32>(src, q * NPB, a.total_pts, a.order, st, vsh);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->init = 0;
+        ctl->since_sort = sort_due ? 1u : since + 1u;
+        ctl->step = step + 1u;
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1)
-        for (int a = 0; a < 3; ++a) acc[a] += __shfl_xor_sync(FULL, acc[a], off);
-    if (lane < 3) vout[3 * gp + lane] = (double)(lane == 0 ? acc[0] : (lane == 1 ? acc[1] : acc[2]));
-}
-
-// Colloid update of every mobile point of the batch (thread per point,
-// Sec. IV with the a_L subtraction, as k_update) and the stencil row of the
-// new position.
-template <typename T>
-__global__ void kb_update(const Entry* __restrict__ ent, const long long* __restrict__ pbegin, const int* __restrict__ pent,
-          int nrep,
-                          long long total_pts, const double* __restrict__ v, T* __restrict__ st) {
-    const long long gp = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gp >= total_pts) return;
-    const int e = pent[gp];
-    const Entry& E = ent[e];
-    const int s = (int)(gp - pbegin[e]);
-    double P[3] = {E.pos[3 * s], E.pos[3 * s + 1], E.pos[3 * s + 2]};
-    if (E.mobile[s]) {
-        const double c = (recip_fp64(E.radius[s]) - E.inv_aL) * E.inv_6pi_eta;
-        const int nn[3] = {E.g.nx, E.g.ny, E.g.nz};
-        for (int a = 0; a < 3; ++a) {
-            const double L = (double)nn[a];
-            double r = P[a] + v[3 * gp + a] + E.force[3 * s + a] * c;
-            if (r < 0.0) r += L;
-            else if (r >= L) r -= L;
-            if (!(r >= 0.0 && r < L)) {  // moved by a period or more
-                r = r - L * floor(r / L);
-                if (r >= L || r < 0.0) r = 0.0;
-            }
-            P[a] = r;
-            E.pos[3 * s + a] = r;
-        }
-    }
-    stencil_row<T>(st + gp * ST_W, P[0], P[1], P[2]);
 }
 
 }  // namespace
@@ -442,30 +470,30 @@ struct lb_batch {
     std::vector<lb_ctx*> ctx;
     cudaStream_t user_stream;
     cudaStream_t stream;       // private stream: graphs cannot capture the legacy stream
-    cudaEvent_t ev_in, ev_out;
+    cudaEvent_t ev_in, ev_out, ev_err;
     Entry* d_ent;
     long long* d_gbegin;
     long long* d_pbegin;
     Work* d_work;
-    long long total_groups, total_pts, n_mobile;
-    int blocks;                // persistent grid of the collide kernel
-    unsigned* d_step;          // step counter seeding the stochastic rounding
+    long long* d_wbegin;
+    long long total_groups, total_windows, total_pts, n_mobile, total_bins;
+    int blocks;                // grid of the persistent kernel
+    int max_blocks;            // co-resident limit of that grid
+    int sms;
+    BatchCtl* d_ctl;
+    int* h_err;                // page-locked copy of the error flag, written after every step call
+    bool err_pending;          // h_err copy enqueued and not yet inspected
     int* d_pent;               // member of every point of the batch
     int* d_order;              // the points in cell order (slot -> point)
-    int* d_sort;               // counting-sort workspace: count, cursor, start, scan sums, keys
-    long long total_bins;      // cell-order bins of all members
-    int steps_since_sort;
+    int* d_sort;               // counting-sort workspace
+    void* d_st;                // stencil rows of every point
     bool flat;                 // the flat collide applies (every nx % 8 == 0, V < 2^24)
     bool walls;                // some member has solid planes
-    long long* d_wbegin;       // first 32-site window of every member (flat collide)
-    long long total_windows;
-    void* d_st;                // stencil rows of every point (ST_W elements of the arithmetic type)
-    double* d_v;               // interpolated velocity of every point (3 doubles)
     int parity;                // batch steps taken since creation, mod 2
     std::vector<int> cur0;     // each member's current buffer at creation
     std::vector<unsigned> version;  // each member's configuration version at creation
     cudaGraphExec_t graph2;    // two steps (parity 0, 1)
-    bool graph_ready;
+    bool graph_ready, graph_failed;
     long long launches;
     std::string err;
 };
@@ -485,112 +513,75 @@ lb_status bfail(lb_batch* b, lb_status s, const std::string& m) {
                          std::string(where) + ": " + cudaGetErrorString(e_));                     \
     } while (0)
 
-// Launch the phases of one step (parity p) on the batch stream: spread
-// (from the stencil rows), collide (writing v at the colloids' stencil
-// nodes and zeroing the consumed field), interpolation, colloid update
-// (which writes the next stencil rows), and the rounding-seed counter of
-// the 16-bit formats.
+StepArgs step_args(const lb_batch* b) {
+    StepArgs a;
+    a.ent = b->d_ent;
+    a.nrep = b->n;
+    a.wbegin = b->d_wbegin;
+    a.total_windows = b->total_windows;
+    a.gbegin = b->d_gbegin;
+    a.work = b->d_work;
+    a.total_groups = b->total_groups;
+    a.pbegin = b->d_pbegin;
+    a.pent = b->d_pent;
+    a.order = b->d_order;
+    a.total_pts = b->total_pts;
+    a.n_mobile = b->n_mobile;
+    a.st = b->d_st;
+    a.sort_ws = b->d_sort;
+    a.total_bins = b->total_bins;
+    a.ctl = b->d_ctl;
+    return a;
+}
+
 template <typename S>
+const void* step_kernel(bool flat, bool walls) {
+    if (flat) return walls ? (const void*)kb_step<S, true, true> : (const void*)kb_step<S, true, false>;
+    return (const void*)kb_step<S, false, true>;
+}
+
+const void* step_kernel_any(const lb_batch* b) {
+    switch (b->prec) {
+        case LB_F64: return step_kernel<double>(b->flat, b->walls);
+        case LB_F32: return step_kernel<float>(b->flat, b->walls);
+        case LB_F16S: return step_kernel<__half>(b->flat, b->walls);
+        default: return step_kernel<__nv_bfloat16>(b->flat, b->walls);
+    }
+}
+
+// One step (parity p): one cooperative launch of the persistent kernel, so
+// that all its blocks are resident together (the barriers need it).
 cudaError_t launch_step(lb_batch* b, int p, int blocks) {
-    using T = typename Store<S>::T;
-    const unsigned wblocks = (unsigned)((b->total_pts + 7) / 8);      // warp per point
-    const unsigned tblocks = (unsigned)((b->total_pts + 127) / 128);  // thread per point
-    T* st = (T*)b->d_st;
-    if (b->total_pts > 0)
-        kb_spread<T><<<wblocks, 256, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->d_pent, b->d_order, b->total_pts, st);
-    if (b->flat && b->walls)
-        kb_collide_flat<S, true><<<blocks, 128, 0, b->stream>>>(b->d_ent, b->d_wbegin, b->n, b->total_windows, p,
-                                                                b->d_step);
-    else if (b->flat)
-        kb_collide_flat<S, false><<<blocks, 128, 0, b->stream>>>(b->d_ent, b->d_wbegin, b->n, b->total_windows, p,
-                                                                 b->d_step);
-    else
-        kb_collide<S><<<blocks, dim3(32, BW), 0, b->stream>>>(b->d_ent, b->d_gbegin, b->d_work, b->n, b->total_groups,
-                                                              p, b->d_step);
-    if (b->n_mobile > 0) {
-        kb_interp<T><<<wblocks, 256, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->d_pent, b->d_order, b->total_pts, st,
-                                                     b->d_v);
-        kb_update<T><<<tblocks, 128, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->d_pent, b->n, b->total_pts, b->d_v, st);
+    StepArgs a = step_args(b);
+    void* args[2] = {&a, &p};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(BT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = b->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, step_kernel_any(b), args);
+}
+
+// Zero the force fields the members hold (where flagged) so that the next
+// step spreads anew at the current positions.
+cudaError_t clear_member_fields(lb_batch* b) {
+    for (lb_ctx* c : b->ctx) {
+        if (c->npts == 0) continue;
+        cudaError_t e = lbk::launch_clear_field(c);
+        if (e != cudaSuccess) return e;
+        c->field_ready = false;
+        b->launches++;
     }
-    if (sizeof(S) == 2) kb_tick<<<1, 1, 0, b->stream>>>(b->d_step);
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
-// The batch's cell order (5 kernel launches): counts per bin, their
-// exclusive scan, and the fill of the order.
-cudaError_t launch_sort(lb_batch* b) {
-    if (b->total_pts == 0) return cudaSuccess;
-    const long long nb = b->total_bins;
-    int* count = b->d_sort;
-    int* cursor = count + nb;
-    int* start = cursor + nb;
-    int* bsum = start + nb + 1;
-    int* key = bsum + scan_ws_ints(nb);
-    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * 2 * (size_t)nb, b->stream);
-    if (e != cudaSuccess) return e;
-    const unsigned blocks = (unsigned)((b->total_pts + 255) / 256);
-    kb_brick_count<<<blocks, 256, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->d_pent, b->total_pts, count, key);
-    e = scan_exclusive(count, nb, start, bsum, b->stream);
-    if (e != cudaSuccess) return e;
-    kb_brick_fill<<<blocks, 256, 0, b->stream>>>(b->total_pts, key, start, cursor, b->d_order);
-    b->launches += 5;
-    b->steps_since_sort = 0;
-    return cudaGetLastError();
-}
-
-// Stencil rows of the members' current positions (before a batch step).
-template <typename S>
-cudaError_t launch_stencils(lb_batch* b) {
-    using T = typename Store<S>::T;
-    if (b->total_pts == 0) return cudaSuccess;
-    kb_stencil<T><<<(unsigned)((b->total_pts + 127) / 128), 128, 0, b->stream>>>(b->d_ent, b->d_pbegin, b->d_pent, b->n,
-                                                                                b->total_pts, (T*)b->d_st);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_stencils_any(lb_batch* b) {
-    switch (b->prec) {
-        case LB_F64: return launch_stencils<double>(b);
-        case LB_F32: return launch_stencils<float>(b);
-        case LB_F16S: return launch_stencils<__half>(b);
-        default: return launch_stencils<__nv_bfloat16>(b);
-    }
-}
-
-cudaError_t launch_step_any(lb_batch* b, int p, int blocks) {
-    switch (b->prec) {
-        case LB_F64: return launch_step<double>(b, p, blocks);
-        case LB_F32: return launch_step<float>(b, p, blocks);
-        case LB_F16S: return launch_step<__half>(b, p, blocks);
-        default: return launch_step<__nv_bfloat16>(b, p, blocks);
-    }
-}
-
-template <typename S>
-cudaError_t launch_collide_only(lb_batch* b, int blocks) {
-    if (b->flat && b->walls)
-        kb_collide_flat<S, true><<<blocks, 128, 0, b->stream>>>(b->d_ent, b->d_wbegin, b->n, b->total_windows,
-                                                                b->parity, b->d_step);
-    else if (b->flat)
-        kb_collide_flat<S, false><<<blocks, 128, 0, b->stream>>>(b->d_ent, b->d_wbegin, b->n, b->total_windows,
-                                                                 b->parity, b->d_step);
-    else
-        kb_collide<S><<<blocks, dim3(32, BW), 0, b->stream>>>(b->d_ent, b->d_gbegin, b->d_work, b->n, b->total_groups,
-                                                              b->parity, b->d_step);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_collide_any(lb_batch* b, int blocks) {
-    switch (b->prec) {
-        case LB_F64: return launch_collide_only<double>(b, blocks);
-        case LB_F32: return launch_collide_only<float>(b, blocks);
-        case LB_F16S: return launch_collide_only<__half>(b, blocks);
-        default: return launch_collide_only<__nv_bfloat16>(b, blocks);
-    }
-}
-
-int launches_per_step(const lb_batch* b) {
-    return 1 + (b->total_pts > 0 ? 1 : 0) + (b->n_mobile > 0 ? 2 : 0) + (b->prec >= LB_F16S ? 1 : 0);
+cudaError_t set_ctl(lb_batch* b, size_t offset, const void* v, size_t bytes) {
+    return cudaMemcpyAsync((char*)b->d_ctl + offset, v, bytes, cudaMemcpyHostToDevice, b->stream);
 }
 
 }  // namespace
@@ -610,10 +601,9 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
     b->user_stream = (cudaStream_t)stream;
     b->parity = 0;
     std::vector<Entry> ent(n);
-    std::vector<long long> gbegin(n), pbegin(n);
+    std::vector<long long> gbegin(n), pbegin(n), wbegin(n);
     std::vector<Work> work(n);
     long long groups = 0, pts = 0, mob = 0, bins = 0, windows = 0;
-    std::vector<long long> wbegin(n);
     bool flat = true, walls = false;
     for (int i = 0; i < n; ++i) {
         lb_ctx* c = ctxs[i];
@@ -680,27 +670,33 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
     b->total_pts = pts;
     b->n_mobile = mob;
     b->total_bins = bins;
-    b->steps_since_sort = SORT_EVERY;  // the first step sorts
     b->flat = flat;
     b->walls = walls;
     b->total_windows = windows;
-    // untuned: the flat collide 8 blocks per SM, the tiled one a block per item
-    b->blocks = flat ? 152 * 8 : (int)std::min<long long>(std::max<long long>(groups, 1), 0x7fffffffLL);
-    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel_any(b), BT, 0);
+    if (e == cudaSuccess && per_sm < 1) e = cudaErrorCooperativeLaunchTooLarge;
+    b->sms = sms;
+    b->max_blocks = sms * per_sm;
+    // untuned: MIN_BLOCKS blocks per SM (or what fits)
+    b->blocks = std::min(b->max_blocks, sms * MIN_BLOCKS);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_err, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&b->h_err, sizeof(int), cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_ent, sizeof(Entry) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_gbegin, sizeof(long long) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_pbegin, sizeof(long long) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_work, sizeof(Work) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_wbegin, sizeof(long long) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_step, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_ctl, sizeof(BatchCtl));
     if (e == cudaSuccess && pts > 0)
         e = cudaMalloc(&b->d_st, lbk::arith_bytes(b->prec) * ST_W * (size_t)pts);
-    if (e == cudaSuccess && pts > 0) e = cudaMalloc(&b->d_v, sizeof(double) * 3 * (size_t)pts);
     if (e == cudaSuccess && pts > 0) e = cudaMalloc(&b->d_order, sizeof(int) * (size_t)pts);
-    if (e == cudaSuccess && pts > 0)
-        e = cudaMalloc(&b->d_sort, sizeof(int) * ((size_t)(3 * bins + 1) + scan_ws_ints(bins) + (size_t)pts));
+    if (e == cudaSuccess && pts > 0) e = cudaMalloc(&b->d_sort, sizeof(int) * ((size_t)(3 * bins + 1) + (size_t)pts));
     if (e == cudaSuccess && pts > 0) {
         std::vector<int> pent((size_t)pts);
         for (int i = 0; i < n; ++i)
@@ -708,7 +704,13 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
         e = cudaMalloc(&b->d_pent, sizeof(int) * (size_t)pts);
         if (e == cudaSuccess) e = cudaMemcpy(b->d_pent, pent.data(), sizeof(int) * (size_t)pts, cudaMemcpyHostToDevice);
     }
-    if (e == cudaSuccess) e = cudaMemset(b->d_step, 0, sizeof(unsigned));
+    if (e == cudaSuccess) {
+        BatchCtl ctl = {};
+        ctl.since_sort = SORT_EVERY;  // the first step sorts
+        ctl.init = 1;
+        ctl.limit = DEFAULT_WAIT;
+        e = cudaMemcpy(b->d_ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaMemcpy(b->d_ent, ent.data(), sizeof(Entry) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_gbegin, gbegin.data(), sizeof(long long) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_pbegin, pbegin.data(), sizeof(long long) * n, cudaMemcpyHostToDevice);
@@ -718,6 +720,7 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
         lb_batch_destroy(b);
         return e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA;
     }
+    *b->h_err = 0;
     *out = b;
     return LB_OK;
 }
@@ -731,47 +734,64 @@ void lb_batch_destroy(lb_batch* b) {
     cudaFree(b->d_pbegin);
     cudaFree(b->d_work);
     cudaFree(b->d_wbegin);
-    cudaFree(b->d_step);
+    cudaFree(b->d_ctl);
     cudaFree(b->d_st);
-    cudaFree(b->d_v);
     cudaFree(b->d_pent);
     cudaFree(b->d_order);
     cudaFree(b->d_sort);
+    if (b->h_err) cudaFreeHost(b->h_err);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->ev_err) cudaEventDestroy(b->ev_err);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
 
 const char* lb_batch_last_error(const lb_batch* b) { return b ? b->err.c_str() : ""; }
 
+lb_status lb_batch_set_wait_limit(lb_batch* b, long long polls) {
+    if (!b) return LB_ERR_ARG;
+    if (polls < 0) return bfail(b, LB_ERR_ARG, "lb_batch_set_wait_limit: polls < 0");
+    LB_BCUDA(set_ctl(b, offsetof(BatchCtl, limit), &polls, sizeof(polls)), "wait limit");
+    LB_BCUDA(cudaStreamSynchronize(b->stream), "stream synchronize");
+    return LB_OK;
+}
+
+lb_status lb_batch_synchronize(lb_batch* b) {
+    if (!b) return LB_ERR_ARG;
+    LB_BCUDA(cudaStreamSynchronize(b->stream), "stream synchronize");
+    if (b->err_pending) {
+        b->err_pending = false;
+        if (*b->h_err) {
+            // a barrier wait ran out: the step's work is incomplete; reset the
+            // barrier state so that later launches start clean
+            *b->h_err = 0;
+            const unsigned zero[2] = {0u, 0u};
+            const int no = 0;
+            LB_BCUDA(set_ctl(b, offsetof(BatchCtl, count), zero, sizeof(zero)), "barrier reset");
+            LB_BCUDA(set_ctl(b, offsetof(BatchCtl, err), &no, sizeof(no)), "error reset");
+            LB_BCUDA(cudaStreamSynchronize(b->stream), "stream synchronize");
+            return bfail(b, LB_ERR_TIMEOUT, "lb_batch: a grid barrier wait ran out; the last steps are incomplete");
+        }
+    }
+    return LB_OK;
+}
+
 lb_status lb_batch_tune(lb_batch* b, int* blocks_out) {
     if (!b) return LB_ERR_ARG;
-    // Whole trial steps are timed (spread, collide + stream, interpolation,
-    // update), since the collide's best grid depends on the phases around
-    // it.  A trial does not advance the batch: the parity is not flipped,
-    // so every trial reads the same current population buffers and writes
-    // the spare ones; the collide zeroes the force it consumed; the
-    // positions and the rounding counter the trials move are saved first
-    // and put back after the last trial.  A spread field of a query is
-    // cleared first (the next step spreads again).
-    for (lb_ctx* c : b->ctx) {
-        if (c->field_ready) {
-            LB_BCUDA(lbk::launch_clear_field(c), "clear force field");
-            c->field_ready = false;
-        }
-        LB_BCUDA(cudaStreamSynchronize(c->stream), "member stream");
-    }
+    // Whole trial steps are timed (the persistent kernel does every phase),
+    // since the best grid depends on all of them.  A trial does not advance
+    // the batch: the parity is not flipped, so every trial reads the same
+    // current population buffers and writes the spare ones; the positions,
+    // the rounding counter and the sort counter the trials move are saved
+    // first and put back after the last trial, and the force fields the
+    // trials spread are cleared (the next step spreads anew).
+    for (lb_ctx* c : b->ctx) LB_BCUDA(cudaStreamSynchronize(c->stream), "member stream");
+    LB_BCUDA(cudaStreamSynchronize(b->stream), "batch stream");
     double* saved_pos = nullptr;
-    unsigned* saved_step = nullptr;
-    LB_BCUDA(cudaMalloc(&saved_step, sizeof(unsigned)), "tuner scratch");
-    if (b->total_pts > 0) {
-        cudaError_t e = cudaMalloc(&saved_pos, sizeof(double) * 3 * (size_t)b->total_pts);
-        if (e != cudaSuccess) {
-            cudaFree(saved_step);
-            return bfail(b, LB_ERR_OOM, "tuner scratch");
-        }
-    }
+    if (b->total_pts > 0) LB_BCUDA(cudaMalloc(&saved_pos, sizeof(double) * 3 * (size_t)b->total_pts), "tuner scratch");
+    BatchCtl saved_ctl;
+    cudaError_t err = cudaMemcpy(&saved_ctl, b->d_ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost);
     const auto copy_positions = [&](bool save) -> cudaError_t {
         size_t off = 0;
         for (lb_ctx* c : b->ctx) {
@@ -782,32 +802,27 @@ lb_status lb_batch_tune(lb_batch* b, int* blocks_out) {
             if (e != cudaSuccess) return e;
             off += 3 * (size_t)c->npts;
         }
-        return save ? cudaMemcpyAsync(saved_step, b->d_step, sizeof(unsigned), cudaMemcpyDeviceToDevice, b->stream)
-                    : cudaMemcpyAsync(b->d_step, saved_step, sizeof(unsigned), cudaMemcpyDeviceToDevice, b->stream);
+        return cudaSuccess;
     };
-    cudaError_t err = copy_positions(true);
-    // the stencil rows and the cell order of the current positions
-    if (err == cudaSuccess) err = launch_stencils_any(b);
-    if (err == cudaSuccess && b->total_pts > 0) err = launch_sort(b);
+    if (err == cudaSuccess) err = copy_positions(true);
+    // trials start from cleared fields (the first trial spreads)
+    if (err == cudaSuccess) err = clear_member_fields(b);
+    if (err == cudaSuccess) {
+        const int one = 1;
+        err = set_ctl(b, offsetof(BatchCtl, init), &one, sizeof(one));
+    }
     int best = b->blocks;
     float best_ms = 1e30f;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     if (err == cudaSuccess) err = cudaEventCreate(&t0);
     if (err == cudaSuccess) err = cudaEventCreate(&t1);
-    // candidates: persistent grids of 2-16 blocks per SM (contiguous chunks of
-    // work per block or warp), and for the tiled collide one block per work
-    // item (no persistence)
-    const long long per_sm_tiled[] = {2, 4, 8, 16, 0};
-    const long long per_sm_flat[] = {4, 6, 8, 12, 16};
-    const long long* per_sm = b->flat ? per_sm_flat : per_sm_tiled;
-    const long long items = b->flat ? (b->total_windows + 3) / 4 : b->total_groups;
-    for (int ci = 0; ci < 5 && err == cudaSuccess; ++ci) {
-        const long long k = per_sm[ci];
-        const long long want = k ? 152LL * k : std::min<long long>(items, 0x7fffffffLL);
-        const int blocks = (int)std::min<long long>(want, std::max<long long>(1, items));
-        err = launch_step_any(b, b->parity, blocks);  // warm
+    // candidates: persistent grids of 2 to 8 blocks per SM (what fits)
+    const int per_sm[] = {2, 4, 6, 8};
+    for (int ci = 0; ci < 4 && err == cudaSuccess; ++ci) {
+        const int blocks = std::min(b->max_blocks, b->sms * per_sm[ci]);
+        err = launch_step(b, b->parity, blocks);  // warm
         if (err == cudaSuccess) err = cudaEventRecord(t0, b->stream);
-        for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = launch_step_any(b, b->parity, blocks);
+        for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = launch_step(b, b->parity, blocks);
         if (err == cudaSuccess) err = cudaEventRecord(t1, b->stream);
         if (err == cudaSuccess) err = cudaEventSynchronize(t1);
         float ms = 0.f;
@@ -816,16 +831,25 @@ lb_status lb_batch_tune(lb_batch* b, int* blocks_out) {
             best_ms = ms;
             best = blocks;
         }
-        b->launches += 4LL * launches_per_step(b);
+        b->launches += 4;
     }
+    // put the state back: positions, counters, cleared fields
     if (err == cudaSuccess) err = copy_positions(false);
-    if (err == cudaSuccess) err = launch_stencils_any(b);
+    if (err == cudaSuccess) err = clear_member_fields(b);
+    int timed_out = 0;
     if (err == cudaSuccess) err = cudaStreamSynchronize(b->stream);
+    if (err == cudaSuccess) err = cudaMemcpy(&timed_out, &b->d_ctl->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (err == cudaSuccess) {
+        saved_ctl.init = 1;
+        saved_ctl.count = 0;
+        saved_ctl.err = 0;
+        err = cudaMemcpy(b->d_ctl, &saved_ctl, sizeof(BatchCtl), cudaMemcpyHostToDevice);
+    }
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
     cudaFree(saved_pos);
-    cudaFree(saved_step);
     if (err != cudaSuccess) return bfail(b, LB_ERR_CUDA, std::string("lb_batch_tune: ") + cudaGetErrorString(err));
+    if (timed_out) return bfail(b, LB_ERR_TIMEOUT, "lb_batch_tune: a grid barrier wait ran out");
     if (best != b->blocks && b->graph_ready) {
         cudaGraphExecDestroy(b->graph2);
         b->graph_ready = false;
@@ -853,51 +877,62 @@ lb_status lb_batch_step(lb_batch* b, int nsteps) {
             LB_BCUDA(cudaEventRecord(b->ev_in, c->stream), "event record");
             LB_BCUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0), "stream wait");
         }
-        if (c->field_ready) {  // forces already spread by a query: clear, the step spreads again
-            LB_BCUDA(lbk::launch_clear_field(c), "clear force field");
-            LB_BCUDA(cudaEventRecord(b->ev_in, c->stream), "event record");
-            LB_BCUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0), "stream wait");
-            c->field_ready = false;
-        }
     }
-    // the positions may have been set since the last batch step
-    LB_BCUDA(launch_stencils_any(b), "stencil kernel");
-    b->launches += b->total_pts > 0 ? 1 : 0;
-    if (!b->graph_ready && nsteps >= 2) {
-        cudaGraph_t g;
-        LB_BCUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-        cudaError_t e = launch_step_any(b, 0, b->blocks);
-        if (e == cudaSuccess) e = launch_step_any(b, 1, b->blocks);
-        cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
-        if (e != cudaSuccess || e2 != cudaSuccess)
-            return bfail(b, LB_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
-        e = cudaGraphInstantiate(&b->graph2, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return bfail(b, LB_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-        b->graph_ready = true;
+    // The force fields: every member with points holds the forces at its
+    // current positions (the last batch step spread them, or a query did),
+    // or none does and the first step spreads.  A mixture is cleared.
+    bool all_ready = true, any_ready = false;
+    for (lb_ctx* c : b->ctx) {
+        if (c->npts == 0) continue;
+        all_ready = all_ready && c->field_ready;
+        any_ready = any_ready || c->field_ready;
+    }
+    if (!all_ready) {
+        if (any_ready) LB_BCUDA(clear_member_fields(b), "clear force field");
+        const int one = 1;
+        LB_BCUDA(set_ctl(b, offsetof(BatchCtl, init), &one, sizeof(one)), "spread flag");
+    }
+    if (!b->graph_ready && !b->graph_failed && nsteps >= 2) {
+        // two cooperative launches captured as a graph; if the capture or
+        // the instantiation is refused, the steps are launched one by one
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = launch_step(b, 0, b->blocks);
+            if (e1 == cudaSuccess) e1 = launch_step(b, 1, b->blocks);
+            e = cudaStreamEndCapture(b->stream, &g);
+            if (e == cudaSuccess) e = e1;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph2, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e == cudaSuccess) b->graph_ready = true;
+        else {
+            cudaGetLastError();
+            b->graph_failed = true;
+        }
     }
     // The graph holds two steps starting at parity 0: a batch at odd parity
     // takes one plain step first.
-    // The cell order is renewed every SORT_EVERY steps (outside the graph).
     int done = 0;
     while (done < nsteps) {
-        if (b->steps_since_sort >= SORT_EVERY) LB_BCUDA(launch_sort(b), "cell order kernels");
         if (b->graph_ready && b->parity == 0 && nsteps - done >= 2) {
             LB_BCUDA(cudaGraphLaunch(b->graph2, b->stream), "graph launch");
             done += 2;
-            b->steps_since_sort += 2;
         } else {
-            LB_BCUDA(launch_step_any(b, b->parity, b->blocks), "batched step");
+            LB_BCUDA(launch_step(b, b->parity, b->blocks), "batched step");
             b->parity ^= 1;
             done += 1;
-            b->steps_since_sort += 1;
         }
     }
-    b->launches += (long long)nsteps * launches_per_step(b);
+    b->launches += nsteps;
     for (lb_ctx* c : b->ctx) {
         c->cur ^= (nsteps & 1);
-        c->field_ready = false;
+        c->field_ready = c->npts > 0;  // the last point phase spread the forces at the new positions
+        c->stencil_ready = false;      // the member's own stencil rows and order are stale
+        c->order_stale = true;
     }
+    LB_BCUDA(cudaMemcpyAsync(b->h_err, &b->d_ctl->err, sizeof(int), cudaMemcpyDeviceToHost, b->stream), "status copy");
+    b->err_pending = true;
     LB_BCUDA(cudaEventRecord(b->ev_out, b->stream), "event record");
     LB_BCUDA(cudaStreamWaitEvent(b->user_stream, b->ev_out, 0), "stream wait");
     for (lb_ctx* c : b->ctx)

@@ -157,7 +157,7 @@ lb_status invalidate_field(lb_ctx* c) {
 // colloids, every SORT_INTERVAL steps.  Correctness never depends on it.
 constexpr int SORT_INTERVAL = 64;
 
-// Per-point buffers (order, sort workspace, stencil rows, velocities),
+// Per-point buffers (order, sort workspace, stencil rows),
 // grown with the point capacity.
 lb_status ensure_point_buffers(lb_ctx* c) {
     const size_t ws = lbk::sort_ws_ints(c->geom, c->npts);
@@ -166,18 +166,15 @@ lb_status ensure_point_buffers(lb_ctx* c) {
     cudaFree(c->order);
     cudaFree(c->sort_ws);
     cudaFree(c->stencil);
-    cudaFree(c->pt_v);
     c->order = nullptr;
     c->sort_ws = nullptr;
     c->stencil = nullptr;
-    c->pt_v = nullptr;
     c->pt_cap = c->sort_ws_ints = 0;
     const size_t cap = std::max<size_t>((size_t)c->npts, (size_t)c->cap);
     const size_t wcap = lbk::sort_ws_ints(c->geom, (long long)cap);
     LB_CUDA(cudaMalloc(&c->order, sizeof(int) * cap), "point order");
     LB_CUDA(cudaMalloc(&c->sort_ws, sizeof(int) * wcap), "point order workspace");
     LB_CUDA(cudaMalloc(&c->stencil, lbk::arith_bytes(c->prec) * lbk::ST_W * cap), "stencil rows");
-    LB_CUDA(cudaMalloc(&c->pt_v, sizeof(double) * 3 * cap), "point velocities");
     c->pt_cap = cap;
     c->sort_ws_ints = wcap;
     c->order_stale = c->npts > 0;
@@ -214,7 +211,7 @@ lb_status ensure_vel(lb_ctx* c) {
 
 // Phase timing: an event recorded on the context's stream before and after
 // the launches of one phase of a step.
-enum { PH_SPREAD = 0, PH_COLLIDE, PH_INTERP, PH_UPDATE, PH_CORRECTION, PH_COUNT };
+enum { PH_SPREAD = 0, PH_COLLIDE, PH_POINTS, PH_SORT, PH_CORRECTION, PH_COUNT };
 
 lb_status phase_event(lb_ctx* c, cudaEvent_t* ev) {
     if (!c->ev_free.empty()) {
@@ -334,7 +331,6 @@ void lb_destroy(lb_ctx* c) {
     cudaFree(c->order);
     cudaFree(c->sort_ws);
     cudaFree(c->stencil);
-    cudaFree(c->pt_v);
     cudaFree(c->fix_list);
     cudaFree(c->pos);
     cudaFree(c->force);
@@ -533,13 +529,13 @@ lb_status lb_step(lb_ctx* c, int nsteps) {
         if (st != LB_OK) return st;
     }
     const int box[3] = {c->geom.nx, c->geom.ny, c->geom.nz};
-    // Step n (Sec. IV with forward Euler): spread F^n at R^n; collide and
-    // stream with F^n, writing v^n = (j + F^n/2) / rho at the stencil nodes;
-    // interpolate v^n at R^n and move the colloids (plus the learned
-    // correction when a network is attached), which also prepares the
-    // stencil rows of R^{n+1}.  With mobile colloids the collide zeroes the
-    // force it consumed; fixed points alone keep their field from step to
-    // step.
+    // Step n (Sec. IV with forward Euler): spread F^n at R^n unless the
+    // previous step (or a query) already did; collide and stream with F^n,
+    // writing v^n = (j + F^n/2) / rho at the stencil nodes and zeroing the
+    // consumed force; then the point phase: interpolate v^n at R^n, move the
+    // colloids (plus the learned correction when a network is attached) and
+    // spread F^{n+1} at R^{n+1} for the next step.  Fixed points alone keep
+    // their field from step to step (no point phase).
 #define LB_PHASE(call)                       \
     do {                                     \
         lb_status ps_ = (call);              \
@@ -549,7 +545,25 @@ lb_status lb_step(lb_ctx* c, int nsteps) {
         LB_PHASE(phase_begin(c, PH_SPREAD));
         lb_status st = ensure_field(c);
         if (st != LB_OK) return st;
+        if (c->n_mobile > 0) {
+            // the point phase needs the per-point buffers and the stencil rows
+            // of the current positions even where the field was spread
+            // elsewhere (a batch step leaves it spread and the rows stale)
+            st = ensure_point_buffers(c);
+            if (st != LB_OK) return st;
+            if (!c->stencil_ready) {
+                LB_CUDA(lbk::launch_stencil(c), "stencil kernel");
+                c->stencil_ready = true;
+            }
+        }
         LB_PHASE(phase_end(c));
+        if (c->n_mobile > 0 && c->order_stale) {  // the point phase's work order
+            LB_PHASE(phase_begin(c, PH_SORT));
+            if (c->npts > lbk::SORT_MIN_POINTS) LB_CUDA(lbk::launch_sort_points(c), "point order kernels");
+            c->order_stale = false;
+            c->steps_since_sort = 0;
+            LB_PHASE(phase_end(c));
+        }
         const bool corrected = c->n_mobile > 0 && c->corr;
         if (corrected) {  // the network's inputs depend on R^n only
             LB_PHASE(phase_begin(c, PH_CORRECTION));
@@ -563,13 +577,11 @@ lb_status lb_step(lb_ctx* c, int nsteps) {
         LB_PHASE(phase_end(c));
         c->cur ^= 1;
         if (c->n_mobile > 0) {
-            LB_PHASE(phase_begin(c, PH_INTERP));
-            LB_CUDA(lbk::launch_interp(c), "interpolation kernel");
+            LB_PHASE(phase_begin(c, PH_POINTS));
+            LB_CUDA(lbk::launch_points(c, corrected ? c->corr_y : nullptr), "point kernel");
             LB_PHASE(phase_end(c));
-            LB_PHASE(phase_begin(c, PH_UPDATE));
-            LB_CUDA(lbk::launch_update(c, corrected ? c->corr_y : nullptr), "colloid update kernel");
-            LB_PHASE(phase_end(c));
-            c->field_ready = false;  // the collide zeroed the consumed field and flags
+            c->field_ready = true;  // the forces at the new positions, spread for the next step
+            c->stencil_ready = true;
             if (++c->steps_since_sort >= SORT_INTERVAL) c->order_stale = true;
         }
     }

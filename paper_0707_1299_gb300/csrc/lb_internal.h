@@ -45,11 +45,10 @@ struct lb_ctx {
     double* fsum;             // 3 doubles: net point force (device)
     double fsum_host[3];      // its host copy, refreshed when the points change
     int* status;              // 1 int: device-side validation result
-    // per-point work buffers of the spread and the interpolation
+    // per-point work buffers of the spread and the point phase
     int* order;               // the points in cell order
     int* sort_ws;
     void* stencil;            // stencil rows (ST_W elements of the arithmetic type per point)
-    double* pt_v;             // interpolated velocity at every point (3 npts)
     size_t pt_cap, sort_ws_ints;
     bool order_stale;         // positions changed since the last sort
     bool stencil_ready;       // stencil rows match the positions
@@ -96,8 +95,7 @@ struct UForce {
 cudaError_t launch_collide(lb_ctx* c);
 cudaError_t launch_spread(lb_ctx* c);
 cudaError_t launch_gather(lb_ctx* c, int n, const double* qpos, double* vout);
-cudaError_t launch_interp(lb_ctx* c);
-cudaError_t launch_update(lb_ctx* c, const float* y);
+cudaError_t launch_points(lb_ctx* c, const float* y);
 cudaError_t launch_stencil(lb_ctx* c);
 constexpr int SORT_MIN_POINTS = 2048;  // fewer points are taken in their own order
 cudaError_t launch_sort_points(lb_ctx* c);

@@ -8,10 +8,13 @@
 //   k_spread    regularised point forces onto the lattice (Sec. III,
 //               Eq. deltadef): one warp per point in cell order, the 12
 //               one-dimensional weights evaluated once and shuffled,
-//               atomic accumulation into the field.
-//   k_interp    colloid velocity interpolated with the same kernel from the
-//               velocity the collide wrote (Sec. IV), with the update
-//               R += v(R) + F (1/a - 1/a_L) / (6 pi eta) (Eq. a_Ldefn).
+//               atomic accumulation into the field (the first spread of a
+//               set of points; later steps spread in k_points).
+//   k_points    the point phase after the collide: colloid velocity
+//               interpolated with the same kernel from the velocity the
+//               collide wrote (Sec. IV), the update
+//               R += v(R) + F (1/a - 1/a_L) / (6 pi eta) (Eq. a_Ldefn), and
+//               the spread at the new positions for the next step.
 //   k_gather    velocity at arbitrary query points, each stencil node
 //               rebuilt from its pulled populations.
 //   k_moments   rho, u fields and FP64 totals (Eq. macrovariables2).
@@ -86,14 +89,6 @@ __device__ __forceinline__ double wrap_pos(double r, int n) {
     return r;
 }
 
-// The same after a step that moved the point by less than one period: one
-// addition instead of a division, except in the cases wrap_pos settles.
-__device__ __forceinline__ double wrap_step(double r, int n) {
-    const double L = (double)n;
-    if (r < 0.0) r += L;
-    else if (r >= L) r -= L;
-    return (r >= 0.0 && r < L) ? r : wrap_pos(r, n);
-}
 
 // ------------------------------------------------------------- k_spread
 // One warp per point, taken in the cell order of `order`; the point's
@@ -144,75 +139,32 @@ __global__ void k_stencil(int n, const double* __restrict__ pos, T* __restrict__
     stencil_row<T>(st + (size_t)t * ST_W, pos[3 * t], pos[3 * t + 1], pos[3 * t + 2]);
 }
 
-// ------------------------------------------------------------- k_interp
-// Velocity at every point, v(R) = sum over the 64 stencil nodes of phi phi
-// phi v (Sec. IV), from the velocity field the collide kernel wrote in the
-// flagged 8-site groups (every fluid stencil node of a point lies in one:
-// the spread flagged it).  One warp per point, in cell order; lane l takes
-// nodes l and l + 32; lanes 0-2 write v[3 s + a] (FP64).
-template <typename T, bool WALLS>
-__global__ void __launch_bounds__(256)
-k_interp(const T* __restrict__ vel, Geom g, int n, const int* __restrict__ order, const T* __restrict__ st,
-         double* __restrict__ vout) {
-    const int q = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (q >= n) return;  // uniform per warp
-    const int lane = threadIdx.x & 31;
-    const int s = order ? order[q] : q;
-    const unsigned FULL = 0xffffffffu;
-    const T r = lane < ST_W ? st[(size_t)s * ST_W + lane] : T(0);
-    const int bx = bits_int(__shfl_sync(FULL, r, 12)), by = bits_int(__shfl_sync(FULL, r, 13)),
-              bz = bits_int(__shfl_sync(FULL, r, 14));
-    const int i = lane & 3, j = (lane >> 2) & 3;
-    const T wxy = __shfl_sync(FULL, r, i) * __shfl_sync(FULL, r, 4 + j);
-    const int x = wrap_node(bx + i, g.nx), y = wrap_node(by + j, g.ny);
-    const unsigned V = (unsigned)g.V;
-    T acc[3] = {T(0), T(0), T(0)};
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int k = (lane >> 4) + 2 * h;
-        const T wz = __shfl_sync(FULL, r, 8 + k);
-        const int z = wrap_node(bz + k, g.nz);
-        if (WALLS && is_solid(g, z)) continue;  // v = 0 on solid nodes
-        const T w = wxy * wz;
-        const unsigned site = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.nx + (unsigned)x;
-        acc[0] += w * vel[site];
-        acc[1] += w * vel[V + site];
-        acc[2] += w * vel[2 * V + site];
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1)
-        for (int a = 0; a < 3; ++a) acc[a] += __shfl_xor_sync(FULL, acc[a], off);
-    if (lane < 3) vout[3 * s + lane] = (double)(lane == 0 ? acc[0] : (lane == 1 ? acc[1] : acc[2]));
-}
-
-// Colloid update, one thread per point (Sec. IV, forward Euler, unit time
-// step): a mobile point moves by
-//   R <- R + v(R) + F (1/a - 1/a_L) / (6 pi eta)          (Eq. a_Ldefn)
-// plus, with a network output y, y |F| / (6 pi eta a); wrapped
-// periodically.  The stencil row of the new position is written for the
-// next step's spread and interpolation.
+// ------------------------------------------------------------- k_points
+// The point phase of a lattice with colloids, after its collide: a block of
+// 8 warps per 32 points in cell order (point_block): every colloid's
+// velocity is interpolated from the velocity field the collide wrote, every
+// point moves (Sec. IV update, with the network output y when a correction
+// is attached) and its stencil row is rewritten, and the forces are spread
+// at the new positions for the next step.
 template <typename T>
-__global__ void k_update(int n, double* __restrict__ pos, const double* __restrict__ v, const float* __restrict__ y,
-                         const double* __restrict__ F, const double* __restrict__ a, const int* __restrict__ mobile,
-                         double inv_aL, double inv_6pi_eta, Geom g, T* __restrict__ st) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    double P[3] = {pos[3 * t], pos[3 * t + 1], pos[3 * t + 2]};
-    if (mobile[t]) {
-        const int nn[3] = {g.nx, g.ny, g.nz};
-        const double ia = recip_fp64(a[t]);
-        const double c = (ia - inv_aL) * inv_6pi_eta;
-        if (y) {
-            const double f0 = F[3 * t], f1 = F[3 * t + 1], f2 = F[3 * t + 2];
-            const double v0 = sqrt(f0 * f0 + f1 * f1 + f2 * f2) * inv_6pi_eta * ia;
-            for (int k = 0; k < 3; ++k)
-                P[k] = wrap_step(P[k] + v[3 * t + k] + F[3 * t + k] * c + (double)y[3 * t + k] * v0, nn[k]);
-        } else {
-            for (int k = 0; k < 3; ++k) P[k] = wrap_step(P[k] + v[3 * t + k] + F[3 * t + k] * c, nn[k]);
-        }
-        for (int k = 0; k < 3; ++k) pos[3 * t + k] = P[k];
+struct LatticePoints {
+    PointView<T> v;
+    const float* yc;
+    __device__ __forceinline__ PointView<T> view(long long gp) const {
+        PointView<T> p = v;
+        p.s = (int)gp;
+        return p;
     }
-    stencil_row<T>(st + (size_t)t * ST_W, P[0], P[1], P[2]);
+    __device__ __forceinline__ const float* y(long long) const { return yc; }
+};
+
+constexpr int PT_WARPS = 8;  // warps of a k_points block: 32 points
+
+template <typename T, bool WALLS>
+__global__ void __launch_bounds__(PT_WARPS * 32) k_points(const LatticePoints<T> src, long long total,
+                                                          const int* __restrict__ order, T* __restrict__ st) {
+    __shared__ double vsh[4 * PT_WARPS][3];
+    point_block<T, WALLS, true, PT_WARPS>(src, (long long)blockIdx.x * (4 * PT_WARPS), total, order, st, vsh);
 }
 
 // ------------------------------------------------------------- k_gather
@@ -758,37 +710,32 @@ cudaError_t launch_gather(lb_ctx* c, int n, const double* qpos, double* vout) {
 }
 
 template <typename T>
-static cudaError_t interp_t(lb_ctx* c) {
-    const unsigned blocks = (unsigned)((c->npts + 7) / 8);
-    const T* vel = (const T*)c->vel;
-    const T* st = (const T*)c->stencil;
+static cudaError_t points_t(lb_ctx* c, const float* y) {
+    LatticePoints<T> src;
+    src.v.g = c->geom;
+    src.v.floc = (T*)c->floc;
+    src.v.flags = c->flags;
+    src.v.vel = (const T*)c->vel;
+    src.v.pos = c->pos;
+    src.v.force = c->force;
+    src.v.radius = c->radius;
+    src.v.mobile = c->mobile;
+    src.v.inv_aL = isinf(c->a_L) ? 0.0 : 1.0 / c->a_L;
+    src.v.inv_6pi_eta = 1.0 / (6.0 * M_PI * (c->tau_s / 3.0));
+    src.v.s = 0;
+    src.yc = y;
+    const unsigned blocks = (unsigned)((c->npts + 4 * PT_WARPS - 1) / (4 * PT_WARPS));
     if (has_walls(c))
-        k_interp<T, true><<<blocks, 256, 0, c->stream>>>(vel, c->geom, c->npts, point_order(c), st, c->pt_v);
+        k_points<T, true><<<blocks, PT_WARPS * 32, 0, c->stream>>>(src, c->npts, point_order(c), (T*)c->stencil);
     else
-        k_interp<T, false><<<blocks, 256, 0, c->stream>>>(vel, c->geom, c->npts, point_order(c), st, c->pt_v);
+        k_points<T, false><<<blocks, PT_WARPS * 32, 0, c->stream>>>(src, c->npts, point_order(c), (T*)c->stencil);
     c->launches++;
     return cudaGetLastError();
 }
 
-cudaError_t launch_interp(lb_ctx* c) {
+cudaError_t launch_points(lb_ctx* c, const float* y) {
     if (c->npts == 0) return cudaSuccess;
-    return c->prec == LB_F64 ? interp_t<double>(c) : interp_t<float>(c);
-}
-
-template <typename T>
-static cudaError_t update_t(lb_ctx* c, const float* y) {
-    const double eta = c->tau_s / 3.0;
-    const double inv_aL = isinf(c->a_L) ? 0.0 : 1.0 / c->a_L;
-    k_update<T><<<(c->npts + 127) / 128, 128, 0, c->stream>>>(c->npts, c->pos, c->pt_v, y, c->force, c->radius,
-                                                              c->mobile, inv_aL, 1.0 / (6.0 * M_PI * eta), c->geom,
-                                                              (T*)c->stencil);
-    c->launches++;
-    return cudaGetLastError();
-}
-
-cudaError_t launch_update(lb_ctx* c, const float* y) {
-    if (c->npts == 0) return cudaSuccess;
-    return c->prec == LB_F64 ? update_t<double>(c, y) : update_t<float>(c, y);
+    return c->prec == LB_F64 ? points_t<double>(c, y) : points_t<float>(c, y);
 }
 
 cudaError_t launch_stencil(lb_ctx* c) {

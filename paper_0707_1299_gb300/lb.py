@@ -33,7 +33,8 @@ EXPORTS = ["lb_create", "lb_destroy", "lb_last_error", "lb_set_body_force", "lb_
            "lb_colloid_velocity", "lb_mlp_num_params", "lb_mlp_create", "lb_mlp_destroy", "lb_mlp_last_error",
            "lb_mlp_get_params", "lb_mlp_set_params", "lb_mlp_features", "lb_mlp_forward", "lb_mlp_grad",
            "lb_mlp_train_step", "lb_set_colloid_correction", "lb_save", "lb_load",
-           "lb_mlp_set_wait_limit", "lb_set_host_async", "lb_set_phase_timing", "lb_phase_times"]
+           "lb_mlp_set_wait_limit", "lb_set_host_async", "lb_set_phase_timing", "lb_phase_times",
+           "lb_batch_synchronize", "lb_batch_set_wait_limit"]
 
 _lib = None
 
@@ -100,6 +101,8 @@ def load():
         "lb_batch_last_error": ([vp], ctypes.c_char_p),
         "lb_batch_tune": ([vp, ip], ctypes.c_int),
         "lb_batch_step": ([vp, ctypes.c_int], ctypes.c_int),
+        "lb_batch_synchronize": ([vp], ctypes.c_int),
+        "lb_batch_set_wait_limit": ([vp, ctypes.c_longlong], ctypes.c_int),
         "lb_batch_info": ([vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), ip,
                            ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
     }
@@ -225,7 +228,7 @@ def lb_kernel_launches(ctx):
     return n.value
 
 
-PHASES = ("spread", "collide", "interp", "update", "correction")
+PHASES = ("spread", "collide", "points", "sort", "correction")
 
 
 def lb_set_phase_timing(ctx, on):
@@ -414,6 +417,14 @@ def lb_batch_tune(batch):
 
 def lb_batch_step(batch, nsteps):
     _bcheck(batch, load().lb_batch_step(batch, int(nsteps)))
+
+
+def lb_batch_synchronize(batch):
+    _bcheck(batch, load().lb_batch_synchronize(batch))
+
+
+def lb_batch_set_wait_limit(batch, polls):
+    _bcheck(batch, load().lb_batch_set_wait_limit(batch, int(polls)))
 
 
 def lb_batch_info(batch):

@@ -1,6 +1,6 @@
-"""Batched replicas (one launch per phase over all members, graph-replayed
-steps, tuned persistent grid) against the oracle and against stepping each
-member on its own."""
+"""Batched replicas (one persistent cooperative launch per step over all
+members, graph-replayed steps, tuned grid) against the oracle and against
+stepping each member on its own; the bounded grid-barrier wait."""
 import numpy as np
 import pytest
 
@@ -135,5 +135,68 @@ def test_batch_refuses_stale_members():
     with pytest.raises(lb.LBError):
         lb.lb_batch_step(batch, 1)
     lb.lb_batch_destroy(batch)
+    for g in gs:
+        g.close()
+
+
+def test_batch_one_launch_per_step_and_barrier_timeout():
+    # Every batch step is one kernel launch.  A barrier wait bounded to zero
+    # polls gives up at once: the call reports LB_ERR_TIMEOUT through
+    # lb_batch_synchronize (the context stays usable), and with the default
+    # bound restored a fresh batch of fresh members steps correctly again.
+    lb = _lb()
+    probs = _uneven_members("x8")
+    gs = [gpu_lattice(p, lb.LB_F64) for p in probs]
+    batch = lb.lb_batch_create([g.ctx for g in gs])
+    l0 = lb.lb_batch_info(batch)["launches"]
+    lb.lb_batch_step(batch, 6)
+    lb.lb_batch_synchronize(batch)
+    assert lb.lb_batch_info(batch)["launches"] - l0 == 6
+    lb.lb_batch_set_wait_limit(batch, 0)
+    lb.lb_batch_step(batch, 2)
+    with pytest.raises(lb.LBError) as e:
+        lb.lb_batch_synchronize(batch)
+    assert e.value.status == lb.LB_ERR_TIMEOUT
+    lb.lb_batch_synchronize(batch)  # reported once
+    lb.lb_batch_destroy(batch)
+    for g in gs:
+        g.close()
+    gs = [gpu_lattice(p, lb.LB_F64) for p in probs]
+    batch = lb.lb_batch_create([g.ctx for g in gs])
+    lb.lb_batch_step(batch, 5)
+    lb.lb_batch_synchronize(batch)
+    for p, g in zip(probs, gs):
+        _, u, _ = g.moments()
+        o = oracle_lattice(p)
+        o.step(5)
+        assert rel_err(u.cpu().numpy(), o.observe()["u"]) < TOL["f64"], p.name
+    lb.lb_batch_destroy(batch)
+    for g in gs:
+        g.close()
+
+
+def test_members_step_on_after_the_batch():
+    # A batch leaves each member's force field spread at the new positions
+    # and its own stencil rows stale: stepping the members alone afterwards
+    # (the batch destroyed) continues the same trajectories as the oracle.
+    lb = _lb()
+    probs = _uneven_members("x8")
+    gs = [gpu_lattice(p, lb.LB_F64) for p in probs]
+    batch = lb.lb_batch_create([g.ctx for g in gs])
+    lb.lb_batch_step(batch, 10)
+    lb.lb_batch_synchronize(batch)
+    lb.lb_batch_destroy(batch)
+    for g in gs:
+        g.step(7)
+    for p, g in zip(probs, gs):
+        _, u, _ = g.moments()
+        o = oracle_lattice(p)
+        p0 = o.pos.copy()
+        o.step(17)
+        assert rel_err(u.cpu().numpy(), o.observe()["u"]) < TOL["f64"], p.name
+        if len(o.pos):
+            pos, _ = g.particles()
+            d = periodic_diff(pos.cpu().numpy(), p0, p.grid)
+            assert rel_err(d, periodic_diff(o.pos, p0, p.grid)) < TOL["f64"], p.name
     for g in gs:
         g.close()
