@@ -2,6 +2,7 @@
 // ownership of device memory, host/device pointer handling, and the order
 // of the kernels within a time step.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -266,6 +267,10 @@ lb_status lb_create(lb_ctx** out, const int grid[3], double tau_shear, double ta
     if (precision < LB_F64 || precision > LB_BF16S) return fail(nullptr, LB_ERR_ARG, "lb_create: unknown precision");
 
     c = new (std::nothrow) lb_ctx();
+    if (c) {  // spreading of the point phase: direct global reductions, or staged in shared memory
+        const char* sp = getenv("GB300LB_SPREAD");
+        c->spread_shared = sp && strcmp(sp, "shared") == 0;
+    }
     if (!c) return fail(nullptr, LB_ERR_OOM, "lb_create: host allocation failed");
     c->prec = precision;
     c->tau_s = tau_shear;

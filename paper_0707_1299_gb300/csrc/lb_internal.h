@@ -76,6 +76,8 @@ struct lb_ctx {
     std::vector<int> mark_phase;        // phase of each recorded pair
     std::vector<cudaEvent_t> mark_ev;   // start, end of each recorded pair
 
+    int spread_shared;        // 1: the point phase stages its spread in shared memory (GB300LB_SPREAD)
+
     long long launches;       // kernels launched so far
     unsigned seed;            // seed of the stochastic rounding of the 16-bit formats
     unsigned version;         // bumped by every configuration change (batches check it)

@@ -160,11 +160,13 @@ struct LatticePoints {
 
 constexpr int PT_WARPS = 8;  // warps of a k_points block: 32 points
 
-template <typename T, bool WALLS>
+template <typename T, bool WALLS, bool SHARED>
 __global__ void __launch_bounds__(PT_WARPS * 32) k_points(const LatticePoints<T> src, long long total,
                                                           const int* __restrict__ order, T* __restrict__ st) {
     __shared__ double vsh[4 * PT_WARPS][3];
-    point_block<T, WALLS, true, PT_WARPS>(src, (long long)blockIdx.x * (4 * PT_WARPS), total, order, st, vsh);
+    extern __shared__ __align__(16) unsigned char pt_tile[];
+    point_block<T, WALLS, true, PT_WARPS, LatticePoints<T>, SHARED>(src, (long long)blockIdx.x * (4 * PT_WARPS), total,
+                                                                    order, st, vsh, (T*)pt_tile);
 }
 
 // ------------------------------------------------------------- k_gather
@@ -725,10 +727,16 @@ static cudaError_t points_t(lb_ctx* c, const float* y) {
     src.v.s = 0;
     src.yc = y;
     const unsigned blocks = (unsigned)((c->npts + 4 * PT_WARPS - 1) / (4 * PT_WARPS));
-    if (has_walls(c))
-        k_points<T, true><<<blocks, PT_WARPS * 32, 0, c->stream>>>(src, c->npts, point_order(c), (T*)c->stencil);
-    else
-        k_points<T, false><<<blocks, PT_WARPS * 32, 0, c->stream>>>(src, c->npts, point_order(c), (T*)c->stencil);
+    const size_t tile = SHARED_NODES_BYTES;
+    const int* ord = point_order(c);
+    T* st = (T*)c->stencil;
+    if (c->spread_shared) {
+        if (has_walls(c)) k_points<T, true, true><<<blocks, PT_WARPS * 32, tile, c->stream>>>(src, c->npts, ord, st);
+        else k_points<T, false, true><<<blocks, PT_WARPS * 32, tile, c->stream>>>(src, c->npts, ord, st);
+    } else {
+        if (has_walls(c)) k_points<T, true, false><<<blocks, PT_WARPS * 32, 0, c->stream>>>(src, c->npts, ord, st);
+        else k_points<T, false, false><<<blocks, PT_WARPS * 32, 0, c->stream>>>(src, c->npts, ord, st);
+    }
     c->launches++;
     return cudaGetLastError();
 }

@@ -188,6 +188,97 @@ __device__ __forceinline__ void update_point(const PointView<T>& P, const double
     }
 }
 
+// The spread of a block's n points staged in shared memory (the variant
+// the shared-memory pre-reduction design calls for): when the stencils of
+// the block's points fit in a box of at most SHARED_NODES nodes, every
+// contribution is added into a shared tile of that box first (shared-memory
+// atomics), and each tile node that received force is added to the field
+// with one global atomic per component -- stencils that overlap then cost
+// one global reduction per node instead of one per stencil.  The groups'
+// flags are set as in the direct spread.  bases[t] holds the stencil base
+// of point t (as doubles); tile holds 3 SHARED_NODES elements.  Returns
+// false, having done nothing, when the box does not fit (the caller then
+// spreads directly).  All points of the block belong to one lattice.
+constexpr int SHARED_NODES_BYTES = 40 * 1024;  // with the block's static shared memory, within the 48 KiB a launch gets without opting in
+template <typename T, bool WALLS, int NP, typename Src>
+__device__ __forceinline__ bool spread_block_shared(const Src& src, int n, long long gk, const T* __restrict__ st,
+                                                    double (*bases)[3], T* tile, int l, unsigned gmask) {
+    constexpr int MAXN = SHARED_NODES_BYTES / (3 * (int)sizeof(T));
+    __shared__ int box[7];  // lo x, y, z; extent x, y, z; fits
+    if (threadIdx.x == 0) {
+        int lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = (int)bases[0][a];
+            hi[a] = lo[a];
+        }
+        for (int t = 1; t < n; ++t)
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = min(lo[a], (int)bases[t][a]);
+                hi[a] = max(hi[a], (int)bases[t][a]);
+            }
+        long long vol = 1;
+        for (int a = 0; a < 3; ++a) {
+            box[a] = lo[a];
+            box[3 + a] = hi[a] - lo[a] + 4;
+            vol *= box[3 + a];
+        }
+        box[6] = vol <= MAXN;
+    }
+    __syncthreads();
+    if (!box[6]) return false;  // uniform per block
+    const int ex = box[3], ey = box[4], ez = box[5];
+    const int vol = ex * ey * ez;
+    for (int q = threadIdx.x; q < 3 * vol; q += blockDim.x) tile[q] = T(0);
+    __syncthreads();
+    if (gk >= 0) {  // eight lanes a point, as spread_part, into the tile
+        const PointView<T> P = src.view(gk);
+        const T* row = st + gk * ST_W;
+        const T e0 = row[l], e1 = row[8 + l];
+        const int i = l & 3, j0 = l >> 2;
+        const T wx = __shfl_sync(gmask, e0, i, 8);
+        const T wy[2] = {__shfl_sync(gmask, e0, 4 + j0, 8), __shfl_sync(gmask, e0, 6 + j0, 8)};
+        T wz[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) wz[k] = __shfl_sync(gmask, e1, k, 8);
+        const int bx = bits_int(__shfl_sync(gmask, e1, 4, 8)), by = bits_int(__shfl_sync(gmask, e1, 5, 8)),
+                  bz = bits_int(__shfl_sync(gmask, e1, 6, 8));
+        const T F0 = (T)P.force[3 * P.s], F1 = (T)P.force[3 * P.s + 1], F2 = (T)P.force[3 * P.s + 2];
+        const int xw = wrap_node(bx + i, P.g.nx);
+        const bool marker = i == 0 || (xw & (GROUP_X - 1)) == 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = j0 + 2 * h;
+                const T w = wx * wy[h] * wz[k];
+                const int q = ((bz + k - box[2]) * ey + (by + j - box[1])) * ex + (bx + i - box[0]);
+                atomicAdd(&tile[3 * q], F0 * w);
+                atomicAdd(&tile[3 * q + 1], F1 * w);
+                atomicAdd(&tile[3 * q + 2], F2 * w);
+                const int zw = wrap_node(bz + k, P.g.nz);
+                if (marker && !(WALLS && is_solid(P.g, zw))) {
+                    const unsigned rw = (unsigned)zw * (unsigned)P.g.ny + (unsigned)wrap_node(by + j, P.g.ny);
+                    P.flags[rw * (unsigned)P.g.ntx * (TILE_X / GROUP_X) + (unsigned)xw / GROUP_X] = 1;
+                }
+            }
+    }
+    __syncthreads();
+    const PointView<T> P = src.view(0);  // the lattice of every point of the block
+    const unsigned V = (unsigned)P.g.V;
+    for (int q = threadIdx.x; q < vol; q += blockDim.x) {
+        const T f0 = tile[3 * q], f1 = tile[3 * q + 1], f2 = tile[3 * q + 2];
+        if (f0 == T(0) && f1 == T(0) && f2 == T(0)) continue;
+        const int x = wrap_node(box[0] + q % ex, P.g.nx), y = wrap_node(box[1] + (q / ex) % ey, P.g.ny),
+                  z = wrap_node(box[2] + q / (ex * ey), P.g.nz);
+        if (WALLS && is_solid(P.g, z)) continue;
+        const unsigned site = ((unsigned)z * (unsigned)P.g.ny + (unsigned)y) * (unsigned)P.g.nx + (unsigned)x;
+        atomicAdd(P.floc + site, f0);
+        atomicAdd(P.floc + V + site, f1);
+        atomicAdd(P.floc + 2 * V + site, f2);
+    }
+    return true;
+}
+
 // The point phase of one block of NW warps over up to 4 NW consecutive
 // slots of the work order (slot0 ..; point of slot q = order[q], or q
 // itself without an order), in three parts separated by block barriers:
@@ -203,10 +294,10 @@ __device__ __forceinline__ void update_point(const PointView<T>& P, const double
 // positions run (a first spread).  src.view(gp) gives a point's PointView,
 // src.y(gp) its network output rows (or null).  Every thread of the block
 // must call it (it holds block barriers).
-template <typename T, bool WALLS, bool INTERP, int NW, typename Src>
+template <typename T, bool WALLS, bool INTERP, int NW, typename Src, bool SHARED = false>
 __device__ __forceinline__ void point_block(const Src& src, long long slot0, long long total,
                                             const int* __restrict__ order, T* __restrict__ st,
-                                            double (*vsh)[3]) {
+                                            double (*vsh)[3], T* tile = nullptr) {
     constexpr int NP = 4 * NW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n = (int)min((long long)NP, total - slot0);
@@ -246,8 +337,12 @@ __device__ __forceinline__ void point_block(const Src& src, long long slot0, lon
             R[2] = P.pos[3 * P.s + 2];
         }
         stencil_row<T>(st + gp * ST_W, R[0], R[1], R[2]);
+        if (SHARED)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) vsh[t][a] = floor(R[a]) - 1.0;  // stencil base, for the block's box
     }
     __syncthreads();
+    if (SHARED && n > 0 && spread_block_shared<T, WALLS, NP>(src, n, gk, st, vsh, tile, l, gmask)) return;
     if (gk >= 0) {
         const PointView<T> P = src.view(gk);
         const StencilPartT<T> sp = stencil_part<T>(P.g, st + gk * ST_W, gmask, l);
