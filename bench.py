@@ -267,7 +267,7 @@ def run_gpu(args, rank, world):
     torch.cuda.set_device(dev)
     prec = args.precision
     L = args.size
-    n = args.colloids if args.colloids else default_colloids(L)
+    n = args.colloids if args.colloids is not None else default_colloids(L)
     V = L ** 3
     stream = torch.cuda.current_stream()
     g, aL = colloid_lattice(prec, L, n)

@@ -168,18 +168,27 @@ k_collide_pair(const Pops<S> src, const Pops<S> dst, float* __restrict__ floc, f
     const unsigned tile = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.ntx + x0 / TILE_X;
     const unsigned fl = (FIELD && active) ? group_flag(__ldg((const unsigned*)flags + tile), x0 % TILE_X) : 0u;
     const Nbr n = neighbours(g, 0, y, z);
-    unsigned w[NQ];
-    pull19_pair<S, WALLS>(src, n, x0, nx, lane, active, w);
     const unsigned V = (unsigned)g.V;
+    unsigned w[NQ];
+    float2 fa = make_float2(0.0f, 0.0f), fb = fa, fc = fa;
+    // the force loads are issued after the population loads and before the
+    // shuffles wait for those, so both are in flight together
+    pull19_pair<S, WALLS>(src, n, x0, nx, lane, active, w, [&] {
+        if (FIELD && fl) {
+            fa = __ldg((const float2*)(floc + row + x0));
+            fb = __ldg((const float2*)(floc + V + row + x0));
+            fc = __ldg((const float2*)(floc + 2 * V + row + x0));
+        }
+    });
     F2 f[NQ];
 #pragma unroll
     for (int i = 0; i < NQ; ++i) f[i] = F2(St::unpack2(w[i]));
     F2 Fx(fu.F[0]), Fy(fu.F[1]), Fz(fu.F[2]);
-    if (FIELD && fl) {  // after the population loads, so both are in flight together
+    if (FIELD && fl) {
         const F2 sc(SC ? scale : 1.0f);
-        Fx = fma(F2(__ldg((const float2*)(floc + row + x0))), sc, Fx);
-        Fy = fma(F2(__ldg((const float2*)(floc + V + row + x0))), sc, Fy);
-        Fz = fma(F2(__ldg((const float2*)(floc + 2 * V + row + x0))), sc, Fz);
+        Fx = fma(F2(fa), sc, Fx);
+        Fy = fma(F2(fb), sc, Fy);
+        Fz = fma(F2(fc), sc, Fz);
     }
     Coef<F2> k2;
     k2.tau_s = F2(k.tau_s);
@@ -207,6 +216,90 @@ k_collide_pair(const Pops<S> src, const Pops<S> dst, float* __restrict__ floc, f
         for (int a = 0; a < 3; ++a) {
             *(float2*)(vel + a * V + row + x0) = v3[a].v;
             *(float2*)(floc + a * V + row + x0) = make_float2(0.0f, 0.0f);  // the consumed force
+        }
+    }
+    if (VOUT) reset_group_flag(flags, tile, x0 % TILE_X, fl);
+}
+
+// The collide for the 16-bit formats with nx a multiple of 4: four
+// x-adjacent sites a thread, one 64-bit word per population loaded
+// (pull19_quad), so a site costs half the load instructions of
+// k_collide_pair and each load moves twice the bytes (the pair kernel is
+// bound by memory latency at its occupancy: more bytes in flight a warp).
+// The two site pairs run one after the other through the packed FP32x2
+// collision of k_collide_pair, rounded and stored as 32-bit words with the
+// stochastic-rounding conversion (one random stream a thread, seeded by its
+// first site).  The four sites share one 8-site force group.
+// Grid: (ceil(nx / 128), ceil(ny / 4), nz).
+template <typename S, bool WALLS, int FMODE>
+__global__ void __launch_bounds__(CS_THREADS, 5)
+k_collide_quad(const Pops<S> src, const Pops<S> dst, float* __restrict__ floc, flag_t* __restrict__ flags,
+               float* __restrict__ vel, Geom g, Coef<float> k, UForce<float> fu, float scale, float inv_scale,
+               unsigned seed) {
+    using St = Store<S>;
+    constexpr bool SC = St::kScaled, FIELD = FMODE != FM_NONE, VOUT = FMODE == FM_VEL;
+    const int y = blockIdx.y * CS_WARPS + threadIdx.y;
+    if (y >= g.ny) return;  // uniform per warp
+    const int z = blockIdx.z, lane = threadIdx.x;
+    const unsigned nx = (unsigned)g.nx;
+    const unsigned x0 = (blockIdx.x * 32u + (unsigned)lane) * 4u;
+    const bool active = x0 < nx;
+    const unsigned row = (unsigned)z * g.plane + (unsigned)y * nx;
+    if (WALLS && is_solid(g, z)) {  // uniform per warp
+        if (active)
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) *(uint2*)(dst.p[i] + row + x0) = make_uint2(0u, 0u);
+        return;
+    }
+    const unsigned tile = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.ntx + x0 / TILE_X;
+    const unsigned fl = (FIELD && active) ? group_flag(__ldg((const unsigned*)flags + tile), x0 % TILE_X) : 0u;
+    const Nbr n = neighbours(g, 0, y, z);
+    unsigned lo[NQ], hi[NQ];
+    const unsigned V = (unsigned)g.V;
+    float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f), b = a, d = a;
+    pull19_quad<S, WALLS>(src, n, x0, nx, lane, active, lo, hi, [&] {
+        if (FIELD && fl) {  // in flight with the population loads
+            a = __ldg((const float4*)(floc + row + x0));
+            b = __ldg((const float4*)(floc + V + row + x0));
+            d = __ldg((const float4*)(floc + 2 * V + row + x0));
+        }
+    });
+    F2 Fx[2] = {F2(fu.F[0]), F2(fu.F[0])}, Fy[2] = {F2(fu.F[1]), F2(fu.F[1])}, Fz[2] = {F2(fu.F[2]), F2(fu.F[2])};
+    if (FIELD && fl) {
+        const float sc = SC ? scale : 1.0f;
+        Fx[0] = fma(F2(make_float2(a.x, a.y)), F2(sc), Fx[0]);
+        Fx[1] = fma(F2(make_float2(a.z, a.w)), F2(sc), Fx[1]);
+        Fy[0] = fma(F2(make_float2(b.x, b.y)), F2(sc), Fy[0]);
+        Fy[1] = fma(F2(make_float2(b.z, b.w)), F2(sc), Fy[1]);
+        Fz[0] = fma(F2(make_float2(d.x, d.y)), F2(sc), Fz[0]);
+        Fz[1] = fma(F2(make_float2(d.z, d.w)), F2(sc), Fz[1]);
+    }
+    Coef<F2> k2;
+    k2.tau_s = F2(k.tau_s);
+    k2.tau_b = F2(k.tau_b);
+    k2.om_s = F2(k.om_s);
+    k2.om_b = F2(k.om_b);
+    F2 v3[2][3];
+    unsigned rs = rng_seed(row + x0, seed);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {  // the site pairs (x0, x0 + 1) and (x0 + 2, x0 + 3)
+        F2 f[NQ];
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) f[i] = F2(St::unpack2(h ? hi[i] : lo[i]));
+        const unsigned e = row + x0 + 2u * (unsigned)h;
+        // each population is rounded and stored as soon as it is computed
+        const auto emit = [&](int i, F2 v) {
+            const unsigned word = St::bits2_rs(v.v.x, v.v.y, rng_next2(rs));
+            if (active) *(unsigned*)(dst.p[i] + e) = word;
+        };
+        collide19<F2, false, SC, VOUT>(f, Fx[h], Fy[h], Fz[h], k2, emit, F2(inv_scale), v3[h]);
+    }
+    if (VOUT && fl && active) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            *(float4*)(vel + a * V + row + x0) =
+                make_float4(v3[0][a].v.x, v3[0][a].v.y, v3[1][a].v.x, v3[1][a].v.y);
+            *(float4*)(floc + a * V + row + x0) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // the consumed force
         }
     }
     if (VOUT) reset_group_flag(flags, tile, x0 % TILE_X, fl);
@@ -281,10 +374,21 @@ static cudaError_t collide_t(lb_ctx* c) {
     // the 16-bit formats take two sites a thread when the rows pair up
     constexpr bool PAIRABLE = sizeof(S) == 2;
     const bool pair = PAIRABLE && (c->geom.nx % 2) == 0;
+    // four sites a thread (64-bit words) when no force field is read: 4-5 %
+    // faster there; with a force field the pair kernel measured as fast or
+    // faster (the flagged groups' scattered force and velocity
+    // accesses, not the load count, set its time)
+    const bool quad = PAIRABLE && (c->geom.nx % 4) == 0 && mode == FM_NONE;
     const dim3 pgrid((unsigned)((c->geom.nx + 63) / 64), grid.y, grid.z);
+    const dim3 qgrid((unsigned)((c->geom.nx + 127) / 128), grid.y, grid.z);
 #define LB_COLLIDE(W, FM)                                                                                          \
     do {                                                                                                           \
-        if (PAIRABLE && pair)                                                                                      \
+        if (PAIRABLE && quad)                                                                                      \
+            k_collide_quad<PairS<S>, W, FM><<<qgrid, site_block(), 0, c->stream>>>(                                \
+                pops<PairS<S>>(c->f[c->cur], c->geom.V), pops<PairS<S>>(c->f[1 - c->cur], c->geom.V),              \
+                (float*)floc, c->flags, (float*)vel, c->geom, coef_f(k), uforce_f(fu), c->scale, c->inv_scale, \
+                c->seed);                                                                                          \
+        else if (PAIRABLE && pair)                                                                                 \
             k_collide_pair<PairS<S>, W, FM><<<pgrid, site_block(), 0, c->stream>>>(                                \
                 pops<PairS<S>>(c->f[c->cur], c->geom.V), pops<PairS<S>>(c->f[1 - c->cur], c->geom.V),              \
                 (float*)floc, c->flags, (float*)vel, c->geom, coef_f(k), uforce_f(fu), c->scale, c->inv_scale, \

@@ -260,9 +260,9 @@ __host__ __device__ constexpr int pair_shift(int i) {
 // opposite population of the site itself, unshifted (uniform per warp).
 // Every load is issued first (the own-row word of each population, and the
 // edge lanes' words beyond the warp), then the shuffles and permutes.
-template <typename S, bool BOUNCE>
+template <typename S, bool BOUNCE, typename Between>
 __device__ __forceinline__ void pull19_pair_impl(const Pops<S>& src, const Nbr& n, unsigned x0, unsigned nx, int lane,
-                                                 bool active, unsigned w[NQ]) {
+                                                 bool active, unsigned w[NQ], Between&& between) {
     const unsigned c = n.c, ym = n.c + n.dym, yp = n.c + n.dyp, zm = n.c + n.dzm, zp = n.c + n.dzp;
     const bool bm = BOUNCE && n.solid_zm, bp = BOUNCE && n.solid_zp;
     // source population and row of each pull; a bounced pull is unshifted
@@ -321,6 +321,7 @@ __device__ __forceinline__ void pull19_pair_impl(const Pops<S>& src, const Nbr& 
         if (pair_shift(i) < 0 && shifted[i] && active && first) edge[i] = ldw(ptr[i], row[i] + xb);
         if (pair_shift(i) > 0 && shifted[i] && active && last) edge[i] = ldw(ptr[i], row[i] + xa);
     }
+    between();  // more loads of the caller, in flight with these before the shuffles wait for them
 #pragma unroll
     for (int i = 0; i < NQ; ++i) {
         if (pair_shift(i) < 0 && shifted[i]) {  // (element x0 - 1, element x0)
@@ -337,11 +338,120 @@ __device__ __forceinline__ void pull19_pair_impl(const Pops<S>& src, const Nbr& 
 
 // A plane next to a solid one takes the bounce-back selections; every other
 // plane (uniform per warp) the plain pulls.
-template <typename S, bool WALLS>
+// `between()` runs after the loads are issued and before the shuffles that
+// wait for them (the collide issues its force loads there).
+template <typename S, bool WALLS, typename Between>
 __device__ __forceinline__ void pull19_pair(const Pops<S>& src, const Nbr& n, unsigned x0, unsigned nx, int lane,
-                                            bool active, unsigned w[NQ]) {
-    if (WALLS && (n.solid_zm || n.solid_zp)) pull19_pair_impl<S, true>(src, n, x0, nx, lane, active, w);
-    else pull19_pair_impl<S, false>(src, n, x0, nx, lane, active, w);
+                                            bool active, unsigned w[NQ], Between&& between) {
+    if (WALLS && (n.solid_zm || n.solid_zp)) pull19_pair_impl<S, true>(src, n, x0, nx, lane, active, w, between);
+    else pull19_pair_impl<S, false>(src, n, x0, nx, lane, active, w, between);
+}
+
+// ------------------------------------------ pull stream, four sites a thread
+// The 16-bit formats with nx a multiple of 4: a thread takes the sites x0 ..
+// x0 + 3 (x0 a multiple of 4), whose values of one population form one
+// 64-bit word (lo: x0, x0 + 1; hi: x0 + 2, x0 + 3), loaded aligned (nx % 4
+// == 0 makes every population row and V multiples of 4 elements).  A pull
+// from x - 1 needs element x0 - 1, the high half of the previous lane's hi
+// word; a pull from x + 1 needs element x0 + 4, the low half of the next
+// lane's lo word: they arrive by shuffle (the lane at a warp or row edge
+// loads them, wrapping periodically) and byte permutes assemble the two
+// shifted words.  Inactive lanes (x0 >= nx) load nothing but take part in
+// the shuffles.  Returns the two words of each population: lo[i] for the
+// sites x0, x0 + 1 and hi[i] for x0 + 2, x0 + 3.
+template <typename S>
+__device__ __forceinline__ uint2 ldw2(const S* p, unsigned e) {
+    return __ldg((const uint2*)(p + e));
+}
+
+template <typename S, bool BOUNCE, typename Between>
+__device__ __forceinline__ void pull19_quad_impl(const Pops<S>& src, const Nbr& n, unsigned x0, unsigned nx, int lane,
+                                                 bool active, unsigned lo[NQ], unsigned hi[NQ], Between&& between) {
+    const unsigned c = n.c, ym = n.c + n.dym, yp = n.c + n.dyp, zm = n.c + n.dzm, zp = n.c + n.dzp;
+    const bool bm = BOUNCE && n.solid_zm, bp = BOUNCE && n.solid_zp;
+    const S* ptr[NQ];
+    unsigned row[NQ];
+    bool shifted[NQ];
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+        ptr[i] = src.p[i];
+        shifted[i] = pair_shift(i) != 0;
+    }
+    row[0] = c;
+    row[1] = c;
+    row[2] = c;
+    row[3] = ym;
+    row[4] = yp;
+    row[7] = ym;
+    row[8] = yp;
+    row[9] = yp;
+    row[10] = ym;
+    row[5] = zm;
+    row[11] = zm;
+    row[14] = zm;
+    row[15] = zm + n.dym;
+    row[18] = zm + n.dyp;
+    row[6] = zp;
+    row[12] = zp;
+    row[13] = zp;
+    row[16] = zp + n.dyp;
+    row[17] = zp + n.dym;
+    if (bm) {
+        ptr[5] = src.p[6];
+        ptr[11] = src.p[12];
+        ptr[14] = src.p[13];
+        ptr[15] = src.p[16];
+        ptr[18] = src.p[17];
+        row[5] = row[11] = row[14] = row[15] = row[18] = c;
+        shifted[11] = shifted[14] = false;
+    }
+    if (bp) {
+        ptr[6] = src.p[5];
+        ptr[12] = src.p[11];
+        ptr[13] = src.p[14];
+        ptr[16] = src.p[15];
+        ptr[17] = src.p[18];
+        row[6] = row[12] = row[13] = row[16] = row[17] = c;
+        shifted[12] = shifted[13] = false;
+    }
+    const bool first = lane == 0, last = lane == 31 || x0 + 4 >= nx;
+    // the 32-bit words holding element x0 - 1 (as its high half) and x0 + 4
+    // (as its low half), wrapped periodically along the row
+    const unsigned xb = x0 == 0 ? nx - 2 : x0 - 2, xa = x0 + 4 >= nx ? 0 : x0 + 4;
+    uint2 w[NQ];
+    unsigned edge[NQ];
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+        w[i] = active ? ldw2(ptr[i], row[i] + x0) : make_uint2(0u, 0u);
+        edge[i] = 0u;
+        if (pair_shift(i) < 0 && shifted[i] && active && first) edge[i] = ldw(ptr[i], row[i] + xb);
+        if (pair_shift(i) > 0 && shifted[i] && active && last) edge[i] = ldw(ptr[i], row[i] + xa);
+    }
+    between();
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+        if (pair_shift(i) < 0 && shifted[i]) {  // (x0 - 1, x0), (x0 + 1, x0 + 2)
+            unsigned prev = __shfl_up_sync(0xffffffffu, w[i].y, 1);
+            if (first) prev = edge[i];
+            lo[i] = __byte_perm(prev, w[i].x, 0x5432);
+            hi[i] = __byte_perm(w[i].x, w[i].y, 0x5432);
+        } else if (pair_shift(i) > 0 && shifted[i]) {  // (x0 + 1, x0 + 2), (x0 + 3, x0 + 4)
+            unsigned next = __shfl_down_sync(0xffffffffu, w[i].x, 1);
+            if (last) next = edge[i];
+            lo[i] = __byte_perm(w[i].x, w[i].y, 0x5432);
+            hi[i] = __byte_perm(w[i].y, next, 0x5432);
+        } else {
+            lo[i] = w[i].x;
+            hi[i] = w[i].y;
+        }
+    }
+}
+
+template <typename S, bool WALLS, typename Between>
+__device__ __forceinline__ void pull19_quad(const Pops<S>& src, const Nbr& n, unsigned x0, unsigned nx, int lane,
+                                            bool active, unsigned lo[NQ], unsigned hi[NQ], Between&& between) {
+    if (WALLS && (n.solid_zm || n.solid_zp)) pull19_quad_impl<S, true>(src, n, x0, nx, lane, active, lo, hi, between);
+    else pull19_quad_impl<S, false>(src, n, x0, nx, lane, active, lo, hi, between);
 }
 
 // Pulled populations in stored units -> df (only the half format is scaled).
