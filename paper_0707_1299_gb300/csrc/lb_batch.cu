@@ -33,7 +33,10 @@ using namespace lbk;
 constexpr int BW = 4;               // warps (tiles) per work item of the tiled collide
 constexpr int BT = BW * 32;         // threads per block of the persistent kernel
 constexpr int SORT_EVERY = 64;      // steps between renewals of the batch's cell order
-constexpr int MIN_BLOCKS = 8;       // occupancy bound of the persistent kernel (blocks of 128 threads per SM)
+// occupancy bound of the persistent kernel (blocks of 128 threads per SM): 6
+// (85 registers) measured fastest on the 64-replica batch, 1.665 ms a step
+// against 1.705 at 8 (64 registers), 1.754 at 5 and 1.937 at 10 (spills)
+constexpr int MIN_BLOCKS = 6;
 constexpr long long DEFAULT_WAIT = 1LL << 22;  // polls of a barrier wait (~1 s) before it gives up
 
 // Barrier and step state of a batch, in device memory.
@@ -816,7 +819,7 @@ lb_status lb_batch_tune(lb_batch* b, int* blocks_out) {
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     if (err == cudaSuccess) err = cudaEventCreate(&t0);
     if (err == cudaSuccess) err = cudaEventCreate(&t1);
-    // candidates: persistent grids of 2 to 8 blocks per SM (what fits)
+    // candidates: persistent grids of 2 to 8 blocks per SM (as many as fit)
     const int per_sm[] = {2, 4, 6, 8};
     for (int ci = 0; ci < 4 && err == cudaSuccess; ++ci) {
         const int blocks = std::min(b->max_blocks, b->sms * per_sm[ci]);
