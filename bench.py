@@ -117,6 +117,22 @@ FP64_LANES_PER_SM_CLK = 2
 SM_COUNT, SM_MAX_HZ = 152, 2.07e9
 
 
+def fp64_roofline(V, coll_ms):
+    """The FP64 collide against the FP64 pipe: FP64 thread-instructions per
+    site (committed instruction-mix capture) x sites / the phase-timed
+    collide, over 152 SMs x 2.07 GHz x 2 FP64 lanes."""
+    peak = SM_COUNT * SM_MAX_HZ * FP64_LANES_PER_SM_CLK
+    out = {"bound": "alu", "kernel": "k_collide<f64> (FP64 pipe)", "unit": "FP64 inst/s", "peak": peak,
+           "peak_kind": "nominal: 152 SMs x 2.07 GHz x 2 FP64 lanes", "launch_ms": coll_ms}
+    mix = committed_fp64_mix()
+    if mix is None or not coll_ms:
+        return dict(out, achieved=None, frac=None)
+    inst, flop = mix
+    rate = inst * V / (coll_ms * 1e-3)
+    return dict(out, achieved=round(rate, -7), frac=round(rate / peak, 4),
+                tflops=round(flop * V / (coll_ms * 1e-3) / 1e12, 4), fp64_inst_per_site=inst)
+
+
 def cpu_model():
     try:
         out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
@@ -339,7 +355,8 @@ def run_gpu(args, rank, world):
                    "l2": "inputs larger than L2 (each population buffer %.2f GB)" % (19 * BYTES[prec] * V / 1e9),
                    "parallelism": f"replicas{world}"},
         "roofline": {"bound": "hbm",
-                     "kernel": f"k_collide<{prec}, periodic, FM_VEL> ({L}^3, {n} colloids; one launch per step)",
+                     "kernel": f"k_collide<{prec}, periodic, {'FM_VEL' if n else 'FM_NONE'}> ({L}^3, {n} colloids; "
+                               "one launch per step)",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
                      "launch_ms": round(coll_ms, 5), "launches_timed": phases["collide"][1],
@@ -377,6 +394,7 @@ def per_precision_colloids(L, n, steps, head_prec, head_snap, head, timed=40):
     steps, the last `timed` device-timed; errors per field against the FP64
     run.  The FP64 run goes first and is kept as the reference."""
     import torch
+    from paper_0707_1299_gb300 import lb
     peak, _ = measured_peaks()
     stream = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -393,11 +411,15 @@ def per_precision_colloids(L, n, steps, head_prec, head_snap, head, timed=40):
         p0, _ = g.particles()
         g.step(steps - timed)
         torch.cuda.synchronize()
+        lb.lb_set_phase_timing(g.ctx, 1)
         e0.record(stream)
         g.step(timed)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / timed
+        ph = lb.lb_phase_times(g.ctx)
+        lb.lb_set_phase_timing(g.ctx, 0)
+        coll_ms = ph["collide"][0] / ph["collide"][1] if ph["collide"][1] else None
         snap = field_snapshot(g, p0, L)
         row = {"value": round(V / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS", "ms_per_step": round(ms, 4),
                "hbm_frac_of_step": round(step_bytes(prec, V, n) / (ms * 1e-3) / 1e9 / peak, 4)}
@@ -405,7 +427,7 @@ def per_precision_colloids(L, n, steps, head_prec, head_snap, head, timed=40):
             ref = snap
             t = snap["totals"].cpu().numpy()
             row["totals"] = {"mass_minus_V": float(t[0] - V), "momentum": [float(x) for x in t[1:]]}
-            row["bound"] = "alu (FP64 pipe)"
+            row["roofline"] = fp64_roofline(V, coll_ms)
             head["error"] = dict(field_errors(head_snap, ref), steps=steps,
                                  reference="FP64 run (CUDA, oracle-checked) of the same box")
             del head_snap
