@@ -644,7 +644,15 @@ def learned_correction(train_pairs=32, test_pairs=4, L_pair=64, T_pair=1000, ste
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
-        out[name] = {"ms_per_step": round(ms, 4), "value": round(256 ** 3 / (ms * 1e-3) / 1e6, 1)}
+        # the phases on their own streams (the correction runs beside the
+        # collide), in separate steps after the timed ones
+        lb.lb_set_phase_timing(g.ctx, 1)
+        g.step(steps)
+        ph = lb.lb_phase_times(g.ctx)
+        lb.lb_set_phase_timing(g.ctx, 0)
+        out[name] = {"ms_per_step": round(ms, 4), "value": round(256 ** 3 / (ms * 1e-3) / 1e6, 1),
+                     "phase_ms": {k: round(t / c_, 5) for k, (t, c_) in ph.items() if c_}}
+    out["corrected"]["overhead"] = round(out["corrected"]["ms_per_step"] / out["plain"]["ms_per_step"] - 1, 4)
     lb.lb_set_colloid_correction(g.ctx, None)
     g.close()
     lb.lb_mlp_destroy(net)
@@ -663,9 +671,6 @@ def learned_correction(train_pairs=32, test_pairs=4, L_pair=64, T_pair=1000, ste
                                      "rms_plain_over_v0": round(ev["rms_plain"], 6),
                                      "rms_corrected_over_v0": round(ev["rms_corrected"], 6),
                                      "gain": round(ev["gain"], 3)}}
-
-
-# ---------------------------------------------------------- oracle (CPU)
 
 
 # ---------------------------------------------------------- oracle (CPU)

@@ -488,9 +488,9 @@ lb_status lb_set_positions(lb_ctx* c, const double* pos) {
 }
 
 namespace {
+// Buffers of the learned correction and its candidate lists.
 lb_status ensure_corr_buffers(lb_ctx* c) {
     const int box[3] = {c->geom.nx, c->geom.ny, c->geom.nz};
-    const size_t ws = lbk::mlp_features_ws_ints(c->npts, box);
     if ((size_t)c->npts > c->corr_cap) {
         cudaStreamSynchronize(c->stream);
         cudaFree(c->corr_feat);
@@ -503,13 +503,22 @@ lb_status ensure_corr_buffers(lb_ctx* c) {
         LB_CUDA(cudaMalloc(&c->corr_y, sizeof(float) * 3 * n), "correction buffers");
         c->corr_cap = n;
     }
-    if (ws > c->corr_ws_ints) {
+    const int slots = lbk::verlet_capacity(c->npts, box);
+    const size_t ws = lbk::verlet_ws_bytes(c->npts, box, slots);
+    bool fresh = c->corr_ws_n != c->npts || c->corr_ws_slots != slots;
+    if (ws > c->corr_ws_bytes) {
         cudaStreamSynchronize(c->stream);
         cudaFree(c->corr_ws);
         c->corr_ws = nullptr;
-        c->corr_ws_ints = 0;
-        LB_CUDA(cudaMalloc(&c->corr_ws, sizeof(int) * ws), "correction workspace");
-        c->corr_ws_ints = ws;
+        c->corr_ws_bytes = 0;
+        LB_CUDA(cudaMalloc(&c->corr_ws, ws), "correction workspace");
+        c->corr_ws_bytes = ws;
+        fresh = true;
+    }
+    if (fresh) {  // a rebuild on the next step (the lists index the points)
+        LB_CUDA(lbk::verlet_reset(c->corr_ws, c->npts, box, slots, c->stream), "correction workspace");
+        c->corr_ws_n = c->npts;
+        c->corr_ws_slots = slots;
     }
     return LB_OK;
 }
@@ -570,9 +579,14 @@ lb_status lb_step(lb_ctx* c, int nsteps) {
             LB_PHASE(phase_end(c));
         }
         const bool corrected = c->n_mobile > 0 && c->corr;
-        if (corrected) {  // the network's inputs depend on R^n only
+        if (corrected) {
+            // the network's inputs depend on R^n only.  (They do not depend
+            // on the collide either, but run beside it on a second stream
+            // they slow the bandwidth-bound collide by about as much as they
+            // hide: in series on the one stream.)
             LB_PHASE(phase_begin(c, PH_CORRECTION));
-            LB_CUDA(lbk::mlp_features(c->npts, c->pos, box, c->corr_feat, c->corr_ws, c->stream), "feature kernels");
+            LB_CUDA(lbk::verlet_features(c->corr_ws, c->npts, c->corr_ws_slots, c->pos, box, c->corr_feat, c->stream),
+                    "feature kernels");
             LB_CUDA(lbk::mlp_forward(c->corr, c->npts, c->corr_feat, c->corr_y, c->stream), "forward kernel");
             c->launches += lbk::MLP_FEATURE_LAUNCHES + 1;
             LB_PHASE(phase_end(c));

@@ -66,8 +66,10 @@ struct lb_ctx {
     lb_mlp* corr;
     float* corr_feat;         // features (27 npts)
     float* corr_y;            // network output (3 npts)
-    int* corr_ws;             // feature workspace
-    size_t corr_cap, corr_ws_ints;
+    void* corr_ws;            // candidate lists of the features (verlet_features)
+    size_t corr_cap, corr_ws_bytes;
+    long long corr_ws_n;      // points and list slots the lists were laid out for
+    int corr_ws_slots;
 
     // phase timing (lb_set_phase_timing): an event pair around each phase of
     // every lb_step, summed by lb_phase_times
@@ -117,9 +119,17 @@ cudaError_t launch_convert_in(lb_ctx* c, const double* df);
 cudaError_t launch_clear_field(lb_ctx* c);
 template <typename T>
 UForce<T> uniform_force(const lb_ctx* c);
-constexpr int MLP_FEATURE_LAUNCHES = 6;  // kernels of one mlp_features call
+constexpr int MLP_FEATURE_LAUNCHES = 6;  // kernels of one mlp_features or verlet_features call
 size_t mlp_features_ws_ints(long long n, const int box[3]);
 cudaError_t mlp_features(long long n, const double* pos, const int box[3], float* feat, int* ws, cudaStream_t st);
+// Features of a lattice's colloids with candidate lists kept between steps
+// (rebuilt on the device when a point has moved too far): list slots per
+// point, workspace bytes, reset (forces a rebuild), and the feature call.
+int verlet_capacity(long long n, const int box[3]);
+size_t verlet_ws_bytes(long long n, const int box[3], int cap);
+cudaError_t verlet_reset(void* ws, long long n, const int box[3], int cap, cudaStream_t st);
+cudaError_t verlet_features(void* ws, long long n, int cap, const double* pos, const int box[3], float* feat,
+                            cudaStream_t st);
 cudaError_t mlp_forward(const lb_mlp* net, long long n, const float* feat, float* out, cudaStream_t st);
 cudaError_t compute_inv_aL(const int grid[3], const double R[3], const double dir[3], double* inv_aL);
 

@@ -34,6 +34,31 @@ constexpr int NNB = 8;
 
 __device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 __device__ __forceinline__ float silu(float z) { return z / (1.0f + expf(-z)); }
+
+// SiLU of the inference forward, z / (1 + e^-z), from the hardware base-2
+// exponential and reciprocal (about 10 instructions against about 25 for
+// expf and the IEEE division).  e^-z = 2^t, t = -z log2(e), by Cody and
+// Waite's additive range reduction: t_hi = fl(-z L_hi), and the rest
+// r = (-z L_hi - t_hi) + (-z) L_lo (the first term exact from an FMA,
+// L_hi + L_lo = log2(e) to 2^-50), so 2^t = 2^t_hi (1 + r ln 2) to O(r^2),
+// r < 2^-17.  ex2.approx and rcp.approx are each within 2 ulp: the result
+// is within a few ulp of z / (1 + e^-z), the class of the library path,
+// and the bfloat16 rounding that follows it decides the same way save for
+// values within those few ulp of a rounding boundary.  t is clamped at 126
+// so that 1 + 2^t stays finite (there z < -87 and z / (1 + e^-z) is below
+// 2^-119 in magnitude either way).
+__device__ __forceinline__ float silu_fwd(float z) {
+    constexpr float L_HI = 1.44269502162933349609375f;  // log2(e) rounded to float
+    constexpr float L_LO = 1.925962989091e-8f;        // log2(e) - L_HI
+    constexpr float LN2 = 0.693147180559945309f;
+    const float t = -z * L_HI;
+    const float r = fmaf(-z, L_HI, -t) + (-z) * L_LO;
+    float e, q;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(fminf(t, 126.0f)));
+    e = fmaf(e, r * LN2, e);
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(q) : "f"(1.0f + e));
+    return z * q;
+}
 __device__ __forceinline__ float dsilu(float z) {
     const float s = 1.0f / (1.0f + expf(-z));
     return s * (1.0f + z * (1.0f - s));
@@ -60,17 +85,22 @@ constexpr int NCOL = 64;        // tensor-memory columns (both layers reuse them
 // shared-memory layout (bytes)
 constexpr int B1 = 0;                       // W1 [64][32] bf16
 constexpr int B2 = B1 + D1 * K1 * 2;        // W2 [64][64] bf16
-constexpr int A1 = B2 + D2 * D1 * 2;        // x  [128][32] bf16
-constexpr int A2 = A1 + M * K1 * 2;         // h1 [128][64] bf16
+constexpr int A2 = B2 + D2 * D1 * 2;        // h1 [128][64] bf16
+constexpr int A1 = A2;                      // x  [128][32] bf16, in h1's place: the first
+                                            // product has completed before h1 is written,
+                                            // the second before the next tile's x
 constexpr int W3S = A2 + M * D1 * 2;        // W3 [3][64] float (bf16-rounded)
 constexpr int BIAS = W3S + D3 * D2 * 4;     // b1 b2 b3 float
 constexpr int MBAR = BIAS + 132 * 4;        // mbarrier (8 bytes)
 constexpr int TADDR = MBAR + 8;             // tensor-memory address from tcgen05.alloc
 constexpr int USED = TADDR + 8;
-// requested dynamic shared memory: at most 4 CTAs per SM, so 4 x 64 of the
-// 512 tensor-memory columns are ever allocated at once (alloc never waits)
-constexpr int SMEM = 56 * 1024;
+// requested dynamic shared memory: it admits at most 7 CTAs per SM (with the
+// 1 KB the SM reserves per CTA), so at most 7 x 64 of the 512 tensor-memory
+// columns are ever allocated at once (alloc never waits)
+constexpr int FWD_CTAS = 7;
+constexpr int SMEM = 30 * 1024;
 static_assert(USED <= SMEM, "shared layout");
+static_assert((FWD_CTAS + 1) * (SMEM + 1024) > 228 * 1024 && FWD_CTAS * NCOL <= 512, "CTAs per SM");
 
 // byte offset of element (row, k) in a K-major no-swizzle operand with K columns
 __host__ __device__ constexpr int kmajor_off(int row, int k, int K) {
@@ -157,6 +187,16 @@ __device__ __forceinline__ void load_row32(uint32_t taddr, float* v) {
     for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+__device__ __forceinline__ void load_row8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
+}
+
 __device__ __forceinline__ void load_row16(uint32_t taddr, float* v) {
     uint32_t r[16];
     asm volatile(
@@ -190,10 +230,9 @@ __device__ __forceinline__ void store_row64(uint32_t taddr, const float (&v)[64]
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
-    const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
-    return a | (b << 16);
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {  // both rounded to nearest even
+    const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&p);
 }
 
 // Transposed write of 2-byte values into a K-major operand whose K runs
@@ -221,7 +260,7 @@ __device__ __forceinline__ void write_transposed(unsigned char* base, int row0, 
 // polls at most `polls` times.  On a timeout status[0] is set to 1 and the
 // kernel stops: it first waits (default bound) for the work it issued, then
 // frees its tensor memory.
-__global__ void __launch_bounds__(tc::M) km_forward_tc(const float* __restrict__ params, long long n,
+__global__ void __launch_bounds__(tc::M, tc::FWD_CTAS) km_forward_tc(const float* __restrict__ params, long long n,
                                                        const float* __restrict__ feat, float* __restrict__ out,
                                                        int* __restrict__ status, long long polls) {
     using namespace tc;
@@ -231,19 +270,28 @@ __global__ void __launch_bounds__(tc::M) km_forward_tc(const float* __restrict__
     float* w3 = (float*)(smem + W3S);
     float* bias = (float*)(smem + BIAS);
 
-    // weights, rounded to bfloat16, in the K-major layout
-    for (int i = tid; i < D1 * K1; i += M) {
-        const int r = i / K1, k = i % K1;
+    // weights, rounded to bfloat16, in the K-major layout; the loops have
+    // fixed trip counts and are unrolled so that every load of a thread is
+    // in flight at once (a CTA starts with one memory latency, not 50)
+    static_assert(D1 * K1 % M == 0 && D2 * D1 % M == 0 && D1 <= M && D2 <= M, "staging loops");
+#pragma unroll
+    for (int it = 0; it < D1 * K1 / M; ++it) {
+        const int i = it * M + tid, r = i / K1, k = i % K1;
         const float w = k < D0 ? params[OFF_W1 + r * D0 + k] : 0.0f;
         *(__nv_bfloat16*)(smem + B1 + kmajor_off(r, k, K1)) = __float2bfloat16_rn(w);
     }
-    for (int i = tid; i < D2 * D1; i += M) {
-        const int r = i / D1, k = i % D1;
+#pragma unroll
+    for (int it = 0; it < D2 * D1 / M; ++it) {
+        const int i = it * M + tid, r = i / D1, k = i % D1;
         *(__nv_bfloat16*)(smem + B2 + kmajor_off(r, k, D1)) = __float2bfloat16_rn(params[OFF_W2 + i]);
     }
-    for (int i = tid; i < D3 * D2; i += M) w3[i] = bf16r(params[OFF_W3 + i]);
-    for (int i = tid; i < D1; i += M) bias[i] = params[OFF_B1 + i];
-    for (int i = tid; i < D2; i += M) bias[D1 + i] = params[OFF_B2 + i];
+#pragma unroll
+    for (int it = 0; it < (D3 * D2 + M - 1) / M; ++it) {
+        const int i = it * M + tid;
+        if (i < D3 * D2) w3[i] = bf16r(params[OFF_W3 + i]);
+    }
+    if (tid < D1) bias[tid] = params[OFF_B1 + tid];
+    if (tid < D2) bias[D1 + tid] = params[OFF_B2 + tid];
     if (tid < D3) bias[D1 + D2 + tid] = params[OFF_B3 + tid];
     if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
     if (warp == 0) {
@@ -294,14 +342,14 @@ __global__ void __launch_bounds__(tc::M) km_forward_tc(const float* __restrict__
         phase ^= 1u;
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        float z[64];
-        load_row64(trow, z);
-        // h1 = bf16(silu(z1 + b1)) into the layer-2 operand
-#pragma unroll
+        // h1 = bf16(silu(z1 + b1)) into the layer-2 operand, 8 accumulator
+        // columns at a time (a rolled loop: few registers, little code)
+#pragma unroll 1
         for (int kg = 0; kg < D1 / 8; ++kg) {
-            float h[8];
+            float z[8], h[8];
+            load_row8(trow + 8 * kg, z);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) h[e] = silu(z[8 * kg + e] + bias[8 * kg + e]);
+            for (int e = 0; e < 8; ++e) h[e] = silu_fwd(z[e] + bias[8 * kg + e]);
             uint4 v;
             v.x = pack_bf16(h[0], h[1]);
             v.y = pack_bf16(h[2], h[3]);
@@ -323,15 +371,21 @@ __global__ void __launch_bounds__(tc::M) km_forward_tc(const float* __restrict__
         phase ^= 1u;
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        load_row64(trow, z);
-        // h2 = bf16(silu(z2 + b2)); y = W3 h2 + b3 on the CUDA cores
+        // h2 = bf16(silu(z2 + b2)); y = W3 h2 + b3 on the CUDA cores, summed
+        // over k = 0..63 in order
         float y0 = bias[D1 + D2], y1 = bias[D1 + D2 + 1], y2 = bias[D1 + D2 + 2];
+#pragma unroll 1
+        for (int kg = 0; kg < D2 / 8; ++kg) {
+            float z[8];
+            load_row8(trow + 8 * kg, z);
 #pragma unroll
-        for (int k = 0; k < D2; ++k) {
-            const float h = bf16r(silu(z[k] + bias[D1 + k]));
-            y0 = fmaf(h, w3[k], y0);
-            y1 = fmaf(h, w3[D2 + k], y1);
-            y2 = fmaf(h, w3[2 * D2 + k], y2);
+            for (int e = 0; e < 8; ++e) {
+                const int k = 8 * kg + e;
+                const float h = bf16r(silu_fwd(z[e] + bias[D1 + k]));
+                y0 = fmaf(h, w3[k], y0);
+                y1 = fmaf(h, w3[D2 + k], y1);
+                y2 = fmaf(h, w3[2 * D2 + k], y2);
+            }
         }
         if (s < n) {
             out[s * D3] = y0;
@@ -783,6 +837,268 @@ kf_knn(const double* __restrict__ pos, long long n, Geom g, int3 nc, const int* 
     }
 }
 
+// ------------------------------------------- features with a Verlet list
+// The same features for a lattice's colloids step after step.  Positions
+// move far less than a lattice spacing per step, so the candidates of a
+// point are kept from one rebuild to the next.  Let MOVE bound how far any
+// point has moved since the rebuild (float32 displacement, minimum image;
+// a larger one raises the rebuild flag), so that the distance of any pair
+// has changed by at most 2 MOVE (exact distances obey the triangle
+// inequality of the periodic box; the float32 ones differ from them by far
+// less than 1/64 in boxes below 2^12).  Then the kept candidates of a
+// point p are the others within
+//   r_in = min(e8 + 4 MOVE + 1/16, R_CUT + SKIN)
+// at the rebuild, e8 the 8th smallest distance of another point within
+// R_CUT + SKIN (all of them when there are fewer than 8): the 8 points
+// nearest at the rebuild are now within e8 + 2 MOVE, so a point beyond r_in
+// at the rebuild is now farther than all 8 and is not selected; and if one
+// of those 8 is now beyond R_CUT, then e8 > R_CUT - 2 MOVE and r_in reaches
+// R_CUT + SKIN >= R_CUT + 2 MOVE, which holds every point now within
+// R_CUT.  Selection and ordering then run over the kept candidates with
+// the current positions, exactly as over all points.  The rebuild kernels
+// run every step but return at once unless the displacement check of the
+// step raised the flag.
+constexpr float SKIN = 0.25f;
+constexpr float MOVE = 0.5f * SKIN - 1.0f / 64.0f;
+constexpr float INNER = 4.0f * MOVE + 1.0f / 16.0f;
+constexpr float LIST_R = R_CUT + SKIN;
+constexpr float CELL_WV = LIST_R + 1.0f / 64.0f;
+constexpr float LIST_R2 = LIST_R * LIST_R;
+constexpr float MOVE_R2 = MOVE * MOVE;
+
+struct Verlet {
+    float4* fnow;    // current float32 position and index (.w), point order
+    float4* fbuild;  // position at the last rebuild, point order
+    float4* spos;    // positions at the last rebuild in cell order (index in .w)
+    int* cell;       // cell of each point at the last rebuild
+    int* len;        // candidates of cell-order slot q (-1: more than cap; scan the cells)
+    int* list;       // candidate k of slot q at list[k * n + q] (point indices)
+    int* count;      // per cell; zero between rebuilds
+    int* cursor;     // per cell; zero between rebuilds
+    int* start;      // m + 1 cell starts of the last rebuild
+    int* flag;       // 1: rebuild this step
+    long long n, m;
+    int cap;
+    int3 nc;
+};
+
+// Current float32 positions; raise the flag where a point moved too far.
+__global__ void kv_prep(const double* __restrict__ pos, Verlet v, Geom g) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= v.n) return;
+    const float x = (float)pos[3 * i], y = (float)pos[3 * i + 1], z = (float)pos[3 * i + 2];
+    v.fnow[i] = make_float4(x, y, z, __int_as_float((int)i));
+    const float4 b = v.fbuild[i];
+    const float bx = (float)g.nx, by = (float)g.ny, bz = (float)g.nz;
+    const float dx = min_image_f(x, b.x, bx, 0.5f * bx), dy = min_image_f(y, b.y, by, 0.5f * by),
+                dz = min_image_f(z, b.z, bz, 0.5f * bz);
+    if (!(dx * dx + dy * dy + dz * dz <= MOVE_R2)) *v.flag = 1;  // also for a first or non-finite build
+}
+
+__global__ void kv_count(Verlet v, float3 inv_w) {
+    if (!*v.flag) return;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= v.n) return;
+    const float4 p = v.fnow[i];
+    const int c = (cell_of(p.z, inv_w.z, v.nc.z) * v.nc.y + cell_of(p.y, inv_w.y, v.nc.y)) * v.nc.x +
+                  cell_of(p.x, inv_w.x, v.nc.x);
+    v.cell[i] = c;
+    atomicAdd(&v.count[c], 1);
+}
+
+// Exclusive scan of the m cell counts into start[0..m] by one block: each
+// thread sums a contiguous chunk, the block scans the chunk sums.
+constexpr int VSCAN_THREADS = 1024;
+__global__ void __launch_bounds__(VSCAN_THREADS) kv_scan(Verlet v) {
+    if (!*v.flag) return;
+    __shared__ int wsum[VSCAN_THREADS / 32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const long long per = (v.m + VSCAN_THREADS - 1) / VSCAN_THREADS;
+    const long long a = min(v.m, (long long)t * per), b = min(v.m, a + per);
+    int s = 0;
+    for (long long c = a; c < b; ++c) s += v.count[c];
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int w = wsum[lane];
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += u;
+        }
+        wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    int run = wsum[warp] + incl - s;
+    for (long long c = a; c < b; ++c) {
+        v.start[c] = run;
+        run += v.count[c];
+    }
+    if (t == VSCAN_THREADS - 1) v.start[v.m] = run;  // the last chunk ends at m
+}
+
+__global__ void kv_fill(Verlet v) {
+    if (!*v.flag) return;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= v.n) return;
+    const int c = v.cell[i];
+    const float4 p = v.fnow[i];
+    v.spos[v.start[c] + atomicAdd(&v.cursor[c], 1)] = p;
+    v.fbuild[i] = p;
+}
+
+// Walk the 27 cells (fewer when an axis has under 3) around cell c0 of the
+// last rebuild, calling visit(slot) for every cell-order slot in them.
+template <typename Visit>
+__device__ __forceinline__ void walk_cells(const Verlet& v, int c0, Visit&& visit) {
+    const int cx = c0 % v.nc.x, cyz = c0 / v.nc.x;
+    const AxisWalk wy(cyz % v.nc.y, v.nc.y), wz(cyz / v.nc.y, v.nc.z);
+    int xa, xb, xc, xd;  // x cells [xa, xb) and [xc, xd) of every row
+    if (v.nc.x < 3) {
+        xa = 0, xb = v.nc.x, xc = xd = 0;
+    } else if (cx == 0) {
+        xa = 0, xb = 2, xc = v.nc.x - 1, xd = v.nc.x;
+    } else if (cx == v.nc.x - 1) {
+        xa = cx - 1, xb = v.nc.x, xc = 0, xd = 1;
+    } else {
+        xa = cx - 1, xb = cx + 2, xc = xd = 0;
+    }
+    for (int kz = 0; kz < wz.count(); ++kz) {
+        const int rz = wz.at(kz) * v.nc.y;
+        for (int ky = 0; ky < wy.count(); ++ky) {
+            const int row = (rz + wy.at(ky)) * v.nc.x;
+            for (int qq = v.start[row + xa], e = v.start[row + xb]; qq < e; ++qq) visit(qq);
+            for (int qq = v.start[row + xc], e = v.start[row + xd]; qq < e; ++qq) visit(qq);
+        }
+    }
+}
+
+// The kept candidates of every cell-order slot (two walks over the cells:
+// the 8 smallest distances give r_in, then the points within it are
+// listed); then the per-cell counters are cleared for the next rebuild
+// (nothing here reads them).
+__global__ void __launch_bounds__(KNN_THREADS) kv_build(Verlet v, Geom g) {
+    if (!*v.flag) return;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long c = tid; c < v.m; c += (long long)gridDim.x * blockDim.x) {
+        v.count[c] = 0;
+        v.cursor[c] = 0;
+    }
+    const long long q = tid;
+    if (q >= v.n) return;
+    const float4 me = v.spos[q];
+    const float box[3] = {(float)g.nx, (float)g.ny, (float)g.nz};
+    const float half[3] = {0.5f * box[0], 0.5f * box[1], 0.5f * box[2]};
+    const auto dist2 = [&](int qq) {
+        const float4 o = v.spos[qq];
+        const float dx = min_image_f(o.x, me.x, box[0], half[0]);
+        const float dy = min_image_f(o.y, me.y, box[1], half[1]);
+        const float dz = min_image_f(o.z, me.z, box[2], half[2]);
+        return dx * dx + dy * dy + dz * dz;
+    };
+    const int c0 = v.cell[__float_as_int(me.w)];
+    float near[NNB];  // the 8 smallest squared distances within LIST_R, ascending
+#pragma unroll
+    for (int k = 0; k < NNB; ++k) near[k] = INFINITY;
+    walk_cells(v, c0, [&](int qq) {
+        if (qq == q) return;
+        float r2 = dist2(qq);
+        if (!(r2 <= LIST_R2) || r2 >= near[NNB - 1]) return;
+#pragma unroll
+        for (int k = 0; k < NNB; ++k) {
+            const float t = near[k];
+            near[k] = fminf(r2, t);
+            r2 = fmaxf(r2, t);
+        }
+    });
+    const float r_in = near[NNB - 1] <= LIST_R2 ? fminf(sqrtf(near[NNB - 1]) + INNER, LIST_R) : LIST_R;
+    const float r_in2 = r_in * r_in;
+    int cnt = 0;
+    walk_cells(v, c0, [&](int qq) {
+        if (qq == q || !(dist2(qq) <= r_in2)) return;
+        if (cnt < v.cap) v.list[(long long)cnt * v.n + q] = __float_as_int(v.spos[qq].w);
+        ++cnt;
+    });
+    v.len[q] = cnt <= v.cap ? cnt : -1;
+}
+
+// The 27 features of every point from its kept candidates at their current
+// positions (key, order and vectors as kf_knn); a slot whose candidates
+// overflowed the list walks the cells of the last rebuild instead.  Clears
+// the rebuild flag for the next step.
+__global__ void __launch_bounds__(KNN_THREADS)
+kv_knn(const double* __restrict__ pos, Verlet v, Geom g, float* __restrict__ feat) {
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q == 0) *v.flag = 0;
+    if (q >= v.n) return;
+    const int i = __float_as_int(v.spos[q].w);
+    const float4 me = v.fnow[i];
+    const float box[3] = {(float)g.nx, (float)g.ny, (float)g.nz};
+    const float half[3] = {0.5f * box[0], 0.5f * box[1], 0.5f * box[2]};
+    const float rc2 = R_CUT * R_CUT;
+    unsigned long long bk[NNB];  // (r2 bits << 32) | index, ascending
+#pragma unroll
+    for (int k = 0; k < NNB; ++k) bk[k] = ~0ull;
+    const auto consider_at = [&](const float4& o, int j) {
+        const float dx = min_image_f(o.x, me.x, box[0], half[0]);
+        const float dy = min_image_f(o.y, me.y, box[1], half[1]);
+        const float dz = min_image_f(o.z, me.z, box[2], half[2]);
+        const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+        unsigned long long ck = ((unsigned long long)__float_as_uint(r2) << 32) | (unsigned)j;
+        if (!(r2 <= rc2) || ck >= bk[NNB - 1]) return;
+#pragma unroll
+        for (int k = 0; k < NNB; ++k) {
+            const bool lt = ck < bk[k];
+            const unsigned long long tk = bk[k];
+            bk[k] = lt ? ck : tk;
+            ck = lt ? tk : ck;
+        }
+    };
+    const int len = v.len[q];
+    if (len >= 0) {
+        // eight candidates at a time: their indices, then their positions,
+        // each batch of loads in flight together
+        const int* l = v.list + q;
+        for (int k0 = 0; k0 < len; k0 += 8) {
+            int j[8];
+            float4 o[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) j[e] = k0 + e < len ? __ldg(l + (long long)(k0 + e) * v.n) : -1;
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                if (j[e] >= 0) o[e] = __ldg(v.fnow + j[e]);
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                if (j[e] >= 0) consider_at(o[e], j[e]);
+        }
+    } else {
+        walk_cells(v, v.cell[i], [&](int qq) {
+            const int j = __float_as_int(v.spos[qq].w);
+            if (j != i) consider_at(__ldg(v.fnow + j), j);
+        });
+    }
+    float* f = feat + (long long)i * D0;
+    for (int a = 0; a < 3; ++a) f[a] = (float)(pos[3 * (long long)i + a] - floor(pos[3 * (long long)i + a]));
+#pragma unroll
+    for (int k = 0; k < NNB; ++k) {
+        float d[3] = {0.0f, 0.0f, 0.0f};
+        if (bk[k] != ~0ull) {
+            const float4 o = v.fnow[(int)(unsigned)(bk[k] & 0xffffffffull)];
+            d[0] = min_image_f(o.x, me.x, box[0], half[0]);
+            d[1] = min_image_f(o.y, me.y, box[1], half[1]);
+            d[2] = min_image_f(o.z, me.z, box[2], half[2]);
+        }
+        for (int a = 0; a < 3; ++a) f[3 + 3 * k + a] = d[a] * (1.0f / FEAT_LENGTH);
+    }
+}
+
 }  // namespace
 
 struct lb_mlp {
@@ -873,9 +1189,95 @@ cudaError_t mlp_features(long long n, const double* pos, const int box[3], float
     return cudaGetLastError();
 }
 
+static int3 verlet_cells(const int box[3]) {
+    int3 nc;
+    nc.x = std::max(1, (int)((float)box[0] / CELL_WV));
+    nc.y = std::max(1, (int)((float)box[1] / CELL_WV));
+    nc.z = std::max(1, (int)((float)box[2] / CELL_WV));
+    return nc;
+}
+
+int verlet_capacity(long long n, const int box[3]) {
+    // mean candidates of a uniform arrangement, plus six standard deviations
+    // of a Poisson count and a margin; fuller slots walk the cells
+    const double vol = (double)box[0] * box[1] * box[2];
+    const double r = LIST_R;
+    const double mu = (double)std::max<long long>(n - 1, 0) * (4.0 / 3.0) * 3.14159265358979 * r * r * r / vol;
+    const int cap = (int)(mu + 6.0 * sqrt(mu) + 16.0);
+    return std::min(512, std::max(32, (cap + 7) / 8 * 8));
+}
+
+static size_t up16(size_t b) { return (b + 15) / 16 * 16; }
+
+size_t verlet_ws_bytes(long long n, const int box[3], int cap) {
+    const int3 nc = verlet_cells(box);
+    const size_t m = (size_t)nc.x * nc.y * nc.z, N = (size_t)n;
+    return 3 * up16(16 * N) + 2 * up16(4 * N) + up16(4 * N * (size_t)cap) + 2 * up16(4 * m) + up16(4 * (m + 1)) + 16;
+}
+
+static Verlet verlet_view(void* ws, long long n, const int box[3], int cap) {
+    Verlet v;
+    const int3 nc = verlet_cells(box);
+    const size_t m = (size_t)nc.x * nc.y * nc.z, N = (size_t)n;
+    char* p = (char*)ws;
+    v.fnow = (float4*)p;
+    p += up16(16 * N);
+    v.fbuild = (float4*)p;
+    p += up16(16 * N);
+    v.spos = (float4*)p;
+    p += up16(16 * N);
+    v.cell = (int*)p;
+    p += up16(4 * N);
+    v.len = (int*)p;
+    p += up16(4 * N);
+    v.list = (int*)p;
+    p += up16(4 * N * (size_t)cap);
+    v.count = (int*)p;
+    p += up16(4 * m);
+    v.cursor = (int*)p;
+    p += up16(4 * m);
+    v.start = (int*)p;
+    p += up16(4 * (m + 1));
+    v.flag = (int*)p;
+    v.n = n;
+    v.m = (long long)m;
+    v.cap = cap;
+    v.nc = nc;
+    return v;
+}
+
+cudaError_t verlet_reset(void* ws, long long n, const int box[3], int cap, cudaStream_t st) {
+    const Verlet v = verlet_view(ws, n, box, cap);
+    cudaError_t e = cudaMemsetAsync(v.count, 0, sizeof(int) * (size_t)v.m, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.cursor, 0, sizeof(int) * (size_t)v.m, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.flag, 0xff, sizeof(int), st);  // nonzero: rebuild
+    return e;
+}
+
+cudaError_t verlet_features(void* ws, long long n, int cap, const double* pos, const int box[3], float* feat,
+                            cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const Verlet v = verlet_view(ws, n, box, cap);
+    Geom g{};
+    g.nx = box[0];
+    g.ny = box[1];
+    g.nz = box[2];
+    const float3 inv_w = make_float3((float)v.nc.x / (float)box[0], (float)v.nc.y / (float)box[1],
+                                     (float)v.nc.z / (float)box[2]);
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    const unsigned kblocks = (unsigned)((n + KNN_THREADS - 1) / KNN_THREADS);
+    kv_prep<<<blocks, 256, 0, st>>>(pos, v, g);
+    kv_count<<<blocks, 256, 0, st>>>(v, inv_w);
+    kv_scan<<<1, VSCAN_THREADS, 0, st>>>(v);
+    kv_fill<<<blocks, 256, 0, st>>>(v);
+    kv_build<<<kblocks, KNN_THREADS, 0, st>>>(v, g);
+    kv_knn<<<kblocks, KNN_THREADS, 0, st>>>(pos, v, g, feat);
+    return cudaGetLastError();
+}
+
 cudaError_t mlp_forward(const lb_mlp* net, long long n, const float* feat, float* out, cudaStream_t st) {
     const long long tiles = (n + tc::M - 1) / tc::M;
-    const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(tiles, 152LL * 4));
+    const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(tiles, 152LL * tc::FWD_CTAS));
     km_forward_tc<<<grid, tc::M, tc::SMEM, st>>>(net->p, n, feat, out, net->status, net->wait_polls);
     return cudaGetLastError();
 }

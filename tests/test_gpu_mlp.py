@@ -250,6 +250,69 @@ def test_corrected_step_moves_colloids_by_network_output():
     lb.lb_mlp_destroy(net)
 
 
+def _jitter(rng, R, delta, box):
+    d = rng.normal(size=R.shape)
+    d *= delta / np.linalg.norm(d, axis=1, keepdims=True)
+    return (R + d) % box
+
+
+@pytest.mark.parametrize("L,n", [(32, 90), (48, 300)])
+def test_kept_candidate_lists_match_a_full_search(L, n):
+    # lb_step keeps each colloid's candidates (others within 8.5 lattice
+    # units) from step to step and rebuilds them on the device once some
+    # colloid has moved more than 0.234 since the last rebuild.  Drive it
+    # through reuse, rebuilds, lists that overflow their slots (a cluster of
+    # 45 colloids within radius 3, more than their 40 slots) and an
+    # unchanged configuration; every step the update must equal the one
+    # rebuilt from the stateless full-search features (lb_mlp_features).
+    lb = _lb()
+    from paper_0707_1299_gb300 import learned, workloads as W
+    prob = W.colloids(L=L, n=n, seed=21, force=1e-5, a_L=1.6)
+    box = np.asarray(prob.grid, float)
+    rng = np.random.default_rng(8)
+    params = (learned.initial_params(3) * 0.3).astype(np.float32)
+    net = lb.lb_mlp_create(params)
+    g = lb.Lattice(prob.grid, 0.6, 0.6, lb.LB_F64)
+    g.set_colloid_aL(1.6)
+    ps = prob.points[0]
+    g.add_point_forces(ps.kind, ps.pos, ps.F, ps.param)
+    lb.lb_set_colloid_correction(g.ctx, net)
+    eta, a = 0.6 / 3, 0.117
+    R, F = g.particles()
+    R = R.cpu().numpy()
+    Fn = F.cpu().numpy()
+    c = (1 / a - 1 / 1.6) / (6 * np.pi * eta)
+    v0 = np.linalg.norm(Fn, axis=1, keepdims=True) / (6 * np.pi * eta * a)
+    schedule = [0.01, 0.01, 0.01, 0.2, 0.02, 0.02, "cluster", 0.01, 0.01, 0.3, 0.0, 0.0, "redraw", 0.05]
+    for move in schedule:
+        if move == "cluster":
+            centre = rng.uniform(0, 1, 3) * box
+            R = R.copy()
+            R[:45] = _jitter(rng, np.tile(centre, (45, 1)), 1.0, box) + rng.uniform(-1, 1, (45, 3))
+            R %= box
+        elif move == "redraw":
+            R = rng.uniform(0, 1, R.shape) * box
+        else:
+            R = _jitter(rng, R, move, box)
+        lb.lb_set_positions(g.ctx, np.ascontiguousarray(R))
+        Rd = torch.as_tensor(R, device="cuda").contiguous()
+        v = g.velocity_at(Rd)
+        feat = torch.empty((n, 27), dtype=torch.float32, device="cuda")
+        lb.lb_mlp_features(net, n, Rd, prob.grid, feat)
+        y = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+        lb.lb_mlp_forward(net, n, feat, y)
+        torch.cuda.synchronize()
+        g.step(1)
+        R1, _ = g.particles()
+        R1 = R1.cpu().numpy()
+        expect = (R + v.cpu().numpy() + Fn * c + y.cpu().numpy().astype(np.float64) * v0) % box
+        assert np.abs(periodic_diff(R1, expect, prob.grid)).max() < 1e-12, move
+        R = R1
+    lb.lb_set_colloid_correction(g.ctx, None)
+    g.close()
+    lb.lb_mlp_destroy(net)
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_corrected_step_matches_oracle(prec):
     # Reading L4 end to end: lb_step with a network attached against the
