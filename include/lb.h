@@ -292,16 +292,18 @@ lb_status lb_set_colloid_correction(lb_ctx *ctx, lb_mlp *net);
 /* ------------------------------------------------------------------------
  * Batches: independent lattices (replicas of uneven sizes, e.g. many small
  * sedimentation boxes) advanced together, one persistent cooperative kernel
- * launch per time step over all members.  Inside the launch, phases are
- * separated by grid-wide barriers whose waits are bounded: every 64 steps
- * the cell order of all colloids (a counting sort); on the first step of a
- * call whose force fields are not spread, the spread; the collide + stream
- * of every site of every member (the 32-site windows of each member's flat
- * site index when every nx is a multiple of 8 and every member has fewer
- * than 2^24 sites, else 4 x 32-site tiles); then the point phase --
- * interpolation, colloid update and the spread of the forces at the new
- * positions for the next step.  Two steps are replayed from a CUDA graph.
- * The method per member is exactly that of lb_step.
+ * launch per time step over all members.  Inside the launch, every 64
+ * steps the cell order of all colloids (a counting sort) and, on the first
+ * step of a call whose force fields are not spread, the spread, each
+ * followed by a grid-wide barrier; then a work queue that the blocks drain:
+ * the collide + stream of every site of every member in chunks, member
+ * after member (32-site windows of each member's flat site index when
+ * every nx is a multiple of 8 and every member has fewer than 2^24 sites,
+ * else 4 x 32-site tiles), then the point items -- interpolation, colloid
+ * update and the spread of the forces at the new positions for the next
+ * step -- each started once the collide of its own member is complete.
+ * Every wait (barrier or queue) is bounded.  Two steps are replayed from a
+ * CUDA graph.  The method per member is exactly that of lb_step.
  * --------------------------------------------------------------------- */
 typedef struct lb_batch lb_batch;
 
@@ -324,7 +326,7 @@ const char *lb_batch_last_error(const lb_batch *batch);
  * write only the spare population buffers, and the positions and counters
  * they move are put back; the force fields they spread are cleared (the
  * next step spreads again).  Waits for the batch's stream; LB_ERR_TIMEOUT
- * if a barrier wait ran out during the trials. */
+ * if a wait ran out during the trials. */
 lb_status lb_batch_tune(lb_batch *batch, int *blocks);
 
 /* Advance every member nsteps >= 0 time steps (Sec. II-IV, as lb_step).
@@ -332,16 +334,17 @@ lb_status lb_batch_tune(lb_batch *batch, int *blocks);
  * the forces at its new positions (queries on a member use it as is). */
 lb_status lb_batch_step(lb_batch *batch, int nsteps);
 
-/* Wait for the batch's stream; LB_ERR_TIMEOUT if a grid-barrier wait of
- * the steps issued since the last call ran out (those steps are then
- * incomplete and the members' state is undefined; the barrier is reset so
- * that the batch can be used again). */
+/* Wait for the batch's stream; LB_ERR_TIMEOUT if a wait (grid barrier or
+ * work queue) of the steps issued since the last call ran out (those steps
+ * are then incomplete and the members' state is undefined; the barrier and
+ * the queue are reset so that the batch can be used again). */
 lb_status lb_batch_synchronize(lb_batch *batch);
 
-/* Bound of every grid-barrier wait of the batch kernel, in polls of the
- * barrier's generation word with a short sleep between polls (default
- * 2^22, about a second).  0 makes every wait give up at once, which drives
- * the timeout path.  Waits for the batch's stream; LB_ERR_ARG for polls < 0. */
+/* Bound of every wait of the batch kernel (grid barrier, or a point item
+ * waiting for its member's collide), in polls of the word waited on with a
+ * short sleep between polls (default 2^22, about a second).  0 makes every
+ * wait that is not already satisfied give up at once, which drives the
+ * timeout path.  Waits for the batch's stream; LB_ERR_ARG for polls < 0. */
 lb_status lb_batch_set_wait_limit(lb_batch *batch, long long polls);
 
 /* Sites and points over all members, the persistent grid size and the

@@ -1,16 +1,20 @@
 // lb_batch.cu -- many independent lattices (replicas of uneven sizes)
 // advanced together, one persistent cooperative launch per time step over
-// all replicas.  Inside the launch, phases separated by grid-wide barriers:
-//   (every 64 steps) the cell order of all points -- a counting sort;
+// all replicas.  Inside the launch:
+//   (every 64 steps) the cell order of all points -- a counting sort between
+//     grid-wide barriers;
 //   (first step of a call, when the force fields are not spread) stencil
-//     rows of the current positions and the spread;
-//   collide + stream of every site of every replica (writing the fluid
-//     velocity at the colloids' stencil nodes, zeroing the consumed force);
-//   the point phase: interpolation, colloid update and the spread of the
-//     forces at the new positions for the next step.
-// Every barrier wait is bounded; a wait that runs out sets an error flag and
-// the kernel returns (lb_batch_synchronize reports LB_ERR_TIMEOUT).  Two
-// steps (the two buffer parities) are replayed from a CUDA graph.  The grid
+//     rows of the current positions and the spread, then a grid barrier;
+//   then a work queue that the blocks drain from one counter: the collide +
+//   stream of every replica in chunks, replica after replica (writing the
+//   fluid velocity at the colloids' stencil nodes, zeroing the consumed
+//   force), then the point items (interpolation, colloid update and the
+//   spread of the forces at the new positions for the next step), each of
+//   which waits until the collide chunks of its own replica are done.  No
+//   block idles at a barrier while others finish their share of the collide.
+// Every wait is bounded; a wait that runs out sets an error flag and the
+// kernel returns (lb_batch_synchronize reports LB_ERR_TIMEOUT).  Two steps
+// (the two buffer parities) are replayed from a CUDA graph.  The grid
 // (blocks per SM) is picked by timing candidates on the batch itself.
 //
 // The method per replica is exactly that of lb_step (same device helpers:
@@ -37,17 +41,28 @@ constexpr int SORT_EVERY = 64;      // steps between renewals of the batch's cel
 // (85 registers) measured fastest on the 64-replica batch, 1.665 ms a step
 // against 1.705 at 8 (64 registers), 1.754 at 5 and 1.937 at 10 (spills)
 constexpr int MIN_BLOCKS = 6;
-constexpr long long DEFAULT_WAIT = 1LL << 22;  // polls of a barrier wait (~1 s) before it gives up
+constexpr long long DEFAULT_WAIT = 1LL << 22;  // polls of a wait (~1 s) before it gives up
+// 32-site windows per collide chunk of the flat walk (8192 sites): measured
+// against 64, 128 and 512 on the 64-replica batch (1.670, 1.644, 1.638 ms
+// a step against 1.626); smaller chunks cost more queue traffic, larger
+// ones a longer tail
+constexpr int FLAT_CHUNK = 256;
+constexpr int TILED_CHUNK = 64;     // 4-tile groups per collide chunk of the tiled walk (8192 sites)
+constexpr int NPB = 4 * (BT / 32);  // points of a block's point item
 
-// Barrier and step state of a batch, in device memory.
+// Barrier, work-queue and step state of a batch, in device memory.  The
+// queue counters return to zero at the end of every launch (the last block
+// to leave resets them).
 struct BatchCtl {
     unsigned count;      // blocks arrived at the current barrier
     unsigned gen;        // barrier generation
-    int err;             // 1: a barrier wait ran out
+    int err;             // 1: a wait ran out
     int init;            // 1: spread the forces at the current positions before the collide
     unsigned since_sort; // steps since the cell order was renewed
     unsigned step;       // step counter seeding the stochastic rounding of the 16-bit formats
-    long long limit;     // polls of a barrier wait
+    long long limit;     // polls of a wait
+    unsigned next;       // next work item of the queue
+    unsigned exits;      // blocks that have left the launch
 };
 
 struct Entry {
@@ -74,9 +89,7 @@ struct Entry {
 };
 
 struct Work {
-    long long group_begin;     // first collide work item of the replica
-    int groups_x, groups_y;    // ntx, ceil(ny / BW)
-    long long pt_begin;        // first point of the replica in the batch order
+    int groups_x, groups_y;    // ntx, ceil(ny / BW): the tiled walk's 4-tile groups per plane
 };
 
 __device__ __forceinline__ int find_entry(const long long* __restrict__ begin, int n, long long w) {
@@ -245,12 +258,18 @@ __device__ __forceinline__ bool grid_sync(BatchCtl* ctl, long long limit) {
 struct StepArgs {
     const Entry* ent;
     int nrep;
-    // collide work: flat windows or tiled groups
-    const long long* wbegin;
-    long long total_windows;
-    const long long* gbegin;
+    // tiled collide walk
     const Work* work;
-    long long total_groups;
+    // the work queue: segment k holds items [sbegin[k], sbegin[k + 1]) of one
+    // member, collide chunks (skind[k] = 0) or point items (1); member e has
+    // nchunk[e] chunks in all, done[e] counts the finished ones
+    const long long* sbegin;
+    const int* smember;
+    const int* skind;
+    int nseg;
+    long long total_items;
+    const int* nchunk;
+    unsigned* done;
     // points
     const long long* pbegin;
     const int* pent;
@@ -350,41 +369,22 @@ __device__ bool sort_points(const StepArgs& a, long long limit) {
     return grid_sync(a.ctl, limit);
 }
 
-// The collide over a block's contiguous chunk of 4-tile work items (any
-// member geometry); warp w of the block takes row y = 4 yg + w of an item.
+// Collide chunk c of replica e, tiled walk (any geometry): TILED_CHUNK
+// 4-tile groups of the replica in order; warp w of the block takes row
+// y = 4 yg + w of a group.
 template <typename S>
-__device__ __forceinline__ void collide_tiled(const StepArgs& a, int parity, unsigned seed) {
+__device__ __forceinline__ void tiled_chunk(const StepArgs& a, int e, long long c, int parity, unsigned seed) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long chunk = (a.total_groups + gridDim.x - 1) / gridDim.x;
-    const long long w0 = (long long)blockIdx.x * chunk;
-    const long long w1 = w0 + chunk < a.total_groups ? w0 + chunk : a.total_groups;
-    if (w0 >= w1) return;
-    int e = find_entry(a.gbegin, a.nrep, w0);
-    int tx, yg, zz;
-    {
-        const long long local = w0 - a.work[e].group_begin;
-        tx = (int)(local % a.work[e].groups_x);
-        const long long r = local / a.work[e].groups_x;
-        yg = (int)(r % a.work[e].groups_y);
-        zz = (int)(r / a.work[e].groups_y);
-    }
-    for (long long w = w0; w < w1; ++w) {
-        if (w > w0) {  // advance (tx, yg, z, entry)
-            if (++tx == a.work[e].groups_x) {
-                tx = 0;
-                if (++yg == a.work[e].groups_y) {
-                    yg = 0;
-                    if (++zz == a.ent[e].g.nz) {
-                        zz = 0;
-                        ++e;
-                    }
-                }
-            }
-        }
-        const Entry& E = a.ent[e];
-        const Geom& g = E.g;
-        const int y = yg * BW + warp;
-        const int z = zz;
+    const Entry& E = a.ent[e];
+    const Geom& g = E.g;
+    const Work& W = a.work[e];
+    const long long n_groups = (long long)W.groups_x * W.groups_y * g.nz;
+    const long long i1 = min((c + 1) * TILED_CHUNK, n_groups);
+    for (long long it = c * TILED_CHUNK; it < i1; ++it) {
+        const int tx = (int)(it % W.groups_x);
+        const long long r = it / W.groups_x;
+        const int y = (int)(r % W.groups_y) * BW + warp;
+        const int z = (int)(r / W.groups_y);
         const int x = tx * TILE_X + lane;
         if (y >= g.ny) continue;  // uniform per warp
         const unsigned tile = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.ntx + (unsigned)tx;
@@ -396,26 +396,18 @@ __device__ __forceinline__ void collide_tiled(const StepArgs& a, int parity, uns
     }
 }
 
-// The collide over flat 32-site windows of each member's site index (see
-// div_small), each warp a contiguous chunk of windows.
+// Collide chunk c of replica e, flat walk: FLAT_CHUNK 32-site windows of the
+// replica's site index (see div_small), window k of the chunk to warp k % 4.
 template <typename S, bool WALLS>
-__device__ __forceinline__ void collide_flat(const StepArgs& a, int parity, unsigned seed) {
+__device__ __forceinline__ void flat_chunk(const StepArgs& a, int e, long long c, int parity, unsigned seed) {
     const unsigned lane = threadIdx.x & 31u;
-    const long long nwarps = (long long)gridDim.x * (BT / 32);
-    long long w = (long long)blockIdx.x * (BT / 32) + (threadIdx.x >> 5);
-    if (w >= a.total_windows) return;
-    int e = find_entry(a.wbegin, a.nrep, w);
-    long long lo = a.wbegin[e], hi = e + 1 < a.nrep ? a.wbegin[e + 1] : a.total_windows;
-    for (; w < a.total_windows; w += nwarps) {
-        while (w >= hi) {  // uniform per warp
-            ++e;
-            lo = hi;
-            hi = e + 1 < a.nrep ? a.wbegin[e + 1] : a.total_windows;
-        }
-        const Entry& E = a.ent[e];
-        const Geom& g = E.g;
-        const unsigned s = (unsigned)(w - lo) * 32u + lane;
-        if (s >= (unsigned)g.V) continue;  // the ragged last window of a member
+    const Entry& E = a.ent[e];
+    const Geom& g = E.g;
+    const long long w0 = c * FLAT_CHUNK;
+    const long long w1 = min(w0 + FLAT_CHUNK, ((long long)g.V + 31) / 32);
+    for (long long w = w0 + (threadIdx.x >> 5); w < w1; w += BT / 32) {
+        const unsigned s = (unsigned)w * 32u + lane;
+        if (s >= (unsigned)g.V) continue;  // the ragged last window of a replica
         const unsigned zy = div_small(s, (unsigned)g.nx, E.inv_nx);
         const unsigned x = s - zy * (unsigned)g.nx;
         const unsigned z = div_small(zy, (unsigned)g.ny, E.inv_ny);
@@ -427,10 +419,44 @@ __device__ __forceinline__ void collide_flat(const StepArgs& a, int parity, unsi
     }
 }
 
+// Thread 0 of a block: wait (bounded) until every collide chunk of the
+// members of the points in cell-order slots [p0, p1) is done, then fence
+// so that the block reads their velocity fields and writes their force
+// fields after the collide.  False after a timeout (error flag set).
+__device__ bool wait_replicas(const StepArgs& a, long long p0, long long p1, long long limit) {
+    int last = -1;
+    for (long long p = p0; p < p1; ++p) {
+        const int e = a.pent[a.order[p]];
+        if (e == last) continue;
+        last = e;
+        const unsigned need = (unsigned)a.nchunk[e];
+        const volatile unsigned* d = a.done + e;
+        long long polls = 0;
+        while (*d < need) {
+            if (polls++ >= limit) {
+                atomicOr(&a.ctl->err, 1);
+                return false;
+            }
+            __nanosleep(64);
+        }
+    }
+    __threadfence();
+    return true;
+}
+
 // One time step of every member (buffer parity `parity`).  The state flags
-// (init, since_sort, step, limit) are read by every block before its first
-// barrier and rewritten by block 0 after its last, so all blocks of a
-// launch see the same values.
+// (init, since_sort, step, limit) are read by every block at its start and
+// rewritten, with the queue counters reset, by the last block to leave, so
+// all blocks of a launch see the same values.  Work items come from one
+// counter in queue order: the collide chunks, member after member, then the
+// point items, member after member (a member's slots of the cell order,
+// which the sort keeps member after member).  A block fetches its next item
+// while it works on the current one.  No wait can stall for good: a point
+// item waits only for chunks, which all come before it in the queue, and a
+// block holds a fetched chunk only while its current item is a chunk (no
+// wait), so every chunk is being worked on or will be next.  (Placing a
+// member's point items among later members' chunks instead, to overlap
+// them with the collide, measured slower: both compete for the memory.)
 template <typename S, bool FLAT, bool WALLS>
 __global__ void __launch_bounds__(BT, MIN_BLOCKS) kb_step(const StepArgs a, int parity) {
     using T = typename Store<S>::T;
@@ -442,9 +468,9 @@ __global__ void __launch_bounds__(BT, MIN_BLOCKS) kb_step(const StepArgs a, int 
     const bool sort_due = since >= (unsigned)SORT_EVERY && a.total_pts > 0;
     const unsigned step = vc->step;
     const unsigned seed = sizeof(S) == 2 ? rng_seed(step, 0xB5297A4Du) : 0u;
-    constexpr int NPB = 4 * (BT / 32);  // points of a block's point-phase item
     const long long items = (a.total_pts + NPB - 1) / NPB;
     __shared__ double vsh[NPB][3];
+    __shared__ unsigned s_item;
     const BatchPoints<T> src{a.ent, a.pbegin, a.pent};
     T* st = (T*)a.st;
     if (sort_due && !sort_points(a, limit)) return;
@@ -453,15 +479,45 @@ __global__ void __launch_bounds__(BT, MIN_BLOCKS) kb_step(const StepArgs a, int 
             point_block<T, WALLS, false, BT / 32>(src, q * NPB, a.total_pts, a.order, st, vsh);
         if (!grid_sync(ctl, limit)) return;
     }
-    if (FLAT) collide_flat<S, WALLS>(a, parity, seed);
-    else collide_tiled<S>(a, parity, seed);
-    if (!grid_sync(ctl, limit)) return;
-    for (long long q = blockIdx.x; q < items; q += gridDim.x)
-        point_block<T, WALLS, true, BT / 32>(src, q * NPB, a.total_pts, a.order, st, vsh);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        ctl->init = 0;
-        ctl->since_sort = sort_due ? 1u : since + 1u;
-        ctl->step = step + 1u;
+    if (threadIdx.x == 0) s_item = atomicAdd(&ctl->next, 1u);
+    __syncthreads();
+    for (;;) {
+        const long long t = s_item;
+        if (t >= a.total_items) break;
+        unsigned t_next = 0;
+        if (threadIdx.x == 0) t_next = atomicAdd(&ctl->next, 1u);  // in flight during this item
+        const int k = find_entry(a.sbegin, a.nseg, t);
+        const int e = a.smember[k];
+        const long long j = t - a.sbegin[k];
+        if (a.skind[k] == 0) {
+            if (FLAT) flat_chunk<S, WALLS>(a, e, j, parity, seed);
+            else tiled_chunk<S>(a, e, j, parity, seed);
+            __threadfence();  // this thread's stores, device-wide, before the count
+            __syncthreads();
+            if (threadIdx.x == 0) atomicAdd(&a.done[e], 1u);
+        } else {
+            const long long p0 = a.pbegin[e] + j * NPB;
+            const long long p1 = min(p0 + NPB, a.pbegin[e] + a.ent[e].npts);
+            int ok = 1;
+            if (threadIdx.x == 0) ok = wait_replicas(a, p0, p1, limit);
+            if (!__syncthreads_and(ok)) return;
+            point_block<T, WALLS, true, BT / 32>(src, p0, p1, a.order, st, vsh);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = t_next;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&ctl->exits, 1u) == gridDim.x - 1) {  // every other block has left
+            for (int m = 0; m < a.nrep; ++m) a.done[m] = 0;
+            ctl->next = 0;
+            ctl->exits = 0;
+            ctl->init = 0;
+            ctl->since_sort = sort_due ? 1u : since + 1u;
+            ctl->step = step + 1u;
+            __threadfence();
+        }
     }
 }
 
@@ -475,11 +531,16 @@ struct lb_batch {
     cudaStream_t stream;       // private stream: graphs cannot capture the legacy stream
     cudaEvent_t ev_in, ev_out, ev_err;
     Entry* d_ent;
-    long long* d_gbegin;
     long long* d_pbegin;
     Work* d_work;
-    long long* d_wbegin;
-    long long total_groups, total_windows, total_pts, n_mobile, total_bins;
+    long long* d_sbegin;       // work-queue segments: first item, member, kind
+    int* d_smember;
+    int* d_skind;
+    int nseg;
+    long long total_items;
+    int* d_nchunk;             // collide chunks of every member
+    unsigned* d_done;          // finished collide chunks of every member (zero between launches)
+    long long total_pts, n_mobile, total_bins;
     int blocks;                // grid of the persistent kernel
     int max_blocks;            // co-resident limit of that grid
     int sms;
@@ -520,11 +581,14 @@ StepArgs step_args(const lb_batch* b) {
     StepArgs a;
     a.ent = b->d_ent;
     a.nrep = b->n;
-    a.wbegin = b->d_wbegin;
-    a.total_windows = b->total_windows;
-    a.gbegin = b->d_gbegin;
     a.work = b->d_work;
-    a.total_groups = b->total_groups;
+    a.sbegin = b->d_sbegin;
+    a.smember = b->d_smember;
+    a.skind = b->d_skind;
+    a.nseg = b->nseg;
+    a.total_items = b->total_items;
+    a.nchunk = b->d_nchunk;
+    a.done = b->d_done;
     a.pbegin = b->d_pbegin;
     a.pent = b->d_pent;
     a.order = b->d_order;
@@ -587,6 +651,19 @@ cudaError_t set_ctl(lb_batch* b, size_t offset, const void* v, size_t bytes) {
     return cudaMemcpyAsync((char*)b->d_ctl + offset, v, bytes, cudaMemcpyHostToDevice, b->stream);
 }
 
+// Barrier and work-queue state back to its between-launches values (after
+// a launch that gave up on a wait and left it mid-way).  Synchronous.
+cudaError_t reset_sync_state(lb_batch* b) {
+    const unsigned zero2[2] = {0u, 0u};
+    const int no = 0;
+    cudaError_t e = set_ctl(b, offsetof(BatchCtl, count), zero2, sizeof(zero2));  // count, gen
+    if (e == cudaSuccess) e = set_ctl(b, offsetof(BatchCtl, err), &no, sizeof(no));
+    if (e == cudaSuccess) e = set_ctl(b, offsetof(BatchCtl, next), zero2, sizeof(zero2));  // next, exits
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_done, 0, sizeof(unsigned) * (size_t)b->n, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -604,9 +681,9 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
     b->user_stream = (cudaStream_t)stream;
     b->parity = 0;
     std::vector<Entry> ent(n);
-    std::vector<long long> gbegin(n), pbegin(n), wbegin(n);
+    std::vector<long long> pbegin(n);
     std::vector<Work> work(n);
-    long long groups = 0, pts = 0, mob = 0, bins = 0, windows = 0;
+    long long pts = 0, mob = 0, bins = 0;
     bool flat = true, walls = false;
     for (int i = 0; i < n; ++i) {
         lb_ctx* c = ctxs[i];
@@ -657,25 +734,44 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
         E.inv_ny = 1.0f / (float)c->geom.ny;
         flat = flat && c->geom.nx % GROUP_X == 0 && c->geom.V < (1LL << 24);
         walls = walls || has_walls(c);
-        wbegin[i] = windows;
-        windows += (c->geom.V + 31) / 32;
         work[i].groups_x = c->geom.ntx;
         work[i].groups_y = (c->geom.ny + BW - 1) / BW;
-        work[i].group_begin = groups;
-        work[i].pt_begin = pts;
-        gbegin[i] = groups;
         pbegin[i] = pts;
-        groups += (long long)work[i].groups_x * work[i].groups_y * c->geom.nz;
         pts += c->npts;
         mob += c->n_mobile;
     }
-    b->total_groups = groups;
+    // the work queue: every member's collide chunks, member after member,
+    // then every member's point items
+    std::vector<int> nchunk(n), skind, smember;
+    std::vector<long long> sbegin;
+    {
+        long long items = 0;
+        for (int i = 0; i < n; ++i) {
+            const Geom& g = ctxs[i]->geom;
+            nchunk[i] = (int)(flat ? ((g.V + 31) / 32 + FLAT_CHUNK - 1) / FLAT_CHUNK
+                                   : ((long long)work[i].groups_x * work[i].groups_y * g.nz + TILED_CHUNK - 1) /
+                                         TILED_CHUNK);
+            sbegin.push_back(items);
+            smember.push_back(i);
+            skind.push_back(0);
+            items += nchunk[i];
+        }
+        for (int i = 0; i < n; ++i) {
+            const long long np = (ctxs[i]->npts + NPB - 1) / NPB;
+            if (np == 0) continue;
+            sbegin.push_back(items);
+            smember.push_back(i);
+            skind.push_back(1);
+            items += np;
+        }
+        b->total_items = items;
+        b->nseg = (int)sbegin.size();
+    }
     b->total_pts = pts;
     b->n_mobile = mob;
     b->total_bins = bins;
     b->flat = flat;
     b->walls = walls;
-    b->total_windows = windows;
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -691,10 +787,14 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_err, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&b->h_err, sizeof(int), cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_ent, sizeof(Entry) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_gbegin, sizeof(long long) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_pbegin, sizeof(long long) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_work, sizeof(Work) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_wbegin, sizeof(long long) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_sbegin, sizeof(long long) * (size_t)b->nseg);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_smember, sizeof(int) * (size_t)b->nseg);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_skind, sizeof(int) * (size_t)b->nseg);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_nchunk, sizeof(int) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_done, sizeof(unsigned) * n);
+    if (e == cudaSuccess) e = cudaMemset(b->d_done, 0, sizeof(unsigned) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_ctl, sizeof(BatchCtl));
     if (e == cudaSuccess && pts > 0)
         e = cudaMalloc(&b->d_st, lbk::arith_bytes(b->prec) * ST_W * (size_t)pts);
@@ -715,10 +815,14 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
         e = cudaMemcpy(b->d_ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaMemcpy(b->d_ent, ent.data(), sizeof(Entry) * n, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_gbegin, gbegin.data(), sizeof(long long) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_pbegin, pbegin.data(), sizeof(long long) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_work, work.data(), sizeof(Work) * n, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_wbegin, wbegin.data(), sizeof(long long) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_sbegin, sbegin.data(), sizeof(long long) * (size_t)b->nseg, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_smember, smember.data(), sizeof(int) * (size_t)b->nseg, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_skind, skind.data(), sizeof(int) * (size_t)b->nseg, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_nchunk, nchunk.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         lb_batch_destroy(b);
         return e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA;
@@ -733,10 +837,13 @@ void lb_batch_destroy(lb_batch* b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->graph_ready) cudaGraphExecDestroy(b->graph2);
     cudaFree(b->d_ent);
-    cudaFree(b->d_gbegin);
     cudaFree(b->d_pbegin);
     cudaFree(b->d_work);
-    cudaFree(b->d_wbegin);
+    cudaFree(b->d_sbegin);
+    cudaFree(b->d_smember);
+    cudaFree(b->d_skind);
+    cudaFree(b->d_nchunk);
+    cudaFree(b->d_done);
     cudaFree(b->d_ctl);
     cudaFree(b->d_st);
     cudaFree(b->d_pent);
@@ -769,12 +876,8 @@ lb_status lb_batch_synchronize(lb_batch* b) {
             // a barrier wait ran out: the step's work is incomplete; reset the
             // barrier state so that later launches start clean
             *b->h_err = 0;
-            const unsigned zero[2] = {0u, 0u};
-            const int no = 0;
-            LB_BCUDA(set_ctl(b, offsetof(BatchCtl, count), zero, sizeof(zero)), "barrier reset");
-            LB_BCUDA(set_ctl(b, offsetof(BatchCtl, err), &no, sizeof(no)), "error reset");
-            LB_BCUDA(cudaStreamSynchronize(b->stream), "stream synchronize");
-            return bfail(b, LB_ERR_TIMEOUT, "lb_batch: a grid barrier wait ran out; the last steps are incomplete");
+            LB_BCUDA(reset_sync_state(b), "barrier and queue reset");
+            return bfail(b, LB_ERR_TIMEOUT, "lb_batch: a wait ran out; the last steps are incomplete");
         }
     }
     return LB_OK;
@@ -846,13 +949,16 @@ lb_status lb_batch_tune(lb_batch* b, int* blocks_out) {
         saved_ctl.init = 1;
         saved_ctl.count = 0;
         saved_ctl.err = 0;
+        saved_ctl.next = 0;
+        saved_ctl.exits = 0;
         err = cudaMemcpy(b->d_ctl, &saved_ctl, sizeof(BatchCtl), cudaMemcpyHostToDevice);
     }
+    if (err == cudaSuccess) err = cudaMemset(b->d_done, 0, sizeof(unsigned) * (size_t)b->n);
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
     cudaFree(saved_pos);
     if (err != cudaSuccess) return bfail(b, LB_ERR_CUDA, std::string("lb_batch_tune: ") + cudaGetErrorString(err));
-    if (timed_out) return bfail(b, LB_ERR_TIMEOUT, "lb_batch_tune: a grid barrier wait ran out");
+    if (timed_out) return bfail(b, LB_ERR_TIMEOUT, "lb_batch_tune: a wait ran out");
     if (best != b->blocks && b->graph_ready) {
         cudaGraphExecDestroy(b->graph2);
         b->graph_ready = false;
