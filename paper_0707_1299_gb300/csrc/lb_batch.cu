@@ -42,12 +42,16 @@ constexpr int SORT_EVERY = 64;      // steps between renewals of the batch's cel
 // against 1.705 at 8 (64 registers), 1.754 at 5 and 1.937 at 10 (spills)
 constexpr int MIN_BLOCKS = 6;
 constexpr long long DEFAULT_WAIT = 1LL << 22;  // polls of a wait (~1 s) before it gives up
-// 32-site windows per collide chunk of the flat walk (8192 sites): measured
-// against 64, 128 and 512 on the 64-replica batch (1.670, 1.644, 1.638 ms
-// a step against 1.626); smaller chunks cost more queue traffic, larger
-// ones a longer tail
-constexpr int FLAT_CHUNK = 256;
-constexpr int TILED_CHUNK = 64;     // 4-tile groups per collide chunk of the tiled walk (8192 sites)
+// Collide chunks: about CHUNKS_PER_BLOCK per resident block, so that the
+// tail (the last chunk a block takes) stays short, in a power of two of
+// 32-site windows (flat walk) or 4-tile groups (tiled walk) between the
+// bounds below.  On the 64-replica batch (53.8 M sites, 912 blocks: 256
+// windows a chunk) 64, 128 and 512 windows measured 1.670, 1.644 and 1.638
+// ms a step against 1.626 (fewer chunks: longer tail; more: more queue
+// traffic); with 8192-site chunks a 12-replica batch (10.5 M sites) left
+// 1.4 chunks a block and took 0.438 ms a step.
+constexpr int CHUNKS_PER_BLOCK = 6;
+constexpr int CHUNK_MIN = 16, CHUNK_MAX = 256;
 constexpr int NPB = 4 * (BT / 32);  // points of a block's point item
 
 // Barrier, work-queue and step state of a batch, in device memory.  The
@@ -260,6 +264,7 @@ struct StepArgs {
     int nrep;
     // tiled collide walk
     const Work* work;
+    int chunk;              // windows (flat walk) or 4-tile groups (tiled walk) a collide chunk
     // the work queue: segment k holds items [sbegin[k], sbegin[k + 1]) of one
     // member, collide chunks (skind[k] = 0) or point items (1); member e has
     // nchunk[e] chunks in all, done[e] counts the finished ones
@@ -369,7 +374,7 @@ __device__ bool sort_points(const StepArgs& a, long long limit) {
     return grid_sync(a.ctl, limit);
 }
 
-// Collide chunk c of replica e, tiled walk (any geometry): TILED_CHUNK
+// Collide chunk c of replica e, tiled walk (any geometry): a.chunk
 // 4-tile groups of the replica in order; warp w of the block takes row
 // y = 4 yg + w of a group.
 template <typename S>
@@ -379,8 +384,8 @@ __device__ __forceinline__ void tiled_chunk(const StepArgs& a, int e, long long 
     const Geom& g = E.g;
     const Work& W = a.work[e];
     const long long n_groups = (long long)W.groups_x * W.groups_y * g.nz;
-    const long long i1 = min((c + 1) * TILED_CHUNK, n_groups);
-    for (long long it = c * TILED_CHUNK; it < i1; ++it) {
+    const long long i1 = min((c + 1) * a.chunk, n_groups);
+    for (long long it = c * a.chunk; it < i1; ++it) {
         const int tx = (int)(it % W.groups_x);
         const long long r = it / W.groups_x;
         const int y = (int)(r % W.groups_y) * BW + warp;
@@ -396,15 +401,15 @@ __device__ __forceinline__ void tiled_chunk(const StepArgs& a, int e, long long 
     }
 }
 
-// Collide chunk c of replica e, flat walk: FLAT_CHUNK 32-site windows of the
+// Collide chunk c of replica e, flat walk: a.chunk 32-site windows of the
 // replica's site index (see div_small), window k of the chunk to warp k % 4.
 template <typename S, bool WALLS>
 __device__ __forceinline__ void flat_chunk(const StepArgs& a, int e, long long c, int parity, unsigned seed) {
     const unsigned lane = threadIdx.x & 31u;
     const Entry& E = a.ent[e];
     const Geom& g = E.g;
-    const long long w0 = c * FLAT_CHUNK;
-    const long long w1 = min(w0 + FLAT_CHUNK, ((long long)g.V + 31) / 32);
+    const long long w0 = c * a.chunk;
+    const long long w1 = min(w0 + a.chunk, ((long long)g.V + 31) / 32);
     for (long long w = w0 + (threadIdx.x >> 5); w < w1; w += BT / 32) {
         const unsigned s = (unsigned)w * 32u + lane;
         if (s >= (unsigned)g.V) continue;  // the ragged last window of a replica
@@ -538,6 +543,7 @@ struct lb_batch {
     int* d_skind;
     int nseg;
     long long total_items;
+    int chunk;                 // windows or 4-tile groups a collide chunk
     int* d_nchunk;             // collide chunks of every member
     unsigned* d_done;          // finished collide chunks of every member (zero between launches)
     long long total_pts, n_mobile, total_bins;
@@ -582,6 +588,7 @@ StepArgs step_args(const lb_batch* b) {
     a.ent = b->d_ent;
     a.nrep = b->n;
     a.work = b->d_work;
+    a.chunk = b->chunk;
     a.sbegin = b->d_sbegin;
     a.smember = b->d_smember;
     a.skind = b->d_skind;
@@ -740,17 +747,39 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
         pts += c->npts;
         mob += c->n_mobile;
     }
+    b->total_pts = pts;
+    b->n_mobile = mob;
+    b->total_bins = bins;
+    b->flat = flat;
+    b->walls = walls;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel_any(b), BT, 0);
+    if (e == cudaSuccess && per_sm < 1) e = cudaErrorCooperativeLaunchTooLarge;
+    b->sms = sms;
+    b->max_blocks = sms * per_sm;
+    // untuned: MIN_BLOCKS blocks per SM (or what fits)
+    b->blocks = std::min(b->max_blocks, sms * MIN_BLOCKS);
     // the work queue: every member's collide chunks, member after member,
     // then every member's point items
     std::vector<int> nchunk(n), skind, smember;
     std::vector<long long> sbegin;
-    {
+    if (e == cudaSuccess) {
+        long long units = 0;  // windows or 4-tile groups of all members
+        for (int i = 0; i < n; ++i) {
+            const Geom& g = ctxs[i]->geom;
+            units += flat ? (g.V + 31) / 32 : (long long)work[i].groups_x * work[i].groups_y * g.nz;
+        }
+        const double ideal = (double)units / ((double)CHUNKS_PER_BLOCK * (double)std::max(1, b->max_blocks));
+        int chunk = CHUNK_MIN;
+        while (chunk < CHUNK_MAX && (double)chunk * 1.41421356 < ideal) chunk *= 2;  // nearest power of two
+        b->chunk = chunk;
         long long items = 0;
         for (int i = 0; i < n; ++i) {
             const Geom& g = ctxs[i]->geom;
-            nchunk[i] = (int)(flat ? ((g.V + 31) / 32 + FLAT_CHUNK - 1) / FLAT_CHUNK
-                                   : ((long long)work[i].groups_x * work[i].groups_y * g.nz + TILED_CHUNK - 1) /
-                                         TILED_CHUNK);
+            const long long u = flat ? (g.V + 31) / 32 : (long long)work[i].groups_x * work[i].groups_y * g.nz;
+            nchunk[i] = (int)((u + b->chunk - 1) / b->chunk);
             sbegin.push_back(items);
             smember.push_back(i);
             skind.push_back(0);
@@ -767,20 +796,6 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
         b->total_items = items;
         b->nseg = (int)sbegin.size();
     }
-    b->total_pts = pts;
-    b->n_mobile = mob;
-    b->total_bins = bins;
-    b->flat = flat;
-    b->walls = walls;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel_any(b), BT, 0);
-    if (e == cudaSuccess && per_sm < 1) e = cudaErrorCooperativeLaunchTooLarge;
-    b->sms = sms;
-    b->max_blocks = sms * per_sm;
-    // untuned: MIN_BLOCKS blocks per SM (or what fits)
-    b->blocks = std::min(b->max_blocks, sms * MIN_BLOCKS);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
