@@ -593,7 +593,8 @@ def batched_replicas(steps=50, seq_steps=10, replicas=64):
     torch.cuda.empty_cache()
     return {"replicas": len(probs), "sites_per_step": sites, "colloids": npts, "precision": "f32",
             "value": round(sites / (ms_b * 1e-3) / 1e6, 1), "unit": "MLUPS", "ms_per_step": round(ms_b, 4),
-            "hbm_frac_of_step": round(152 * sites / (ms_b * 1e-3) / 1e9 / peak, 4),
+            "hbm_frac_of_step": round(step_bytes("f32", sites, npts) / (ms_b * 1e-3) / 1e9 / peak, 4),
+            "bytes_rule": "as the headline step: 2*19*4 B per site + 5*64*3*4 B per colloid",
             "launches_per_step": launches / steps, "persistent_blocks": blocks, "steps": steps,
             "sequential_lb_step": {"value": round(sites / (ms_s * 1e-3) / 1e6, 1), "ms_per_step": round(ms_s, 4),
                                    "steps": seq_steps}}
