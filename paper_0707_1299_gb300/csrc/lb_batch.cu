@@ -179,9 +179,11 @@ __device__ __forceinline__ void batch_site(const Entry& E, int e, int x, int y, 
     T Fx = EP<T>::uf(E, 0), Fy = EP<T>::uf(E, 1), Fz = EP<T>::uf(E, 2);
     if (fl) {
         const T s = SC ? (T)E.scale : T(1);
-        Fx += __ldg(floc + site) * s;
-        Fy += __ldg(floc + V + site) * s;
-        Fz += __ldg(floc + 2 * V + site) * s;
+        T lx, ly, lz;
+        field_ldg(floc, site, lx, ly, lz);
+        Fx += lx * s;
+        Fy += ly * s;
+        Fz += lz * s;
     }
     Coef<T> k;
     k.tau_s = EP<T>::coef(E, 0);
@@ -192,17 +194,8 @@ __device__ __forceinline__ void batch_site(const Entry& E, int e, int x, int y, 
     unsigned rn = rng_seed(site ^ (unsigned)(e * 0x27d4eb2d), seed);
 #pragma unroll
     for (int i = 0; i < NQ; ++i) Store<S>::st(dst, (unsigned)i * V + site, o[i], rng_next(rn));
-    if (fl && E.vel) {  // v at the stencil nodes of the replica's colloids
-        T* vel = (T*)E.vel;
-        vel[site] = v3[0];
-        vel[V + site] = v3[1];
-        vel[2 * V + site] = v3[2];
-    }
-    if (fl) {
-        floc[site] = T(0);
-        floc[V + site] = T(0);
-        floc[2 * V + site] = T(0);
-    }
+    if (fl && E.vel) field_st((T*)E.vel, site, v3[0], v3[1], v3[2]);  // v at the replica's colloids' nodes
+    if (fl) field_st(floc, site, T(0), T(0), T(0));
 }
 
 // The collide over flat 32-site windows of each member's site index (x

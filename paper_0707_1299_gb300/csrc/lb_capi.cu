@@ -298,14 +298,14 @@ lb_status lb_create(lb_ctx** out, const int grid[3], double tau_shear, double ta
     const size_t sb = lbk::storage_bytes(precision), ab = lbk::arith_bytes(precision);
     if (e == cudaSuccess) e = cudaMalloc(&c->f[0], sb * lbk::NQ * (size_t)V);
     if (e == cudaSuccess) e = cudaMalloc(&c->f[1], sb * lbk::NQ * (size_t)V);
-    if (e == cudaSuccess) e = cudaMalloc(&c->floc, ab * 3 * (size_t)V);
+    if (e == cudaSuccess) e = cudaMalloc(&c->floc, ab * lbk::FIELD_W * (size_t)V);
     if (e == cudaSuccess) e = cudaMalloc(&c->flags, sizeof(unsigned) * (size_t)c->geom.ntiles);  // 4 group flags a tile
     if (e == cudaSuccess) e = cudaMalloc(&c->fsum, sizeof(double) * 3);
     if (e == cudaSuccess) e = cudaMalloc(&c->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->partials, sizeof(double) * 4 * (size_t)lbk::moment_blocks(c->geom));
     if (e == cudaSuccess) e = cudaMalloc(&c->totals_dev, sizeof(double) * 4);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->f[0], 0, sb * lbk::NQ * (size_t)V, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->floc, 0, ab * 3 * (size_t)V, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->floc, 0, ab * lbk::FIELD_W * (size_t)V, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, sizeof(unsigned) * (size_t)c->geom.ntiles, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->fsum, 0, sizeof(double) * 3, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

@@ -24,7 +24,7 @@ namespace lbk {
 template <typename S, bool VOUT>
 __device__ __forceinline__ void finish_site(const typename Store<S>::T (&f)[NQ], const Pops<S>& dst,
                                             typename Store<S>::T* floc,
-                                            typename Store<S>::T* __restrict__ vel, unsigned V, unsigned site,
+                                            typename Store<S>::T* __restrict__ vel, unsigned site,
                                             bool field, const Coef<typename Store<S>::T>& k,
                                             const UForce<typename Store<S>::T>& fu, float scale, float inv_scale,
                                             unsigned seed) {
@@ -33,9 +33,11 @@ __device__ __forceinline__ void finish_site(const typename Store<S>::T (&f)[NQ],
     T Fx = fu.F[0], Fy = fu.F[1], Fz = fu.F[2];
     if (field) {  // read-only path: see reset_group_flag
         const T s = SC ? (T)scale : T(1);
-        Fx += __ldg(floc + site) * s;
-        Fy += __ldg(floc + V + site) * s;
-        Fz += __ldg(floc + 2 * V + site) * s;
+        T lx, ly, lz;
+        field_ldg(floc, site, lx, ly, lz);
+        Fx += lx * s;
+        Fy += ly * s;
+        Fz += lz * s;
     }
     T o[NQ], v3[3];
     collide19<T, Store<S>::kCompensate, SC, VOUT>(f, Fx, Fy, Fz, k, o, (T)inv_scale, v3);
@@ -43,12 +45,8 @@ __device__ __forceinline__ void finish_site(const typename Store<S>::T (&f)[NQ],
 #pragma unroll
     for (int i = 0; i < NQ; ++i) Store<S>::st(dst.p[i], site, o[i], rng_next(rn));
     if (VOUT && field) {
-        vel[site] = v3[0];
-        vel[V + site] = v3[1];
-        vel[2 * V + site] = v3[2];
-        floc[site] = T(0);
-        floc[V + site] = T(0);
-        floc[2 * V + site] = T(0);
+        field_st(vel, site, v3[0], v3[1], v3[2]);
+        field_st(floc, site, T(0), T(0), T(0));  // the consumed force
     }
 }
 
@@ -87,7 +85,6 @@ k_collide(const Pops<S> src, const Pops<S> dst, typename Store<S>::T* __restrict
     if (y0 >= g.ny) return;  // uniform per warp
     const int z = blockIdx.z, lane = threadIdx.x;
     const int x = blockIdx.x * TILE_X + lane;
-    const unsigned V = (unsigned)g.V;
     unsigned fl[NY];
 #pragma unroll
     for (int r = 0; r < NY; ++r) {
@@ -117,7 +114,7 @@ k_collide(const Pops<S> src, const Pops<S> dst, typename Store<S>::T* __restrict
             for (int r = 0; r < NY; ++r) {
                 if (y0 + r >= g.ny) break;
                 // the field loads come after the population loads, so both are in flight together
-                finish_site<S, VOUT>(f[r], dst, floc, vel, V, n[r].c + n[r].x, FIELD && fl[r], k, fu, scale, inv_scale,
+                finish_site<S, VOUT>(f[r], dst, floc, vel, n[r].c + n[r].x, FIELD && fl[r], k, fu, scale, inv_scale,
                                      seed);
             }
         }
@@ -168,18 +165,17 @@ k_collide_pair(const Pops<S> src, const Pops<S> dst, float* __restrict__ floc, f
     const unsigned tile = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.ntx + x0 / TILE_X;
     const unsigned fl = (FIELD && active) ? group_flag(__ldg((const unsigned*)flags + tile), x0 % TILE_X) : 0u;
     const Nbr n = neighbours(g, 0, y, z);
-    const unsigned V = (unsigned)g.V;
     unsigned w[NQ];
-    float2 fa = make_float2(0.0f, 0.0f), fb = fa, fc = fa;
+    float4 fs0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), fs1 = fs0;  // the two sites' force words
     // the force loads are issued after the population loads and before the
     // shuffles wait for those, so both are in flight together
     pull19_pair<S, WALLS>(src, n, x0, nx, lane, active, w, [&] {
         if (FIELD && fl) {
-            fa = __ldg((const float2*)(floc + row + x0));
-            fb = __ldg((const float2*)(floc + V + row + x0));
-            fc = __ldg((const float2*)(floc + 2 * V + row + x0));
+            fs0 = __ldg((const float4*)floc + row + x0);
+            fs1 = __ldg((const float4*)floc + row + x0 + 1);
         }
     });
+    const float2 fa = make_float2(fs0.x, fs1.x), fb = make_float2(fs0.y, fs1.y), fc = make_float2(fs0.z, fs1.z);
     F2 f[NQ];
 #pragma unroll
     for (int i = 0; i < NQ; ++i) f[i] = F2(St::unpack2(w[i]));
@@ -212,11 +208,10 @@ k_collide_pair(const Pops<S> src, const Pops<S> dst, float* __restrict__ floc, f
         collide19<F2, false, SC, VOUT>(f, Fx, Fy, Fz, k2, emit, F2(inv_scale), v3);
     }
     if (VOUT && fl && active) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            *(float2*)(vel + a * V + row + x0) = v3[a].v;
-            *(float2*)(floc + a * V + row + x0) = make_float2(0.0f, 0.0f);  // the consumed force
-        }
+        field_st(vel, row + x0, v3[0].v.x, v3[1].v.x, v3[2].v.x);
+        field_st(vel, row + x0 + 1, v3[0].v.y, v3[1].v.y, v3[2].v.y);
+        field_st(floc, row + x0, 0.0f, 0.0f, 0.0f);  // the consumed force
+        field_st(floc, row + x0 + 1, 0.0f, 0.0f, 0.0f);
     }
     if (VOUT) reset_group_flag(flags, tile, x0 % TILE_X, fl);
 }
@@ -255,24 +250,23 @@ k_collide_quad(const Pops<S> src, const Pops<S> dst, float* __restrict__ floc, f
     const unsigned fl = (FIELD && active) ? group_flag(__ldg((const unsigned*)flags + tile), x0 % TILE_X) : 0u;
     const Nbr n = neighbours(g, 0, y, z);
     unsigned lo[NQ], hi[NQ];
-    const unsigned V = (unsigned)g.V;
-    float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f), b = a, d = a;
+    float4 fs[4];  // the four sites' force words
+#pragma unroll
+    for (int q = 0; q < 4; ++q) fs[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     pull19_quad<S, WALLS>(src, n, x0, nx, lane, active, lo, hi, [&] {
-        if (FIELD && fl) {  // in flight with the population loads
-            a = __ldg((const float4*)(floc + row + x0));
-            b = __ldg((const float4*)(floc + V + row + x0));
-            d = __ldg((const float4*)(floc + 2 * V + row + x0));
-        }
+        if (FIELD && fl)  // in flight with the population loads
+#pragma unroll
+            for (int q = 0; q < 4; ++q) fs[q] = __ldg((const float4*)floc + row + x0 + q);
     });
     F2 Fx[2] = {F2(fu.F[0]), F2(fu.F[0])}, Fy[2] = {F2(fu.F[1]), F2(fu.F[1])}, Fz[2] = {F2(fu.F[2]), F2(fu.F[2])};
     if (FIELD && fl) {
         const float sc = SC ? scale : 1.0f;
-        Fx[0] = fma(F2(make_float2(a.x, a.y)), F2(sc), Fx[0]);
-        Fx[1] = fma(F2(make_float2(a.z, a.w)), F2(sc), Fx[1]);
-        Fy[0] = fma(F2(make_float2(b.x, b.y)), F2(sc), Fy[0]);
-        Fy[1] = fma(F2(make_float2(b.z, b.w)), F2(sc), Fy[1]);
-        Fz[0] = fma(F2(make_float2(d.x, d.y)), F2(sc), Fz[0]);
-        Fz[1] = fma(F2(make_float2(d.z, d.w)), F2(sc), Fz[1]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            Fx[h] = fma(F2(make_float2(fs[2 * h].x, fs[2 * h + 1].x)), F2(sc), Fx[h]);
+            Fy[h] = fma(F2(make_float2(fs[2 * h].y, fs[2 * h + 1].y)), F2(sc), Fy[h]);
+            Fz[h] = fma(F2(make_float2(fs[2 * h].z, fs[2 * h + 1].z)), F2(sc), Fz[h]);
+        }
     }
     Coef<F2> k2;
     k2.tau_s = F2(k.tau_s);
@@ -296,11 +290,12 @@ k_collide_quad(const Pops<S> src, const Pops<S> dst, float* __restrict__ floc, f
     }
     if (VOUT && fl && active) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            *(float4*)(vel + a * V + row + x0) =
-                make_float4(v3[0][a].v.x, v3[0][a].v.y, v3[1][a].v.x, v3[1][a].v.y);
-            *(float4*)(floc + a * V + row + x0) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // the consumed force
+        for (int h = 0; h < 2; ++h) {
+            field_st(vel, row + x0 + 2 * h, v3[h][0].v.x, v3[h][1].v.x, v3[h][2].v.x);
+            field_st(vel, row + x0 + 2 * h + 1, v3[h][0].v.y, v3[h][1].v.y, v3[h][2].v.y);
         }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) field_st(floc, row + x0 + q, 0.0f, 0.0f, 0.0f);  // the consumed force
     }
     if (VOUT) reset_group_flag(flags, tile, x0 % TILE_X, fl);
 }
@@ -326,7 +321,7 @@ k_fixup(const Pops<S> src, const Pops<S> dst, typename Store<S>::T* __restrict__
     const Nbr n = neighbours(g, x, y, z);
     T f[NQ];
     pull19<S, WALLS>(src, n, f);
-    finish_site<S, false>(f, dst, floc, nullptr, (unsigned)g.V, n.c + n.x, true, k, fu, scale, inv_scale, seed);
+    finish_site<S, false>(f, dst, floc, nullptr, n.c + n.x, true, k, fu, scale, inv_scale, seed);
 }
 
 // The pair kernel exists for the 16-bit formats; for the others PairS maps

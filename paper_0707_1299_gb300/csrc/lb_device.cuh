@@ -53,6 +53,47 @@ __device__ __forceinline__ unsigned group_flag(unsigned word, unsigned x_in_tile
     return (word >> (8u * (x_in_tile / GROUP_X))) & 0xFFu;
 }
 
+// Force and velocity fields: FIELD_W elements of the arithmetic type a site,
+// x, y, z and an unused fourth (kept zero), so that a node's three
+// components are one 16-byte word in float: the spread adds a node with one
+// vector reduction, the interpolation reads it with one load.  field_ldg
+// reads through the read-only path (see reset_group_flag), field_ld with a
+// plain load; field_st writes (zero in the fourth element), field_add adds.
+constexpr int FIELD_W = 4;
+__device__ __forceinline__ void field_ldg(const float* f, size_t site, float& x, float& y, float& z) {
+    const float4 q = __ldg((const float4*)f + site);
+    x = q.x, y = q.y, z = q.z;
+}
+__device__ __forceinline__ void field_ldg(const double* f, size_t site, double& x, double& y, double& z) {
+    const double2 q = __ldg((const double2*)(f + FIELD_W * site));
+    x = q.x, y = q.y, z = __ldg(f + FIELD_W * site + 2);
+}
+__device__ __forceinline__ void field_ld(const float* f, size_t site, float& x, float& y, float& z) {
+    const float4 q = *((const float4*)f + site);
+    x = q.x, y = q.y, z = q.z;
+}
+__device__ __forceinline__ void field_ld(const double* f, size_t site, double& x, double& y, double& z) {
+    const double2 q = *(const double2*)(f + FIELD_W * site);
+    x = q.x, y = q.y, z = f[FIELD_W * site + 2];
+}
+__device__ __forceinline__ void field_st(float* f, size_t site, float x, float y, float z) {
+    *((float4*)f + site) = make_float4(x, y, z, 0.0f);
+}
+__device__ __forceinline__ void field_st(double* f, size_t site, double x, double y, double z) {
+    *(double2*)(f + FIELD_W * site) = make_double2(x, y);
+    *(double2*)(f + FIELD_W * site + 2) = make_double2(z, 0.0);
+}
+__device__ __forceinline__ void field_add(float* f, size_t site, float x, float y, float z) {
+    const size_t a = __cvta_generic_to_global((float4*)f + site);
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(a), "f"(x), "f"(y), "f"(z), "f"(0.0f)
+                 : "memory");
+}
+__device__ __forceinline__ void field_add(double* f, size_t site, double x, double y, double z) {
+    atomicAdd(f + FIELD_W * site, x);
+    atomicAdd(f + FIELD_W * site + 1, y);
+    atomicAdd(f + FIELD_W * site + 2, z);
+}
+
 // ----------------------------------------------------------- storage types
 // df is stored as S and handled in arithmetic type T.  The half-precision
 // formats store df * scale (a power of two) to keep df out of subnormals.

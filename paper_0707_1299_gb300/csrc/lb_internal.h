@@ -26,10 +26,11 @@ struct lb_ctx {
 
     void* f[2];               // population buffers (19 V elements of the storage type)
     int cur;                  // index of the buffer holding the current state
-    void* floc;               // localised force field, 3 V elements of the arithmetic type
+    void* floc;               // localised force field, FIELD_W V elements of the arithmetic type
+                              // (x, y, z, unused per site)
     lbk::flag_t* flags;       // one byte per 8-site x-group (four per 32-site tile): the group
                               // holds spread force
-    void* vel;                // fluid velocity in the flagged groups, 3 V elements of the
+    void* vel;                // fluid velocity in the flagged groups, FIELD_W V elements of the
                               // arithmetic type (lattices with colloids only)
     bool host_async;          // host-memory copies are not waited for (lb_set_host_async)
     bool field_ready;         // floc holds the forces at the current positions

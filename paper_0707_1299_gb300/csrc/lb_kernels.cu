@@ -114,7 +114,6 @@ k_spread(const T* __restrict__ st, const double* __restrict__ force, const int* 
     const T wxy = __shfl_sync(FULL, r, i) * __shfl_sync(FULL, r, 4 + j);
     const int x = wrap_node(bx + i, g.nx), y = wrap_node(by + j, g.ny);
     const bool marker = (i == 0) || ((x & (GROUP_X - 1)) == 0);
-    const unsigned V = (unsigned)g.V;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int k = (lane >> 4) + 2 * h;
@@ -124,9 +123,7 @@ k_spread(const T* __restrict__ st, const double* __restrict__ force, const int* 
         const T w = wxy * wz;
         const unsigned row = (unsigned)z * (unsigned)g.ny + (unsigned)y;
         const unsigned site = row * (unsigned)g.nx + (unsigned)x;
-        atomicAdd(floc + site, F0 * w);
-        atomicAdd(floc + V + site, F1 * w);
-        atomicAdd(floc + 2 * V + site, F2 * w);
+        field_add(floc, site, F0 * w, F1 * w, F2 * w);
         if (marker) flags[row * (unsigned)g.ntx * (TILE_X / GROUP_X) + (unsigned)(x / GROUP_X)] = 1;
     }
 }
@@ -186,7 +183,6 @@ k_gather(const Pops<S> src, const typename Store<S>::T* __restrict__ floc, Geom 
     const StencilLane<T> st = stencil_lane<T>(X, Y, Z, lane);
     const unsigned FULL = 0xffffffffu;
     const int bx = __shfl_sync(FULL, st.base, 0), by = __shfl_sync(FULL, st.base, 4), bz = __shfl_sync(FULL, st.base, 8);
-    const unsigned V = (unsigned)g.V;
     T acc[3] = {T(0), T(0), T(0)};
     for (int h = 0; h < 2; ++h) {
         const int node = lane + 32 * h;
@@ -199,7 +195,9 @@ k_gather(const Pops<S> src, const typename Store<S>::T* __restrict__ floc, Geom 
         T f[NQ];
         pull19<S, WALLS>(src, nb, f);
         unscale19<S>(f, inv_scale);
-        const T Fx = fu.F[0] + floc[site], Fy = fu.F[1] + floc[V + site], Fz = fu.F[2] + floc[2 * V + site];
+        T lx, ly, lz;
+        field_ld(floc, site, lx, ly, lz);
+        const T Fx = fu.F[0] + lx, Fy = fu.F[1] + ly, Fz = fu.F[2] + lz;
         T drho, vx, vy, vz;
         macro19<T, Store<S>::kCompensate>(f, Fx, Fy, Fz, drho, vx, vy, vz);
         acc[0] += w * vx;
@@ -249,7 +247,9 @@ k_moments(const Pops<S> src, const typename Store<S>::T* __restrict__ floc, Geom
             T f[NQ];
             pull19<S, WALLS>(src, nb, f);
             unscale19<S>(f, inv_scale);
-            const T Fx = fu.F[0] + floc[site], Fy = fu.F[1] + floc[V + site], Fz = fu.F[2] + floc[2 * V + site];
+            T lx, ly, lz;
+            field_ld(floc, site, lx, ly, lz);
+            const T Fx = fu.F[0] + lx, Fy = fu.F[1] + ly, Fz = fu.F[2] + lz;
             T drho, vx, vy, vz;
             macro19<T, Store<S>::kCompensate>(f, Fx, Fy, Fz, drho, vx, vy, vz);
             r = 1.0 + (double)drho;
@@ -638,7 +638,7 @@ cudaError_t list_fixed_tiles(lb_ctx* c) {
 
 cudaError_t ensure_velocity_field(lb_ctx* c) {
     if (c->vel || c->n_mobile == 0) return cudaSuccess;
-    return cudaMalloc(&c->vel, arith_bytes(c->prec) * 3 * (size_t)c->geom.V);
+    return cudaMalloc(&c->vel, arith_bytes(c->prec) * FIELD_W * (size_t)c->geom.V);
 }
 
 cudaError_t launch_sort_points(lb_ctx* c) {
@@ -861,7 +861,7 @@ cudaError_t launch_convert_in(lb_ctx* c, const double* df) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_clear_groups(Geom g, T* __restrict__ floc, flag_t* __restrict__ flags) {
     const unsigned lane = threadIdx.x & 31u;
-    const unsigned V = (unsigned)g.V, ntiles = (unsigned)g.ntiles, ntx = (unsigned)g.ntx;
+    const unsigned ntiles = (unsigned)g.ntiles, ntx = (unsigned)g.ntx;
     const unsigned ngroups = (ntiles + 31u) >> 5;
     const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
     unsigned* words = (unsigned*)flags;
@@ -879,9 +879,7 @@ __global__ void __launch_bounds__(256) k_clear_groups(Geom g, T* __restrict__ fl
             const unsigned x = (tile - row * ntx) * TILE_X + lane;
             if (x < (unsigned)g.nx && group_flag(wt, lane)) {
                 const unsigned site = row * (unsigned)g.nx + x;
-                floc[site] = T(0);
-                floc[V + site] = T(0);
-                floc[2 * V + site] = T(0);
+                field_st(floc, site, T(0), T(0), T(0));
             }
         }
     }

@@ -107,7 +107,6 @@ __device__ __forceinline__ StencilPartT<T> stencil_part(const Geom& g, const T* 
 // (Sec. IV) from the velocity the collide wrote (v = 0 on solid nodes).
 template <typename T, bool WALLS>
 __device__ __forceinline__ void interp_part(const PointView<T>& P, const StencilPartT<T>& sp, T acc[3]) {
-    const unsigned V = (unsigned)P.g.V;
     const unsigned nx = (unsigned)P.g.nx, ny = (unsigned)P.g.ny;
     acc[0] = acc[1] = acc[2] = T(0);
 #pragma unroll
@@ -117,9 +116,11 @@ __device__ __forceinline__ void interp_part(const PointView<T>& P, const Stencil
         for (int h = 0; h < 2; ++h) {
             const T w = (h ? sp.wxy1 : sp.wxy0) * sp.wz[k];
             const unsigned site = ((unsigned)sp.zk[k] * ny + (unsigned)(h ? sp.y1 : sp.y0)) * nx + (unsigned)sp.x;
-            acc[0] += w * P.vel[site];
-            acc[1] += w * P.vel[V + site];
-            acc[2] += w * P.vel[2 * V + site];
+            T vx, vy, vz;
+            field_ld(P.vel, site, vx, vy, vz);
+            acc[0] += w * vx;
+            acc[1] += w * vy;
+            acc[2] += w * vz;
         }
     }
 }
@@ -129,7 +130,6 @@ __device__ __forceinline__ void interp_part(const PointView<T>& P, const Stencil
 template <typename T, bool WALLS>
 __device__ __forceinline__ void spread_part(const PointView<T>& P, const StencilPartT<T>& sp, int l) {
     const T F0 = (T)P.force[3 * P.s], F1 = (T)P.force[3 * P.s + 1], F2 = (T)P.force[3 * P.s + 2];
-    const unsigned V = (unsigned)P.g.V;
     const unsigned nx = (unsigned)P.g.nx, ny = (unsigned)P.g.ny;
     const bool marker = (l & 3) == 0 || (sp.x & (GROUP_X - 1)) == 0;
 #pragma unroll
@@ -140,9 +140,7 @@ __device__ __forceinline__ void spread_part(const PointView<T>& P, const Stencil
             const T w = (h ? sp.wxy1 : sp.wxy0) * sp.wz[k];
             const unsigned rw = (unsigned)sp.zk[k] * ny + (unsigned)(h ? sp.y1 : sp.y0);
             const unsigned site = rw * nx + (unsigned)sp.x;
-            atomicAdd(P.floc + site, F0 * w);
-            atomicAdd(P.floc + V + site, F1 * w);
-            atomicAdd(P.floc + 2 * V + site, F2 * w);
+            field_add(P.floc, site, F0 * w, F1 * w, F2 * w);
             if (marker) P.flags[rw * (unsigned)P.g.ntx * (TILE_X / GROUP_X) + (unsigned)sp.x / GROUP_X] = 1;
         }
     }
@@ -264,7 +262,6 @@ __device__ __forceinline__ bool spread_block_shared(const Src& src, int n, long 
     }
     __syncthreads();
     const PointView<T> P = src.view(0);  // the lattice of every point of the block
-    const unsigned V = (unsigned)P.g.V;
     for (int q = threadIdx.x; q < vol; q += blockDim.x) {
         const T f0 = tile[3 * q], f1 = tile[3 * q + 1], f2 = tile[3 * q + 2];
         if (f0 == T(0) && f1 == T(0) && f2 == T(0)) continue;
@@ -272,9 +269,7 @@ __device__ __forceinline__ bool spread_block_shared(const Src& src, int n, long 
                   z = wrap_node(box[2] + q / (ex * ey), P.g.nz);
         if (WALLS && is_solid(P.g, z)) continue;
         const unsigned site = ((unsigned)z * (unsigned)P.g.ny + (unsigned)y) * (unsigned)P.g.nx + (unsigned)x;
-        atomicAdd(P.floc + site, f0);
-        atomicAdd(P.floc + V + site, f1);
-        atomicAdd(P.floc + 2 * V + site, f2);
+        field_add(P.floc, site, f0, f1, f2);
     }
     return true;
 }
