@@ -37,10 +37,15 @@ using namespace lbk;
 constexpr int BW = 4;               // warps (tiles) per work item of the tiled collide
 constexpr int BT = BW * 32;         // threads per block of the persistent kernel
 constexpr int SORT_EVERY = 64;      // steps between renewals of the batch's cell order
-// occupancy bound of the persistent kernel (blocks of 128 threads per SM): 6
-// (85 registers) measured fastest on the 64-replica batch, 1.665 ms a step
-// against 1.705 at 8 (64 registers), 1.754 at 5 and 1.937 at 10 (spills)
-constexpr int MIN_BLOCKS = 6;
+// Occupancy bound of the persistent kernel (blocks of 128 threads per SM).
+// With the work queue, 8 (64 registers) measured fastest on the 64-replica
+// FP32 batch: 1.513 ms a step against 1.521 at 7 and 1.569 at 6 (with grid
+// barriers between the phases 6 had been fastest).  The FP64 kernel spills
+// at 64 registers and keeps 6.
+template <typename S>
+constexpr int min_blocks() {
+    return sizeof(typename Store<S>::T) == 8 ? 6 : 8;
+}
 constexpr long long DEFAULT_WAIT = 1LL << 22;  // polls of a wait (~1 s) before it gives up
 // Collide chunks: about CHUNKS_PER_BLOCK per resident block, so that the
 // tail (the last chunk a block takes) stays short, in a power of two of
@@ -456,7 +461,7 @@ __device__ bool wait_replicas(const StepArgs& a, long long p0, long long p1, lon
 // member's point items among later members' chunks instead, to overlap
 // them with the collide, measured slower: both compete for the memory.)
 template <typename S, bool FLAT, bool WALLS>
-__global__ void __launch_bounds__(BT, MIN_BLOCKS) kb_step(const StepArgs a, int parity) {
+__global__ void __launch_bounds__(BT, min_blocks<S>()) kb_step(const StepArgs a, int parity) {
     using T = typename Store<S>::T;
     BatchCtl* ctl = a.ctl;
     const volatile BatchCtl* vc = ctl;
@@ -752,8 +757,8 @@ lb_status lb_batch_create(lb_batch** out, int n, lb_ctx* const* ctxs, void* stre
     if (e == cudaSuccess && per_sm < 1) e = cudaErrorCooperativeLaunchTooLarge;
     b->sms = sms;
     b->max_blocks = sms * per_sm;
-    // untuned: MIN_BLOCKS blocks per SM (or what fits)
-    b->blocks = std::min(b->max_blocks, sms * MIN_BLOCKS);
+    // untuned: the occupancy bound's blocks per SM (or what fits)
+    b->blocks = std::min(b->max_blocks, sms * (b->prec == LB_F64 ? min_blocks<double>() : min_blocks<float>()));
     // the work queue: every member's collide chunks, member after member,
     // then every member's point items
     std::vector<int> nchunk(n), skind, smember;

@@ -369,11 +369,11 @@ static cudaError_t collide_t(lb_ctx* c) {
     // the 16-bit formats take two sites a thread when the rows pair up
     constexpr bool PAIRABLE = sizeof(S) == 2;
     const bool pair = PAIRABLE && (c->geom.nx % 2) == 0;
-    // four sites a thread (64-bit words) when no force field is read: 4-5 %
-    // faster there; with a force field the pair kernel measured as fast or
-    // faster (the flagged groups' scattered force and velocity
-    // accesses, not the load count, set its time)
-    const bool quad = PAIRABLE && (c->geom.nx % 4) == 0 && mode == FM_NONE;
+    // four sites a thread (64-bit words): 4-5 % faster without a force
+    // field; with one, half storage gains as much (512^3 with 1e5 colloids:
+    // 2.10 against 2.26 ms a step) while bfloat16 measured the same as the
+    // pair kernel (2.19 against 2.21 ms; 0.292 against 0.291 ms at 256^3)
+    const bool quad = PAIRABLE && (c->geom.nx % 4) == 0 && (mode == FM_NONE || Store<S>::kScaled);
     const dim3 pgrid((unsigned)((c->geom.nx + 63) / 64), grid.y, grid.z);
     const dim3 qgrid((unsigned)((c->geom.nx + 127) / 128), grid.y, grid.z);
 #define LB_COLLIDE(W, FM)                                                                                          \
