@@ -617,7 +617,7 @@ def learned_correction(train_pairs=32, test_pairs=4, L_pair=64, T_pair=1000, ste
         ltr = torch.cat([d[1] for d in data[:train_pairs]]).contiguous()
         fte = torch.cat([d[0] for d in data[train_pairs:]]).contiguous()
         lte = torch.cat([d[1] for d in data[train_pairs:]]).contiguous()
-        warm, _ = learned.train(ftr, ltr, steps=5, batch=4096, lr=2e-3)  # first use of torch's sampling kernels
+        warm, _ = learned.train(ftr, ltr, steps=5, batch=4096, lr=2e-3)  # first use of the training kernels
         lb.lb_mlp_destroy(warm)
         torch.cuda.synchronize()
         t0 = time.perf_counter()

@@ -280,6 +280,21 @@ lb_status lb_mlp_grad(lb_mlp *net, long long n, const float *feat, const float *
  * be NULL) receives the sum of squared errors before the step */
 lb_status lb_mlp_train_step(lb_mlp *net, long long n, const float *feat, const float *target, float lr,
                             float *sse);
+/* `steps` Adam steps on minibatches drawn on the device: minibatch s takes
+ * `batch` samples of (feat[n][27], target[n][3]) (device pointers), sample
+ * b the row j = h(seed, s, b) mod n, h the SplitMix64 finaliser of
+ * seed + (s * batch + b + 1) * 0x9E3779B97F4A7C15 shifted right by 11 (with
+ * replacement); targets are divided by target_scale (> 0) as they are
+ * gathered.  The learning rate of step s is max(lr (1 + cos(pi s / steps)) / 2,
+ * 1e-6).  loss (host, may be NULL) receives the minibatch's mean squared
+ * error before steps 0, e, 2e, ... (e = loss_every >= 1) and before the last
+ * step: floor((steps - 1) / e) + 2 floats at most (the last step listed
+ * once).  The draws and steps run on the network's stream without waiting;
+ * the call waits once at the end.  Allocates its minibatch buffers on first
+ * use (grown on demand).  LB_ERR_ARG for n < 1, batch < 1, steps < 1,
+ * lr <= 0, target_scale <= 0 or non-finite, loss_every < 1. */
+lb_status lb_mlp_train(lb_mlp *net, long long n, const float *feat, const float *target, float target_scale,
+                       int batch, int steps, float lr, unsigned long long seed, int loss_every, float *loss);
 
 /* Attach (net != NULL) or detach the learned correction to the colloid
  * update of lb_step: each mobile colloid then moves by

@@ -683,6 +683,36 @@ __global__ void __launch_bounds__(tc::M, 1) km_grad_tc(const float* __restrict__
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(GCOLS) : "memory");
 }
 
+// Minibatch s of lb_mlp_train: sample b takes row j = h(seed, s, b) mod n of
+// (feat, target), h the SplitMix64 finaliser (Steele, Lea and Flood, 2014)
+// of seed + (s * batch + b + 1) * golden-ratio constant, shifted right by 11;
+// targets divided by their scale.  One thread a sample.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+    x ^= x >> 30;
+    x *= 0xBF58476D1CE4E5B9ull;
+    x ^= x >> 27;
+    x *= 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+__global__ void km_gather(unsigned long long seed, long long s, int batch, long long n, const float* __restrict__ feat,
+                          const float* __restrict__ target, float inv_scale, float* __restrict__ bfeat,
+                          float* __restrict__ btarget) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    const unsigned long long c = (unsigned long long)s * (unsigned long long)batch + (unsigned long long)b + 1ull;
+    const long long j = (long long)((splitmix64(seed + c * 0x9E3779B97F4A7C15ull) >> 11) % (unsigned long long)n);
+#pragma unroll
+    for (int k = 0; k < D0; ++k) bfeat[(long long)b * D0 + k] = feat[j * D0 + k];
+#pragma unroll
+    for (int a = 0; a < D3; ++a) btarget[(long long)b * D3 + a] = target[j * D3 + a] * inv_scale;
+}
+
+// The minibatch's mean squared error into slot k of the loss record.
+__global__ void km_record_loss(const float* __restrict__ sse, float inv_count, float* __restrict__ rec, int k) {
+    rec[k] = sse[0] * inv_count;
+}
+
 __global__ void km_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                         float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1109,6 +1139,8 @@ struct lb_mlp {
     long long t;              // Adam steps taken
     int *ws;                  // feature workspace (cell lists), grown on demand
     size_t ws_ints;
+    float* mb;                // lb_mlp_train: minibatch features and targets, then the loss record
+    size_t mb_floats;
     std::string err;
 };
 
@@ -1323,6 +1355,7 @@ void lb_mlp_destroy(lb_mlp* net) {
     cudaStreamSynchronize(net->stream);
     cudaFree(net->p);
     cudaFree(net->ws);
+    cudaFree(net->mb);
     cudaFree(net->status);
     delete net;
 }
@@ -1396,16 +1429,56 @@ lb_status lb_mlp_grad(lb_mlp* net, long long n, const float* feat, const float* 
     return LB_OK;
 }
 
-lb_status lb_mlp_train_step(lb_mlp* net, long long n, const float* feat, const float* target, float lr, float* sse) {
-    if (!net || n < 1 || !feat || !target || !(lr > 0)) return mfail(net, LB_ERR_ARG, "lb_mlp_train_step: bad argument");
-    lb_status s = run_grad(net, n, feat, target);
-    if (s != LB_OK) return s;
+static void adam_step(lb_mlp* net, float lr) {
     net->t += 1;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.0f - powf(b1, (float)net->t), c2 = 1.0f - powf(b2, (float)net->t);
     km_adam<<<(NPARAM + 255) / 256, 256, 0, net->stream>>>(net->p, net->g, net->m, net->v, lr, b1, b2, 1e-8f, c1, c2);
+}
+
+lb_status lb_mlp_train_step(lb_mlp* net, long long n, const float* feat, const float* target, float lr, float* sse) {
+    if (!net || n < 1 || !feat || !target || !(lr > 0)) return mfail(net, LB_ERR_ARG, "lb_mlp_train_step: bad argument");
+    lb_status s = run_grad(net, n, feat, target);
+    if (s != LB_OK) return s;
+    adam_step(net, lr);
     LB_MCUDA(cudaGetLastError(), "adam kernel");
     if (sse) LB_MCUDA(cudaMemcpyAsync(sse, net->sse, sizeof(float), cudaMemcpyDefault, net->stream), "copy");
+    return LB_OK;
+}
+
+lb_status lb_mlp_train(lb_mlp* net, long long n, const float* feat, const float* target, float target_scale,
+                       int batch, int steps, float lr, unsigned long long seed, int loss_every, float* loss) {
+    if (!net || n < 1 || !feat || !target || batch < 1 || steps < 1 || !(lr > 0) || !(target_scale > 0) ||
+        !isfinite(target_scale) || loss_every < 1)
+        return mfail(net, LB_ERR_ARG, "lb_mlp_train: bad argument");
+    const int nrec = (steps - 1) / loss_every + 2;
+    const size_t need = (size_t)batch * (D0 + D3) + (size_t)nrec;
+    if (need > net->mb_floats) {
+        LB_MCUDA(cudaStreamSynchronize(net->stream), "stream synchronize");
+        cudaFree(net->mb);
+        net->mb = nullptr;
+        net->mb_floats = 0;
+        LB_MCUDA(cudaMalloc(&net->mb, sizeof(float) * need), "minibatch buffers");
+        net->mb_floats = need;
+    }
+    float* bfeat = net->mb;
+    float* btarget = bfeat + (size_t)batch * D0;
+    float* rec = btarget + (size_t)batch * D3;
+    const float inv_count = 1.0f / (3.0f * (float)batch);
+    int k = 0;
+    for (int s = 0; s < steps; ++s) {
+        km_gather<<<(batch + 127) / 128, 128, 0, net->stream>>>(seed, s, batch, n, feat, target, 1.0f / target_scale,
+                                                                bfeat, btarget);
+        LB_MCUDA(cudaGetLastError(), "minibatch kernel");
+        lb_status st = run_grad(net, batch, bfeat, btarget);
+        if (st != LB_OK) return st;
+        if (s % loss_every == 0 || s == steps - 1) km_record_loss<<<1, 1, 0, net->stream>>>(net->sse, inv_count, rec, k++);
+        const float lr_s = fmaxf(lr * 0.5f * (1.0f + cosf(3.14159265358979f * (float)s / (float)steps)), 1e-6f);
+        adam_step(net, lr_s);
+        LB_MCUDA(cudaGetLastError(), "adam kernel");
+    }
+    if (loss) LB_MCUDA(cudaMemcpyAsync(loss, rec, sizeof(float) * k, cudaMemcpyDefault, net->stream), "loss copy");
+    LB_MCUDA(cudaStreamSynchronize(net->stream), "stream synchronize");
     return LB_OK;
 }
 

@@ -34,7 +34,7 @@ EXPORTS = ["lb_create", "lb_destroy", "lb_last_error", "lb_set_body_force", "lb_
            "lb_mlp_get_params", "lb_mlp_set_params", "lb_mlp_features", "lb_mlp_forward", "lb_mlp_grad",
            "lb_mlp_train_step", "lb_set_colloid_correction", "lb_save", "lb_load",
            "lb_mlp_set_wait_limit", "lb_set_host_async", "lb_set_phase_timing", "lb_phase_times",
-           "lb_batch_synchronize", "lb_batch_set_wait_limit"]
+           "lb_batch_synchronize", "lb_batch_set_wait_limit", "lb_mlp_train"]
 
 _lib = None
 
@@ -95,6 +95,8 @@ def load():
         "lb_mlp_set_wait_limit": ([vp, ctypes.c_longlong], ctypes.c_int),
         "lb_mlp_grad": ([vp, ctypes.c_longlong, vp, vp, vp, vp], ctypes.c_int),
         "lb_mlp_train_step": ([vp, ctypes.c_longlong, vp, vp, ctypes.c_float, vp], ctypes.c_int),
+        "lb_mlp_train": ([vp, ctypes.c_longlong, vp, vp, ctypes.c_float, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                          ctypes.c_ulonglong, ctypes.c_int, vp], ctypes.c_int),
         "lb_batch_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), vp],
                             ctypes.c_int),
         "lb_batch_destroy": ([vp], None),
@@ -383,6 +385,11 @@ def lb_mlp_grad(net, n, feat, target, grad=None, sse=None):
 
 def lb_mlp_train_step(net, n, feat, target, lr, sse=None):
     _mcheck(net, load().lb_mlp_train_step(net, int(n), _addr(feat), _addr(target), float(lr), _addr(sse)))
+
+
+def lb_mlp_train(net, n, feat, target, target_scale, batch, steps, lr, seed=0, loss_every=50, loss=None):
+    _mcheck(net, load().lb_mlp_train(net, int(n), _addr(feat), _addr(target), float(target_scale), int(batch),
+                                     int(steps), float(lr), int(seed) & (2 ** 64 - 1), int(loss_every), _addr(loss)))
 
 
 def _bcheck(batch, status):

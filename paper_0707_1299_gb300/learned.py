@@ -29,9 +29,10 @@ NUMBER_DENSITY = 2e5 / 256 ** 3  # colloids per lattice site of the 256^3, 2e5-c
 
 def pair_samples(L: int = 64, seed: int = 0, T: int = 1000, force: float = 1e-6, a: float = W.A_TABLE1,
                  density: float = NUMBER_DENSITY, tau: float = 0.5, precision: int = lb.LB_F32):
-    """One 1x/2x run pair: returns (features, labels, U1, U2x) as torch
-    tensors on the current device: (n, 27) float32, (n, 3) float32, and the
-    two colloid velocities (n, 3) float64 in coarse lattice units."""
+    """One 1x/2x run pair: returns (features, labels, U1, U2x): features
+    (n, 27) and labels (n, 3) as float32 torch tensors on the current device,
+    and the two colloid velocities (n, 3) as float64 numpy arrays in coarse
+    lattice units."""
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
     r = W.rng(1000 + seed)
@@ -53,8 +54,9 @@ def pair_samples(L: int = 64, seed: int = 0, T: int = 1000, force: float = 1e-6,
         lb.lb_colloid_velocity(g.ctx, n, pos, Ft, rad, U)
         out[k] = U
         g.close()
-    U1, U2x = out[0], 2.0 * out[1]
-    labels = ((U2x - U1) / v0).float().contiguous()
+    U1 = out[0].cpu().numpy()
+    U2x = 2.0 * out[1].cpu().numpy()
+    labels = torch.as_tensor(((U2x - U1) / v0).astype(np.float32), device=dev).contiguous()
     return features(R, (L, L, L)), labels, U1, U2x
 
 
@@ -86,33 +88,25 @@ def initial_params(seed: int = 0) -> np.ndarray:
 
 
 def train(feat, labels, steps: int = 2000, batch: int = 4096, lr: float = 2e-3, seed: int = 0):
-    """Adam on minibatches drawn (seeded) from (feat, labels), with the
-    labels divided by their RMS (folded back into the last layer at the
-    end); returns the lb_mlp handle and the loss history (mean squared
-    error per step, in units of the label RMS squared)."""
-    import torch
+    """Adam on minibatches drawn on the device (`lb_mlp_train`: seeded
+    draws with replacement, cosine-decayed learning rate), with the labels
+    divided by their RMS (folded back into the last layer at the end);
+    returns the lb_mlp handle and the loss history (mean squared error of the
+    minibatch every 50 steps and at the last, in units of the label RMS
+    squared)."""
     net = lb.lb_mlp_create(initial_params(seed))
-    scale = float(labels.double().pow(2).mean().sqrt())
+    lab = labels.cpu().numpy().astype(np.float64)
+    scale = float(np.sqrt(np.mean(lab * lab)))
     scale = scale if scale > 0 else 1.0
-    labels = (labels / scale).contiguous()
-    n = feat.shape[0]
-    gen = torch.Generator(device=feat.device)
-    gen.manual_seed(seed)
-    sse = torch.zeros(1, dtype=torch.float32, device=feat.device)
-    hist = []
-    for s in range(steps):
-        idx = torch.randint(0, n, (min(batch, n),), generator=gen, device=feat.device)
-        fb = feat[idx].contiguous()
-        tb = labels[idx].contiguous()
-        lr_s = lr * (0.5 * (1 + math.cos(math.pi * s / steps)))  # cosine decay
-        lb.lb_mlp_train_step(net, fb.shape[0], fb, tb, max(lr_s, 1e-6), sse)
-        if s % 50 == 0 or s == steps - 1:
-            hist.append(float(sse.item()) / (3 * fb.shape[0]))
+    every = 50
+    hist = np.zeros((steps - 1) // every + 2, dtype=np.float32)
+    lb.lb_mlp_train(net, feat.shape[0], feat, labels, scale, min(batch, feat.shape[0]), steps, lr, seed, every, hist)
+    k = (steps - 1) // every + 1 + (1 if (steps - 1) % every else 0)
     p = np.zeros(lb.lb_mlp_num_params(), dtype=np.float32)
     lb.lb_mlp_get_params(net, p)
     p[-(3 * 64 + 3):] *= scale  # W3, b3 predict the unscaled label
     lb.lb_mlp_set_params(net, p)
-    return net, hist
+    return net, [float(h) for h in hist[:k]]
 
 
 def predict(net, feat):
@@ -125,9 +119,10 @@ def predict(net, feat):
 def evaluate(net, feat, labels):
     """RMS error of the plain method (the label itself: 2 U_2x - U_1x in
     units of v0) and of the corrected velocity (label - prediction)."""
-    p = predict(net, feat)
-    plain = float(labels.double().pow(2).mean().sqrt())
-    corr = float((labels - p).double().pow(2).mean().sqrt())
+    p = predict(net, feat).cpu().numpy().astype(np.float64)
+    lab = labels.cpu().numpy().astype(np.float64)
+    plain = float(np.sqrt(np.mean(lab * lab)))
+    corr = float(np.sqrt(np.mean((lab - p) ** 2)))
     return {"rms_plain": plain, "rms_corrected": corr, "gain": plain / corr if corr > 0 else float("inf")}
 
 

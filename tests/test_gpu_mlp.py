@@ -186,6 +186,67 @@ def test_adam_steps_match_oracle():
     lb.lb_mlp_destroy(net)
 
 
+def _splitmix64_rows(seed, s, batch, n):
+    # SplitMix64 (Steele, Lea and Flood) of seed + (s batch + b + 1) * 0x9E3779B97F4A7C15,
+    # shifted right by 11, mod n: the rows lb_mlp_train documents for minibatch s
+    M = (1 << 64) - 1
+    rows = []
+    for b in range(batch):
+        x = (seed + ((s * batch + b + 1) * 0x9E3779B97F4A7C15)) & M
+        x ^= x >> 30
+        x = (x * 0xBF58476D1CE4E5B9) & M
+        x ^= x >> 27
+        x = (x * 0x94D049BB133111EB) & M
+        x ^= x >> 31
+        rows.append((x >> 11) % n)
+    return np.array(rows)
+
+
+def test_native_training_draws_the_documented_minibatches():
+    # Two steps of lb_mlp_train against lb_mlp_train_step on the minibatches
+    # its documented draw selects (rows from SplitMix64 of seed, step and
+    # slot; targets divided by the scale), with the cosine-decayed rate; the
+    # recorded losses are the minibatch mean squared errors before each step.
+    lb = _lb()
+    n, batch, steps, lr, seed, scale = 700, 256, 2, 1e-3, 12345, 0.7
+    P, x, t = _random_problem(n, 8)
+    v = mlp.flatten(P).astype(np.float32)
+    X = torch.as_tensor(x, dtype=torch.float32, device="cuda").contiguous()
+    T = torch.as_tensor(t, dtype=torch.float32, device="cuda").contiguous()
+    a = lb.lb_mlp_create(v)
+    loss = np.zeros(3, dtype=np.float32)
+    lb.lb_mlp_train(a, n, X, T, scale, batch, steps, lr, seed, 1, loss)
+    b = lb.lb_mlp_create(v)
+    sse = np.zeros(1, dtype=np.float32)
+    ref_loss = []
+    x32, t32 = x.astype(np.float32), t.astype(np.float32)
+    for s in range(steps):
+        rows = _splitmix64_rows(seed, s, batch, n)
+        fb = torch.as_tensor(x32[rows], device="cuda").contiguous()
+        tb = torch.as_tensor(t32[rows] * np.float32(1 / scale), device="cuda").contiguous()
+        lr_s = max(lr * 0.5 * (1 + np.cos(np.pi * s / steps)), 1e-6)
+        lb.lb_mlp_train_step(b, batch, fb, tb, lr_s, sse)
+        torch.cuda.synchronize()
+        ref_loss.append(sse[0] / (3 * batch))
+    pa = np.zeros_like(v)
+    pb = np.zeros_like(v)
+    lb.lb_mlp_get_params(a, pa)
+    lb.lb_mlp_get_params(b, pb)
+    assert np.abs(pa - v).max() > 0.5 * lr  # the steps moved the parameters
+    # same draws, same steps: equal up to the order of the gradient's FP32
+    # sums across CTAs, which can flip the sign of a near-zero gradient
+    # component and with it that entry's Adam step
+    differ = np.abs(pa - pb) > 1e-3 * lr
+    assert differ.mean() < 0.01 and np.abs(pa - pb).max() <= 2.5 * lr
+    assert np.allclose(loss[:2], ref_loss, rtol=1e-4)
+    lb.lb_mlp_destroy(a)
+    lb.lb_mlp_destroy(b)
+    c = lb.lb_mlp_create(v)
+    with pytest.raises(lb.LBError):
+        lb.lb_mlp_train(c, n, X, T, 0.0, batch, 1, lr)  # a target scale must be positive
+    lb.lb_mlp_destroy(c)
+
+
 def test_trained_network_reduces_subgrid_error():
     # Pairs of runs of the method at 1x and 2x resolution (48^3 boxes at the
     # number density of the 2e5-colloids-in-256^3 workload): train on 10
