@@ -138,7 +138,7 @@ __global__ void k_stencil(int n, const double* __restrict__ pos, T* __restrict__
 
 // ------------------------------------------------------------- k_points
 // The point phase of a lattice with colloids, after its collide: a block of
-// 8 warps per 32 points in cell order (point_block): every colloid's
+// 2 warps per 8 points in cell order (point_block): every colloid's
 // velocity is interpolated from the velocity field the collide wrote, every
 // point moves (Sec. IV update, with the network output y when a correction
 // is attached) and its stencil row is rewritten, and the forces are spread
@@ -155,7 +155,11 @@ struct LatticePoints {
     __device__ __forceinline__ const float* y(long long) const { return yc; }
 };
 
-constexpr int PT_WARPS = 8;  // warps of a k_points block: 32 points
+// warps of a k_points block (8 points): measured on GB300 against 8 and 4
+// warps (32 and 16 points), the small block is 7 % (1e5 colloids in 512^3)
+// and 13 % (2e5 in 256^3) faster -- the phase waits on memory, and fewer
+// warps a block barrier hold fewer warps idle
+constexpr int PT_WARPS = 2;
 
 template <typename T, bool WALLS, bool SHARED>
 __global__ void __launch_bounds__(PT_WARPS * 32) k_points(const LatticePoints<T> src, long long total,

@@ -304,10 +304,10 @@ __device__ __forceinline__ void point_block(const Src& src, long long slot0, lon
         T acc[3] = {T(0), T(0), T(0)};
         if (gk >= 0) {  // uniform per group of eight
             const PointView<T> P = src.view(gk);
-            if (P.mobile[P.s]) {
-                const StencilPartT<T> sp = stencil_part<T>(P.g, st + gk * ST_W, gmask, l);
-                interp_part<T, WALLS>(P, sp, acc);
-            }
+            // the stencil row is loaded beside the mobile flag, not after it
+            const int mob = P.mobile[P.s];
+            const StencilPartT<T> sp = stencil_part<T>(P.g, st + gk * ST_W, gmask, l);
+            if (mob) interp_part<T, WALLS>(P, sp, acc);
         }
 #pragma unroll
         for (int off = 4; off > 0; off >>= 1)
