@@ -192,11 +192,8 @@ lb_status ensure_field(lb_ctx* c) {
         c->order_stale = false;
         c->steps_since_sort = 0;
     }
-    if (!c->stencil_ready) {
-        LB_CUDA(lbk::launch_stencil(c), "stencil kernel");
-        c->stencil_ready = true;
-    }
-    LB_CUDA(lbk::launch_spread(c), "spread kernel");
+    LB_CUDA(lbk::launch_spread(c), "spread kernel");  // writes the stencil rows too
+    c->stencil_ready = true;
     c->field_ready = true;
     // fixed points keep this field: list its tiles once for the fix-up path
     if (c->n_mobile == 0) LB_CUDA(lbk::list_fixed_tiles(c), "tile list");
@@ -464,26 +461,30 @@ lb_status lb_set_positions(lb_ctx* c, const double* pos) {
     if (!pos) return fail(c, LB_ERR_ARG, "lb_set_positions: pos is NULL");
     // host positions are checked on the host, so the call need not wait for
     // the device; device positions are checked by the kernel
+    // the update is all or nothing: host positions are checked on the host
+    // (so the call need not wait for the device), device positions by a
+    // checking pass whose result is read before anything changes
     const bool on_device = is_device_ptr(pos);
     if (!on_device)
         for (long long i = 0; i < 3LL * c->npts; ++i)
             if (!isfinite(pos[i])) return fail(c, LB_ERR_NONFINITE, "lb_set_positions: non-finite position");
+    if (on_device) {
+        LB_CUDA(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "status reset");
+        LB_CUDA(lbk::launch_set_positions(c, pos, true), "position check kernel");
+        int status = 0;
+        LB_CUDA(cudaMemcpyAsync(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "status read");
+        LB_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+        if (status) return fail(c, LB_ERR_NONFINITE, "lb_set_positions: non-finite position");
+    }
     lb_status s = invalidate_field(c);
     if (s != LB_OK) return s;
     Arg args[1] = {{pos, sizeof(double) * 3 * c->npts, false, nullptr, false}};
     bool any_host;
     s = resolve(c, args, 1, &any_host);
     if (s != LB_OK) return s;
-    if (on_device) LB_CUDA(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "status reset");
-    LB_CUDA(lbk::launch_set_positions(c, (const double*)args[0].dev), "position kernel");
+    LB_CUDA(lbk::launch_set_positions(c, (const double*)args[0].dev, false), "position kernel");
     c->order_stale = true;
     c->stencil_ready = false;
-    if (on_device) {
-        int status = 0;
-        LB_CUDA(cudaMemcpyAsync(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "status read");
-        LB_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
-        if (status) return fail(c, LB_ERR_NONFINITE, "lb_set_positions: non-finite position");
-    }
     return LB_OK;
 }
 

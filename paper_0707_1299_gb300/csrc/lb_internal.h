@@ -98,7 +98,7 @@ struct UForce {
 };
 
 cudaError_t launch_collide(lb_ctx* c);
-cudaError_t launch_spread(lb_ctx* c);
+cudaError_t launch_spread(lb_ctx* c);  // stencil rows at the positions, and the spread there
 cudaError_t launch_gather(lb_ctx* c, int n, const double* qpos, double* vout);
 cudaError_t launch_points(lb_ctx* c, const float* y);
 cudaError_t launch_stencil(lb_ctx* c);
@@ -114,7 +114,9 @@ cudaError_t launch_expand(lb_ctx* c, int n, const double* pos, const double* F, 
                           int mult);
 cudaError_t launch_fsum(lb_ctx* c);
 cudaError_t launch_faxen(lb_ctx* c, int n, const double* F, const double* a, double* U);
-cudaError_t launch_set_positions(lb_ctx* c, const double* pos);
+// check: only test pos (device) for non-finite values into c->status; else
+// copy the checked positions in, wrapped into the box.
+cudaError_t launch_set_positions(lb_ctx* c, const double* pos, bool check);
 cudaError_t launch_convert_out(lb_ctx* c, double* df);
 cudaError_t launch_convert_in(lb_ctx* c, const double* df);
 cudaError_t launch_clear_field(lb_ctx* c);

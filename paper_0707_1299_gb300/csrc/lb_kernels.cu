@@ -2,19 +2,18 @@
 // Boltzmann method with singular point forces, and their launchers.
 //
 //   (the collide kernels are in lb_collide.cu: they read the localised
-//   force only in the 8-site groups flagged by k_spread and, for lattices
-//   with colloids, write the fluid velocity there and zero the consumed
-//   force and flags)
-//   k_spread    regularised point forces onto the lattice (Sec. III,
-//               Eq. deltadef): one warp per point in cell order, the 12
-//               one-dimensional weights evaluated once and shuffled,
-//               atomic accumulation into the field (the first spread of a
-//               set of points; later steps spread in k_points).
+//   force only in the 8-site groups flagged by the spread and, for
+//   lattices with colloids, write the fluid velocity there and zero the
+//   consumed force and flags)
 //   k_points    the point phase after the collide: colloid velocity
 //               interpolated with the same kernel from the velocity the
 //               collide wrote (Sec. IV), the update
 //               R += v(R) + F (1/a - 1/a_L) / (6 pi eta) (Eq. a_Ldefn), and
-//               the spread at the new positions for the next step.
+//               the spread at the new positions for the next step
+//               (regularised point forces, Sec. III, Eq. deltadef: the 12
+//               one-dimensional weights evaluated once and shuffled,
+//               atomic accumulation into the field); without the
+//               interpolation, the first spread of a set of points.
 //   k_gather    velocity at arbitrary query points, each stencil node
 //               rebuilt from its pulled populations.
 //   k_moments   rho, u fields and FP64 totals (Eq. macrovariables2).
@@ -90,44 +89,6 @@ __device__ __forceinline__ double wrap_pos(double r, int n) {
 }
 
 
-// ------------------------------------------------------------- k_spread
-// One warp per point, taken in the cell order of `order`; the point's
-// stencil row (12 weights, 3 base nodes) is read once and shuffled; lane l
-// adds the force to nodes l and l + 32 (node = i + 4 j + 16 k: i along x, j
-// along y, k along z) and flags their tiles (the lane of the first node of
-// a tile in the row: i = 0, or x at a tile start).
-template <typename T, bool WALLS>
-__global__ void __launch_bounds__(256)
-k_spread(const T* __restrict__ st, const double* __restrict__ force, const int* __restrict__ order, int npts,
-         T* __restrict__ floc, flag_t* __restrict__ flags, Geom g) {
-    const int q = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (q >= npts) return;  // uniform per warp
-    const int lane = threadIdx.x & 31;
-    const int s = order ? order[q] : q;
-    const unsigned FULL = 0xffffffffu;
-    const T r = lane < ST_W ? st[(size_t)s * ST_W + lane] : T(0);
-    const T fl = lane < 3 ? (T)force[3 * s + lane] : T(0);
-    const int bx = bits_int(__shfl_sync(FULL, r, 12)), by = bits_int(__shfl_sync(FULL, r, 13)),
-              bz = bits_int(__shfl_sync(FULL, r, 14));
-    const T F0 = __shfl_sync(FULL, fl, 0), F1 = __shfl_sync(FULL, fl, 1), F2 = __shfl_sync(FULL, fl, 2);
-    const int i = lane & 3, j = (lane >> 2) & 3;
-    const T wxy = __shfl_sync(FULL, r, i) * __shfl_sync(FULL, r, 4 + j);
-    const int x = wrap_node(bx + i, g.nx), y = wrap_node(by + j, g.ny);
-    const bool marker = (i == 0) || ((x & (GROUP_X - 1)) == 0);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int k = (lane >> 4) + 2 * h;
-        const T wz = __shfl_sync(FULL, r, 8 + k);
-        const int z = wrap_node(bz + k, g.nz);
-        if (WALLS && is_solid(g, z)) continue;
-        const T w = wxy * wz;
-        const unsigned row = (unsigned)z * (unsigned)g.ny + (unsigned)y;
-        const unsigned site = row * (unsigned)g.nx + (unsigned)x;
-        field_add(floc, site, F0 * w, F1 * w, F2 * w);
-        if (marker) flags[row * (unsigned)g.ntx * (TILE_X / GROUP_X) + (unsigned)(x / GROUP_X)] = 1;
-    }
-}
-
 // Stencil rows of n points.
 template <typename T>
 __global__ void k_stencil(int n, const double* __restrict__ pos, T* __restrict__ st) {
@@ -161,13 +122,15 @@ struct LatticePoints {
 // warps a block barrier hold fewer warps idle
 constexpr int PT_WARPS = 2;
 
-template <typename T, bool WALLS, bool SHARED>
+// With INTERP false the kernel only writes the stencil rows at the current
+// positions and spreads there: the first spread of a set of points.
+template <typename T, bool WALLS, bool SHARED, bool INTERP = true>
 __global__ void __launch_bounds__(PT_WARPS * 32) k_points(const LatticePoints<T> src, long long total,
                                                           const int* __restrict__ order, T* __restrict__ st) {
     __shared__ double vsh[4 * PT_WARPS][3];
     extern __shared__ __align__(16) unsigned char pt_tile[];
-    point_block<T, WALLS, true, PT_WARPS, LatticePoints<T>, SHARED>(src, (long long)blockIdx.x * (4 * PT_WARPS), total,
-                                                                    order, st, vsh, (T*)pt_tile);
+    point_block<T, WALLS, INTERP, PT_WARPS, LatticePoints<T>, SHARED>(src, (long long)blockIdx.x * (4 * PT_WARPS),
+                                                                      total, order, st, vsh, (T*)pt_tile);
 }
 
 // ------------------------------------------------------------- k_gather
@@ -389,6 +352,9 @@ __global__ void k_fsum(const double* __restrict__ force, int npts, double* __res
     }
 }
 
+// New positions: with pos null only the check (status set where a value
+// is not finite), else the wrapped copy of values already checked, so a
+// rejected update leaves every position as it was.
 __global__ void k_set_positions(const double* __restrict__ in, int npts, Geom g, double* __restrict__ pos,
                                 int* __restrict__ status) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -396,11 +362,11 @@ __global__ void k_set_positions(const double* __restrict__ in, int npts, Geom g,
     const int nn[3] = {g.nx, g.ny, g.nz};
     for (int a = 0; a < 3; ++a) {
         const double r = in[3 * t + a];
-        if (!isfinite(r)) {
-            atomicOr(status, 1);
-            return;
+        if (!pos) {
+            if (!isfinite(r)) atomicOr(status, 1);
+        } else {
+            pos[3 * t + a] = wrap_pos(r, nn[a]);
         }
-        pos[3 * t + a] = wrap_pos(r, nn[a]);
     }
 }
 
@@ -670,20 +636,39 @@ cudaError_t launch_sort_points(lb_ctx* c) {
 // The cell order of the points, or null (their own order) for a few.
 static const int* point_order(const lb_ctx* c) { return c->npts > SORT_MIN_POINTS ? c->order : nullptr; }
 
+// The point arrays and fields of a context for the point kernels (network
+// output y of the correction, or null).
+template <typename T>
+static LatticePoints<T> lattice_points(const lb_ctx* c, const float* y) {
+    LatticePoints<T> src;
+    src.v.g = c->geom;
+    src.v.floc = (T*)c->floc;
+    src.v.flags = c->flags;
+    src.v.vel = (const T*)c->vel;
+    src.v.pos = c->pos;
+    src.v.force = c->force;
+    src.v.radius = c->radius;
+    src.v.mobile = c->mobile;
+    src.v.inv_aL = isinf(c->a_L) ? 0.0 : 1.0 / c->a_L;
+    src.v.inv_6pi_eta = 1.0 / (6.0 * M_PI * (c->tau_s / 3.0));
+    src.v.s = 0;
+    src.yc = y;
+    return src;
+}
+
 template <typename T>
 static cudaError_t spread_t(lb_ctx* c) {
-    const unsigned blocks = (unsigned)((c->npts + 7) / 8);  // 8 warps per block, one point each
-    const T* st = (const T*)c->stencil;
-    if (has_walls(c))
-        k_spread<T, true><<<blocks, 256, 0, c->stream>>>(st, c->force, point_order(c), c->npts, (T*)c->floc,
-                                                          c->flags, c->geom);
-    else
-        k_spread<T, false><<<blocks, 256, 0, c->stream>>>(st, c->force, point_order(c), c->npts, (T*)c->floc,
-                                                           c->flags, c->geom);
+    const LatticePoints<T> src = lattice_points<T>(c, nullptr);
+    const unsigned blocks = (unsigned)((c->npts + 4 * PT_WARPS - 1) / (4 * PT_WARPS));
+    const int* ord = point_order(c);
+    T* st = (T*)c->stencil;
+    if (has_walls(c)) k_points<T, true, false, false><<<blocks, PT_WARPS * 32, 0, c->stream>>>(src, c->npts, ord, st);
+    else k_points<T, false, false, false><<<blocks, PT_WARPS * 32, 0, c->stream>>>(src, c->npts, ord, st);
     c->launches++;
     return cudaGetLastError();
 }
 
+// Stencil rows at the current positions and the spread there (Sec. III).
 cudaError_t launch_spread(lb_ctx* c) {
     if (c->npts == 0) return cudaSuccess;
     return c->prec == LB_F64 ? spread_t<double>(c) : spread_t<float>(c);
@@ -717,19 +702,7 @@ cudaError_t launch_gather(lb_ctx* c, int n, const double* qpos, double* vout) {
 
 template <typename T>
 static cudaError_t points_t(lb_ctx* c, const float* y) {
-    LatticePoints<T> src;
-    src.v.g = c->geom;
-    src.v.floc = (T*)c->floc;
-    src.v.flags = c->flags;
-    src.v.vel = (const T*)c->vel;
-    src.v.pos = c->pos;
-    src.v.force = c->force;
-    src.v.radius = c->radius;
-    src.v.mobile = c->mobile;
-    src.v.inv_aL = isinf(c->a_L) ? 0.0 : 1.0 / c->a_L;
-    src.v.inv_6pi_eta = 1.0 / (6.0 * M_PI * (c->tau_s / 3.0));
-    src.v.s = 0;
-    src.yc = y;
+    const LatticePoints<T> src = lattice_points<T>(c, y);
     const unsigned blocks = (unsigned)((c->npts + 4 * PT_WARPS - 1) / (4 * PT_WARPS));
     const size_t tile = SHARED_NODES_BYTES;
     const int* ord = point_order(c);
@@ -818,9 +791,10 @@ cudaError_t launch_fsum(lb_ctx* c) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_set_positions(lb_ctx* c, const double* pos) {
+cudaError_t launch_set_positions(lb_ctx* c, const double* pos, bool check) {
     if (c->npts == 0) return cudaSuccess;
-    k_set_positions<<<(c->npts + 127) / 128, 128, 0, c->stream>>>(pos, c->npts, c->geom, c->pos, c->status);
+    k_set_positions<<<(c->npts + 127) / 128, 128, 0, c->stream>>>(pos, c->npts, c->geom, check ? nullptr : c->pos,
+                                                                  c->status);
     c->launches++;
     return cudaGetLastError();
 }
@@ -891,7 +865,9 @@ __global__ void __launch_bounds__(256) k_clear_groups(Geom g, T* __restrict__ fl
 
 cudaError_t launch_clear_field(lb_ctx* c) {
     const long long warps = (c->geom.ntiles + 31) / 32;
-    const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>(152 * 4, (warps + 7) / 8));
+    // a warp a flag word group: the walk is a dependent load then a few
+    // stores, so every group gets its own warp
+    const unsigned blocks = (unsigned)std::max<long long>(1, (warps + 7) / 8);
     if (c->prec == LB_F64)
         k_clear_groups<double><<<blocks, 256, 0, c->stream>>>(c->geom, (double*)c->floc, c->flags);
     else

@@ -464,6 +464,37 @@ def test_argument_validation():
     g.close()
 
 
+def test_set_positions_is_all_or_nothing():
+    # A position update with a non-finite value is rejected whole, from
+    # host and from device memory: every position stays as it was, and the
+    # lattice steps on; a valid update then lands wrapped into the box.
+    lb = _lb()
+    g = lb.Lattice((16, 12, 10), 0.5, 0.5, lb.LB_F64)
+    r = W.rng(8)
+    pos = r.uniform(0, 1, size=(6, 3)) * np.array([16.0, 12.0, 10.0])
+    g.add_point_forces(lb.LB_COLLOID, pos, np.tile([0.0, 0.0, -1e-5], (6, 1)), np.full(6, 0.117))
+    g.step(2)
+    p0 = g.particles()[0].cpu().numpy()
+    for bad_value in (float("nan"), float("inf")):
+        bad = p0 + 0.25
+        bad[3, 1] = bad_value
+        for where in ("host", "device"):
+            arg = np.ascontiguousarray(bad) if where == "host" else torch.as_tensor(bad, device="cuda").contiguous()
+            with pytest.raises(lb.LBError) as e:
+                lb.lb_set_positions(g.ctx, arg)
+            assert e.value.status == lb.LB_ERR_NONFINITE
+            assert np.array_equal(g.particles()[0].cpu().numpy(), p0), (bad_value, where)
+    g.step(1)
+    p1 = g.particles()[0].cpu().numpy()
+    new = p1 + np.array([16.0, -12.0, 0.5])  # wraps in x and y
+    lb.lb_set_positions(g.ctx, torch.as_tensor(new, device="cuda").contiguous())
+    got = g.particles()[0].cpu().numpy()
+    assert np.abs(periodic_diff(got, new, (16, 12, 10))).max() < 1e-12
+    assert (got >= 0).all() and (got < np.array([16.0, 12.0, 10.0])).all()
+    g.step(1)
+    g.close()
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_degenerate_point_positions(prec):
     # Points exactly on nodes (the outermost stencil weight is 0), at
