@@ -137,7 +137,10 @@ lb_status lb_clear_point_forces(lb_ctx *ctx);
 lb_status lb_num_points(const lb_ctx *ctx, int *n_out);
 
 /* Replace the positions of all monopoles (3 * lb_num_points doubles, host
- * or device, in the order they were created); forces are kept. */
+ * or device, in the order they were created), each wrapped into the box;
+ * forces are kept.  A NaN or an infinity anywhere rejects the whole update
+ * with LB_ERR_NONFINITE and leaves every position as it was.  Device
+ * positions are checked on the device, so that case waits for the stream. */
 lb_status lb_set_positions(lb_ctx *ctx, const double *pos);
 
 /* Host memory without waiting (default off).  With on != 0, a call that
