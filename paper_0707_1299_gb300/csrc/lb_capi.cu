@@ -472,8 +472,6 @@ lb_status lb_set_positions(lb_ctx* c, const double* pos) {
     if (!c) return LB_ERR_ARG;
     if (c->npts == 0) return LB_OK;
     if (!pos) return fail(c, LB_ERR_ARG, "lb_set_positions: pos is NULL");
-    // host positions are checked on the host, so the call need not wait for
-    // the device; device positions are checked by the kernel
     // The update is all or nothing.  Device positions are checked by a
     // kernel whose result is read before anything changes.  Host positions
     // are checked on the host (the call need not wait for the device) while
@@ -495,9 +493,11 @@ lb_status lb_set_positions(lb_ctx* c, const double* pos) {
     bool any_host;
     s = resolve(c, args, 1, &any_host);
     if (s != LB_OK) return s;
-    if (!on_device && !all_finite(pos, 3LL * c->npts))
-        return fail(c, LB_ERR_NONFINITE, "lb_set_positions: non-finite position");
-    LB_CUDA(lbk::launch_set_positions(c, (const double*)args[0].dev, false), "position kernel");
+    const bool finite = on_device || all_finite(pos, 3LL * c->npts);
+    if (finite) LB_CUDA(lbk::launch_set_positions(c, (const double*)args[0].dev, false), "position kernel");
+    // a host buffer is read by the time the call returns, unless host-async
+    if (any_host && !c->host_async) LB_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+    if (!finite) return fail(c, LB_ERR_NONFINITE, "lb_set_positions: non-finite position");
     c->order_stale = true;
     c->stencil_ready = false;
     return LB_OK;
