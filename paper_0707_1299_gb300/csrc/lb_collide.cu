@@ -222,12 +222,16 @@ k_collide_pair(const Pops<S> src, const Pops<S> dst, float* __restrict__ floc, f
 // k_collide_pair and each load moves twice the bytes (the pair kernel is
 // bound by memory latency at its occupancy: more bytes in flight a warp).
 // The two site pairs run one after the other through the packed FP32x2
-// collision of k_collide_pair, rounded and stored as 32-bit words with the
+// collision of k_collide_pair, each rounded to a 32-bit word by the
 // stochastic-rounding conversion (one random stream a thread, seeded by its
-// first site).  The four sites share one 8-site force group.
+// first site), and the two words of a population go out as one 64-bit store.
+// The four sites share one 8-site force group.  Occupancy bound, measured on
+// GB300: 5 blocks an SM without a force field (96 registers), 4 with one
+// (where 5 spills): 512^3 with 1e5 colloids, half storage, 1.887 ms against
+// 1.936 at 5; field-free 256^3, 0.214 ms against 0.232 at 4.
 // Grid: (ceil(nx / 128), ceil(ny / 4), nz).
 template <typename S, bool WALLS, int FMODE>
-__global__ void __launch_bounds__(CS_THREADS, 5)
+__global__ void __launch_bounds__(CS_THREADS, FMODE == FM_NONE ? 5 : 4)
 k_collide_quad(const Pops<S> src, const Pops<S> dst, float* __restrict__ floc, flag_t* __restrict__ flags,
                float* __restrict__ vel, Geom g, Coef<float> k, UForce<float> fu, float scale, float inv_scale,
                unsigned seed) {
@@ -275,16 +279,20 @@ k_collide_quad(const Pops<S> src, const Pops<S> dst, float* __restrict__ floc, f
     k2.om_b = F2(k.om_b);
     F2 v3[2][3];
     unsigned rs = rng_seed(row + x0, seed);
+    unsigned keep[NQ];  // the first pair's rounded words, stored with the second's
 #pragma unroll
     for (int h = 0; h < 2; ++h) {  // the site pairs (x0, x0 + 1) and (x0 + 2, x0 + 3)
         F2 f[NQ];
 #pragma unroll
         for (int i = 0; i < NQ; ++i) f[i] = F2(St::unpack2(h ? hi[i] : lo[i]));
-        const unsigned e = row + x0 + 2u * (unsigned)h;
-        // each population is rounded and stored as soon as it is computed
+        // each population of the second pair is rounded and stored, with
+        // the first pair's word, as soon as it is computed: one 64-bit store
+        // a population (a warp writes 256 contiguous bytes), not two 32-bit
+        // ones that each fill half of every sector they touch
         const auto emit = [&](int i, F2 v) {
             const unsigned word = St::bits2_rs(v.v.x, v.v.y, rng_next2(rs));
-            if (active) *(unsigned*)(dst.p[i] + e) = word;
+            if (h == 0) keep[i] = word;
+            else if (active) *(uint2*)(dst.p[i] + row + x0) = make_uint2(keep[i], word);
         };
         collide19<F2, false, SC, VOUT>(f, Fx[h], Fy[h], Fz[h], k2, emit, F2(inv_scale), v3[h]);
     }
@@ -369,11 +377,10 @@ static cudaError_t collide_t(lb_ctx* c) {
     // the 16-bit formats take two sites a thread when the rows pair up
     constexpr bool PAIRABLE = sizeof(S) == 2;
     const bool pair = PAIRABLE && (c->geom.nx % 2) == 0;
-    // four sites a thread (64-bit words): 4-5 % faster without a force
-    // field; with one, half storage gains as much (512^3 with 1e5 colloids:
-    // 2.10 against 2.26 ms a step) while bfloat16 measured the same as the
-    // pair kernel (2.19 against 2.21 ms; 0.292 against 0.291 ms at 256^3)
-    const bool quad = PAIRABLE && (c->geom.nx % 4) == 0 && (mode == FM_NONE || Store<S>::kScaled);
+    // four sites a thread (64-bit loads and stores) wherever the rows allow:
+    // at 512^3 with 1e5 colloids, 1.99 (half) and 2.01 ms (bfloat16) a step
+    // against 2.26 and 2.19 ms with the pair kernel
+    const bool quad = PAIRABLE && (c->geom.nx % 4) == 0;
     const dim3 pgrid((unsigned)((c->geom.nx + 63) / 64), grid.y, grid.z);
     const dim3 qgrid((unsigned)((c->geom.nx + 127) / 128), grid.y, grid.z);
 #define LB_COLLIDE(W, FM)                                                                                          \
